@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the PM-LSH (c,k)-ANN query path on GB300.
+
+One step = one batch of the throughput workload (n = 1,000,000 points,
+d = 128, a 1,000-cluster Gaussian mixture, 10,000 queries, m = 15, c = 1.5,
+k = 50, beta = 0.2809, alpha1 = 1/e) through pmlsh_knn: query projection,
+the range rounds of Algorithm 2, the budget cut, verification, top-k and the
+stop rules.  The index is built once before the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank serves its own copy
+of the batch against its own replica of the index (no collective on the data
+path), so `value` is the aggregate queries/s of all ranks ("scaling": weak).
+`--impl reference` times the FP64 CPU oracle on the host cores on bounded
+samples of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "c-ANN queries/s at fixed ratio, 1M×128 k=50; serve p50/p99 ms vs plain FP32"
+K, C, BETA, M_PROJ = 50, 1.5, 0.2809, 15
+ALPHA1 = 1 / math.e
+
+
+def workload_desc(nq):
+    return ("c-ANN, n=1,000,000 d=128 FP32, Gaussian mixture of 1,000 clusters "
+            "(centres N(0,100 I), sigma U[0.5,2]), %d queries from the same mixture, "
+            "m=15, c=1.5, k=50, beta=0.2809, alpha1=1/e, r_min by the Sec. 5.2 rule, "
+            "seed 0" % nq)
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def traffic_record():
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def cpu_baseline(X, Q, A, budget_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the queries."""
+    import oracle
+    t, _, _ = oracle.params(M_PROJ, C, ALPHA1)
+    B = oracle.budget(len(X), BETA, K)
+    O = oracle.project(X, A)
+    rmin = oracle.rmin_auto(X, BETA, K, C, 3)
+    t0 = time.perf_counter()
+    probe = 32
+    oracle.knn(X, A, Q[:probe], K, C, t, B, rmin, 0, Oproj=O)
+    per_q = (time.perf_counter() - t0) / probe
+    ns = int(max(probe, min(len(Q), budget_s / max(per_q, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.knn(X, A, Q[:ns], K, C, t, B, rmin, 0, Oproj=O)
+    el = time.perf_counter() - t0
+    return {"value": ns / el, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "first %d of the %d queries (FP64 Algorithm 2, OpenMP over queries), "
+                      "%.1f s" % (ns, len(Q), el)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import datagen
+    import oracle
+    w = datagen.workload("c2")
+    X, Q = w["X"], w["Q"]
+    A = oracle.gen_projection(2, M_PROJ, X.shape[1]).astype(np.float32)
+    t, _, _ = oracle.params(M_PROJ, C, ALPHA1)
+    B = oracle.budget(len(X), BETA, K)
+    O = oracle.project(X, A)
+    rmin = oracle.rmin_auto(X, BETA, K, C, 3)
+    per_step = args.ref_queries
+    for s in range(args.warmup):
+        oracle.knn(X, A, Q[s * per_step % len(Q):][:per_step], K, C, t, B, rmin, 0, Oproj=O)
+    total = 0.0
+    for s in range(args.steps):
+        q0 = (args.warmup + s) * per_step % len(Q)
+        t0 = time.perf_counter()
+        oracle.knn(X, A, Q[q0:q0 + per_step], K, C, t, B, rmin, 0, Oproj=O)
+        total += time.perf_counter() - t0
+    v = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total * 1000 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(per_step) + " (sample of %d queries per step)" % per_step},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "%d queries per step, %d steps" % (per_step, args.steps)},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--ref-queries", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+
+    import datagen
+    import paper_2107_05537_gb300 as pm
+    torch.cuda.set_device(local)
+    w = datagen.workload("c2", nq=args.nq)
+    X, Q = w["X"], w["Q"]
+    nq, d = Q.shape
+    Xd = torch.from_numpy(X).cuda()
+    t0 = time.perf_counter()
+    ix = pm.Index(Xd, m=M_PROJ, leaf_size=256, seed=0)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del Xd
+    prec = pm.PMLSH_BF16_RERANK if args.precision == "bf16" else pm.PMLSH_FP32_PLAIN
+    Qd = torch.from_numpy(Q).cuda()
+    ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, K), dtype=torch.float32, device="cuda")
+    er = torch.empty((nq, K), dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        return ix.knn(Qd, k=K, c=C, alpha1=ALPHA1, beta=BETA, precision=prec,
+                      out=(ids, dd, er))
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    pm.profile(True)
+    pm.profile_read()
+    launches0 = pm.launch_count()
+    total_ms = 0.0
+    nver = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        nver += int(res["stats"]["nver"].sum())
+    launches = pm.launch_count() - launches0
+    prof = pm.profile_read()
+    pm.profile(False)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    total_s = max_over_ranks(total_ms / 1000.0, ws)
+    value = nq * args.steps * ws / total_s
+    stats = res["stats"]
+
+    # quality at the operating point: Eq. 11 / Eq. 12 on a query sample
+    # against exact neighbours (plain PyTorch FP64 on the GPU)
+    with torch.no_grad():
+        sq = torch.arange(0, nq, max(1, nq // 64), device="cuda")[:64]
+        Xe = torch.from_numpy(X).cuda().double()
+        Qe = Qd[sq].double()
+        dist = torch.cdist(Qe, Xe)
+        ex_d, ex_i = torch.topk(dist, K, largest=False)
+        got_d = dd[sq].double()
+        ratio = float((got_d / ex_d.clamp_min(1e-300)).mean())
+        rec = float(np.mean([len(set(ids[q].tolist()) & set(ex_i[j].tolist())) / K
+                             for j, q in enumerate(sq.tolist())]))
+        del Xe, dist
+
+    # end to end through the public API with host buffers (pinned), the
+    # host->device copy of Q and the device->host copy of the results inside
+    e2e = None
+    if not args.no_e2e:
+        Qh = torch.from_numpy(Q).pin_memory()
+        idh = torch.empty((nq, K), dtype=torch.int64).pin_memory()
+        ddh = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+        erh = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+        ix.knn(Qh.numpy(), k=K, c=C, beta=BETA, precision=prec, out=(idh.numpy(), ddh.numpy(), erh.numpy()))
+        el = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ix.knn(Qh.numpy(), k=K, c=C, beta=BETA, precision=prec,
+                   out=(idh.numpy(), ddh.numpy(), erh.numpy()))
+            el += time.perf_counter() - t0
+        el = max_over_ranks(el, ws)
+        e2e = {"value": nq * args.steps * ws / el, "unit": "queries/s",
+               "h2d_bytes_per_step": nq * d * 4, "d2h_bytes_per_step": nq * K * (8 + 4 + 4)}
+
+    # roofline of the dominant kernel
+    pk, pk_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roof = None
+    if dom:
+        launches_dom, ms_dom = prof[dom]
+        avg_s = ms_dom / 1000.0 / launches_dom
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        nsm = props.multi_processor_count
+        smhz = pk.get("sm_max_mhz", 2070.0)
+        tr = traffic_record().get(dom)
+        if dom == "k_verify":
+            # algorithmic work: 3 flops (sub, mul, add) per coordinate of every
+            # verified candidate; FP32 lanes: 128 per SM, 2 instructions
+            # (FSUB, FFMA) per coordinate
+            flops = nver / args.steps * d * 3.0 / launches_dom * args.steps
+            achieved = flops / avg_s / 1e12
+            peak = nsm * 128 * smhz * 1e6 / 2 * 3 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "kernel": dom,
+                    "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 instr x 3 flop per coordinate" % (nsm, smhz),
+                    "traffic": tr.get("bytes_per_launch") if tr else None}
+        else:
+            roof = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": None, "kernel": dom, "traffic": tr.get("bytes_per_launch") if tr else None}
+        roof["kernels"] = {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in prof.items()}
+        roof["peak_kind"] = pk_kind
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        A = ix.projection()
+        cpu = cpu_baseline(X, Q, A)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_s * 1000 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_desc(nq), "precision": args.precision,
+                           "l2": "flushed between steps (512 MB write)",
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "gpu_launches": launches,
+                "quality": {"overall_ratio": ratio, "recall": rec, "sample_queries": int(len(sq))},
+                "trace": {"mean_rounds": float(stats["rounds"].mean()),
+                          "mean_candidates": float(stats["ncand"].mean()),
+                          "rule_counts": np.bincount(stats["rule"], minlength=4).tolist()},
+                "build_s": build_s,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    ix.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

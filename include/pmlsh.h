@@ -1,0 +1,208 @@
+/*
+ * pmlsh.h -- C ABI of the GB300 PM-LSH library (libpmlsh.so).
+ *
+ * PM-LSH (Zheng, Zhao, Weng, Hung, Liu, Jensen) answers (c,k)-approximate
+ * nearest-neighbour queries (Definition 2) and (c,k)-approximate closest-pair
+ * queries (Definition 4) over a data set D of n points in R^d by projecting
+ * every point onto m Gaussian directions (Sec. 3.2, Eq. 3), running range
+ * queries in the projected space whose radius t*r comes from a chi-square
+ * confidence interval (Lemma 3, Eq. 9) and grows by c per round
+ * (Algorithm 2), and verifying candidates by their exact distance.
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only: no call aborts, throws across the ABI or traps on
+ *     the device.  On failure the call returns a code != PMLSH_OK and
+ *     pmlsh_last_error() describes it (thread-local string).
+ *   - Pointers may be host or device memory; the library asks the CUDA
+ *     runtime which kind each one is.  The caller owns every buffer it
+ *     passes; the library copies what it keeps.  Results written to host
+ *     buffers are complete when the call returns; results written to device
+ *     buffers are complete when `stream` reaches the end of the work the
+ *     call enqueued (the call still synchronises internally once per round
+ *     of Algorithm 2 to read small per-query decisions).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Distances are Euclidean (not squared).  Results are sorted by
+ *     ascending distance, ties by smaller id; closest pairs are (i, j) with
+ *     i < j and ties by (i, j).
+ *   - Floating-point decisions (range membership, the budget cut, the k-th
+ *     neighbour, the stop rules) are taken on FP32 values with a proven
+ *     error bound and re-taken in FP64 wherever the FP32 value lies inside
+ *     that bound, so they equal the decisions of an FP64 evaluation of the
+ *     same formulas (sequential sums, separate multiply and add).
+ *   - Not thread-safe per index, except through the pmlsh_serve_* API.
+ */
+#ifndef PMLSH_H
+#define PMLSH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PMLSH_OK = 0,
+    PMLSH_EINVAL = 1,     /* an argument is out of range or NULL */
+    PMLSH_ENOMEM = 2,     /* device or host allocation failed */
+    PMLSH_ETIMEOUT = 3,   /* a bounded wait expired */
+    PMLSH_ECUDA = 4,      /* a CUDA runtime call failed */
+    PMLSH_ECANCELED = 5,  /* request cancelled or server stopped */
+    PMLSH_EINTERNAL = 6   /* an internal capacity was exceeded */
+} pmlsh_status;
+
+typedef struct pmlsh_index pmlsh_index;   /* opaque */
+
+/* ------------------------------------------------------------ parameters */
+
+/* Eq. 9 (Sec. 5.3) and Lemma 5: t = sqrt(chi^2_{alpha1}(m)) (upper
+ * quantile, Lemma 3), alpha2 = Pr[chi^2(m) <= t^2 / c^2], beta = 2 alpha2.
+ * Requires 1 <= m <= 16, c > 1, 0 < alpha1 < 1.  Any output may be NULL. */
+pmlsh_status pmlsh_params(int m, double c, double alpha1,
+                          double *t, double *alpha2, double *beta_eq9);
+
+/* Algorithm 2 budget: the smallest integer B with B >= beta n + k,
+ * computed as ceil(beta n - 1e-9) + k. */
+int64_t pmlsh_budget(int64_t n, double beta, int64_t k);
+
+/* ------------------------------------------------------------------ build */
+
+typedef struct {
+    int m;              /* number of projections (Eq. 3), 1..16; default 15 */
+    int s;              /* number of global pivots (Sec. 4.1), 0..8; default 5 */
+    int leaf_size;      /* leaf capacity M (points per leaf); 0 = default 256 */
+    int cp_leaf_size;   /* unused by pmlsh_build; see pmlsh_cp_opts */
+    uint64_t seed;      /* the projection uses stream seed+2 of the
+                           counter-based SplitMix64 generator with the
+                           Box-Muller transform; the r_min sample uses seed+3 */
+    const float *proj;  /* optional caller projection A, row-major [m][d]
+                           FP32, host or device; NULL = draw from `seed` */
+    int64_t rmin_pairs; /* pairs sampled for the distance distribution F of
+                           Sec. 5.2 (r_min rule); 0 = default 10000 */
+    int bf16_shadow;    /* 1 = also keep a BF16 copy of the leaf-centred
+                           points for the BF16_RERANK verification mode */
+} pmlsh_build_opts;
+
+/* Fills `o` with the defaults above. */
+void pmlsh_build_opts_default(pmlsh_build_opts *o);
+
+/* Builds an index over X [n][d] (row-major FP32, host or device).
+ *   Projects every point (Eq. 3) in FP64 and FP32, partitions the projected
+ *   points into leaves of at most M points by recursive bisection, records
+ *   each leaf's ball (centre, radius) and pivot rings (the PM-tree node
+ *   entries of Sec. 4.1) and a binary hierarchy of leaves (used by
+ *   pmlsh_closest_pair), samples the distance distribution for r_min and
+ *   keeps a permuted device copy of X.  X is not referenced afterwards.
+ * Errors: EINVAL (NULL pointers, n < 1, d < 1, m outside 1..16, s outside
+ *   0..8, leaf_size outside 0 or 16..1024, n >= 2^31), ENOMEM, ECUDA.
+ * On success *out owns device memory until pmlsh_free(*out). */
+pmlsh_status pmlsh_build(const float *X, int64_t n, int d,
+                         const pmlsh_build_opts *opts, void *stream,
+                         pmlsh_index **out);
+
+void pmlsh_free(pmlsh_index *index);
+
+/* Index facts: n, d, m, leaf count, leaf size, node count. Any may be NULL. */
+pmlsh_status pmlsh_index_info(const pmlsh_index *index, int64_t *n, int *d,
+                              int *m, int64_t *leaves, int *leaf_size,
+                              int64_t *nodes);
+
+/* Copies the projection actually used, [m][d] FP32, to host memory. */
+pmlsh_status pmlsh_get_projection(const pmlsh_index *index, float *A_host);
+
+/* Copies the FP64 projected coordinates [n][m], in original id order, to
+ * host memory (Eq. 3). */
+pmlsh_status pmlsh_get_projected(const pmlsh_index *index, double *O_host);
+
+/* Exports the leaf hierarchy to host buffers (sizes from pmlsh_index_info):
+ *   perm [n] int32       point id at each leaf-order position
+ *   leaf_off [L+1]       leaf l holds positions [leaf_off[l], leaf_off[l+1])
+ *   node_lo, node_hi [N] node e covers leaves [node_lo[e], node_hi[e])
+ *   node_left, node_right [N] children, -1 for a leaf node; node 0 = root.
+ * Any pointer may be NULL to skip that array. */
+pmlsh_status pmlsh_export_layout(const pmlsh_index *index, int32_t *perm,
+                                 int64_t *leaf_off, int64_t *node_lo,
+                                 int64_t *node_hi, int32_t *node_left,
+                                 int32_t *node_right);
+
+/* ------------------------------------------------------- (c,k)-ANN query */
+
+enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_RERANK = 1 };
+enum { PMLSH_STOP_LITERAL = 0, PMLSH_STOP_BC_CONSISTENT = 1 };
+
+typedef struct {
+    int k;            /* neighbours per query, 1..min(n, 256) */
+    double c;         /* approximation ratio c > 1 (Definition 2) */
+    double alpha1;    /* E1 failure probability (Lemma 4); default 1/e */
+    double beta;      /* candidate budget fraction, 0 < beta <= 1;
+                         default 0.2809 (Sec. 7.1) */
+    double r_min;     /* first radius; <= 0: the Sec. 5.2 rule (r* with
+                         F(rstar) = (beta n + k)/n on the sampled distance
+                         distribution, r_min = rstar / c) */
+    int precision;    /* PMLSH_FP32_PLAIN or PMLSH_BF16_RERANK; both return
+                         the same ids and distances */
+    double t;         /* projected radius factor of Lemma 4; <= 0: t from
+                         alpha1 by Eq. 9 (t = sqrt(chi^2_{alpha1}(m))) */
+    int stop_rule;    /* PMLSH_STOP_LITERAL: stop rule 1 tested at the loop
+                         top after r <- c r, as printed in Algorithm 2;
+                         PMLSH_STOP_BC_CONSISTENT: tested after the range
+                         query with the same r (Algorithm 1's form) */
+} pmlsh_knn_opts;
+
+void pmlsh_knn_opts_default(pmlsh_knn_opts *o);
+
+typedef struct {
+    int32_t rounds;        /* range queries run */
+    int32_t stop_rule;     /* 1: >= k verified within c r; 2: budget
+                              |C| >= beta n + k reached; 3: C = D */
+    int64_t n_cand;        /* |C| at return */
+    double r_final;        /* r at return */
+    int32_t fp64_checks;   /* decisions re-taken in FP64 */
+    int32_t reserved;
+    int64_t n_verified;    /* exact distances computed, over all rounds */
+} pmlsh_query_stats;
+
+/* Algorithm 2 for nq queries Q [nq][d] (FP32, host or device).
+ * Outputs (host or device): out_ids [nq][k] int64 original ids,
+ * out_dists [nq][k] FP32 distances (the FP64 distance rounded to FP32),
+ * out_err [nq][k] or NULL: |out_dist - FP64 distance| per result,
+ * stats [nq] or NULL.
+ * Candidate set reading: C_i is the closed range set {o : ||o',q'|| <=
+ * t r_i}; once |C_i| >= B (B = pmlsh_budget(n, beta, k)) C_i keeps the B
+ * points with the smallest (||o',q'||, id) and stop rule 2 returns.
+ * Errors: EINVAL (NULL pointers, nq < 0, k < 1, k > min(n, 256), c <= 1,
+ *   beta outside (0,1], alpha1 outside (0,1)), ENOMEM, ECUDA, EINTERNAL
+ *   (more than the internal capacity of points tied within one FP32 error
+ *   band; the message says which). nq = 0 returns PMLSH_OK at once. */
+pmlsh_status pmlsh_knn(pmlsh_index *index, const float *Q, int64_t nq,
+                       const pmlsh_knn_opts *opts, int64_t *out_ids,
+                       float *out_dists, float *out_err,
+                       pmlsh_query_stats *stats, void *stream);
+
+/* ------------------------------------------------------------- profiling */
+
+/* Turns per-kernel timing on (1) or off (0), process-wide.  While on, every
+ * kernel launch of the library is bracketed by two CUDA events recorded on
+ * the launch's own stream (a few microseconds of overhead per launch). */
+pmlsh_status pmlsh_profile(int enable);
+
+/* Writes the timings gathered since the last read as a JSON object
+ * {"kernel_name": [launches, total_ms], ...} into buf (cap bytes, host) and
+ * clears them; waits for the recorded events.  EINVAL if cap is too small. */
+pmlsh_status pmlsh_profile_read(char *buf, int64_t cap);
+
+/* Number of kernel launches the library has issued in this process. */
+long long pmlsh_launch_count(void);
+
+/* ------------------------------------------------------------ thread info */
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *pmlsh_last_error(void);
+
+/* Library version string. */
+const char *pmlsh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMLSH_H */

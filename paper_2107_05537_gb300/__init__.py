@@ -1,0 +1,259 @@
+"""GB300 PM-LSH: Python binding of libpmlsh.so (argument marshalling only).
+
+Every step of the query and build path runs in the library's CUDA kernels;
+this module only converts arrays to pointers, allocates output tensors with
+PyTorch and passes the current CUDA stream.  If the compiled library is
+missing, every call raises: there is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpmlsh.so")
+
+PMLSH_FP32_PLAIN = 0
+PMLSH_BF16_RERANK = 1
+STOP_LITERAL = 0
+STOP_BC_CONSISTENT = 1
+
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ETIMEOUT", 4: "ECUDA",
+           5: "ECANCELED", 6: "EINTERNAL"}
+
+
+class PmlshError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pmlsh %s: %s" % (_STATUS.get(code, code), msg))
+        self.code = code
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("s", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("cp_leaf_size", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("proj", ctypes.c_void_p), ("rmin_pairs", ctypes.c_int64),
+                ("bf16_shadow", ctypes.c_int)]
+
+
+class KnnOpts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("c", ctypes.c_double), ("alpha1", ctypes.c_double),
+                ("beta", ctypes.c_double), ("r_min", ctypes.c_double),
+                ("precision", ctypes.c_int), ("t", ctypes.c_double),
+                ("stop_rule", ctypes.c_int)]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
+                ("n_cand", ctypes.c_int64), ("r_final", ctypes.c_double),
+                ("fp64_checks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_verified", ctypes.c_int64)]
+
+
+# name -> (restype, argtypes); the exported C ABI of include/pmlsh.h
+_P = ctypes.c_void_p
+_SIGS = {
+    "pmlsh_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
+    "pmlsh_budget": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_double, ctypes.c_int64]),
+    "pmlsh_build_opts_default": (None, [_P]),
+    "pmlsh_build": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
+    "pmlsh_free": (None, [_P]),
+    "pmlsh_index_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_get_projection": (ctypes.c_int, [_P, _P]),
+    "pmlsh_get_projected": (ctypes.c_int, [_P, _P]),
+    "pmlsh_export_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_knn_opts_default": (None, [_P]),
+    "pmlsh_knn": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_profile": (ctypes.c_int, [ctypes.c_int]),
+    "pmlsh_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
+    "pmlsh_launch_count": (ctypes.c_longlong, []),
+    "pmlsh_last_error": (ctypes.c_char_p, []),
+    "pmlsh_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads the in-tree library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PmlshError(4, "libpmlsh.so not built (%s); run "
+                             "`python -m paper_2107_05537_gb300.build`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise PmlshError(code, lib().pmlsh_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _as_f32(a):
+    """Returns (object keeping memory alive, pointer) for a 2-D float32 array
+    (numpy or torch, host or device)."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        t = a.detach()
+        if t.dtype != torch.float32:
+            t = t.float()
+        t = t.contiguous()
+        return t, ctypes.c_void_p(t.data_ptr())
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def params(m=15, c=1.5, alpha1=1 / math.e):
+    """Eq. 9: returns (t, alpha2, beta = 2 alpha2)."""
+    t, a2, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().pmlsh_params(m, c, alpha1, ctypes.byref(t), ctypes.byref(a2), ctypes.byref(b)))
+    return t.value, a2.value, b.value
+
+
+def budget(n, beta, k):
+    return lib().pmlsh_budget(n, beta, k)
+
+
+def version():
+    return lib().pmlsh_version().decode()
+
+
+def profile(enable=True):
+    """Per-kernel CUDA-event timing of every library launch (on/off)."""
+    _check(lib().pmlsh_profile(1 if enable else 0))
+
+
+def profile_read():
+    """{kernel: (launches, total_ms)} since the last read (waits for events)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().pmlsh_profile_read(buf, len(buf)))
+    return {k: (v[0], v[1]) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def launch_count():
+    return lib().pmlsh_launch_count()
+
+
+class Index:
+    """A PM-LSH index resident on the current CUDA device."""
+
+    def __init__(self, X, m=15, s=5, leaf_size=256, seed=0, proj=None, rmin_pairs=10000):
+        L = lib()
+        o = BuildOpts()
+        L.pmlsh_build_opts_default(ctypes.byref(o))
+        o.m, o.s, o.leaf_size, o.seed, o.rmin_pairs = m, s, leaf_size, seed, rmin_pairs
+        keep = []
+        if proj is not None:
+            pa, pp = _as_f32(proj)
+            keep.append(pa)
+            o.proj = pp
+        xa, xp = _as_f32(X)
+        n, d = int(xa.shape[0]), int(xa.shape[1])
+        h = ctypes.c_void_p()
+        _check(L.pmlsh_build(xp, n, d, ctypes.byref(o), _stream(), ctypes.byref(h)))
+        self._h = h
+        self.n, self.d, self.m = n, d, m
+        nl, ns = ctypes.c_int64(), ctypes.c_int64()
+        lsz = ctypes.c_int()
+        _check(L.pmlsh_index_info(h, None, None, None, ctypes.byref(nl), ctypes.byref(lsz),
+                                  ctypes.byref(ns)))
+        self.leaves, self.leaf_size, self.nodes = nl.value, lsz.value, ns.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pmlsh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def projection(self):
+        A = np.empty((self.m, self.d), dtype=np.float32)
+        _check(lib().pmlsh_get_projection(self._h, A.ctypes.data_as(ctypes.c_void_p)))
+        return A
+
+    def projected(self):
+        O = np.empty((self.n, self.m), dtype=np.float64)
+        _check(lib().pmlsh_get_projected(self._h, O.ctypes.data_as(ctypes.c_void_p)))
+        return O
+
+    def layout(self):
+        perm = np.empty(self.n, dtype=np.int32)
+        loff = np.empty(self.leaves + 1, dtype=np.int64)
+        nlo = np.empty(self.nodes, dtype=np.int64)
+        nhi = np.empty(self.nodes, dtype=np.int64)
+        nl = np.empty(self.nodes, dtype=np.int32)
+        nr = np.empty(self.nodes, dtype=np.int32)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().pmlsh_export_layout(self._h, ptr(perm), ptr(loff), ptr(nlo), ptr(nhi),
+                                         ptr(nl), ptr(nr)))
+        return dict(perm=perm, leaf_off=loff, node_lo=nlo, node_hi=nhi, node_left=nl,
+                    node_right=nr)
+
+    def knn(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
+            precision=PMLSH_FP32_PLAIN, stop_rule=STOP_LITERAL, t=0.0, out=None,
+            with_err=True, with_stats=True):
+        """Algorithm 2 for the rows of Q.  Outputs live on the GPU when Q is a
+        CUDA tensor (or when `out` tensors are given), else in numpy arrays.
+        Returns dict(ids, dists, err, stats)."""
+        torch = _torch()
+        qa, qp = _as_f32(Q)
+        nq = int(qa.shape[0])
+        o = KnnOpts()
+        lib().pmlsh_knn_opts_default(ctypes.byref(o))
+        o.k, o.c, o.alpha1, o.beta, o.r_min = k, c, alpha1, beta, r_min
+        o.precision, o.stop_rule, o.t = precision, stop_rule, t
+        on_gpu = isinstance(qa, torch.Tensor) and qa.is_cuda
+        if out is not None:
+            ids, dists, err = out
+        elif on_gpu:
+            ids = torch.empty((nq, k), dtype=torch.int64, device=qa.device)
+            dists = torch.empty((nq, k), dtype=torch.float32, device=qa.device)
+            err = torch.empty((nq, k), dtype=torch.float32, device=qa.device) if with_err else None
+        else:
+            ids = np.empty((nq, k), dtype=np.int64)
+            dists = np.empty((nq, k), dtype=np.float32)
+            err = np.empty((nq, k), dtype=np.float32) if with_err else None
+
+        def ptr(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return ctypes.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(ctypes.c_void_p)
+        stats = (QueryStats * max(1, nq))() if with_stats else None
+        _check(lib().pmlsh_knn(self._h, qp, nq, ctypes.byref(o), ptr(ids), ptr(dists), ptr(err),
+                               ctypes.cast(stats, ctypes.c_void_p) if stats is not None else None,
+                               _stream()))
+        res = dict(ids=ids, dists=dists, err=err)
+        if with_stats:
+            res["stats"] = dict(
+                rounds=np.array([s.rounds for s in stats[:nq]], dtype=np.int32),
+                rule=np.array([s.stop_rule for s in stats[:nq]], dtype=np.int32),
+                ncand=np.array([s.n_cand for s in stats[:nq]], dtype=np.int64),
+                r=np.array([s.r_final for s in stats[:nq]], dtype=np.float64),
+                fp64=np.array([s.fp64_checks for s in stats[:nq]], dtype=np.int32),
+                nver=np.array([s.n_verified for s in stats[:nq]], dtype=np.int64))
+        return res

@@ -1,0 +1,212 @@
+// C ABI of libpmlsh: argument validation, pointer-kind detection, handles,
+// thread-local error text.  Every entry point returns a status code; nothing
+// throws across the boundary.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pmlsh_impl.h"
+
+static thread_local char g_err[1024] = "";
+
+void pm_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+bool pm_is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+#define PM_CHECK(cond, ...)                                                    \
+    do {                                                                       \
+        if (!(cond)) {                                                         \
+            pm_set_error(__VA_ARGS__);                                         \
+            return PMLSH_EINVAL;                                               \
+        }                                                                      \
+    } while (0)
+
+extern "C" {
+
+const char *pmlsh_last_error(void) { return g_err; }
+
+const char *pmlsh_version(void) { return "pmlsh-gb300 0.1 (sm_103a)"; }
+
+pmlsh_status pmlsh_params(int m, double c, double alpha1, double *t, double *alpha2, double *beta_eq9)
+{
+    PM_CHECK(m >= 1 && m <= PM_MP, "m must be in 1..16 (got %d)", m);
+    PM_CHECK(c > 1.0, "c must be > 1 (got %g)", c);
+    PM_CHECK(alpha1 > 0.0 && alpha1 < 1.0, "alpha1 must be in (0,1) (got %g)", alpha1);
+    // Eq. 9: t^2 = chi^2_{alpha1}(m); t^2 / c^2 = chi^2_{1-alpha2}(m), i.e.
+    // Pr[chi^2(m) > t^2/c^2] = 1 - alpha2.  Lemma 5: beta = 2 alpha2.
+    double t2 = pm_chi2_upper_quantile(alpha1, m);
+    double a2 = 1.0 - pm_chi2_sf(t2 / (c * c), m);
+    if (t) *t = std::sqrt(t2);
+    if (alpha2) *alpha2 = a2;
+    if (beta_eq9) *beta_eq9 = 2.0 * a2;
+    return PMLSH_OK;
+}
+
+int64_t pmlsh_budget(int64_t n, double beta, int64_t k)
+{
+    return (int64_t)std::ceil(beta * (double)n - 1e-9) + k;
+}
+
+void pmlsh_build_opts_default(pmlsh_build_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->m = 15;
+    o->s = 5;
+    o->leaf_size = 256;
+    o->cp_leaf_size = 16;
+    o->seed = 0;
+    o->proj = nullptr;
+    o->rmin_pairs = 10000;
+    o->bf16_shadow = 0;
+}
+
+void pmlsh_knn_opts_default(pmlsh_knn_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->k = 10;
+    o->c = 1.5;
+    o->alpha1 = 0.36787944117144233;  // 1/e (Sec. 5.3)
+    o->beta = 0.2809;                 // Sec. 7.1
+    o->r_min = 0.0;
+    o->precision = PMLSH_FP32_PLAIN;
+    o->t = 0.0;
+    o->stop_rule = PMLSH_STOP_LITERAL;
+}
+
+pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opts *opts, void *stream,
+                         pmlsh_index **out)
+{
+    PM_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    PM_CHECK(X != nullptr, "X is NULL");
+    PM_CHECK(n >= 1 && n < (int64_t)1 << 31, "n must be in 1..2^31-1 (got %lld)", (long long)n);
+    PM_CHECK(d >= 1 && d <= 65536, "d must be in 1..65536 (got %d)", d);
+    pmlsh_build_opts o;
+    if (opts) o = *opts;
+    else pmlsh_build_opts_default(&o);
+    if (o.leaf_size == 0) o.leaf_size = 256;
+    PM_CHECK(o.m >= 1 && o.m <= PM_MP, "m must be in 1..16 (got %d)", o.m);
+    PM_CHECK(o.s >= 0 && o.s <= PM_MAX_PIVOTS, "s must be in 0..8 (got %d)", o.s);
+    PM_CHECK(o.leaf_size >= 16 && o.leaf_size <= 1024, "leaf_size must be 0 or 16..1024 (got %d)",
+             o.leaf_size);
+    PM_CHECK(o.rmin_pairs >= 0, "rmin_pairs must be >= 0");
+    pmlsh_index *ix = new (std::nothrow) pmlsh_index();
+    if (!ix) {
+        pm_set_error("host allocation failed");
+        return PMLSH_ENOMEM;
+    }
+    ix->n = n;
+    ix->d = d;
+    ix->ld = (d + 31) / 32 * 32;
+    ix->m = o.m;
+    ix->s = std::min<int64_t>(o.s, (n + o.leaf_size - 1) / o.leaf_size);
+    ix->M = o.leaf_size;
+    ix->seed = o.seed;
+    pmlsh_status s = pm_build_index(ix, X, pm_is_device_ptr(X), &o, (cudaStream_t)stream);
+    if (s != PMLSH_OK) {
+        pm_free_index(ix);
+        delete ix;
+        return s;
+    }
+    *out = ix;
+    return PMLSH_OK;
+}
+
+void pmlsh_free(pmlsh_index *index)
+{
+    if (!index) return;
+    pm_free_index(index);
+    delete index;
+}
+
+pmlsh_status pmlsh_index_info(const pmlsh_index *ix, int64_t *n, int *d, int *m, int64_t *leaves,
+                              int *leaf_size, int64_t *nodes)
+{
+    PM_CHECK(ix != nullptr, "index is NULL");
+    if (n) *n = ix->n;
+    if (d) *d = ix->d;
+    if (m) *m = ix->m;
+    if (leaves) *leaves = ix->L;
+    if (leaf_size) *leaf_size = ix->M;
+    if (nodes) *nodes = (int64_t)ix->nodeLo.size();
+    return PMLSH_OK;
+}
+
+pmlsh_status pmlsh_get_projection(const pmlsh_index *ix, float *A_host)
+{
+    PM_CHECK(ix && A_host, "NULL argument");
+    std::memcpy(A_host, ix->A_host.data(), ix->A_host.size() * sizeof(float));
+    return PMLSH_OK;
+}
+
+pmlsh_status pmlsh_get_projected(const pmlsh_index *ix, double *O_host)
+{
+    PM_CHECK(ix && O_host, "NULL argument");
+    std::vector<double> tmp((size_t)ix->n * PM_MP);
+    PM_CUDA(cudaMemcpy(tmp.data(), ix->O64, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t pos = 0; pos < ix->n; pos++) {
+        int64_t id = ix->permH[pos];
+        for (int j = 0; j < ix->m; j++) O_host[id * ix->m + j] = tmp[(size_t)pos * PM_MP + j];
+    }
+    return PMLSH_OK;
+}
+
+pmlsh_status pmlsh_export_layout(const pmlsh_index *ix, int32_t *perm, int64_t *leaf_off, int64_t *node_lo,
+                                 int64_t *node_hi, int32_t *node_left, int32_t *node_right)
+{
+    PM_CHECK(ix != nullptr, "index is NULL");
+    if (perm) std::memcpy(perm, ix->permH.data(), ix->permH.size() * sizeof(int32_t));
+    if (leaf_off) std::memcpy(leaf_off, ix->leafOffH.data(), ix->leafOffH.size() * sizeof(int64_t));
+    size_t N = ix->nodeLo.size();
+    if (node_lo) std::memcpy(node_lo, ix->nodeLo.data(), N * sizeof(int64_t));
+    if (node_hi) std::memcpy(node_hi, ix->nodeHi.data(), N * sizeof(int64_t));
+    if (node_left) std::memcpy(node_left, ix->nodeLeft.data(), N * sizeof(int32_t));
+    if (node_right) std::memcpy(node_right, ix->nodeRight.data(), N * sizeof(int32_t));
+    return PMLSH_OK;
+}
+
+pmlsh_status pmlsh_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn_opts *opts,
+                       int64_t *out_ids, float *out_dists, float *out_err, pmlsh_query_stats *stats,
+                       void *stream)
+{
+    PM_CHECK(ix != nullptr, "index is NULL");
+    PM_CHECK(opts != nullptr, "opts is NULL");
+    PM_CHECK(nq >= 0, "nq must be >= 0");
+    if (nq == 0) return PMLSH_OK;
+    PM_CHECK(Q && out_ids && out_dists, "NULL argument");
+    const pmlsh_knn_opts &o = *opts;
+    PM_CHECK(o.k >= 1 && o.k <= PM_MAX_K && o.k <= ix->n, "k must be in 1..min(n, %d) (got %d)",
+             PM_MAX_K, o.k);
+    PM_CHECK(o.c > 1.0 && std::isfinite(o.c), "c must be > 1 (got %g)", o.c);
+    PM_CHECK(o.alpha1 > 0.0 && o.alpha1 < 1.0, "alpha1 must be in (0,1)");
+    PM_CHECK(o.beta > 0.0 && o.beta <= 1.0, "beta must be in (0,1]");
+    PM_CHECK(std::isfinite(o.r_min), "r_min must be finite");
+    PM_CHECK(std::isfinite(o.t), "t must be finite");
+    PM_CHECK(o.stop_rule == PMLSH_STOP_LITERAL || o.stop_rule == PMLSH_STOP_BC_CONSISTENT,
+             "unknown stop_rule %d", o.stop_rule);
+    PM_CHECK(o.precision == PMLSH_FP32_PLAIN, "precision mode %d is not available in this build",
+             o.precision);
+    return pm_knn(ix, Q, nq, &o, out_ids, out_dists, out_err, stats, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,1086 @@
+// (c,k)-ANN query path: Algorithm 2 over a batch of queries.
+//
+// One round of Algorithm 2 for every still-active query is a fixed sequence
+// of kernels:
+//   k_thresholds   radius R = t r and the FP32 classification thresholds
+//   k_class        Eq. 5 leaf test for (query block x leaf); builds each query
+//                  block's list of leaves and counts whole-leaf members
+//   k_count        per-point test in partially covered leaves; points whose
+//                  FP32 distance is inside the error band go to a band list
+//   k_band64       FP64 decision for band points (equal to the FP64 oracle)
+//   [host]         |S_i| per query -> which queries reach the budget B
+//   k_collect,     for budget queries: the B nearest in projected space
+//   k_select       (radix select, FP64 resolution of the band at the cut)
+//   k_verify       exact FP32 distance of every candidate, leaf-major tiles
+//                  of (64 queries x 64 points), per-query top-KP in shared
+//                  memory
+//   k_merge        merge of the partial top-KP lists, FP64 distances for the
+//                  guard set, exact top-k, k-th distance for stop rule 1
+//   [host]         stop rules, r <- c r for the rest
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "pmlsh_impl.h"
+
+namespace {
+
+constexpr int QB = 64;          // queries per block
+constexpr int TN = 64;          // points per verify tile
+constexpr int BCAP = 256;       // band-in entries per query
+constexpr int SELBAND = 2048;   // band at the budget cut, per query
+constexpr int GCAP = 1024;      // guard set per query
+constexpr float SLACK = 1e-5f;  // relative slack of the conservative leaf tests
+
+enum : unsigned char { CL_OUT = 0, CL_FULL = 1, CL_PART = 2 };
+
+// Eq. 5 (Sec. 4.2): a leaf can hold a point of B(q', R) only if
+// ||q', RO|| <= r + R and, for every pivot p_i,
+// ||q', p_i|| - R <= HR[i].max and ||q', p_i|| + R >= HR[i].min.
+// CL_OUT: every point certainly has FP32 distance^2 > Rout^2 (out-ball);
+// CL_FULL: every point certainly has FP32 distance^2 <= Rin^2;
+// otherwise CL_PART.  Slack covers the FP32 rounding of every term.
+__device__ __forceinline__ unsigned char leaf_class(const float *q, const float *qpiv, int s,
+                                                    float Rin, float Rout, const float *M)
+{
+    // explicit round-to-nearest intrinsics: never contracted, so every kernel
+    // that inlines this test takes the same decision
+    const float lo_f = 1.f - SLACK, hi_f = 1.f + SLACK;
+    float dc = __fsqrt_rn(pm_pd2_32(q, M));
+    float rr = M[16];
+    float ro = __fmul_rn(Rout, hi_f);
+    if (__fsub_rn(__fmul_rn(dc, lo_f), rr) > ro) return CL_OUT;
+    for (int i = 0; i < s; i++) {
+        float dq = qpiv[i];
+        if (__fsub_rn(__fmul_rn(dq, lo_f), M[32 + i]) > ro) return CL_OUT;
+        if (__fsub_rn(M[24 + i], __fmul_rn(dq, hi_f)) > ro) return CL_OUT;
+    }
+    if (Rin > 0.f && __fadd_rn(__fmul_rn(dc, hi_f), rr) <= __fmul_rn(Rin, lo_f)) return CL_FULL;
+    return CL_PART;
+}
+
+// |sqrt(FP32 d'^2) - FP64 d'| <= eps: coordinate rounding (2^-24 relative per
+// coordinate of o' and q') plus the FP32 sum (<= 9 u relative), doubled.
+__device__ __forceinline__ double band_eps(double R, double maxNorm, double qn)
+{
+    return 0x1.0p-23 * (maxNorm + qn) + 0x1.0p-19 * R + 1e-300;
+}
+
+// ------------------------------------------------------------ prep kernels
+
+// Routes each query down the bisection hierarchy to a leaf (locality key).
+__global__ void k_leaf_key(const float *__restrict__ qp32, int64_t nq, const int32_t *__restrict__ T,
+                           const float *__restrict__ V, unsigned int *__restrict__ key)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    int e = 0;
+    for (int guard = 0; guard < 64; guard++) {
+        int l = T[e * 4 + 0];
+        if (l < 0) break;
+        int dim = T[e * 4 + 2];
+        e = qp32[q * PM_MP + dim] < V[e] ? l : T[e * 4 + 1];
+    }
+    key[q] = (unsigned int)T[e * 4 + 3];
+}
+
+// q norms (FP64 coordinates) and FP32 distances to the pivots.
+__global__ void k_query_aux(const double *__restrict__ qp64, const float *__restrict__ qp32,
+                            int64_t nq, const float *__restrict__ piv, int s,
+                            double *__restrict__ qnorm, float *__restrict__ qpiv)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double nn = 0.0;
+    for (int j = 0; j < PM_MP; j++) nn = fma(qp64[q * PM_MP + j], qp64[q * PM_MP + j], nn);
+    qnorm[q] = sqrt(nn);
+    for (int i = 0; i < PM_MAX_PIVOTS; i++)
+        qpiv[q * PM_MAX_PIVOTS + i] = i < s ? sqrtf(pm_pd2_32(qp32 + q * PM_MP, piv + i * PM_MP)) : 0.f;
+}
+
+// Per-round thresholds for the active queries.
+struct Thr {
+    double R;      // t r (FP64, as in the oracle)
+    float lo, hi;  // FP32 d'^2 <= lo: surely in; > hi: surely out
+    float lov;     // verification threshold (lo, or the budget cut)
+    float pad;
+};
+
+__global__ void k_thresholds(const int32_t *__restrict__ act, int na, const double *__restrict__ r,
+                             double t, double maxNorm, const double *__restrict__ qnorm,
+                             Thr *__restrict__ thr)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= na) return;
+    int q = act[a];
+    double R = t * r[q];
+    double eps = band_eps(R, maxNorm, qnorm[q]);
+    Thr T;
+    T.R = R;
+    T.lo = R - eps > 0.0 ? __double2float_rd((R - eps) * (R - eps)) : -1.f;
+    T.hi = __double2float_ru((R + eps) * (R + eps));
+    T.lov = T.lo;
+    T.pad = 0.f;
+    thr[a] = T;
+}
+
+// ------------------------------------------------------------ range round
+
+// Block b of the active list (QB queries) x 128 leaves: leaf classification,
+// whole-leaf counts, and the block's leaf list (leaves not out for some
+// query of the block, under the out-radius).
+__global__ void __launch_bounds__(128)
+k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
+        const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
+        const float *__restrict__ meta, const int64_t *__restrict__ off, int64_t L,
+        int *__restrict__ cntSure, int *__restrict__ blkCnt, int *__restrict__ blkLeaves)
+{
+    __shared__ float sq[QB][PM_MP];
+    __shared__ float sp[QB][PM_MAX_PIVOTS];
+    __shared__ float sRin[QB], sRout[QB];
+    __shared__ int sCnt[QB];
+    const int b = blockIdx.y;
+    const int a0 = b * QB;
+    const int nb = min(QB, na - a0);
+    for (int e = threadIdx.x; e < QB * PM_MP; e += blockDim.x) {
+        int qq = e / PM_MP, j = e % PM_MP;
+        sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
+    }
+    for (int e = threadIdx.x; e < QB * PM_MAX_PIVOTS; e += blockDim.x) {
+        int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
+        sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
+    }
+    for (int qq = threadIdx.x; qq < QB; qq += blockDim.x) {
+        if (qq < nb) {
+            Thr T = thr[a0 + qq];
+            sRin[qq] = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
+            sRout[qq] = __fsqrt_rn(T.hi);
+        }
+        sCnt[qq] = 0;
+    }
+    __syncthreads();
+    const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool any = false;
+    if (l < L) {
+        float Mv[PM_LEAF_STRIDE];
+#pragma unroll
+        for (int j = 0; j < PM_LEAF_STRIDE; j++) Mv[j] = meta[l * PM_LEAF_STRIDE + j];
+        int cnt = (int)(off[l + 1] - off[l]);
+        for (int qq = 0; qq < nb; qq++) {
+            unsigned char c = leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv);
+            if (c != CL_OUT) any = true;
+            if (c == CL_FULL) atomicAdd(&sCnt[qq], cnt);
+        }
+    }
+    if (any) {
+        int slot = atomicAdd(&blkCnt[b], 1);
+        blkLeaves[(int64_t)b * L + slot] = (int)l;
+    }
+    __syncthreads();
+    for (int qq = threadIdx.x; qq < nb; qq += blockDim.x)
+        if (sCnt[qq]) atomicAdd(&cntSure[a0 + qq], sCnt[qq]);
+}
+
+// Per-point test in partially covered leaves.  Grid (block, split).
+__global__ void __launch_bounds__(256)
+k_count(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
+        const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
+        const float *__restrict__ meta, const int64_t *__restrict__ off, const float *__restrict__ O32,
+        const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, int64_t L,
+        int *__restrict__ cntSure, int *__restrict__ cntBand,
+        int *__restrict__ bandN, int bandCap, int *__restrict__ bandA, int *__restrict__ bandPos)
+{
+    __shared__ float sq[QB][PM_MP];
+    __shared__ float sp[QB][PM_MAX_PIVOTS];
+    __shared__ float sRin[QB], sRout[QB], sLo[QB], sHi[QB];
+    __shared__ int sSure[QB], sBand[QB];
+    __shared__ unsigned long long sPart;
+    const int b = blockIdx.x;
+    const int a0 = b * QB;
+    const int nb = min(QB, na - a0);
+    for (int e = threadIdx.x; e < QB * PM_MP; e += blockDim.x) {
+        int qq = e / PM_MP, j = e % PM_MP;
+        sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
+    }
+    for (int e = threadIdx.x; e < QB * PM_MAX_PIVOTS; e += blockDim.x) {
+        int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
+        sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
+    }
+    for (int qq = threadIdx.x; qq < QB; qq += blockDim.x) {
+        if (qq < nb) {
+            Thr T = thr[a0 + qq];
+            sRin[qq] = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
+            sRout[qq] = __fsqrt_rn(T.hi);
+            sLo[qq] = T.lo;
+            sHi[qq] = T.hi;
+        }
+        sSure[qq] = 0;
+        sBand[qq] = 0;
+    }
+    const int nl = blkCnt[b];
+    for (int li = blockIdx.y; li < nl; li += gridDim.y) {
+        const int l = blkLeaves[(int64_t)b * L + li];
+        __syncthreads();
+        if (threadIdx.x == 0) sPart = 0ull;
+        __syncthreads();
+        if (threadIdx.x < nb) {
+            unsigned char c = leaf_class(sq[threadIdx.x], sp[threadIdx.x], s, sRin[threadIdx.x],
+                                         sRout[threadIdx.x], meta + (int64_t)l * PM_LEAF_STRIDE);
+            if (c == CL_PART) atomicOr(&sPart, 1ull << threadIdx.x);
+        }
+        __syncthreads();
+        const unsigned long long part = sPart;
+        if (!part) continue;
+        const int64_t p0 = off[l], p1 = off[l + 1];
+        for (int64_t base = p0; base < p1; base += blockDim.x) {
+            const int64_t pos = base + threadIdx.x;
+            const bool valid = pos < p1;
+            float o[PM_MP];
+#pragma unroll
+            for (int j = 0; j < PM_MP; j++) o[j] = valid ? O32[pos * PM_MP + j] : 0.f;
+            unsigned long long bits = part;
+            while (bits) {
+                const int qq = __ffsll(bits) - 1;
+                bits &= bits - 1;
+                float v = pm_pd2_32(o, sq[qq]);
+                bool sure = valid && v <= sLo[qq];
+                bool band = valid && !sure && v <= sHi[qq];
+                unsigned bs = __ballot_sync(0xffffffffu, sure);
+                unsigned bb = __ballot_sync(0xffffffffu, band);
+                if ((threadIdx.x & 31) == 0) {
+                    if (bs) atomicAdd(&sSure[qq], __popc(bs));
+                    if (bb) atomicAdd(&sBand[qq], __popc(bb));
+                }
+                if (band) {
+                    int e = atomicAdd(bandN, 1);
+                    if (e < bandCap) {
+                        bandA[e] = a0 + qq;
+                        bandPos[e] = (int)pos;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int qq = threadIdx.x; qq < nb; qq += blockDim.x) {
+        if (sSure[qq]) atomicAdd(&cntSure[a0 + qq], sSure[qq]);
+        if (sBand[qq]) atomicAdd(&cntBand[a0 + qq], sBand[qq]);
+    }
+}
+
+// FP64 decision for band points: ||o', q'|| <= t r exactly as the oracle.
+__global__ void k_band64(const int *__restrict__ bandN, int bandCap, const int *__restrict__ bandA,
+                         const int *__restrict__ bandPos, const int32_t *__restrict__ act,
+                         const Thr *__restrict__ thr, const double *__restrict__ O64,
+                         const double *__restrict__ qp64, int m, int *__restrict__ inTrue,
+                         int *__restrict__ inN, int *__restrict__ inPos, int *__restrict__ fp64cnt,
+                         int *__restrict__ errFlag)
+{
+    int nbd = min(*bandN, bandCap);
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nbd) return;
+    int a = bandA[e];
+    int64_t pos = bandPos[e];
+    int q = act[a];
+    double pd = pm_pdist64(O64 + pos * PM_MP, qp64 + (int64_t)q * PM_MP, m);
+    atomicAdd(&fp64cnt[a], 1);
+    if (pd <= thr[a].R) {
+        atomicAdd(&inTrue[a], 1);
+        int slot = atomicAdd(&inN[a], 1);
+        if (slot < BCAP) inPos[(int64_t)a * BCAP + slot] = (int)pos;
+        else atomicOr(errFlag, 2);
+    }
+}
+
+// --------------------------------------------------------- budget (rule 2)
+
+// Collects (FP32 d'^2, position) of every point with d'^2 <= hi for one
+// budget query.  Grid (budget query, leaf chunk of 256).
+__global__ void k_collect(const int32_t *__restrict__ sel, const int32_t *__restrict__ act,
+                          const Thr *__restrict__ thr, const float *__restrict__ qp32,
+                          const float *__restrict__ qpiv, int s, const float *__restrict__ meta,
+                          const int64_t *__restrict__ off, int64_t L, const float *__restrict__ O32,
+                          const int64_t *__restrict__ selOff, const int64_t *__restrict__ selCap,
+                          int *__restrict__ selCnt, float *__restrict__ selKey,
+                          int *__restrict__ selPos, int *__restrict__ errFlag)
+{
+    const int si = blockIdx.x;
+    const int a = sel[si];
+    const int q = act[a];
+    const int64_t l = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    float qv[PM_MP], qpv[PM_MAX_PIVOTS];
+    for (int j = 0; j < PM_MP; j++) qv[j] = qp32[(int64_t)q * PM_MP + j];
+    for (int i = 0; i < PM_MAX_PIVOTS; i++) qpv[i] = qpiv[(int64_t)q * PM_MAX_PIVOTS + i];
+    Thr T = thr[a];
+    float Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f, Rout = __fsqrt_rn(T.hi);
+    unsigned char c = leaf_class(qv, qpv, s, Rin, Rout, meta + l * PM_LEAF_STRIDE);
+    if (c == CL_OUT) return;
+    for (int64_t pos = off[l]; pos < off[l + 1]; pos++) {
+        float v = pm_pd2_32(O32 + pos * PM_MP, qv);
+        if (c == CL_FULL || v <= T.hi) {
+            int e = atomicAdd(&selCnt[si], 1);
+            if (e < selCap[si]) {
+                selKey[selOff[si] + e] = v;
+                selPos[selOff[si] + e] = (int)pos;
+            } else {
+                atomicOr(errFlag, 64);
+            }
+        }
+    }
+}
+
+// Radix select of the B-th smallest FP32 key, then the FP64-resolved cut:
+// keys < LO are surely among the B nearest, keys in [LO, HI] are ordered by
+// (FP64 d', id) and the first B - |{key < LO}| of them join.  One block of
+// 1024 threads per budget query.
+__global__ void __launch_bounds__(1024)
+k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *__restrict__ thr,
+         const int64_t *__restrict__ selOff, const int *__restrict__ selCnt,
+         const float *__restrict__ selKey, const int *__restrict__ selPos, int64_t B,
+         double maxNorm, const double *__restrict__ qnorm, const double *__restrict__ O64,
+         const double *__restrict__ qp64, int m, const int32_t *__restrict__ perm,
+         int *__restrict__ inN, int *__restrict__ inPos, int *__restrict__ fp64cnt,
+         int *__restrict__ errFlag)
+{
+    __shared__ unsigned int hist[2048];
+    __shared__ unsigned int sPrefix, sNeed;
+    __shared__ double bd[SELBAND];
+    __shared__ int bpos[SELBAND];
+    __shared__ int bid[SELBAND];
+    __shared__ int sSure, sBand;
+    const int si = blockIdx.x;
+    const int a = sel[si];
+    const int q = act[a];
+    const int64_t base = selOff[si];
+    const int cnt = min(selCnt[si], (int)(selOff[si + 1] - selOff[si]));
+    const unsigned int *keys = (const unsigned int *)(selKey + base);
+    if (threadIdx.x == 0) { sPrefix = 0; sNeed = (unsigned int)B; }
+    const int shifts[3] = {21, 10, 0};
+    const int widths[3] = {11, 11, 10};
+    for (int pass = 0; pass < 3; pass++) {
+        for (int i = threadIdx.x; i < 2048; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        const int sh = shifts[pass];
+        const unsigned int hiMask = pass == 0 ? 0u : (0xffffffffu << (sh + widths[pass]));
+        const unsigned int pre = sPrefix;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            unsigned int k = keys[e];
+            if ((k & hiMask) == (pre & hiMask))
+                atomicAdd(&hist[(k >> sh) & ((1u << widths[pass]) - 1)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned int need = sNeed, acc = 0;
+            int bin = 0;
+            for (; bin < (1 << widths[pass]); bin++) {
+                if (acc + hist[bin] >= need) break;
+                acc += hist[bin];
+            }
+            sNeed = need - acc;
+            sPrefix = pre | ((unsigned int)bin << sh);
+        }
+        __syncthreads();
+    }
+    const float tau32 = __uint_as_float(sPrefix);
+    const double tau = sqrt((double)tau32);
+    const double eps = band_eps(tau, maxNorm, qnorm[q]);
+    const float LO = tau - 2.0 * eps > 0.0 ? __double2float_rd((tau - 2.0 * eps) * (tau - 2.0 * eps)) : 0.f;
+    const float HI = __double2float_ru((tau + 2.0 * eps) * (tau + 2.0 * eps));
+    if (threadIdx.x == 0) { sSure = 0; sBand = 0; }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        float v = selKey[base + e];
+        if (v < LO) atomicAdd(&sSure, 1);
+        else if (v <= HI) {
+            int slot = atomicAdd(&sBand, 1);
+            if (slot < SELBAND) {
+                int64_t pos = selPos[base + e];
+                bd[slot] = pm_pdist64(O64 + pos * PM_MP, qp64 + (int64_t)q * PM_MP, m);
+                bpos[slot] = (int)pos;
+                bid[slot] = perm[pos];
+            }
+        }
+    }
+    __syncthreads();
+    const int nband = sBand;
+    const int need = (int)B - sSure;
+    if (nband > SELBAND || need < 0 || need > nband) {
+        if (threadIdx.x == 0) atomicOr(errFlag, 4);
+        return;
+    }
+    // bitonic sort of the band by (FP64 d', id)
+    int P = 1;
+    while (P < nband) P <<= 1;
+    for (int i = nband + threadIdx.x; i < P; i += blockDim.x) { bd[i] = INFINITY; bid[i] = 0x7fffffff; bpos[i] = -1; }
+    __syncthreads();
+    for (int k2 = 2; k2 <= P; k2 <<= 1)
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool up = (i & k2) == 0;
+                    bool gt = bd[i] > bd[ixj] || (bd[i] == bd[ixj] && bid[i] > bid[ixj]);
+                    if (gt == up) {
+                        double td = bd[i]; bd[i] = bd[ixj]; bd[ixj] = td;
+                        int ti = bid[i]; bid[i] = bid[ixj]; bid[ixj] = ti;
+                        int tp = bpos[i]; bpos[i] = bpos[ixj]; bpos[ixj] = tp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (need > BCAP) {
+        if (threadIdx.x == 0) atomicOr(errFlag, 8);
+        return;
+    }
+    for (int i = threadIdx.x; i < need; i += blockDim.x) inPos[(int64_t)a * BCAP + i] = bpos[i];
+    if (threadIdx.x == 0) {
+        inN[a] = need;
+        atomicAdd(&fp64cnt[a], nband);
+        Thr T = thr[a];
+        T.lov = LO > 0.f ? __uint_as_float(__float_as_uint(LO) - 1u) : -1.f;  // v <= lov  <=>  v < LO
+        thr[a] = T;
+    }
+}
+
+// ------------------------------------------------------------ verification
+
+struct VerifySmem {
+    // dynamic layout, see k_verify
+};
+
+// Exact FP32 distances of candidate pairs, (64 queries x 64 points) tiles over
+// each leaf of the block's list (split s of S), with a per-query top-KP in
+// shared memory.  Candidates: FP32 d'^2 <= lov (leaf tests with Rin = Rout =
+// sqrt(lov)).  d^2 = sum_i (x_i - q_i)^2 accumulated sequentially in i.
+__global__ void __launch_bounds__(256)
+k_verify(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
+         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
+         const float *__restrict__ meta, const int64_t *__restrict__ off,
+         const float *__restrict__ O32, const float *__restrict__ X, const float *__restrict__ Qd, int ld,
+         const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, int64_t L, int KP,
+         float *__restrict__ partD, int *__restrict__ partI, int *__restrict__ partSeen,
+         float *__restrict__ partMax)
+{
+    extern __shared__ __align__(16) float smem[];
+    float(*Qs)[QB + 4] = (float(*)[QB + 4])smem;                 // [32][68]
+    float(*Xs)[TN + 4] = (float(*)[TN + 4])(smem + 32 * (QB + 4));  // [32][68]
+    float(*Dt)[TN + 1] = (float(*)[TN + 1])(smem + 32 * (QB + 4) + 32 * (TN + 4));  // [64][65]
+    float(*sq)[PM_MP] = (float(*)[PM_MP])((float *)Dt + QB * (TN + 1));            // [64][16]
+    float(*op)[PM_MP] = (float(*)[PM_MP])((float *)sq + QB * PM_MP);                // [64][16]
+    float(*sp)[PM_MAX_PIVOTS] = (float(*)[PM_MAX_PIVOTS])((float *)op + TN * PM_MP);  // [64][8]
+    float *sLo = (float *)sp + QB * PM_MAX_PIVOTS;
+    float *sRv = sLo + QB;
+    float *cmax = sRv + QB;
+    int *cslot = (int *)(cmax + QB);
+    int *seen = cslot + QB;
+    int *qid = seen + QB;
+    unsigned char *cls = (unsigned char *)(qid + QB);
+    float *vals = (float *)(cls + QB);           // [QB][KP]
+    int *idxs = (int *)(vals + QB * KP);         // [QB][KP]
+
+    const int b = blockIdx.x, S = gridDim.y, sidx = blockIdx.y;
+    const int a0 = b * QB;
+    const int nb = min(QB, na - a0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int e = tid; e < QB * PM_MP; e += blockDim.x) {
+        int qq = e / PM_MP, j = e % PM_MP;
+        sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
+    }
+    for (int e = tid; e < QB * PM_MAX_PIVOTS; e += blockDim.x) {
+        int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
+        sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
+    }
+    for (int qq = tid; qq < QB; qq += blockDim.x) {
+        float lov = qq < nb ? thr[a0 + qq].lov : -1.f;
+        sLo[qq] = lov;
+        sRv[qq] = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
+        cmax[qq] = INFINITY;
+        cslot[qq] = 0;
+        seen[qq] = 0;
+        qid[qq] = qq < nb ? act[a0 + qq] : -1;
+    }
+    for (int e = tid; e < QB * KP; e += blockDim.x) {
+        vals[e] = INFINITY;
+        idxs[e] = -1;
+    }
+    __syncthreads();
+    const int nl = blkCnt[b];
+    for (int li = sidx; li < nl; li += S) {
+        const int l = blkLeaves[(int64_t)b * L + li];
+        if (tid < QB) {
+            unsigned char c = CL_OUT;
+            if (tid < nb && sRv[tid] > 0.f)
+                c = leaf_class(sq[tid], sp[tid], s, sRv[tid], sRv[tid], meta + (int64_t)l * PM_LEAF_STRIDE);
+            cls[tid] = c;
+        }
+        __syncthreads();
+        int anyq = 0;
+        for (int qq = 0; qq < QB; qq++) anyq |= cls[qq];
+        if (!anyq) { __syncthreads(); continue; }
+        const int64_t p0 = off[l], p1 = off[l + 1];
+        for (int64_t c0 = p0; c0 < p1; c0 += TN) {
+            const int cntc = (int)min((int64_t)TN, p1 - c0);
+            for (int e = tid; e < TN * PM_MP; e += blockDim.x) {
+                int pp = e / PM_MP, j = e % PM_MP;
+                op[pp][j] = pp < cntc ? O32[(c0 + pp) * PM_MP + j] : 0.f;
+            }
+            __syncthreads();
+            unsigned int mask = 0;
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int qq = 4 * ty + r;
+                const unsigned char c = cls[qq];
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) {
+                    const int pp = 4 * tx + cc;
+                    bool cand = false;
+                    if (pp < cntc) {
+                        if (c == CL_FULL) cand = true;
+                        else if (c == CL_PART) cand = pm_pd2_32(op[pp], sq[qq]) <= sLo[qq];
+                    }
+                    mask |= (unsigned)cand << (r * 4 + cc);
+                }
+            }
+            if (!__syncthreads_or(mask != 0)) continue;
+            float acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++) acc[r][cc] = 0.f;
+            for (int k0 = 0; k0 < ld; k0 += 32) {
+                // stage the query rows and the point rows (k-major)
+                for (int e = tid; e < QB * 32; e += blockDim.x) {
+                    int qq = e >> 5, kk = e & 31;
+                    int qg = qid[qq];
+                    Qs[kk][qq] = qg >= 0 ? Qd[(int64_t)qg * ld + k0 + kk] : 0.f;
+                }
+                for (int e = tid; e < TN * 32; e += blockDim.x) {
+                    int pp = e >> 5, kk = e & 31;
+                    Xs[kk][pp] = pp < cntc ? X[(c0 + pp) * ld + k0 + kk] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int kk = 0; kk < 32; kk++) {
+                    float4 qa = *(const float4 *)&Qs[kk][4 * ty];
+                    float4 xb = *(const float4 *)&Xs[kk][4 * tx];
+                    float qv[4] = {qa.x, qa.y, qa.z, qa.w};
+                    float xv[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+                    for (int r = 0; r < 4; r++)
+#pragma unroll
+                        for (int cc = 0; cc < 4; cc++) {
+                            float t = __fsub_rn(qv[r], xv[cc]);
+                            acc[r][cc] = __fmaf_rn(t, t, acc[r][cc]);
+                        }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++)
+                    Dt[4 * ty + r][4 * tx + cc] = (mask >> (r * 4 + cc)) & 1u ? acc[r][cc] : INFINITY;
+            __syncthreads();
+            // top-KP update, warp w owns query rows 8w .. 8w+7
+            for (int rr = 0; rr < QB / 8; rr++) {
+                const int qq = warp * (QB / 8) + rr;
+                if (qq >= nb) break;
+                float v[2] = {Dt[qq][lane], Dt[qq][lane + 32]};
+                int addSeen = __popc(__ballot_sync(0xffffffffu, v[0] < INFINITY)) +
+                              __popc(__ballot_sync(0xffffffffu, v[1] < INFINITY));
+                if (lane == 0) seen[qq] += addSeen;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    unsigned bits = __ballot_sync(0xffffffffu, v[h] < cmax[qq]);
+                    while (bits) {
+                        const int src = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const float val = __shfl_sync(0xffffffffu, v[h], src);
+                        if (val < cmax[qq]) {
+                            if (lane == 0) {
+                                vals[qq * KP + cslot[qq]] = val;
+                                idxs[qq * KP + cslot[qq]] = (int)(c0 + src + 32 * h);
+                            }
+                            __syncwarp();
+                            float best = -1.f;
+                            int bs = 0;
+                            for (int e = lane; e < KP; e += 32) {
+                                float x = vals[qq * KP + e];
+                                if (x > best) { best = x; bs = e; }
+                            }
+                            for (int o = 16; o; o >>= 1) {
+                                float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                                int os = __shfl_xor_sync(0xffffffffu, bs, o);
+                                if (ob > best || (ob == best && os < bs)) { best = ob; bs = os; }
+                            }
+                            if (lane == 0) { cmax[qq] = best; cslot[qq] = bs; }
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int qq = warp; qq < nb; qq += 8) {
+        const int64_t base = ((int64_t)(a0 + qq) * S + sidx) * KP;
+        for (int e = lane; e < KP; e += 32) {
+            partD[base + e] = vals[qq * KP + e];
+            partI[base + e] = idxs[qq * KP + e];
+        }
+        if (lane == 0) {
+            partSeen[(int64_t)(a0 + qq) * S + sidx] = seen[qq];
+            partMax[(int64_t)(a0 + qq) * S + sidx] = seen[qq] > KP ? cmax[qq] : INFINITY;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- merge
+
+// One block (256 threads) per active query: merges the S partial lists and
+// the band-in points, takes the guard set {d^2_32 <= K32 (1 + 3 eps_v)} (K32
+// the k-th smallest FP32 d^2, eps_v = (ld + 4) 2^-24 the FP32 sum bound),
+// computes FP64 distances for it, sorts by (FP64 distance, id) and writes the
+// top-k and the FP64 k-th distance.
+__global__ void __launch_bounds__(256)
+k_merge(const int32_t *__restrict__ act, int S, int KP, int k, const float *__restrict__ partD,
+        const int *__restrict__ partI, const float *__restrict__ partMax,
+        const int *__restrict__ inN, const int *__restrict__ inPos,
+        const float *__restrict__ X, const float *__restrict__ Qd, int ld, int d,
+        const int32_t *__restrict__ perm, int64_t *__restrict__ outIds, float *__restrict__ outD,
+        float *__restrict__ outErr, double *__restrict__ dk, int *__restrict__ fp64cnt,
+        int *__restrict__ errFlag, int P)
+{
+    extern __shared__ __align__(16) unsigned char msm[];
+    float *mv = (float *)msm;                       // [P]
+    int *mp = (int *)(mv + P);                      // [P]
+    double *gd = (double *)(mp + P);                // [GCAP]
+    long long *gid = (long long *)(gd + GCAP);      // [GCAP]
+    __shared__ int sG;
+    __shared__ float sThr;
+    const int a = blockIdx.x;
+    const int q = act[a];
+    const int tid = threadIdx.x;
+    const int nPart = S * KP;
+    const int nIn = min(inN[a], BCAP);
+    for (int e = tid; e < P; e += blockDim.x) {
+        float v = INFINITY;
+        int p = 0x7fffffff;
+        if (e < nPart) {
+            v = partD[(int64_t)a * nPart + e];
+            p = partI[(int64_t)a * nPart + e];
+            if (!(v < INFINITY)) p = 0x7fffffff;
+        } else if (e < nPart + nIn) {
+            p = inPos[(int64_t)a * BCAP + (e - nPart)];
+            const float *xr = X + (int64_t)p * ld;
+            const float *qr = Qd + (int64_t)q * ld;
+            float acc = 0.f;
+            for (int i = 0; i < ld; i++) {
+                float t = __fsub_rn(qr[i], xr[i]);
+                acc = __fmaf_rn(t, t, acc);
+            }
+            v = acc;
+        }
+        mv[e] = v;
+        mp[e] = p;
+    }
+    __syncthreads();
+    for (int k2 = 2; k2 <= P; k2 <<= 1)
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool up = (i & k2) == 0;
+                    bool gt = mv[i] > mv[ixj] || (mv[i] == mv[ixj] && mp[i] > mp[ixj]);
+                    if (gt == up) {
+                        float tv = mv[i]; mv[i] = mv[ixj]; mv[ixj] = tv;
+                        int tp = mp[i]; mp[i] = mp[ixj]; mp[ixj] = tp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (tid == 0) {
+        const float K32 = mv[k - 1];
+        const double epsv = (double)(ld + 4) * 0x1.0p-24;
+        float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
+        int G = 0;
+        while (G < P && mv[G] <= thrv && mv[G] < INFINITY) G++;
+        sThr = thrv;
+        sG = G;
+        for (int sp2 = 0; sp2 < S; sp2++)
+            // a split that dropped entries (finite max) below the guard bound
+            if (partMax[(int64_t)a * S + sp2] < INFINITY && partMax[(int64_t)a * S + sp2] <= thrv)
+                atomicOr(errFlag, 16);
+        if (G > GCAP) atomicOr(errFlag, 32);
+    }
+    __syncthreads();
+    const int G = min(sG, GCAP);
+    int Pg = 1;
+    while (Pg < G) Pg <<= 1;
+    for (int e = tid; e < Pg; e += blockDim.x) {
+        if (e < G) {
+            int p = mp[e];
+            gd[e] = pm_dist64(X + (int64_t)p * ld, Qd + (int64_t)q * ld, d);
+            gid[e] = perm[p];
+        } else {
+            gd[e] = INFINITY;
+            gid[e] = 0x7fffffffffffffffLL;
+        }
+    }
+    __syncthreads();
+    for (int k2 = 2; k2 <= Pg; k2 <<= 1)
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < Pg; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool up = (i & k2) == 0;
+                    bool gt = gd[i] > gd[ixj] || (gd[i] == gd[ixj] && gid[i] > gid[ixj]);
+                    if (gt == up) {
+                        double td = gd[i]; gd[i] = gd[ixj]; gd[ixj] = td;
+                        long long ti = gid[i]; gid[i] = gid[ixj]; gid[ixj] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int e = tid; e < k; e += blockDim.x) {
+        const int64_t o = (int64_t)q * k + e;
+        if (e < G) {
+            double dv = gd[e];
+            float f = __double2float_rn(dv);
+            outIds[o] = gid[e];
+            outD[o] = f;
+            outErr[o] = (float)fabs((double)f - dv);
+        } else {
+            outIds[o] = -1;
+            outD[o] = INFINITY;
+            outErr[o] = 0.f;
+        }
+    }
+    if (tid == 0) {
+        dk[a] = G >= k ? gd[k - 1] : INFINITY;
+        atomicAdd(&fp64cnt[a], G);
+    }
+}
+
+// Locality order: counting sort of queries by leaf key.
+__global__ void k_hist(const unsigned int *__restrict__ key, int64_t nq, int *__restrict__ h)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < nq) atomicAdd(&h[key[q]], 1);
+}
+
+__global__ void k_scan_single(int *__restrict__ h, int64_t L)
+{
+    // one block: exclusive scan of L counters, 1024 at a time
+    __shared__ int carry;
+    __shared__ int buf[1024];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < L; b0 += 1024) {
+        int64_t i = b0 + threadIdx.x;
+        int v = i < L ? h[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int t = threadIdx.x >= o ? buf[threadIdx.x - o] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < L) h[i] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scatter_order(const unsigned int *__restrict__ key, int64_t nq, int *__restrict__ h,
+                                int32_t *__restrict__ order)
+{
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < nq) order[atomicAdd(&h[key[q]], 1)] = (int32_t)q;
+}
+
+size_t verify_smem(int KP)
+{
+    size_t f = 32 * (QB + 4) + 32 * (TN + 4) + QB * (TN + 1) + QB * PM_MP + TN * PM_MP +
+               QB * PM_MAX_PIVOTS + 3 * QB;
+    size_t bytes = f * 4 + 3 * QB * 4 + QB + (size_t)QB * KP * 8 + 16;
+    return (bytes + 15) & ~(size_t)15;
+}
+
+template <class T> T *grow(DevBuf &b, size_t count, pmlsh_status &st)
+{
+    if (st != PMLSH_OK) return nullptr;
+    st = b.reserve(count * sizeof(T));
+    return st == PMLSH_OK ? b.as<T>() : nullptr;
+}
+
+}  // namespace
+
+pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn_opts *o,
+                    int64_t *ids, float *dists, float *err, pmlsh_query_stats *stats,
+                    cudaStream_t st)
+{
+    const int64_t n = ix->n;
+    const int d = ix->d, ld = ix->ld, m = ix->m, k = o->k;
+    const int64_t L = ix->L;
+    KnnWork &w = ix->work;
+    // parameters (Eq. 9; budget of Algorithm 2; r_min rule of Sec. 5.2)
+    const double t = o->t > 0.0 ? o->t : std::sqrt(pm_chi2_upper_quantile(o->alpha1, m));
+    const int64_t B = pmlsh_budget(n, o->beta, k);
+    double rmin = o->r_min;
+    if (!(rmin > 0.0)) {
+        const std::vector<double> &v = ix->distSample;
+        double rstar = 1.0;
+        if (!v.empty()) {
+            double p = std::min(1.0, (o->beta * (double)n + (double)k) / (double)n);
+            int64_t N = (int64_t)v.size();
+            int64_t rank = (int64_t)std::ceil(p * (double)N - 1e-9);
+            rank = std::max<int64_t>(1, std::min<int64_t>(N, rank));
+            rstar = v[rank - 1];
+            if (!(rstar > 0.0)) {
+                rstar = 0.0;
+                for (double x : v) if (x > 0.0) { rstar = x; break; }
+            }
+            rmin = rstar > 0.0 ? rstar / o->c : 1.0;
+        } else {
+            rmin = 1.0;
+        }
+    }
+    const int KP = (k + 32 + 31) / 32 * 32;
+    const bool qdev = pm_is_device_ptr(Q);
+    pmlsh_status s = PMLSH_OK;
+    float *Qd = grow<float>(w.Qd, (size_t)nq * ld, s);
+    double *qp64 = grow<double>(w.qp64, (size_t)nq * PM_MP, s);
+    float *qp32 = grow<float>(w.qp32, (size_t)nq * PM_MP, s);
+    double *qnorm = grow<double>(w.qnorm, nq, s);
+    float *qpiv = grow<float>(w.qpiv, (size_t)nq * PM_MAX_PIVOTS, s);
+    unsigned int *key = grow<unsigned int>(w.keys, nq, s);
+    int32_t *order = grow<int32_t>(w.order, nq, s);
+    int *hist = grow<int>(w.keys2, L + 1, s);
+    double *rq = grow<double>(w.qstate, nq, s);
+    int64_t *oIds = grow<int64_t>(w.outIds, (size_t)nq * k, s);
+    float *oD = grow<float>(w.outD64, (size_t)nq * k, s);
+    float *oE = grow<float>(w.outErr, (size_t)nq * k, s);
+    if (s != PMLSH_OK) return s;
+    PM_CUDA(cudaMemsetAsync(Qd, 0, (size_t)nq * ld * sizeof(float), st));
+    PM_CUDA(cudaMemcpy2DAsync(Qd, ld * sizeof(float), Q, d * sizeof(float), d * sizeof(float), nq,
+                              qdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    pm_launch_project64(Qd, nq, ld, d, m, ix->A32, qp64, qp32, nullptr, st);
+    const unsigned gq = (unsigned)((nq + 255) / 256);
+    PM_LAUNCH("k_query_aux", st, k_query_aux<<<gq, 256, 0, st>>>(qp64, qp32, nq, ix->piv32, ix->s, qnorm, qpiv));
+    PM_LAUNCH("k_leaf_key", st, k_leaf_key<<<gq, 256, 0, st>>>(qp32, nq, ix->treeI, ix->treeV, key));
+    PM_CUDA(cudaMemsetAsync(hist, 0, (L + 1) * sizeof(int), st));
+    PM_LAUNCH("k_hist", st, k_hist<<<gq, 256, 0, st>>>(key, nq, hist));
+    PM_LAUNCH("k_scan_single", st, k_scan_single<<<1, 1024, 0, st>>>(hist, L + 1));
+    PM_LAUNCH("k_scatter_order", st, k_scatter_order<<<gq, 256, 0, st>>>(key, nq, hist, order));
+    PM_CUDA(cudaGetLastError());
+    std::vector<int32_t> orderH(nq);
+    PM_CUDA(cudaMemcpyAsync(orderH.data(), order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+
+    // host round state
+    std::vector<double> r(nq, rmin);
+    std::vector<int32_t> rounds(nq, 0), rule(nq, 0), fp64(nq, 0);
+    std::vector<int64_t> ncand(nq, 0), nver(nq, 0);
+    std::vector<char> done(nq, 0);
+    PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
+
+    const int bandCap = 1 << 20;
+    int *act = grow<int32_t>(w.active, nq, s);
+    Thr *thr = grow<Thr>(w.thr, nq, s);
+    int *cntSure = grow<int>(w.cntSure, nq, s);
+    int *cntBand = grow<int>(w.cntBand, nq, s);
+    int *inTrue = grow<int>(w.bandCnt, nq, s);
+    int *inN = grow<int>(w.bandIn, nq, s);
+    int *inPos = grow<int>(w.bandInQ, (size_t)nq * BCAP, s);
+    int *bandA = grow<int>(w.bandQ, bandCap, s);
+    int *bandPos = grow<int>(w.bandPos, bandCap, s);
+    int *fpc = grow<int>(w.flags, nq + 8, s);
+    double *dk = grow<double>(w.dk, nq, s);
+    if (s != PMLSH_OK) return s;
+    int *bandN = fpc + nq;       // counters after the per-query array
+    int *errFlag = fpc + nq + 1;
+
+    const int S_cap = std::max(1, (4096 - BCAP) / KP);
+    int nsm = 148;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const size_t vsmem = verify_smem(KP);
+    PM_CUDA(cudaFuncSetAttribute(k_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
+
+    std::vector<int32_t> actH;
+    actH.reserve(nq);
+    for (int round = 0; round < 100000; round++) {
+        actH.clear();
+        for (int64_t i = 0; i < nq; i++)
+            if (!done[orderH[i]]) actH.push_back(orderH[i]);
+        const int na = (int)actH.size();
+        if (na == 0) break;
+        const int nblk = (na + QB - 1) / QB;
+        PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        int *blkCnt = grow<int>(w.blkCnt, nblk, s);
+        int *blkLeaves = grow<int>(w.blkLeaves, (size_t)nblk * L, s);
+        if (s != PMLSH_OK) return s;
+        PM_CUDA(cudaMemsetAsync(blkCnt, 0, nblk * sizeof(int), st));
+        PM_CUDA(cudaMemsetAsync(cntSure, 0, na * sizeof(int), st));
+        PM_CUDA(cudaMemsetAsync(cntBand, 0, na * sizeof(int), st));
+        PM_CUDA(cudaMemsetAsync(inTrue, 0, na * sizeof(int), st));
+        PM_CUDA(cudaMemsetAsync(inN, 0, na * sizeof(int), st));
+        PM_CUDA(cudaMemsetAsync(fpc, 0, (nq + 8) * sizeof(int), st));
+        PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
+        dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblk);
+        PM_LAUNCH("k_class", st, k_class<<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
+                                    cntSure, blkCnt, blkLeaves));
+        int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
+        PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
+                                                    ix->leafOff, ix->O32, blkCnt, blkLeaves, L,
+                                                    cntSure, cntBand, bandN, bandCap, bandA, bandPos));
+        // FP64 band resolution (grid sized by the capacity; empty threads exit)
+        {
+            int hBand = 0;
+            PM_CUDA(cudaMemcpyAsync(&hBand, bandN, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaStreamSynchronize(st));
+            if (hBand > bandCap) {
+                pm_set_error("more than %d projected distances fell inside the FP32 error band in one round", bandCap);
+                return PMLSH_EINTERNAL;
+            }
+            if (hBand > 0)
+                PM_LAUNCH("k_band64", st, k_band64<<<(hBand + 255) / 256, 256, 0, st>>>(bandN, bandCap, bandA, bandPos, act, thr,
+                                                             ix->O64, qp64, m, inTrue, inN, inPos, fpc,
+                                                             errFlag));
+        }
+        PM_CUDA(cudaGetLastError());
+        std::vector<int> hs(na), hb(na), hin(na);
+        PM_CUDA(cudaMemcpyAsync(hs.data(), cntSure, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(hb.data(), cntBand, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(hin.data(), inTrue, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        // which queries reached the budget (rule 2)
+        std::vector<int32_t> selH;
+        std::vector<int64_t> selOffH;
+        std::vector<int64_t> count(na);
+        int64_t selTotal = 0;
+        for (int a = 0; a < na; a++) {
+            count[a] = (int64_t)hs[a] + hin[a];
+            if (count[a] >= B) {
+                selH.push_back(a);
+                selOffH.push_back(selTotal);
+                selTotal += (int64_t)hs[a] + hb[a];
+            }
+        }
+        if (!selH.empty()) {
+            const int ns = (int)selH.size();
+            int32_t *sel = grow<int32_t>(w.selTau, ns, s);
+            int64_t *selOff = grow<int64_t>(w.selOff, 2 * ns + 1, s);
+            int *selCnt = grow<int>(w.selCnt, ns, s);
+            float *selKey = grow<float>(w.selBuf, (size_t)selTotal, s);
+            int *selPos = grow<int>(w.misc, (size_t)selTotal, s);
+            if (s != PMLSH_OK) return s;
+            PM_CUDA(cudaMemcpyAsync(sel, selH.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            selOffH.push_back(selTotal);
+            std::vector<int64_t> capH(ns);
+            for (int i = 0; i < ns; i++) capH[i] = selOffH[i + 1] - selOffH[i];
+            PM_CUDA(cudaMemcpyAsync(selOff, selOffH.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            PM_CUDA(cudaMemcpyAsync(selOff + ns + 1, capH.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            PM_CUDA(cudaMemsetAsync(selCnt, 0, ns * sizeof(int), st));
+            PM_LAUNCH("k_collect", st, k_collect<<<dim3(ns, (unsigned)((L + 255) / 256)), 256, 0, st>>>(
+                sel, act, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L, ix->O32, selOff,
+                selOff + ns + 1, selCnt, selKey, selPos, errFlag));
+            PM_LAUNCH("k_select", st, k_select<<<ns, 1024, 0, st>>>(sel, act, thr, selOff, selCnt, selKey, selPos, B, ix->maxNorm,
+                                          qnorm, ix->O64, qp64, m, ix->perm, inN, inPos, fpc, errFlag));
+            PM_CUDA(cudaGetLastError());
+        }
+        // verification
+        int S = std::max(1, std::min(S_cap, (2 * nsm + nblk - 1) / nblk));
+        float *partD = grow<float>(w.partD, (size_t)na * S * KP, s);
+        int *partI = grow<int>(w.partI, (size_t)na * S * KP, s);
+        int *partSeen = grow<int>(w.partSeen, (size_t)na * S, s);
+        float *partMax = grow<float>(w.sortTmp, (size_t)na * S, s);
+        if (s != PMLSH_OK) return s;
+        PM_LAUNCH("k_verify", st, k_verify<<<dim3(nblk, S), 256, vsmem, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
+                                                    ix->leafOff, ix->O32, ix->X, Qd, ld, blkCnt, blkLeaves,
+                                                    L, KP, partD, partI, partSeen, partMax));
+        int P = 1;
+        while (P < S * KP + BCAP) P <<= 1;
+        size_t msmem = (size_t)P * 8 + (size_t)GCAP * 16;
+        PM_CUDA(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+        PM_LAUNCH("k_merge", st, k_merge<<<na, 256, msmem, st>>>(act, S, KP, k, partD, partI, partMax, inN, inPos, ix->X, Qd, ld, d,
+                                        ix->perm, oIds, oD, oE, dk, fpc, errFlag, P));
+        PM_CUDA(cudaGetLastError());
+        std::vector<double> dkH(na);
+        std::vector<int> fpH(na);
+        int errH = 0;
+        PM_CUDA(cudaMemcpyAsync(dkH.data(), dk, na * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(fpH.data(), fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(&errH, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        if (errH) {
+            pm_set_error("internal capacity exceeded (code %d): too many points tied within one FP32 "
+                         "error band", errH);
+            return PMLSH_EINTERNAL;
+        }
+        // stop rules (Algorithm 2, with the readings of pmlsh.h)
+        bool changed = false;
+        for (int a = 0; a < na; a++) {
+            const int q = actH[a];
+            rounds[q]++;
+            fp64[q] += fpH[a];
+            const bool budget = count[a] >= B;
+            nver[q] += budget ? B : count[a];
+            if (budget) { done[q] = 1; rule[q] = 2; ncand[q] = B; continue; }
+            ncand[q] = count[a];
+            if (count[a] == n) { done[q] = 1; rule[q] = 3; continue; }
+            if (o->stop_rule == PMLSH_STOP_BC_CONSISTENT) {
+                if (dkH[a] <= o->c * r[q]) { done[q] = 1; rule[q] = 1; continue; }
+                r[q] = o->c * r[q];
+            } else {
+                r[q] = o->c * r[q];
+                if (count[a] > 0 && dkH[a] <= o->c * r[q]) { done[q] = 1; rule[q] = 1; continue; }
+            }
+            changed = true;
+        }
+        if (changed)
+            PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (round == 99999) {
+            pm_set_error("Algorithm 2 did not stop within 100000 rounds");
+            return PMLSH_EINTERNAL;
+        }
+    }
+    // results
+    const bool idev = pm_is_device_ptr(ids), ddev = pm_is_device_ptr(dists);
+    PM_CUDA(cudaMemcpyAsync(ids, oIds, (size_t)nq * k * sizeof(int64_t),
+                            idev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaMemcpyAsync(dists, oD, (size_t)nq * k * sizeof(float),
+                            ddev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (err)
+        PM_CUDA(cudaMemcpyAsync(err, oE, (size_t)nq * k * sizeof(float),
+                                pm_is_device_ptr(err) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (stats) {
+        std::vector<pmlsh_query_stats> sv(nq);
+        for (int64_t q = 0; q < nq; q++) {
+            sv[q].rounds = rounds[q];
+            sv[q].stop_rule = rule[q];
+            sv[q].n_cand = ncand[q];
+            sv[q].r_final = r[q];
+            sv[q].fp64_checks = fp64[q];
+            sv[q].reserved = 0;
+            sv[q].n_verified = nver[q];
+        }
+        PM_CUDA(cudaMemcpyAsync(stats, sv.data(), nq * sizeof(pmlsh_query_stats),
+                                pm_is_device_ptr(stats) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+    }
+    if (!idev || !ddev) PM_CUDA(cudaStreamSynchronize(st));
+    return PMLSH_OK;
+}

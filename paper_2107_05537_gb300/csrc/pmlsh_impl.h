@@ -1,0 +1,171 @@
+// Internal declarations of libpmlsh (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pmlsh.h"
+
+// Projected coordinates are padded to 16 lanes (m <= 16); padded lanes are 0
+// for points, queries and pivots, so they add nothing to any distance.
+#define PM_MP 16
+// Leaf metadata, FP32, per leaf: [0,16) centre RO, [16] radius (over FP32
+// coordinates, rounded up), [17] unused, [24,32) ring minima, [32,40) ring
+// maxima (Sec. 4.1: e.RO, e.r, e.HR[s]).
+#define PM_LEAF_STRIDE 40
+#define PM_MAX_PIVOTS 8
+#define PM_MAX_K 256
+
+// Thread-local error reporting.
+void pm_set_error(const char *fmt, ...);
+
+struct PmStatus {
+    pmlsh_status code = PMLSH_OK;
+    bool ok() const { return code == PMLSH_OK; }
+};
+
+#define PM_CUDA(call)                                                          \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            pm_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                         __FILE__, __LINE__);                                  \
+            return e_ == cudaErrorMemoryAllocation ? PMLSH_ENOMEM : PMLSH_ECUDA; \
+        }                                                                      \
+    } while (0)
+
+#define PM_TRY(expr)                                                           \
+    do {                                                                       \
+        pmlsh_status s_ = (expr);                                              \
+        if (s_ != PMLSH_OK) return s_;                                         \
+    } while (0)
+
+// A grow-only device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    pmlsh_status reserve(size_t b);
+    void release();
+    template <class T> T *as() const { return (T *)p; }
+};
+
+// Per-call scratch buffers of the query path (kept in the index, grown on
+// demand, reused across calls).
+struct KnnWork {
+    DevBuf Qd, qp32, qp64, qnorm, qpiv, order, keys, keys2, vals2, sortTmp;
+    DevBuf qstate, thr, blkCnt, blkLeaves, cntSure, cntBand, bandQ, bandPos,
+        bandIn, bandCnt;
+    DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
+    DevBuf selBuf, selOff, selCnt, selTau;
+    DevBuf active, misc;
+};
+
+struct pmlsh_index {
+    int64_t n = 0;
+    int d = 0, ld = 0;      // ld: padded row length (multiple of 32)
+    int m = 0, s = 0, M = 0;
+    int64_t L = 0;          // leaves
+    uint64_t seed = 0;
+    // device arrays (leaf order)
+    float *X = nullptr;     // [n][ld]
+    int32_t *perm = nullptr;  // [n] position -> id
+    float *O32 = nullptr;   // [n][16]
+    double *O64 = nullptr;  // [n][16]
+    float *A32 = nullptr;   // [16][ld]
+    int64_t *leafOff = nullptr;  // [L+1]
+    float *leafMeta = nullptr;   // [L][PM_LEAF_STRIDE]
+    float *piv32 = nullptr;      // [PM_MAX_PIVOTS][16]
+    // host copies
+    std::vector<float> A_host;       // [m][d]
+    std::vector<int64_t> leafOffH;   // [L+1]
+    std::vector<int32_t> permH;      // [n]
+    std::vector<int64_t> nodeLo, nodeHi;
+    std::vector<int32_t> nodeLeft, nodeRight, nodeDim;
+    std::vector<float> nodeVal;
+    // device copy of the hierarchy used to route queries to a leaf:
+    // [e] = {left, right, split dim, leaf index}, split value
+    int32_t *treeI = nullptr;   // [N][4]
+    float *treeV = nullptr;     // [N]
+    std::vector<double> distSample;  // sorted sampled distances (r_min rule)
+    double maxNorm = 0.0;            // max ||o'|| (FP64 coordinates)
+    KnnWork work;
+};
+
+// Build helpers (build.cu)
+pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
+                            const pmlsh_build_opts *o, cudaStream_t st);
+void pm_free_index(pmlsh_index *ix);
+
+// FP64 + FP32 projection of rows (build.cu), original row order.
+void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const float *A,
+                         double *O64, float *O32, unsigned long long *maxNormBits,
+                         cudaStream_t st);
+
+// Query path (knn.cu)
+pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq,
+                    const pmlsh_knn_opts *o, int64_t *ids, float *dists,
+                    float *err, pmlsh_query_stats *stats, cudaStream_t st);
+
+// Parameters (params.cpp)
+double pm_chi2_sf(double x, int m);
+double pm_chi2_upper_quantile(double alpha, int m);
+
+// Counter-based SplitMix64 (rng.cpp)
+uint64_t pm_splitmix64(uint64_t seed, uint64_t i);
+void pm_gaussian_projection(uint64_t seed, int m, int d, float *A);
+
+bool pm_is_device_ptr(const void *p);
+
+// Launch bookkeeping (prof.cpp): counts every launch; brackets it with CUDA
+// events while profiling is enabled.
+int pm_prof_begin(const char *name, cudaStream_t st);
+void pm_prof_end(int token, cudaStream_t st);
+#define PM_LAUNCH(name, st, ...)                                               \
+    do {                                                                       \
+        int tok_ = pm_prof_begin(name, st);                                    \
+        __VA_ARGS__;                                                           \
+        pm_prof_end(tok_, st);                                                 \
+    } while (0)
+
+// ------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+// Squared projected distance in FP32 with a fixed operation order; every
+// kernel that classifies a point against a radius uses this one function, so
+// all of them see bit-identical values.
+__device__ __forceinline__ float pm_pd2_32(const float *a, const float *b)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < PM_MP; j++) {
+        float t = __fsub_rn(a[j], b[j]);
+        s = __fmaf_rn(t, t, s);
+    }
+    return s;
+}
+
+// FP64 distance of two FP64 coordinate vectors: sequential sum, separate
+// multiply and add, correctly rounded square root.
+__device__ __forceinline__ double pm_pdist64(const double *a, const double *b, int m)
+{
+    double s = 0.0;
+    for (int j = 0; j < m; j++) {
+        double t = __dsub_rn(a[j], b[j]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return __dsqrt_rn(s);
+}
+
+// FP64 Euclidean distance of two FP32 rows of length d, same arithmetic.
+__device__ __forceinline__ double pm_dist64(const float *x, const float *y, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; i++) {
+        double t = __dsub_rn((double)x[i], (double)y[i]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return __dsqrt_rn(s);
+}
+#endif
