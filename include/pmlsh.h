@@ -124,6 +124,16 @@ pmlsh_status pmlsh_export_layout(const pmlsh_index *index, int32_t *perm,
                                  int64_t *node_hi, int32_t *node_left,
                                  int32_t *node_right);
 
+/* Projects the rows of Q [nq][d] (FP32, host or device) onto the index's m
+ * directions (Eq. 3, the first step of Algorithm 2): out64 [nq][m] holds the
+ * FP64 coordinates (sequential sums over d, the same arithmetic as the
+ * build-time projection of the data set), out32 [nq][m] the same values
+ * rounded to FP32.  Outputs may be host or device memory; either may be
+ * NULL.  Uses (and may grow) the index's scratch buffers, so calls on one
+ * index must not overlap.  Errors: EINVAL, ENOMEM, ECUDA. */
+pmlsh_status pmlsh_project(pmlsh_index *index, const float *Q, int64_t nq,
+                           double *out64, float *out32, void *stream);
+
 /* ------------------------------------------------------- (c,k)-ANN query */
 
 enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_RERANK = 1 };

@@ -62,6 +62,7 @@ _SIGS = {
     "pmlsh_get_projection": (ctypes.c_int, [_P, _P]),
     "pmlsh_get_projected": (ctypes.c_int, [_P, _P]),
     "pmlsh_export_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_project": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_knn_opts_default": (None, [_P]),
     "pmlsh_knn": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "pmlsh_profile": (ctypes.c_int, [ctypes.c_int]),
@@ -211,6 +212,23 @@ class Index:
                                          ptr(nl), ptr(nr)))
         return dict(perm=perm, leaf_off=loff, node_lo=nlo, node_hi=nhi, node_left=nl,
                     node_right=nr)
+
+    def project(self, Q):
+        """Eq. 3 for query rows: returns (FP64 [nq, m], FP32 [nq, m]) on the
+        device of Q (numpy for host input)."""
+        torch = _torch()
+        qa, qp = _as_f32(Q)
+        nq = int(qa.shape[0])
+        if isinstance(qa, torch.Tensor) and qa.is_cuda:
+            o64 = torch.empty((nq, self.m), dtype=torch.float64, device=qa.device)
+            o32 = torch.empty((nq, self.m), dtype=torch.float32, device=qa.device)
+            p64, p32 = ctypes.c_void_p(o64.data_ptr()), ctypes.c_void_p(o32.data_ptr())
+        else:
+            o64 = np.empty((nq, self.m), dtype=np.float64)
+            o32 = np.empty((nq, self.m), dtype=np.float32)
+            p64, p32 = o64.ctypes.data_as(ctypes.c_void_p), o32.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().pmlsh_project(self._h, qp, nq, p64, p32, _stream()))
+        return o64, o32
 
     def knn(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
             precision=PMLSH_FP32_PLAIN, stop_rule=STOP_LITERAL, t=0.0, out=None,

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "pmlsh_impl.h"
@@ -207,6 +208,33 @@ pmlsh_status pmlsh_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_
     PM_CHECK(o.precision == PMLSH_FP32_PLAIN, "precision mode %d is not available in this build",
              o.precision);
     return pm_knn(ix, Q, nq, &o, out_ids, out_dists, out_err, stats, (cudaStream_t)stream);
+}
+
+pmlsh_status pmlsh_project(pmlsh_index *ix, const float *Q, int64_t nq, double *out64, float *out32,
+                           void *stream)
+{
+    PM_CHECK(ix != nullptr, "index is NULL");
+    PM_CHECK(nq >= 0, "nq must be >= 0");
+    if (nq == 0) return PMLSH_OK;
+    PM_CHECK(Q != nullptr && (out64 || out32), "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool d64 = !out64 || pm_is_device_ptr(out64), d32 = !out32 || pm_is_device_ptr(out32);
+    KnnWork &w = ix->work;
+    PM_TRY(w.Qd.reserve((size_t)nq * ix->ld * sizeof(float)));
+    double *o64 = out64;
+    float *o32 = out32;
+    size_t n64 = out64 ? (size_t)nq * ix->m : 0, n32 = out32 ? (size_t)nq * ix->m : 0;
+    if (!d64 || !d32) {
+        PM_TRY(w.qp64.reserve(std::max<size_t>(n64, 1) * sizeof(double)));
+        PM_TRY(w.qp32.reserve(std::max<size_t>(n32, 1) * sizeof(float)));
+        if (out64 && !d64) o64 = w.qp64.as<double>();
+        if (out32 && !d32) o32 = w.qp32.as<float>();
+    }
+    PM_TRY(pm_project_rows(ix, Q, nq, w.Qd.as<float>(), o64, o32, ix->m, st));
+    if (out64 && !d64) PM_CUDA(cudaMemcpyAsync(out64, o64, n64 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (out32 && !d32) PM_CUDA(cudaMemcpyAsync(out32, o32, n32 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (!d64 || !d32) PM_CUDA(cudaStreamSynchronize(st));
+    return PMLSH_OK;
 }
 
 }  // extern "C"

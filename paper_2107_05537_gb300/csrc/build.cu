@@ -20,7 +20,7 @@ constexpr int PROJ_PTS = 128;
 __global__ void __launch_bounds__(PROJ_PTS)
 k_project64(const float *__restrict__ X, int64_t n, int ld, int d, int m,
             const float *__restrict__ A, double *__restrict__ O64,
-            float *__restrict__ O32, unsigned long long *maxNormBits)
+            float *__restrict__ O32, int ostride, unsigned long long *maxNormBits)
 {
     __shared__ float As[PM_MP][33];
     __shared__ float Xs[PROJ_PTS][33];
@@ -56,8 +56,10 @@ k_project64(const float *__restrict__ X, int64_t n, int ld, int d, int m,
     double nn = 0.0;
 #pragma unroll
     for (int j = 0; j < PM_MP; j++) {
-        O64[p * PM_MP + j] = acc[j];
-        O32[p * PM_MP + j] = __double2float_rn(acc[j]);
+        if (j < ostride) {
+            if (O64) O64[p * ostride + j] = acc[j];
+            if (O32) O32[p * ostride + j] = __double2float_rn(acc[j]);
+        }
         nn = __fma_rn(acc[j], acc[j], nn);
     }
     if (maxNormBits) atomicMax(maxNormBits, (unsigned long long)__double_as_longlong(sqrt(nn)));
@@ -191,11 +193,11 @@ __global__ void k_sample_dist(const float *__restrict__ X, int ld, int d,
 
 void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const float *A,
                          double *O64, float *O32, unsigned long long *maxNormBits,
-                         cudaStream_t st)
+                         cudaStream_t st, int ostride)
 {
     if (n <= 0) return;
     int grid = (int)((n + PROJ_PTS - 1) / PROJ_PTS);
-    PM_LAUNCH("k_project64", st, k_project64<<<grid, PROJ_PTS, 0, st>>>(X, n, ld, d, m, A, O64, O32, maxNormBits));
+    PM_LAUNCH("k_project64", st, k_project64<<<grid, PROJ_PTS, 0, st>>>(X, n, ld, d, m, A, O64, O32, ostride, maxNormBits));
 }
 
 namespace {

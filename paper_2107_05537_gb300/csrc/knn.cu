@@ -824,6 +824,18 @@ template <class T> T *grow(DevBuf &b, size_t count, pmlsh_status &st)
 
 }  // namespace
 
+pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, float *staging,
+                             double *out64, float *out32, int ostride, cudaStream_t st)
+{
+    const int d = ix->d, ld = ix->ld;
+    PM_CUDA(cudaMemsetAsync(staging, 0, (size_t)nq * ld * sizeof(float), st));
+    PM_CUDA(cudaMemcpy2DAsync(staging, ld * sizeof(float), Q, d * sizeof(float), d * sizeof(float), nq,
+                              pm_is_device_ptr(Q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    pm_launch_project64(staging, nq, ld, d, ix->m, ix->A32, out64, out32, nullptr, st, ostride);
+    PM_CUDA(cudaGetLastError());
+    return PMLSH_OK;
+}
+
 pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn_opts *o,
                     int64_t *ids, float *dists, float *err, pmlsh_query_stats *stats,
                     cudaStream_t st)
@@ -855,7 +867,6 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         }
     }
     const int KP = (k + 32 + 31) / 32 * 32;
-    const bool qdev = pm_is_device_ptr(Q);
     pmlsh_status s = PMLSH_OK;
     float *Qd = grow<float>(w.Qd, (size_t)nq * ld, s);
     double *qp64 = grow<double>(w.qp64, (size_t)nq * PM_MP, s);
@@ -870,10 +881,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     float *oD = grow<float>(w.outD64, (size_t)nq * k, s);
     float *oE = grow<float>(w.outErr, (size_t)nq * k, s);
     if (s != PMLSH_OK) return s;
-    PM_CUDA(cudaMemsetAsync(Qd, 0, (size_t)nq * ld * sizeof(float), st));
-    PM_CUDA(cudaMemcpy2DAsync(Qd, ld * sizeof(float), Q, d * sizeof(float), d * sizeof(float), nq,
-                              qdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    pm_launch_project64(Qd, nq, ld, d, m, ix->A32, qp64, qp32, nullptr, st);
+    PM_TRY(pm_project_rows(ix, Q, nq, Qd, qp64, qp32, PM_MP, st));
     const unsigned gq = (unsigned)((nq + 255) / 256);
     PM_LAUNCH("k_query_aux", st, k_query_aux<<<gq, 256, 0, st>>>(qp64, qp32, nq, ix->piv32, ix->s, qnorm, qpiv));
     PM_LAUNCH("k_leaf_key", st, k_leaf_key<<<gq, 256, 0, st>>>(qp32, nq, ix->treeI, ix->treeV, key));

@@ -99,10 +99,17 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
                             const pmlsh_build_opts *o, cudaStream_t st);
 void pm_free_index(pmlsh_index *ix);
 
-// FP64 + FP32 projection of rows (build.cu), original row order.
+// FP64 + FP32 projection of rows X [n][ld] (build.cu), original row order;
+// outputs [n][ostride] (ostride = 16 for the padded internal layout, or m),
+// either output may be NULL.
 void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const float *A,
                          double *O64, float *O32, unsigned long long *maxNormBits,
-                         cudaStream_t st);
+                         cudaStream_t st, int ostride = PM_MP);
+
+// Query projection (api.cu helper in knn.cu): stages Q into `staging`
+// ([nq][ld], device) and projects it.
+pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, float *staging,
+                             double *out64, float *out32, int ostride, cudaStream_t st);
 
 // Query path (knn.cu)
 pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq,

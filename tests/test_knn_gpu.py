@@ -201,3 +201,16 @@ def test_c2_full_size_sampled_parity():
     # the last bit; the trace check still holds unless a point sits exactly
     # at the radius
     _assert_parity(sub, ref)
+
+
+def test_query_projection_entry_point(c1):
+    X, Q, A = c1
+    ix = pm.Index(X, proj=A)
+    ref = oracle.project(Q, A)
+    o64, o32 = ix.project(torch.from_numpy(Q).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(o64.cpu().numpy(), ref)
+    assert np.array_equal(o32.cpu().numpy(), ref.astype(np.float32))
+    h64, h32 = ix.project(Q[:7])
+    assert np.array_equal(h64, ref[:7])
+    ix.close()
