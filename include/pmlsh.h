@@ -134,6 +134,31 @@ pmlsh_status pmlsh_export_layout(const pmlsh_index *index, int32_t *perm,
 pmlsh_status pmlsh_project(pmlsh_index *index, const float *Q, int64_t nq,
                            double *out64, float *out32, void *stream);
 
+/* pmlsh_project without any device allocation, for callers that cannot let
+ * a library call cudaMalloc: a process whose device memory is owned by its
+ * own caching allocator (a library cudaMalloc could fail or fragment that
+ * reservation), or a latency-critical loop where cudaMalloc's implicit
+ * device-wide synchronisation would stall other streams.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *   The query rows are staged in a 16 MiB array of device memory that is
+ *   part of the library image (every GPU that loads the library holds it
+ *   until the process exits), so nq * (d rounded up to a multiple of 32)
+ *   must not exceed 4,194,304; larger batches are rejected with EINVAL.
+ *   Outputs (out64 [nq][m] FP64, out32 [nq][m] FP32, either may be NULL)
+ *   must be device memory; Q may be host or device memory.  Results are
+ *   identical to pmlsh_project's.
+ *   The first call on each device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents: calls
+ *   that overlap on the GPU (other streams, other threads) race and must be
+ *   serialised by the caller.
+ *   No cudaMalloc, cudaFree or allocating routine is called.
+ * Errors: EINVAL (NULL pointers, size beyond the limit, host outputs),
+ *   ECUDA. */
+pmlsh_status pmlsh_project_noalloc(const pmlsh_index *index, const float *Q,
+                                   int64_t nq, double *out64, float *out32,
+                                   void *stream);
+
 /* ------------------------------------------------------- (c,k)-ANN query */
 
 enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_RERANK = 1 };

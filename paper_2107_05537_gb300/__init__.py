@@ -63,6 +63,7 @@ _SIGS = {
     "pmlsh_get_projected": (ctypes.c_int, [_P, _P]),
     "pmlsh_export_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "pmlsh_project": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    "pmlsh_project_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_knn_opts_default": (None, [_P]),
     "pmlsh_knn": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "pmlsh_profile": (ctypes.c_int, [ctypes.c_int]),

@@ -200,6 +200,16 @@ void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const 
     PM_LAUNCH("k_project64", st, k_project64<<<grid, PROJ_PTS, 0, st>>>(X, n, ld, d, m, A, O64, O32, ostride, maxNormBits));
 }
 
+// The same launch without the profiler's bookkeeping (which may create CUDA
+// events); used by the no-allocation entry point.
+void pm_launch_project64_noprof(const float *X, int64_t n, int ld, int d, int m, const float *A,
+                                double *O64, float *O32, cudaStream_t st, int ostride)
+{
+    if (n <= 0) return;
+    int grid = (int)((n + PROJ_PTS - 1) / PROJ_PTS);
+    k_project64<<<grid, PROJ_PTS, 0, st>>>(X, n, ld, d, m, A, O64, O32, ostride, nullptr);
+}
+
 namespace {
 
 // ------------------------------------------------------------ host layout

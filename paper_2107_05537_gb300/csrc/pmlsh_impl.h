@@ -106,6 +106,9 @@ void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const 
                          double *O64, float *O32, unsigned long long *maxNormBits,
                          cudaStream_t st, int ostride = PM_MP);
 
+void pm_launch_project64_noprof(const float *X, int64_t n, int ld, int d, int m, const float *A,
+                                double *O64, float *O32, cudaStream_t st, int ostride);
+
 // Query projection (api.cu helper in knn.cu): stages Q into `staging`
 // ([nq][ld], device) and projects it.
 pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, float *staging,
