@@ -347,6 +347,8 @@ def main():
                 "quality": {"overall_ratio": ratio, "recall": rec, "sample_queries": int(len(sq))},
                 "trace": {"mean_rounds": float(stats["rounds"].mean()),
                           "mean_candidates": float(stats["ncand"].mean()),
+                          "mean_verified": float(stats["nver"].mean()),
+                          "mean_leaves_visited": float(stats["leaves"].mean()),
                           "rule_counts": np.bincount(stats["rule"], minlength=4).tolist()},
                 "build_s": build_s,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}

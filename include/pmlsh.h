@@ -192,7 +192,7 @@ typedef struct {
     int64_t n_cand;        /* |C| at return */
     double r_final;        /* r at return */
     int32_t fp64_checks;   /* decisions re-taken in FP64 */
-    int32_t reserved;
+    int32_t leaves_visited; /* leaves whose candidates were verified */
     int64_t n_verified;    /* exact distances computed, over all rounds */
 } pmlsh_query_stats;
 

@@ -46,7 +46,7 @@ class KnnOpts(ctypes.Structure):
 class QueryStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("n_cand", ctypes.c_int64), ("r_final", ctypes.c_double),
-                ("fp64_checks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("fp64_checks", ctypes.c_int32), ("leaves_visited", ctypes.c_int32),
                 ("n_verified", ctypes.c_int64)]
 
 
@@ -274,5 +274,6 @@ class Index:
                 ncand=np.array([s.n_cand for s in stats[:nq]], dtype=np.int64),
                 r=np.array([s.r_final for s in stats[:nq]], dtype=np.float64),
                 fp64=np.array([s.fp64_checks for s in stats[:nq]], dtype=np.int32),
-                nver=np.array([s.n_verified for s in stats[:nq]], dtype=np.int64))
+                nver=np.array([s.n_verified for s in stats[:nq]], dtype=np.int64),
+                leaves=np.array([s.leaves_visited for s in stats[:nq]], dtype=np.int32))
         return res

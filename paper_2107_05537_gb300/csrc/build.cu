@@ -2,6 +2,7 @@
 // the PM-tree of Sec. 4.1), leaf balls and pivot rings, distance sample for
 // the r_min rule of Sec. 5.2.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -179,6 +180,43 @@ __global__ void k_leaf_rings(const float *__restrict__ O32, const int64_t *__res
     }
 }
 
+// Original-space leaf centre mu (FP32 rounding of the FP64 mean) and a radius
+// Rx >= the exact distance of every member to mu (FP64, inflated, rounded up):
+// ||x - q|| >= ||q - mu|| - Rx bounds the distance of any member from below.
+// One block (256 threads) per leaf.
+__global__ void k_leaf_orig(const float *__restrict__ X, const int64_t *__restrict__ off, int ld,
+                            float *__restrict__ mu, float *__restrict__ rx)  // also used for chunks
+{
+    __shared__ double sred[8];
+    const int64_t l = blockIdx.x;
+    const int64_t a = off[l], b = off[l + 1];
+    const double inv = 1.0 / (double)(b - a);
+    float *M = mu + l * ld;
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = a; p < b; p++) s += (double)X[p * ld + j];
+        M[j] = (float)(s * inv);
+    }
+    __syncthreads();
+    double r = 0.0;
+    for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < ld; j++) {
+            double t = (double)X[p * ld + j] - (double)M[j];
+            s = fma(t, t, s);
+        }
+        r = fmax(r, sqrt(s));
+    }
+    r = warp_max(r);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = fmax(r, sred[w]);
+        r = fmax(r, sred[0]);
+        rx[l] = __double2float_ru(r * (1.0 + 1e-6) + 1e-30);
+    }
+}
+
 // FP64 distances of the sampled pairs (r_min rule), original point order.
 __global__ void k_sample_dist(const float *__restrict__ X, int ld, int d,
                               const int64_t *__restrict__ pi, const int64_t *__restrict__ pj,
@@ -216,54 +254,359 @@ namespace {
 
 struct Bisect {
     const float *O;   // [n][16] FP32 coordinates, original order
+    const float *Xh;  // [n][d] original-space points, original order (host)
+    int d;
     int m, M;
     std::vector<int32_t> perm;
     std::vector<int64_t> leafOff;
     std::vector<int64_t> nlo, nhi;
-    std::vector<int32_t> nl, nr, ndim;
-    std::vector<float> nval;
+    std::vector<int32_t> nl, nr;
+    std::vector<float> nw;   // [N][16] split hyperplane normal
+    std::vector<float> nt;   // [N] split threshold: right iff w . o' >= t
+    std::vector<double> key;
+    std::vector<int64_t> chunkOff{0};   // chunk c holds positions [chunkOff[c], chunkOff[c+1])
+    std::vector<int32_t> leafChunk{0};  // leaf l holds chunks [leafChunk[l], leafChunk[l+1])
 
-    // Splits positions [lo, hi) of perm; returns the node id.
-    int32_t split(int64_t lo, int64_t hi)
+    const float *pt(int32_t id) const { return O + (int64_t)id * PM_MP; }
+
+    static double d2(const double *a, const float *b)
+    {
+        double s = 0.0;
+        for (int j = 0; j < PM_MP; j++) {
+            double t = a[j] - (double)b[j];
+            s += t * t;
+        }
+        return s;
+    }
+
+    // Radius of the bounding-box-centred ball of perm[lo, hi).
+    double radius(int64_t lo, int64_t hi) const
+    {
+        double mn[PM_MP], mx[PM_MP], c[PM_MP];
+        for (int j = 0; j < PM_MP; j++) { mn[j] = INFINITY; mx[j] = -INFINITY; }
+        for (int64_t e = lo; e < hi; e++)
+            for (int j = 0; j < PM_MP; j++) {
+                double v = pt(perm[e])[j];
+                mn[j] = std::min(mn[j], v);
+                mx[j] = std::max(mx[j], v);
+            }
+        for (int j = 0; j < PM_MP; j++) c[j] = 0.5 * (mn[j] + mx[j]);
+        double r = 0.0;
+        for (int64_t e = lo; e < hi; e++) r = std::max(r, d2(c, pt(perm[e])));
+        return std::sqrt(r);
+    }
+
+    // 2-means of perm[lo, hi) started from a farthest pair; returns the
+    // hyperplane (w, t) separating the two means.
+    void two_means(int64_t lo, int64_t hi, double *w, double &t)
+    {
+        double c0[PM_MP], a[PM_MP], b[PM_MP];
+        for (int j = 0; j < PM_MP; j++) c0[j] = pt(perm[lo])[j];
+        int64_t ia = lo;
+        double best = -1.0;
+        for (int64_t e = lo; e < hi; e++) {
+            double v = d2(c0, pt(perm[e]));
+            if (v > best) { best = v; ia = e; }
+        }
+        for (int j = 0; j < PM_MP; j++) a[j] = pt(perm[ia])[j];
+        int64_t ib = lo;
+        best = -1.0;
+        for (int64_t e = lo; e < hi; e++) {
+            double v = d2(a, pt(perm[e]));
+            if (v > best) { best = v; ib = e; }
+        }
+        for (int j = 0; j < PM_MP; j++) b[j] = pt(perm[ib])[j];
+        for (int it = 0; it < 6; it++) {
+            double sa[PM_MP] = {0}, sb[PM_MP] = {0};
+            int64_t na = 0, nb = 0;
+            for (int64_t e = lo; e < hi; e++) {
+                const float *p = pt(perm[e]);
+                if (d2(b, p) < d2(a, p)) { nb++; for (int j = 0; j < PM_MP; j++) sb[j] += p[j]; }
+                else { na++; for (int j = 0; j < PM_MP; j++) sa[j] += p[j]; }
+            }
+            if (na == 0 || nb == 0) break;
+            bool moved = false;
+            for (int j = 0; j < PM_MP; j++) {
+                double na_ = sa[j] / na, nb_ = sb[j] / nb;
+                moved |= na_ != a[j] || nb_ != b[j];
+                a[j] = na_;
+                b[j] = nb_;
+            }
+            if (!moved) break;
+        }
+        // right side: closer to b  <=>  (b - a) . p >= (|b|^2 - |a|^2) / 2
+        double aa = 0.0, bb = 0.0;
+        for (int j = 0; j < PM_MP; j++) {
+            w[j] = b[j] - a[j];
+            aa += a[j] * a[j];
+            bb += b[j] * b[j];
+        }
+        t = 0.5 * (bb - aa);
+    }
+
+    int32_t new_node()
     {
         int32_t id = (int32_t)nlo.size();
         nlo.push_back((int64_t)leafOff.size() - 1);
         nhi.push_back(-1);
         nl.push_back(-1);
         nr.push_back(-1);
-        ndim.push_back(-1);
-        nval.push_back(0.f);
-        int64_t size = hi - lo;
-        if (size <= M) {
-            std::sort(perm.begin() + lo, perm.begin() + hi);
-            leafOff.push_back(hi);
-            nhi[id] = (int64_t)leafOff.size() - 1;
-            return id;
-        }
-        // split dimension: largest extent of the projected points
-        int best = 0;
-        float bestExt = -1.f;
-        for (int j = 0; j < m; j++) {
-            float mn = INFINITY, mx = -INFINITY;
-            for (int64_t e = lo; e < hi; e++) {
-                float v = O[(int64_t)perm[e] * PM_MP + j];
-                mn = std::min(mn, v);
-                mx = std::max(mx, v);
+        for (int j = 0; j < PM_MP; j++) nw.push_back(0.f);
+        nt.push_back(0.f);
+        return id;
+    }
+
+    // 2-means of perm[lo, hi) in the original space (two starts, at most 6
+    // Lloyd steps each); side[] = 1 for points nearer the second mean.
+    // Returns the number of points on side 0 and each side's sum of squared
+    // distances to its mean.
+    int64_t two_means_orig(int64_t lo, int64_t hi, std::vector<double> &ca, std::vector<double> &cb,
+                           std::vector<char> &sd, double *rad0, double *rad1)
+    {
+        auto dd = [this](const double *c, int32_t id) {
+            const float *x = Xh + (int64_t)id * d;
+            double s = 0.0;
+            for (int j = 0; j < d; j++) { double t = c[j] - (double)x[j]; s += t * t; }
+            return s;
+        };
+        auto row = [this](std::vector<double> &c, int32_t id) {
+            for (int j = 0; j < d; j++) c[j] = Xh[(int64_t)id * d + j];
+        };
+        const int64_t size = hi - lo;
+        // Lloyd steps from the given start; returns (side-0 count, SSEs)
+        auto lloyd = [&](std::vector<double> &a, std::vector<double> &b, std::vector<char> &side, double &s0,
+                         double &s1) {
+            int64_t n0 = 0;
+            side.assign(size, 0);
+            for (int it = 0; it < 6; it++) {
+                n0 = 0;
+                for (int64_t e = lo; e < hi; e++) {
+                    side[e - lo] = dd(b.data(), perm[e]) < dd(a.data(), perm[e]);
+                    n0 += !side[e - lo];
+                }
+                if (n0 == 0 || n0 == size) break;
+                std::vector<double> na(d, 0.0), nb(d, 0.0);
+                for (int64_t e = lo; e < hi; e++) {
+                    const float *x = Xh + (int64_t)perm[e] * d;
+                    double *t = side[e - lo] ? nb.data() : na.data();
+                    for (int j = 0; j < d; j++) t[j] += x[j];
+                }
+                bool moved = false;
+                for (int j = 0; j < d; j++) {
+                    double av = na[j] / (double)n0, bv = nb[j] / (double)(size - n0);
+                    moved |= av != a[j] || bv != b[j];
+                    a[j] = av;
+                    b[j] = bv;
+                }
+                if (!moved) break;
             }
-            if (mx - mn > bestExt) { bestExt = mx - mn; best = j; }
+            s0 = s1 = 0.0;
+            for (int64_t e = lo; e < hi; e++) {
+                if (side[e - lo]) s1 += dd(b.data(), perm[e]);
+                else s0 += dd(a.data(), perm[e]);
+            }
+            return n0;
+        };
+        // start 1: the mean and the point farthest from it (isolates a far
+        // group); start 2: that point and the point farthest from it (splits
+        // two large groups); the lower sum of squared deviations wins
+        std::vector<double> mu(d, 0.0), a2(d), b2(d);
+        for (int64_t e = lo; e < hi; e++)
+            for (int j = 0; j < d; j++) mu[j] += Xh[(int64_t)perm[e] * d + j];
+        for (int j = 0; j < d; j++) mu[j] /= (double)size;
+        int64_t ib = lo;
+        double best = -1.0;
+        for (int64_t e = lo; e < hi; e++) { double v = dd(mu.data(), perm[e]); if (v > best) { best = v; ib = e; } }
+        ca = mu;
+        cb.assign(d, 0.0);
+        row(cb, perm[ib]);
+        row(a2, perm[ib]);
+        int64_t ic = lo;
+        best = -1.0;
+        for (int64_t e = lo; e < hi; e++) { double v = dd(a2.data(), perm[e]); if (v > best) { best = v; ic = e; } }
+        row(b2, perm[ic]);
+        double s0, s1, t0, t1;
+        std::vector<char> side2;
+        int64_t n0 = lloyd(ca, cb, sd, s0, s1);
+        int64_t m0 = lloyd(a2, b2, side2, t0, t1);
+        if (m0 > 0 && m0 < size && (t0 + t1 < s0 + s1 || n0 == 0 || n0 == size)) {
+            sd.swap(side2);
+            ca.swap(a2);
+            cb.swap(b2);
+            n0 = m0;
+            s0 = t0;
+            s1 = t1;
         }
-        // balanced: the left part holds ceil(leaves/2) full leaves
-        int64_t leaves = (size + M - 1) / M;
-        int64_t left = ((leaves + 1) / 2) * M;
-        const float *O_ = O;
-        const int dim = best;
-        std::nth_element(perm.begin() + lo, perm.begin() + lo + left, perm.begin() + hi,
-                         [O_, dim](int32_t a, int32_t b) {
-                             float va = O_[(int64_t)a * PM_MP + dim], vb = O_[(int64_t)b * PM_MP + dim];
-                             return va < vb || (va == vb && a < b);
-                         });
-        ndim[id] = dim;
-        nval[id] = O_[(int64_t)perm[lo + left] * PM_MP + dim];
+        *rad0 = s0;
+        *rad1 = s1;
+        return n0;
+    }
+
+    // Sum of squared distances of perm[lo, hi) to its mean.
+    double sse_orig(int64_t lo, int64_t hi) const
+    {
+        std::vector<double> c(d, 0.0);
+        for (int64_t e = lo; e < hi; e++)
+            for (int j = 0; j < d; j++) c[j] += Xh[(int64_t)perm[e] * d + j];
+        for (int j = 0; j < d; j++) c[j] /= (double)(hi - lo);
+        double r = 0.0;
+        for (int64_t e = lo; e < hi; e++) {
+            const float *x = Xh + (int64_t)perm[e] * d;
+            double s = 0.0;
+            for (int j = 0; j < d; j++) { double t = c[j] - (double)x[j]; s += t * t; }
+            r += s;
+        }
+        return r;
+    }
+
+    // Stable move of side-0 points of perm[lo, hi) to the front.
+    void apply_sides(int64_t lo, int64_t hi, const std::vector<char> &sd)
+    {
+        std::vector<int32_t> a, b2;
+        for (int64_t e = lo; e < hi; e++) (sd[e - lo] ? b2 : a).push_back(perm[e]);
+        std::copy(a.begin(), a.end(), perm.begin() + lo);
+        std::copy(b2.begin(), b2.end(), perm.begin() + lo + (int64_t)a.size());
+    }
+
+    // Splits a leaf's points perm[lo, hi) into chunks of at most 32 points by
+    // original-space 2-means (the unit that verification stages and bounds);
+    // points inside a chunk are kept in id order.
+    void chunks(int64_t lo, int64_t hi, std::vector<double> &ca, std::vector<double> &cb, std::vector<char> &sd)
+    {
+        const int64_t size = hi - lo;
+        if (size <= 32) {
+            std::sort(perm.begin() + lo, perm.begin() + hi);
+            chunkOff.push_back(hi);
+            return;
+        }
+        double r0, r1;
+        int64_t left = two_means_orig(lo, hi, ca, cb, sd, &r0, &r1);
+        const int64_t minside = std::max<int64_t>(1, size / 16);
+        if (left < minside || left > size - minside) {
+            left = size / 2;   // degenerate: split by position
+        } else {
+            apply_sides(lo, hi, sd);
+        }
+        chunks(lo, lo + left, ca, cb, sd);
+        chunks(lo + left, hi, ca, cb, sd);
+    }
+
+    // A projected-space leaf is refined in the original space (a leaf that
+    // straddles separate groups of points would give the verification's
+    // distance bounds nothing to prune): outliers are split off, then groups
+    // that 2-means separates well (one Gaussian blob split in two keeps almost
+    // all of its squared deviation); each part is refined again.
+    // Makes node `id` an inner node over perm[lo, lo+left) and perm[lo+left, hi),
+    // each refined again.  Routing hyperplane w = 0, t = 0: queries go right
+    // (the split is in the original space, which routing does not see).
+    int32_t refine_split(int32_t id, int64_t lo, int64_t left, int64_t hi)
+    {
+        int32_t Lc = new_node();
+        leaf(Lc, lo, lo + left);
+        int32_t Rc = new_node();
+        leaf(Rc, lo + left, hi);
+        nl[id] = Lc;
+        nr[id] = Rc;
+        nhi[id] = (int64_t)leafOff.size() - 1;
+        return id;
+    }
+
+    int32_t leaf(int32_t id, int64_t lo, int64_t hi)
+    {
+        std::vector<double> ca, cb;
+        std::vector<char> sd;
+        const int64_t size = hi - lo;
+        if (size >= 2) {
+            // (1) outliers: points farther from the mean than twice the median
+            //     distance are split off (a few stray points of other groups
+            //     would otherwise set the whole leaf's radius; in a Gaussian
+            //     blob of dimension >= 16 the largest distance stays well
+            //     below twice the median)
+            std::vector<double> mu(d, 0.0), dist(size);
+            for (int64_t e = lo; e < hi; e++)
+                for (int j = 0; j < d; j++) mu[j] += Xh[(int64_t)perm[e] * d + j];
+            for (int j = 0; j < d; j++) mu[j] /= (double)size;
+            for (int64_t e = lo; e < hi; e++) {
+                const float *x = Xh + (int64_t)perm[e] * d;
+                double s = 0.0;
+                for (int j = 0; j < d; j++) { double t = mu[j] - (double)x[j]; s += t * t; }
+                dist[e - lo] = std::sqrt(s);
+            }
+            std::vector<double> tmp(dist);
+            const int64_t kmed = size / 2;
+            std::nth_element(tmp.begin(), tmp.begin() + kmed, tmp.end());
+            const double cut = 2.0 * tmp[kmed];
+            int64_t nout = 0;
+            for (int64_t e = 0; e < size; e++) nout += dist[e] > cut;
+            if (nout > 0 && nout < size) {
+                sd.assign(size, 0);
+                for (int64_t e = 0; e < size; e++) sd[e] = dist[e] > cut;
+                apply_sides(lo, hi, sd);
+                return refine_split(id, lo, size - nout, hi);
+            }
+            // (2) separate groups: an original-space 2-means split that lowers
+            //     the sum of squared deviations below 0.85 of the whole's (a
+            //     Gaussian blob of dimension d keeps about 1 - 2/(pi d) of it;
+            //     k separate equal groups keep about (k-2)/(k-1))
+            double s0, s1;
+            int64_t left = two_means_orig(lo, hi, ca, cb, sd, &s0, &s1);
+            if (left >= 1 && left <= size - 1 && s0 + s1 < 0.85 * sse_orig(lo, hi)) {
+                apply_sides(lo, hi, sd);
+                return refine_split(id, lo, left, hi);
+            }
+        }
+        chunks(lo, hi, ca, cb, sd);
+        leafChunk.push_back((int32_t)chunkOff.size() - 1);
+        leafOff.push_back(hi);
+        nhi[id] = (int64_t)leafOff.size() - 1;
+        return id;
+    }
+
+    // Splits perm[lo, hi) by 2-means in the projected space (Sec. 4.1 builds
+    // the PM-tree so that node balls are tight; the m_RAD promotion of
+    // Sec. 6.3 minimises covering radii).  Segments above M points are always
+    // split; smaller ones only when both halves' balls shrink below 0.85 of
+    // the parent's (a segment holding separate groups of points), so that a
+    // leaf does not straddle groups.  A degenerate 2-means split of a large
+    // segment falls back to the median along the same direction.
+    int32_t split(int64_t lo, int64_t hi)
+    {
+        const int32_t id = new_node();
+        const int64_t size = hi - lo;
+        if (size <= 8) return leaf(id, lo, hi);
+        double w[PM_MP], t;
+        two_means(lo, hi, w, t);
+        for (int64_t e = lo; e < hi; e++) {
+            const float *p = pt(perm[e]);
+            double s = 0.0;
+            for (int j = 0; j < PM_MP; j++) s += w[j] * (double)p[j];
+            key[perm[e]] = s;
+        }
+        const double *K = key.data();
+        auto less = [K](int32_t a, int32_t b) { return K[a] < K[b] || (K[a] == K[b] && a < b); };
+        int64_t nright = 0;
+        for (int64_t e = lo; e < hi; e++) nright += K[perm[e]] >= t;
+        int64_t left = size - nright;
+        if (size > M) {
+            if (left < size / 16 || left > size - size / 16) {
+                left = size / 2;
+                std::nth_element(perm.begin() + lo, perm.begin() + lo + left, perm.begin() + hi, less);
+                t = K[perm[lo + left]];
+            } else {
+                std::partition(perm.begin() + lo, perm.begin() + hi, [K, t](int32_t a) { return K[a] < t; });
+            }
+        } else {
+            if (left == 0 || left == size) return leaf(id, lo, hi);
+            std::vector<int32_t> saved(perm.begin() + lo, perm.begin() + hi);
+            std::partition(perm.begin() + lo, perm.begin() + hi, [K, t](int32_t a) { return K[a] < t; });
+            double rp = radius(lo, hi), rl = radius(lo, lo + left), rr = radius(lo + left, hi);
+            if (!(std::max(rl, rr) < 0.85 * rp)) {
+                std::copy(saved.begin(), saved.end(), perm.begin() + lo);
+                return leaf(id, lo, hi);
+            }
+        }
+        for (int j = 0; j < PM_MP; j++) nw[(size_t)id * PM_MP + j] = (float)w[j];
+        nt[id] = (float)t;
         int32_t L = split(lo, lo + left);
         int32_t R = split(lo + left, hi);
         nl[id] = L;
@@ -293,6 +636,12 @@ void pm_free_index(pmlsh_index *ix)
     cudaFree(ix->piv32);
     cudaFree(ix->treeI);
     cudaFree(ix->treeV);
+    cudaFree(ix->leafMu);
+    cudaFree(ix->leafRx);
+    cudaFree(ix->chunkOff);
+    cudaFree(ix->leafChunk);
+    cudaFree(ix->chunkMu);
+    cudaFree(ix->chunkRx);
     KnnWork &w = ix->work;
     DevBuf *bufs[] = {&w.Qd, &w.qp32, &w.qp64, &w.qnorm, &w.qpiv, &w.order, &w.keys,
                       &w.keys2, &w.vals2, &w.sortTmp, &w.qstate, &w.thr, &w.blkCnt,
@@ -409,35 +758,49 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
         std::memcpy(&mn, &mxh, sizeof(mn));
         ix->maxNorm = mn;
     }
+    std::vector<float> Xhost;
+    const float *Xh = X;
+    if (x_on_device) {
+        Xhost.resize((size_t)n * d);
+        PM_CUDA(cudaMemcpy(Xhost.data(), X, Xhost.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        Xh = Xhost.data();
+    }
     Bisect bs;
     bs.O = O32h.data();
+    bs.Xh = Xh;
+    bs.d = d;
     bs.m = m;
     bs.M = ix->M;
     bs.perm.resize(n);
+    bs.key.resize(n);
     std::iota(bs.perm.begin(), bs.perm.end(), 0);
     bs.leafOff.push_back(0);
     bs.split(0, n);
     ix->permH = std::move(bs.perm);
+    ix->chunkOffH = std::move(bs.chunkOff);
+    ix->leafChunkH = std::move(bs.leafChunk);
     ix->leafOffH = std::move(bs.leafOff);
     ix->nodeLo = std::move(bs.nlo);
     ix->nodeHi = std::move(bs.nhi);
     ix->nodeLeft = std::move(bs.nl);
     ix->nodeRight = std::move(bs.nr);
-    ix->nodeDim = std::move(bs.ndim);
-    ix->nodeVal = std::move(bs.nval);
     {
         size_t N = ix->nodeLo.size();
         std::vector<int32_t> ti(N * 4);
+        std::vector<float> tv(N * (PM_MP + 1));
         for (size_t e = 0; e < N; e++) {
             ti[e * 4 + 0] = ix->nodeLeft[e];
             ti[e * 4 + 1] = ix->nodeRight[e];
-            ti[e * 4 + 2] = ix->nodeDim[e];
+            ti[e * 4 + 2] = 0;
             ti[e * 4 + 3] = (int32_t)ix->nodeLo[e];
+            for (int j = 0; j < PM_MP; j++) tv[e * (PM_MP + 1) + j] = bs.nw[e * PM_MP + j];
+            tv[e * (PM_MP + 1) + PM_MP] = bs.nt[e];
         }
         PM_TRY(dalloc(&ix->treeI, ti.size()));
-        PM_TRY(dalloc(&ix->treeV, N));
+        PM_TRY(dalloc(&ix->treeV, tv.size()));
         PM_CUDA(cudaMemcpyAsync(ix->treeI, ti.data(), ti.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        PM_CUDA(cudaMemcpyAsync(ix->treeV, ix->nodeVal.data(), N * sizeof(float), cudaMemcpyHostToDevice, st));
+        PM_CUDA(cudaMemcpyAsync(ix->treeV, tv.data(), tv.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        PM_CUDA(cudaStreamSynchronize(st));
     }
     ix->L = (int64_t)ix->leafOffH.size() - 1;
     const int64_t L = ix->L;
@@ -490,6 +853,22 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
         PM_LAUNCH("k_leaf_rings", st, k_leaf_rings<<<(unsigned)L, 256, 0, st>>>(ix->O32, ix->leafOff, ix->piv32, ix->s, ix->leafMeta));
         PM_CUDA(cudaGetLastError());
     }
+    // 8. original-space leaf centres and radii (lower bounds for verification)
+    PM_TRY(dalloc(&ix->leafMu, (size_t)L * ld));
+    PM_TRY(dalloc(&ix->leafRx, (size_t)L));
+    PM_LAUNCH("k_leaf_orig", st, k_leaf_orig<<<(unsigned)L, 256, 0, st>>>(ix->X, ix->leafOff, ld, ix->leafMu, ix->leafRx));
+    PM_CUDA(cudaGetLastError());
+    // chunks of <= 32 points inside the leaves, with their own balls
+    const int64_t C = (int64_t)ix->chunkOffH.size() - 1;
+    ix->nChunks = C;
+    PM_TRY(dalloc(&ix->chunkOff, C + 1));
+    PM_TRY(dalloc(&ix->leafChunk, L + 1));
+    PM_CUDA(cudaMemcpyAsync(ix->chunkOff, ix->chunkOffH.data(), (C + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemcpyAsync(ix->leafChunk, ix->leafChunkH.data(), (L + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PM_TRY(dalloc(&ix->chunkMu, (size_t)C * ld));
+    PM_TRY(dalloc(&ix->chunkRx, (size_t)C));
+    PM_LAUNCH("k_leaf_orig", st, k_leaf_orig<<<(unsigned)C, 128, 0, st>>>(ix->X, ix->chunkOff, ld, ix->chunkMu, ix->chunkRx));
+    PM_CUDA(cudaGetLastError());
     PM_CUDA(cudaStreamSynchronize(st));
     return PMLSH_OK;
 }

@@ -11,11 +11,10 @@
 //   [host]         |S_i| per query -> which queries reach the budget B
 //   k_collect,     for budget queries: the B nearest in projected space
 //   k_select       (radix select, FP64 resolution of the band at the cut)
-//   k_verify       exact FP32 distance of every candidate, leaf-major tiles
-//                  of (64 queries x 64 points), per-query top-KP in shared
-//                  memory
-//   k_merge        merge of the partial top-KP lists, FP64 distances for the
-//                  guard set, exact top-k, k-th distance for stop rule 1
+//   k_bestfirst    exact FP32 distances of the candidates that can reach the
+//                  top-k (leaves visited in order of an original-space lower
+//                  bound, rows staged by TMA), guard set, FP64 distances,
+//                  exact top-k and the k-th distance for stop rule 1
 //   [host]         stop rules, r <- c r for the rest
 #include <algorithm>
 #include <cmath>
@@ -26,7 +25,6 @@
 namespace {
 
 constexpr int QB = 64;          // queries per block
-constexpr int TN = 64;          // points per verify tile
 constexpr int BCAP = 256;       // band-in entries per query
 constexpr int SELBAND = 2048;   // band at the budget cut, per query
 constexpr int GCAP = 1024;      // guard set per query
@@ -75,11 +73,13 @@ __global__ void k_leaf_key(const float *__restrict__ qp32, int64_t nq, const int
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nq) return;
     int e = 0;
-    for (int guard = 0; guard < 64; guard++) {
+    for (int guard = 0; guard < 4096; guard++) {
         int l = T[e * 4 + 0];
         if (l < 0) break;
-        int dim = T[e * 4 + 2];
-        e = qp32[q * PM_MP + dim] < V[e] ? l : T[e * 4 + 1];
+        const float *w = V + (int64_t)e * (PM_MP + 1);
+        float s = 0.f;
+        for (int j = 0; j < PM_MP; j++) s = fmaf(w[j], qp32[q * PM_MP + j], s);
+        e = s < w[PM_MP] ? l : T[e * 4 + 1];
     }
     key[q] = (unsigned int)T[e * 4 + 3];
 }
@@ -444,328 +444,428 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
     }
 }
 
-// ------------------------------------------------------------ verification
+// ------------------------------------------------- best-first verification
 
-struct VerifySmem {
-    // dynamic layout, see k_verify
-};
-
-// Exact FP32 distances of candidate pairs, (64 queries x 64 points) tiles over
-// each leaf of the block's list (split s of S), with a per-query top-KP in
-// shared memory.  Candidates: FP32 d'^2 <= lov (leaf tests with Rin = Rout =
-// sqrt(lov)).  d^2 = sum_i (x_i - q_i)^2 accumulated sequentially in i.
-__global__ void __launch_bounds__(256)
-k_verify(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
-         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
-         const float *__restrict__ meta, const int64_t *__restrict__ off,
-         const float *__restrict__ O32, const float *__restrict__ X, const float *__restrict__ Qd, int ld,
-         const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, int64_t L, int KP,
-         float *__restrict__ partD, int *__restrict__ partI, int *__restrict__ partSeen,
-         float *__restrict__ partMax)
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    extern __shared__ __align__(16) float smem[];
-    float(*Qs)[QB + 4] = (float(*)[QB + 4])smem;                 // [32][68]
-    float(*Xs)[TN + 4] = (float(*)[TN + 4])(smem + 32 * (QB + 4));  // [32][68]
-    float(*Dt)[TN + 1] = (float(*)[TN + 1])(smem + 32 * (QB + 4) + 32 * (TN + 4));  // [64][65]
-    float(*sq)[PM_MP] = (float(*)[PM_MP])((float *)Dt + QB * (TN + 1));            // [64][16]
-    float(*op)[PM_MP] = (float(*)[PM_MP])((float *)sq + QB * PM_MP);                // [64][16]
-    float(*sp)[PM_MAX_PIVOTS] = (float(*)[PM_MAX_PIVOTS])((float *)op + TN * PM_MP);  // [64][8]
-    float *sLo = (float *)sp + QB * PM_MAX_PIVOTS;
-    float *sRv = sLo + QB;
-    float *cmax = sRv + QB;
-    int *cslot = (int *)(cmax + QB);
-    int *seen = cslot + QB;
-    int *qid = seen + QB;
-    unsigned char *cls = (unsigned char *)(qid + QB);
-    float *vals = (float *)(cls + QB);           // [QB][KP]
-    int *idxs = (int *)(vals + QB * KP);         // [QB][KP]
-
-    const int b = blockIdx.x, S = gridDim.y, sidx = blockIdx.y;
-    const int a0 = b * QB;
-    const int nb = min(QB, na - a0);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = tid & 15, ty = tid >> 4;
-    for (int e = tid; e < QB * PM_MP; e += blockDim.x) {
-        int qq = e / PM_MP, j = e % PM_MP;
-        sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
-    }
-    for (int e = tid; e < QB * PM_MAX_PIVOTS; e += blockDim.x) {
-        int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
-        sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
-    }
-    for (int qq = tid; qq < QB; qq += blockDim.x) {
-        float lov = qq < nb ? thr[a0 + qq].lov : -1.f;
-        sLo[qq] = lov;
-        sRv[qq] = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
-        cmax[qq] = INFINITY;
-        cslot[qq] = 0;
-        seen[qq] = 0;
-        qid[qq] = qq < nb ? act[a0 + qq] : -1;
-    }
-    for (int e = tid; e < QB * KP; e += blockDim.x) {
-        vals[e] = INFINITY;
-        idxs[e] = -1;
-    }
-    __syncthreads();
-    const int nl = blkCnt[b];
-    for (int li = sidx; li < nl; li += S) {
-        const int l = blkLeaves[(int64_t)b * L + li];
-        if (tid < QB) {
-            unsigned char c = CL_OUT;
-            if (tid < nb && sRv[tid] > 0.f)
-                c = leaf_class(sq[tid], sp[tid], s, sRv[tid], sRv[tid], meta + (int64_t)l * PM_LEAF_STRIDE);
-            cls[tid] = c;
-        }
-        __syncthreads();
-        int anyq = 0;
-        for (int qq = 0; qq < QB; qq++) anyq |= cls[qq];
-        if (!anyq) { __syncthreads(); continue; }
-        const int64_t p0 = off[l], p1 = off[l + 1];
-        for (int64_t c0 = p0; c0 < p1; c0 += TN) {
-            const int cntc = (int)min((int64_t)TN, p1 - c0);
-            for (int e = tid; e < TN * PM_MP; e += blockDim.x) {
-                int pp = e / PM_MP, j = e % PM_MP;
-                op[pp][j] = pp < cntc ? O32[(c0 + pp) * PM_MP + j] : 0.f;
-            }
-            __syncthreads();
-            unsigned int mask = 0;
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int qq = 4 * ty + r;
-                const unsigned char c = cls[qq];
-#pragma unroll
-                for (int cc = 0; cc < 4; cc++) {
-                    const int pp = 4 * tx + cc;
-                    bool cand = false;
-                    if (pp < cntc) {
-                        if (c == CL_FULL) cand = true;
-                        else if (c == CL_PART) cand = pm_pd2_32(op[pp], sq[qq]) <= sLo[qq];
-                    }
-                    mask |= (unsigned)cand << (r * 4 + cc);
-                }
-            }
-            if (!__syncthreads_or(mask != 0)) continue;
-            float acc[4][4];
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int cc = 0; cc < 4; cc++) acc[r][cc] = 0.f;
-            for (int k0 = 0; k0 < ld; k0 += 32) {
-                // stage the query rows and the point rows (k-major)
-                for (int e = tid; e < QB * 32; e += blockDim.x) {
-                    int qq = e >> 5, kk = e & 31;
-                    int qg = qid[qq];
-                    Qs[kk][qq] = qg >= 0 ? Qd[(int64_t)qg * ld + k0 + kk] : 0.f;
-                }
-                for (int e = tid; e < TN * 32; e += blockDim.x) {
-                    int pp = e >> 5, kk = e & 31;
-                    Xs[kk][pp] = pp < cntc ? X[(c0 + pp) * ld + k0 + kk] : 0.f;
-                }
-                __syncthreads();
-#pragma unroll 8
-                for (int kk = 0; kk < 32; kk++) {
-                    float4 qa = *(const float4 *)&Qs[kk][4 * ty];
-                    float4 xb = *(const float4 *)&Xs[kk][4 * tx];
-                    float qv[4] = {qa.x, qa.y, qa.z, qa.w};
-                    float xv[4] = {xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-                    for (int r = 0; r < 4; r++)
-#pragma unroll
-                        for (int cc = 0; cc < 4; cc++) {
-                            float t = __fsub_rn(qv[r], xv[cc]);
-                            acc[r][cc] = __fmaf_rn(t, t, acc[r][cc]);
-                        }
-                }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int cc = 0; cc < 4; cc++)
-                    Dt[4 * ty + r][4 * tx + cc] = (mask >> (r * 4 + cc)) & 1u ? acc[r][cc] : INFINITY;
-            __syncthreads();
-            // top-KP update, warp w owns query rows 8w .. 8w+7
-            for (int rr = 0; rr < QB / 8; rr++) {
-                const int qq = warp * (QB / 8) + rr;
-                if (qq >= nb) break;
-                float v[2] = {Dt[qq][lane], Dt[qq][lane + 32]};
-                int addSeen = __popc(__ballot_sync(0xffffffffu, v[0] < INFINITY)) +
-                              __popc(__ballot_sync(0xffffffffu, v[1] < INFINITY));
-                if (lane == 0) seen[qq] += addSeen;
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    unsigned bits = __ballot_sync(0xffffffffu, v[h] < cmax[qq]);
-                    while (bits) {
-                        const int src = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const float val = __shfl_sync(0xffffffffu, v[h], src);
-                        if (val < cmax[qq]) {
-                            if (lane == 0) {
-                                vals[qq * KP + cslot[qq]] = val;
-                                idxs[qq * KP + cslot[qq]] = (int)(c0 + src + 32 * h);
-                            }
-                            __syncwarp();
-                            float best = -1.f;
-                            int bs = 0;
-                            for (int e = lane; e < KP; e += 32) {
-                                float x = vals[qq * KP + e];
-                                if (x > best) { best = x; bs = e; }
-                            }
-                            for (int o = 16; o; o >>= 1) {
-                                float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                                int os = __shfl_xor_sync(0xffffffffu, bs, o);
-                                if (ob > best || (ob == best && os < bs)) { best = ob; bs = os; }
-                            }
-                            if (lane == 0) { cmax[qq] = best; cslot[qq] = bs; }
-                            __syncwarp();
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    __syncthreads();
-    for (int qq = warp; qq < nb; qq += 8) {
-        const int64_t base = ((int64_t)(a0 + qq) * S + sidx) * KP;
-        for (int e = lane; e < KP; e += 32) {
-            partD[base + e] = vals[qq * KP + e];
-            partI[base + e] = idxs[qq * KP + e];
-        }
-        if (lane == 0) {
-            partSeen[(int64_t)(a0 + qq) * S + sidx] = seen[qq];
-            partMax[(int64_t)(a0 + qq) * S + sidx] = seen[qq] > KP ? cmax[qq] : INFINITY;
-        }
-    }
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// TMA (bulk-copy engine): global -> shared, completion counted in bytes on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Waits for phase `ph` of `bar` with an iteration limit; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t ph)
+{
+    for (int it = 0; it < (1 << 22); it++)
+        if (mbar_try_wait(bar, ph)) return true;
+    return false;
 }
 
-// ----------------------------------------------------------------- merge
+constexpr int BF_THREADS = 256;
+constexpr int BF_ROWS = 32;     // points per staged chunk
+constexpr int BF_DCH = 256;     // dimensions per staged chunk
+constexpr int BF_LCAP = 8192;   // leaves sorted per query in shared memory
+constexpr int BF_MAXCH = 512;   // chunks per leaf (leaf size <= 1024, chunks >= 2 points)
 
-// One block (256 threads) per active query: merges the S partial lists and
-// the band-in points, takes the guard set {d^2_32 <= K32 (1 + 3 eps_v)} (K32
-// the k-th smallest FP32 d^2, eps_v = (ld + 4) 2^-24 the FP32 sum bound),
-// computes FP64 distances for it, sorts by (FP64 distance, id) and writes the
-// top-k and the FP64 k-th distance.
-__global__ void __launch_bounds__(256)
-k_merge(const int32_t *__restrict__ act, int S, int KP, int k, const float *__restrict__ partD,
-        const int *__restrict__ partI, const float *__restrict__ partMax,
-        const int *__restrict__ inN, const int *__restrict__ inPos,
-        const float *__restrict__ X, const float *__restrict__ Qd, int ld, int d,
-        const int32_t *__restrict__ perm, int64_t *__restrict__ outIds, float *__restrict__ outD,
-        float *__restrict__ outErr, double *__restrict__ dk, int *__restrict__ fp64cnt,
-        int *__restrict__ errFlag, int P)
+// Inserts `val` (position `pos`) into the per-query top-KP held in shared
+// memory if it beats the current maximum; called by one full warp.
+__device__ __forceinline__ void topk_insert_warp(float *vals, int *idxs, int KP, float &cmax, int &cslot,
+                                                 float val, int pos, int lane)
 {
-    extern __shared__ __align__(16) unsigned char msm[];
-    float *mv = (float *)msm;                       // [P]
-    int *mp = (int *)(mv + P);                      // [P]
-    double *gd = (double *)(mp + P);                // [GCAP]
-    long long *gid = (long long *)(gd + GCAP);      // [GCAP]
-    __shared__ int sG;
-    __shared__ float sThr;
+    if (!(val < cmax)) return;
+    if (lane == 0) {
+        vals[cslot] = val;
+        idxs[cslot] = pos;
+    }
+    __syncwarp();
+    float best = -1.f;
+    int bs = 0;
+    for (int e = lane; e < KP; e += 32) {
+        float x = vals[e];
+        if (x > best) { best = x; bs = e; }
+    }
+    for (int o = 16; o; o >>= 1) {
+        float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int os = __shfl_xor_sync(0xffffffffu, bs, o);
+        if (ob > best || (ob == best && os < bs)) { best = ob; bs = os; }
+    }
+    cmax = best;
+    cslot = bs;
+    __syncwarp();
+}
+
+// One CTA per active query.  Candidates are the points with FP32 d'^2 <= lov
+// (plus the FP64-resolved band-in points).  Only the top-k of the candidates
+// matters (stop rule 1 tests the k-th smallest distance), so leaves are
+// visited in increasing order of the distance to their original-space centre
+// mu_l, and a leaf (or a chunk of <= 32 of its points) is skipped when its
+// lower bound ||q - mu|| - Rx excludes every member from the guard set
+// {d^2_32 <= K (1 + 3 eps_v)} (K the current KP-th smallest, an upper bound
+// of the k-th).  Rows of a visited leaf are staged
+// by TMA bulk copies, 32 rows x 256 dimensions per stage, double-buffered.
+// The result equals verifying every candidate.
+__global__ void __launch_bounds__(BF_THREADS)
+k_bestfirst(const int32_t *__restrict__ act, const Thr *__restrict__ thr, const float *__restrict__ qp32,
+            const float *__restrict__ qpiv, int s, const float *__restrict__ meta,
+            const int64_t *__restrict__ off, int64_t L, const float *__restrict__ O32,
+            const float *__restrict__ X, const float *__restrict__ Qd, int ld, int d,
+            const float *__restrict__ leafMu, const float *__restrict__ leafRx,
+            const int64_t *__restrict__ chunkOff, const int32_t *__restrict__ leafChunk,
+            const float *__restrict__ chunkMu, const float *__restrict__ chunkRx, int KP, int k,
+            const int *__restrict__ inN, const int *__restrict__ inPos, const int32_t *__restrict__ perm,
+            int64_t *__restrict__ outIds, float *__restrict__ outD, float *__restrict__ outErr,
+            double *__restrict__ dk, int *__restrict__ fp64cnt, int *__restrict__ nverOut,
+            int *__restrict__ nleafOut, int *__restrict__ errFlag)
+{
+    extern __shared__ __align__(128) unsigned char bsm[];
+    const int dch = ld < BF_DCH ? ld : BF_DCH;
+    const int rs = dch + 8;                                  // staged row stride (floats)
+    float *xs = (float *)bsm;                                // [2][32][rs]
+    float *qs = xs + 2 * BF_ROWS * rs;                       // [ld]
+    float *lbv = qs + ld;                                    // [BF_LCAP]
+    int *lid = (int *)(lbv + BF_LCAP);                       // [BF_LCAP]
+    float *vals = (float *)(lid + BF_LCAP);                  // [KP]
+    int *idxs = (int *)(vals + KP);                          // [KP]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float sq[PM_MP], sp[PM_MAX_PIVOTS], dist[BF_ROWS];
+    __shared__ unsigned int cmask[BF_MAXCH];
+    __shared__ int sCnt, sFail, sSeen, sVer, sG, sLeaves;
+    __shared__ float sCmax;
+    __shared__ int sCslot;
     const int a = blockIdx.x;
     const int q = act[a];
-    const int tid = threadIdx.x;
-    const int nPart = S * KP;
-    const int nIn = min(inN[a], BCAP);
-    for (int e = tid; e < P; e += blockDim.x) {
-        float v = INFINITY;
-        int p = 0x7fffffff;
-        if (e < nPart) {
-            v = partD[(int64_t)a * nPart + e];
-            p = partI[(int64_t)a * nPart + e];
-            if (!(v < INFINITY)) p = 0x7fffffff;
-        } else if (e < nPart + nIn) {
-            p = inPos[(int64_t)a * BCAP + (e - nPart)];
-            const float *xr = X + (int64_t)p * ld;
-            const float *qr = Qd + (int64_t)q * ld;
-            float acc = 0.f;
-            for (int i = 0; i < ld; i++) {
-                float t = __fsub_rn(qr[i], xr[i]);
-                acc = __fmaf_rn(t, t, acc);
-            }
-            v = acc;
-        }
-        mv[e] = v;
-        mp[e] = p;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Thr T = thr[a];
+    const float lov = T.lov;
+    const float Rv = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
+    const double epsv = (double)(ld + 8) * 0x1.0p-24;
+    const float lbSlack = 1.f - (float)((ld + 8) * 0x1.0p-24) - 1e-6f;
+    for (int i = tid; i < ld; i += BF_THREADS) qs[i] = Qd[(int64_t)q * ld + i];
+    if (tid < PM_MP) sq[tid] = qp32[(int64_t)q * PM_MP + tid];
+    if (tid < PM_MAX_PIVOTS) sp[tid] = qpiv[(int64_t)q * PM_MAX_PIVOTS + tid];
+    for (int e = tid; e < KP; e += BF_THREADS) { vals[e] = INFINITY; idxs[e] = -1; }
+    if (tid == 0) {
+        sCnt = 0; sFail = 0; sSeen = 0; sVer = 0; sCmax = INFINITY; sCslot = 0; sLeaves = 0;
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    // pass 1: candidate leaves (Eq. 5 not out) and their lower bounds
+    if (Rv > 0.f) {
+        for (int64_t base = (int64_t)warp * 32; base < L; base += 32 * (BF_THREADS / 32)) {
+            const int64_t l = base + lane;
+            bool cand = false;
+            if (l < L) cand = leaf_class(sq, sp, s, Rv, Rv, meta + l * PM_LEAF_STRIDE) != CL_OUT;
+            unsigned bits = __ballot_sync(0xffffffffu, cand);
+            while (bits) {
+                const int src = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int64_t ll = base + src;
+                const float *mu = leafMu + ll * ld;
+                float acc = 0.f;
+                for (int i = lane; i < ld; i += 32) {
+                    float t = __fsub_rn(qs[i], mu[i]);
+                    acc = __fmaf_rn(t, t, acc);
+                }
+                for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) {
+                    // sort key: distance to the leaf centre (home leaves first)
+                    int slot = atomicAdd(&sCnt, 1);
+                    if (slot < BF_LCAP) { lbv[slot] = __fsqrt_rn(acc); lid[slot] = (int)ll; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int nc = min(sCnt, BF_LCAP);
+    const bool sorted = sCnt <= BF_LCAP;
+    if (!sorted && tid == 0) atomicOr(errFlag, 256);   // more candidate leaves than fit
+    // bitonic sort of (lb, leaf id)
+    int P = 1;
+    while (P < nc) P <<= 1;
+    for (int i = nc + tid; i < P; i += BF_THREADS) { lbv[i] = INFINITY; lid[i] = 0x7fffffff; }
     __syncthreads();
     for (int k2 = 2; k2 <= P; k2 <<= 1)
         for (int j = k2 >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < P; i += blockDim.x) {
+            for (int i = tid; i < P; i += BF_THREADS) {
                 int ixj = i ^ j;
                 if (ixj > i) {
                     bool up = (i & k2) == 0;
-                    bool gt = mv[i] > mv[ixj] || (mv[i] == mv[ixj] && mp[i] > mp[ixj]);
+                    bool gt = lbv[i] > lbv[ixj] || (lbv[i] == lbv[ixj] && lid[i] > lid[ixj]);
                     if (gt == up) {
-                        float tv = mv[i]; mv[i] = mv[ixj]; mv[ixj] = tv;
-                        int tp = mp[i]; mp[i] = mp[ixj]; mp[ixj] = tp;
+                        float tv = lbv[i]; lbv[i] = lbv[ixj]; lbv[ixj] = tv;
+                        int ti = lid[i]; lid[i] = lid[ixj]; lid[ixj] = ti;
                     }
                 }
             }
             __syncthreads();
         }
-    if (tid == 0) {
-        const float K32 = mv[k - 1];
-        const double epsv = (double)(ld + 4) * 0x1.0p-24;
-        float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
-        int G = 0;
-        while (G < P && mv[G] <= thrv && mv[G] < INFINITY) G++;
-        sThr = thrv;
-        sG = G;
-        for (int sp2 = 0; sp2 < S; sp2++)
-            // a split that dropped entries (finite max) below the guard bound
-            if (partMax[(int64_t)a * S + sp2] < INFINITY && partMax[(int64_t)a * S + sp2] <= thrv)
-                atomicOr(errFlag, 16);
-        if (G > GCAP) atomicOr(errFlag, 32);
-    }
+    // lower bounds of the sorted leaves, in parallel, in place of the sort
+    // keys (the walk below is serial)
+    for (int e = tid; e < nc; e += BF_THREADS)
+        lbv[e] = __fsub_rn(__fmul_rn(lbv[e], lbSlack), leafRx[lid[e]]);
     __syncthreads();
-    const int G = min(sG, GCAP);
-    int Pg = 1;
-    while (Pg < G) Pg <<= 1;
-    for (int e = tid; e < Pg; e += blockDim.x) {
-        if (e < G) {
-            int p = mp[e];
-            gd[e] = pm_dist64(X + (int64_t)p * ld, Qd + (int64_t)q * ld, d);
-            gid[e] = perm[p];
-        } else {
-            gd[e] = INFINITY;
-            gid[e] = 0x7fffffffffffffffLL;
+    // pass 2: visit leaves in order of lb; inside a leaf, chunks (<= 32
+    // points) whose own ball bound excludes them are skipped too
+    uint32_t phase[2] = {0u, 0u};
+    const int nDch = (ld + dch - 1) / dch;
+    const int pp = tid >> 3, g = tid & 7;
+    for (int e = 0; e < nc; e++) {
+        const int l = lid[e];
+        // lower bound of every member's distance: ||q - mu_l|| - Rx_l
+        const float lb = lbv[e];
+        const float cm = sCmax;
+        if (lb > 0.f && (double)lb * lb * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv)) continue;
+        if (tid == 0) sLeaves++;
+        const unsigned char cl = leaf_class(sq, sp, s, Rv, Rv, meta + (int64_t)l * PM_LEAF_STRIDE);
+        const int cb = leafChunk[l];
+        const int nch = min(leafChunk[l + 1] - cb, BF_MAXCH);
+        if (tid == 0 && leafChunk[l + 1] - cb > BF_MAXCH) atomicOr(errFlag, 512);
+        // chunk bounds and candidate masks, one warp per chunk
+        for (int ci = warp; ci < nch; ci += BF_THREADS / 32) {
+            const int c = cb + ci;
+            const int64_t r0 = chunkOff[c];
+            const int rows = (int)(chunkOff[c + 1] - r0);
+            const float *mu = chunkMu + (int64_t)c * ld;
+            float acc = 0.f;
+            for (int i = lane; i < ld; i += 32) {
+                float t = __fsub_rn(qs[i], mu[i]);
+                acc = __fmaf_rn(t, t, acc);
+            }
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const float lbc = __fsub_rn(__fmul_rn(__fsqrt_rn(acc), lbSlack), chunkRx[c]);
+            const bool alive = !(lbc > 0.f && (double)lbc * lbc * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv));
+            bool cand = false;
+            if (alive && lane < rows)
+                cand = cl == CL_FULL || pm_pd2_32(O32 + (r0 + lane) * PM_MP, sq) <= lov;
+            unsigned m = __ballot_sync(0xffffffffu, cand);
+            if (lane == 0) cmask[ci] = m;
         }
-    }
-    __syncthreads();
-    for (int k2 = 2; k2 <= Pg; k2 <<= 1)
-        for (int j = k2 >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < Pg; i += blockDim.x) {
-                int ixj = i ^ j;
-                if (ixj > i) {
-                    bool up = (i & k2) == 0;
-                    bool gt = gd[i] > gd[ixj] || (gd[i] == gd[ixj] && gid[i] > gid[ixj]);
-                    if (gt == up) {
-                        double td = gd[i]; gd[i] = gd[ixj]; gd[ixj] = td;
-                        long long ti = gid[i]; gid[i] = gid[ixj]; gid[ixj] = ti;
+        __syncthreads();
+        int nextC = 0;
+        while (nextC < nch && cmask[nextC] == 0u) nextC++;
+        int job = 0;   // running job counter selects the stage
+        auto issue = [&](int ci, int dc, int stage) {
+            if (tid == 0) {
+                const int64_t r0 = chunkOff[cb + ci];
+                const int rows = (int)(chunkOff[cb + ci + 1] - r0);
+                const int w = min(dch, ld - dc * dch);
+                fence_async_shared();
+                mbar_expect_tx(&bar[stage], (uint32_t)(rows * w * 4));
+                for (int r = 0; r < rows; r++)
+                    bulk_g2s(xs + (stage * BF_ROWS + r) * rs, X + (r0 + r) * ld + dc * dch, (uint32_t)(w * 4),
+                             &bar[stage]);
+            }
+        };
+        if (nextC < nch) issue(nextC, 0, 0);
+        for (int ci = nextC; ci < nch;) {
+            const unsigned m = cmask[ci];
+            const int64_t r0 = chunkOff[cb + ci];
+            const int rows = (int)(chunkOff[cb + ci + 1] - r0);
+            float acc = 0.f;
+            int cn = ci + 1;
+            while (cn < nch && cmask[cn] == 0u) cn++;
+            for (int dc = 0; dc < nDch; dc++) {
+                const int stage = job & 1;
+                // prefetch the next job into the other stage
+                if (dc + 1 < nDch) issue(ci, dc + 1, stage ^ 1);
+                else if (cn < nch) issue(cn, 0, stage ^ 1);
+                bool ok = mbar_wait_bounded(&bar[stage], phase[stage]);
+                if (!ok) atomicOr(&sFail, 1);
+                phase[stage] ^= 1u;
+                const int w = min(dch, ld - dc * dch);
+                if (pp < rows && ((m >> pp) & 1u)) {
+                    const float *xr = xs + (stage * BF_ROWS + pp) * rs;
+                    const float *qr = qs + dc * dch;
+                    for (int i = g; i < w; i += 8) {
+                        float t = __fsub_rn(qr[i], xr[i]);
+                        acc = __fmaf_rn(t, t, acc);
                     }
+                }
+                __syncthreads();
+                if (sFail) goto fail;
+                job++;
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (g == 0) dist[pp] = (pp < rows && ((m >> pp) & 1u)) ? acc : INFINITY;
+            __syncthreads();
+            if (warp == 0) {
+                float cmx = sCmax;
+                int csl = sCslot;
+                const float v = dist[lane];
+                unsigned bits = __ballot_sync(0xffffffffu, v < cmx);
+                while (bits) {
+                    const int src = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const float val = __shfl_sync(0xffffffffu, v, src);
+                    topk_insert_warp(vals, idxs, KP, cmx, csl, val, (int)(r0 + src), lane);
+                }
+                if (lane == 0) {
+                    sCmax = cmx;
+                    sCslot = csl;
+                    sSeen += __popc(m);
+                    sVer += __popc(m);
                 }
             }
             __syncthreads();
-        }
-    for (int e = tid; e < k; e += blockDim.x) {
-        const int64_t o = (int64_t)q * k + e;
-        if (e < G) {
-            double dv = gd[e];
-            float f = __double2float_rn(dv);
-            outIds[o] = gid[e];
-            outD[o] = f;
-            outErr[o] = (float)fabs((double)f - dv);
-        } else {
-            outIds[o] = -1;
-            outD[o] = INFINITY;
-            outErr[o] = 0.f;
+            ci = cn;
         }
     }
+    // band-in points (FP64-resolved members just inside the radius)
+    if (warp == 0) {
+        const int nIn = min(inN[a], BCAP);
+        float cmx = sCmax;
+        int csl = sCslot;
+        for (int e = 0; e < nIn; e++) {
+            const int pos = inPos[(int64_t)a * BCAP + e];
+            const float *xr = X + (int64_t)pos * ld;
+            float acc = 0.f;
+            for (int i = lane; i < ld; i += 32) {
+                float t = __fsub_rn(qs[i], xr[i]);
+                acc = __fmaf_rn(t, t, acc);
+            }
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            topk_insert_warp(vals, idxs, KP, cmx, csl, acc, pos, lane);
+        }
+        if (lane == 0) { sCmax = cmx; sCslot = csl; sSeen += nIn; sVer += nIn; }
+    }
+    __syncthreads();
+    {
+        // guard set: sort the top-KP by FP32 d^2, then FP64 for {d^2 <= K32 (1 + 3 eps_v)}
+        float *gv = lbv;                 // reuse the leaf list area
+        int *gp = lid;
+        double *gd = (double *)(lid + 2048);
+        long long *gid = (long long *)(gd + GCAP);
+        int PK = 1;
+        while (PK < KP) PK <<= 1;
+        for (int i = tid; i < PK; i += BF_THREADS) {
+            gv[i] = i < KP ? vals[i] : INFINITY;
+            gp[i] = i < KP ? idxs[i] : 0x7fffffff;
+            if (!(gv[i] < INFINITY)) gp[i] = 0x7fffffff;
+        }
+        __syncthreads();
+        for (int k2 = 2; k2 <= PK; k2 <<= 1)
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < PK; i += BF_THREADS) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        bool up = (i & k2) == 0;
+                        bool gt = gv[i] > gv[ixj] || (gv[i] == gv[ixj] && gp[i] > gp[ixj]);
+                        if (gt == up) {
+                            float tv = gv[i]; gv[i] = gv[ixj]; gv[ixj] = tv;
+                            int tp = gp[i]; gp[i] = gp[ixj]; gp[ixj] = tp;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        if (tid == 0) {
+            const float K32 = gv[k - 1];
+            const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
+            int G = 0;
+            while (G < KP && gv[G] <= thrv && gv[G] < INFINITY) G++;
+            // entries dropped from the top-KP are >= its final maximum
+            if (sSeen > KP && sCmax <= thrv) atomicOr(errFlag, 16);
+            sG = G;
+        }
+        __syncthreads();
+        const int G = min(sG, GCAP);
+        int Pg = 1;
+        while (Pg < G) Pg <<= 1;
+        for (int e = tid; e < Pg; e += BF_THREADS) {
+            if (e < G) {
+                int p = gp[e];
+                gd[e] = pm_dist64(X + (int64_t)p * ld, qs, d);
+                gid[e] = perm[p];
+            } else {
+                gd[e] = INFINITY;
+                gid[e] = 0x7fffffffffffffffLL;
+            }
+        }
+        __syncthreads();
+        for (int k2 = 2; k2 <= Pg; k2 <<= 1)
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < Pg; i += BF_THREADS) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        bool up = (i & k2) == 0;
+                        bool gt = gd[i] > gd[ixj] || (gd[i] == gd[ixj] && gid[i] > gid[ixj]);
+                        if (gt == up) {
+                            double td = gd[i]; gd[i] = gd[ixj]; gd[ixj] = td;
+                            long long ti = gid[i]; gid[i] = gid[ixj]; gid[ixj] = ti;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int e = tid; e < k; e += BF_THREADS) {
+            const int64_t o = (int64_t)q * k + e;
+            if (e < G) {
+                double dv = gd[e];
+                float f = __double2float_rn(dv);
+                outIds[o] = gid[e];
+                outD[o] = f;
+                outErr[o] = (float)fabs((double)f - dv);
+            } else {
+                outIds[o] = -1;
+                outD[o] = INFINITY;
+                outErr[o] = 0.f;
+            }
+        }
+        if (tid == 0) {
+            dk[a] = G >= k ? gd[k - 1] : INFINITY;
+            atomicAdd(&fp64cnt[a], G);
+            nverOut[a] = sVer;
+            nleafOut[a] = sLeaves;
+        }
+    }
+    return;
+fail:
+    // a staged copy did not complete in time: record it, give copies still in
+    // flight a bounded time to land, and leave
     if (tid == 0) {
-        dk[a] = G >= k ? gd[k - 1] : INFINITY;
-        atomicAdd(&fp64cnt[a], G);
+        atomicOr(errFlag, 128);
+        mbar_wait_bounded(&bar[0], phase[0]);
+        mbar_wait_bounded(&bar[1], phase[1]);
     }
+}
+
+size_t bestfirst_smem(int ld, int KP)
+{
+    const int dch = ld < BF_DCH ? ld : BF_DCH;
+    size_t f = (size_t)2 * BF_ROWS * (dch + 8) + ld + 2 * BF_LCAP + 2 * (size_t)KP;
+    return (f * 4 + 127) & ~(size_t)127;
 }
 
 // Locality order: counting sort of queries by leaf key.
@@ -805,14 +905,6 @@ __global__ void k_scatter_order(const unsigned int *__restrict__ key, int64_t nq
 {
     int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q < nq) order[atomicAdd(&h[key[q]], 1)] = (int32_t)q;
-}
-
-size_t verify_smem(int KP)
-{
-    size_t f = 32 * (QB + 4) + 32 * (TN + 4) + QB * (TN + 1) + QB * PM_MP + TN * PM_MP +
-               QB * PM_MAX_PIVOTS + 3 * QB;
-    size_t bytes = f * 4 + 3 * QB * 4 + QB + (size_t)QB * KP * 8 + 16;
-    return (bytes + 15) & ~(size_t)15;
 }
 
 template <class T> T *grow(DevBuf &b, size_t count, pmlsh_status &st)
@@ -898,6 +990,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     std::vector<double> r(nq, rmin);
     std::vector<int32_t> rounds(nq, 0), rule(nq, 0), fp64(nq, 0);
     std::vector<int64_t> ncand(nq, 0), nver(nq, 0);
+    std::vector<int32_t> nleaf(nq, 0);
     std::vector<char> done(nq, 0);
     PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
 
@@ -917,15 +1010,18 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     int *bandN = fpc + nq;       // counters after the per-query array
     int *errFlag = fpc + nq + 1;
 
-    const int S_cap = std::max(1, (4096 - BCAP) / KP);
     int nsm = 148;
     {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
-    const size_t vsmem = verify_smem(KP);
-    PM_CUDA(cudaFuncSetAttribute(k_verify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
+    const size_t bsmem = bestfirst_smem(ld, KP);
+    if (bsmem > 227 * 1024) {
+        pm_set_error("d = %d is too large for the verification kernel's shared memory", d);
+        return PMLSH_EINVAL;
+    }
+    PM_CUDA(cudaFuncSetAttribute(k_bestfirst, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
 
     std::vector<int32_t> actH;
     actH.reserve(nq);
@@ -1009,26 +1105,19 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                           qnorm, ix->O64, qp64, m, ix->perm, inN, inPos, fpc, errFlag));
             PM_CUDA(cudaGetLastError());
         }
-        // verification
-        int S = std::max(1, std::min(S_cap, (2 * nsm + nblk - 1) / nblk));
-        float *partD = grow<float>(w.partD, (size_t)na * S * KP, s);
-        int *partI = grow<int>(w.partI, (size_t)na * S * KP, s);
-        int *partSeen = grow<int>(w.partSeen, (size_t)na * S, s);
-        float *partMax = grow<float>(w.sortTmp, (size_t)na * S, s);
+        // verification: best-first over candidate leaves, guard set, FP64
+        int *nverD = grow<int>(w.partSeen, (size_t)2 * na, s);
         if (s != PMLSH_OK) return s;
-        PM_LAUNCH("k_verify", st, k_verify<<<dim3(nblk, S), 256, vsmem, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                                    ix->leafOff, ix->O32, ix->X, Qd, ld, blkCnt, blkLeaves,
-                                                    L, KP, partD, partI, partSeen, partMax));
-        int P = 1;
-        while (P < S * KP + BCAP) P <<= 1;
-        size_t msmem = (size_t)P * 8 + (size_t)GCAP * 16;
-        PM_CUDA(cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
-        PM_LAUNCH("k_merge", st, k_merge<<<na, 256, msmem, st>>>(act, S, KP, k, partD, partI, partMax, inN, inPos, ix->X, Qd, ld, d,
-                                        ix->perm, oIds, oD, oE, dk, fpc, errFlag, P));
+        PM_LAUNCH("k_bestfirst", st, k_bestfirst<<<na, BF_THREADS, bsmem, st>>>(
+            act, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L, ix->O32, ix->X, Qd, ld, d, ix->leafMu,
+            ix->leafRx, ix->chunkOff, ix->leafChunk, ix->chunkMu, ix->chunkRx, KP, k, inN, inPos, ix->perm, oIds,
+            oD, oE, dk, fpc, nverD, nverD + na, errFlag));
         PM_CUDA(cudaGetLastError());
         std::vector<double> dkH(na);
-        std::vector<int> fpH(na);
+        std::vector<int> fpH(na), nvH(na), nlH(na);
+        PM_CUDA(cudaMemcpyAsync(nlH.data(), nverD + na, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         int errH = 0;
+        PM_CUDA(cudaMemcpyAsync(nvH.data(), nverD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(dkH.data(), dk, na * sizeof(double), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(fpH.data(), fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(&errH, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1045,7 +1134,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             rounds[q]++;
             fp64[q] += fpH[a];
             const bool budget = count[a] >= B;
-            nver[q] += budget ? B : count[a];
+            nver[q] += nvH[a];
+            nleaf[q] += nlH[a];
             if (budget) { done[q] = 1; rule[q] = 2; ncand[q] = B; continue; }
             ncand[q] = count[a];
             if (count[a] == n) { done[q] = 1; rule[q] = 3; continue; }
@@ -1082,7 +1172,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             sv[q].n_cand = ncand[q];
             sv[q].r_final = r[q];
             sv[q].fp64_checks = fp64[q];
-            sv[q].reserved = 0;
+            sv[q].leaves_visited = nleaf[q];
             sv[q].n_verified = nver[q];
         }
         PM_CUDA(cudaMemcpyAsync(stats, sv.data(), nq * sizeof(pmlsh_query_stats),

@@ -78,17 +78,28 @@ struct pmlsh_index {
     int64_t *leafOff = nullptr;  // [L+1]
     float *leafMeta = nullptr;   // [L][PM_LEAF_STRIDE]
     float *piv32 = nullptr;      // [PM_MAX_PIVOTS][16]
+    float *leafMu = nullptr;     // [L][ld] original-space leaf centre (FP32)
+    float *leafRx = nullptr;     // [L] radius around leafMu (rounded up)
+    // chunks: consecutive runs of <= 32 points inside a leaf, with their own
+    // original-space balls
+    int64_t nChunks = 0;
+    int64_t *chunkOff = nullptr;   // [C+1] positions
+    int32_t *leafChunk = nullptr;  // [L+1] chunk range of each leaf
+    float *chunkMu = nullptr;      // [C][ld]
+    float *chunkRx = nullptr;      // [C]
+    std::vector<int64_t> chunkOffH;
+    std::vector<int32_t> leafChunkH;
     // host copies
     std::vector<float> A_host;       // [m][d]
     std::vector<int64_t> leafOffH;   // [L+1]
     std::vector<int32_t> permH;      // [n]
     std::vector<int64_t> nodeLo, nodeHi;
-    std::vector<int32_t> nodeLeft, nodeRight, nodeDim;
-    std::vector<float> nodeVal;
+    std::vector<int32_t> nodeLeft, nodeRight;
     // device copy of the hierarchy used to route queries to a leaf:
-    // [e] = {left, right, split dim, leaf index}, split value
+    // [e] = {left, right, unused, first leaf}; [e] = {w[16], t}: right iff
+    // w . q' >= t
     int32_t *treeI = nullptr;   // [N][4]
-    float *treeV = nullptr;     // [N]
+    float *treeV = nullptr;     // [N][17]
     std::vector<double> distSample;  // sorted sampled distances (r_min rule)
     double maxNorm = 0.0;            // max ||o'|| (FP64 coordinates)
     KnnWork work;
