@@ -492,8 +492,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t ph)
 constexpr int BF_THREADS = 256;
 constexpr int BF_ROWS = 32;     // points per staged chunk
 constexpr int BF_DCH = 256;     // dimensions per staged chunk
-constexpr int BF_LCAP = 8192;   // leaves sorted per query in shared memory
 constexpr int BF_MAXCH = 512;   // chunks per leaf (leaf size <= 1024, chunks >= 2 points)
+constexpr int BF_SURV = 1024;   // leaves sorted per filtering pass
 
 // Inserts `val` (position `pos`) into the per-query top-KP held in shared
 // memory if it beats the current maximum; called by one full warp.
@@ -522,350 +522,445 @@ __device__ __forceinline__ void topk_insert_warp(float *vals, int *idxs, int KP,
     __syncwarp();
 }
 
-// One CTA per active query.  Candidates are the points with FP32 d'^2 <= lov
-// (plus the FP64-resolved band-in points).  Only the top-k of the candidates
-// matters (stop rule 1 tests the k-th smallest distance), so leaves are
-// visited in increasing order of the distance to their original-space centre
-// mu_l, and a leaf (or a chunk of <= 32 of its points) is skipped when its
-// lower bound ||q - mu|| - Rx excludes every member from the guard set
-// {d^2_32 <= K (1 + 3 eps_v)} (K the current KP-th smallest, an upper bound
-// of the k-th).  Rows of a visited leaf are staged
-// by TMA bulk copies, 32 rows x 256 dimensions per stage, double-buffered.
-// The result equals verifying every candidate.
+struct BfArgs {
+    const int32_t *act;
+    int na;
+    const Thr *thr;
+    const float *qp32, *qpiv;
+    int s;
+    const float *meta;
+    const int64_t *off;
+    int64_t L;
+    const float *O32, *X, *Qd;
+    int ld, d;
+    const float *leafMu, *leafRx;
+    const int64_t *chunkOff;
+    const int32_t *leafChunk;
+    const float *chunkMu, *chunkRx;
+    int KP, k;
+    const int *inN, *inPos;
+    const int32_t *perm;
+    int64_t *outIds;
+    float *outD, *outErr;
+    double *dk;
+    int *fp64cnt, *nverOut, *nleafOut, *errFlag;
+    int *workCtr;        // next active query to take (persistent grid)
+    int *dbg;            // [4]: site, value, query of the first failed index check
+    int64_t n;           // points
+    float *scratch;      // [gridDim.x][2][L]: per-CTA leaf bounds and centre distances
+};
+
+// Persistent grid: each CTA takes active queries from a counter.  Per query,
+// the candidates are the points with FP32 d'^2 <= lov plus the FP64-resolved
+// band-in points, and only the top-k of the candidates matters (stop rule 1
+// tests the k-th smallest distance).  Pass 1 computes, for every leaf that
+// Eq. 5 does not exclude, the distance ||q - mu_l|| to its original-space
+// centre and the lower bound lb = ||q - mu_l|| - Rx_l of its members'
+// distances.  The leaf with the nearest centre is verified first; then the
+// leaves whose lb does not exclude them from the guard set
+// {d^2_32 <= K (1 + 3 eps_v)} (K the current KP-th smallest, an upper bound of
+// the k-th) are sorted by centre distance and verified, re-testing lb against
+// the tightening K; chunks of <= 32 points are skipped by their own bound.
+// Rows are staged by TMA bulk copies, 32 rows x 256 dimensions per stage,
+// double-buffered.  The result equals verifying every candidate.
+#define BF_CHECK(cond, site, val)                                              \
+    (((cond)) ? true                                                           \
+              : (atomicCAS(&A.dbg[0], 0, (site)) == 0 ? (A.dbg[1] = (int)(val), A.dbg[2] = a, \
+                                                          atomicOr(A.errFlag, 1024), false)   \
+                                                       : (atomicOr(A.errFlag, 1024), false)))
+
 __global__ void __launch_bounds__(BF_THREADS)
-k_bestfirst(const int32_t *__restrict__ act, const Thr *__restrict__ thr, const float *__restrict__ qp32,
-            const float *__restrict__ qpiv, int s, const float *__restrict__ meta,
-            const int64_t *__restrict__ off, int64_t L, const float *__restrict__ O32,
-            const float *__restrict__ X, const float *__restrict__ Qd, int ld, int d,
-            const float *__restrict__ leafMu, const float *__restrict__ leafRx,
-            const int64_t *__restrict__ chunkOff, const int32_t *__restrict__ leafChunk,
-            const float *__restrict__ chunkMu, const float *__restrict__ chunkRx, int KP, int k,
-            const int *__restrict__ inN, const int *__restrict__ inPos, const int32_t *__restrict__ perm,
-            int64_t *__restrict__ outIds, float *__restrict__ outD, float *__restrict__ outErr,
-            double *__restrict__ dk, int *__restrict__ fp64cnt, int *__restrict__ nverOut,
-            int *__restrict__ nleafOut, int *__restrict__ errFlag)
+k_bestfirst(BfArgs A)
 {
     extern __shared__ __align__(128) unsigned char bsm[];
+    const int ld = A.ld, d = A.d, KP = A.KP, k = A.k, s = A.s;
+    const int64_t L = A.L;
     const int dch = ld < BF_DCH ? ld : BF_DCH;
     const int rs = dch + 8;                                  // staged row stride (floats)
     float *xs = (float *)bsm;                                // [2][32][rs]
     float *qs = xs + 2 * BF_ROWS * rs;                       // [ld]
-    float *lbv = qs + ld;                                    // [BF_LCAP]
-    int *lid = (int *)(lbv + BF_LCAP);                       // [BF_LCAP]
-    float *vals = (float *)(lid + BF_LCAP);                  // [KP]
+    float *vals = qs + ld;                                   // [KP]
     int *idxs = (int *)(vals + KP);                          // [KP]
+    unsigned char *uarea = (unsigned char *)(idxs + KP);     // union: survivors / guard set
+    float *svk = (float *)uarea;                             // [BF_SURV]
+    int *svi = (int *)(svk + BF_SURV);                       // [BF_SURV]
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float sq[PM_MP], sp[PM_MAX_PIVOTS], dist[BF_ROWS];
     __shared__ unsigned int cmask[BF_MAXCH];
-    __shared__ int sCnt, sFail, sSeen, sVer, sG, sLeaves;
-    __shared__ float sCmax;
+    __shared__ int sCnt, sFail, sSeen, sVer, sG, sLeaves, sQ, sHome;
+    __shared__ float sCmax, sHomeD;
     __shared__ int sCslot;
-    const int a = blockIdx.x;
-    const int q = act[a];
+    __shared__ float wMinD[BF_THREADS / 32];
+    __shared__ int wMinL[BF_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const Thr T = thr[a];
-    const float lov = T.lov;
-    const float Rv = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
+    float *lbS = A.scratch + (int64_t)blockIdx.x * 2 * L;    // [L] lower bounds (INF: out or done)
+    float *dcS = lbS + L;                                    // [L] centre distances
     const double epsv = (double)(ld + 8) * 0x1.0p-24;
     const float lbSlack = 1.f - (float)((ld + 8) * 0x1.0p-24) - 1e-6f;
-    for (int i = tid; i < ld; i += BF_THREADS) qs[i] = Qd[(int64_t)q * ld + i];
-    if (tid < PM_MP) sq[tid] = qp32[(int64_t)q * PM_MP + tid];
-    if (tid < PM_MAX_PIVOTS) sp[tid] = qpiv[(int64_t)q * PM_MAX_PIVOTS + tid];
-    for (int e = tid; e < KP; e += BF_THREADS) { vals[e] = INFINITY; idxs[e] = -1; }
+    const int nDch = (ld + dch - 1) / dch;
+    const int pp = tid >> 3, g = tid & 7;
+    uint32_t phase[2] = {0u, 0u};
     if (tid == 0) {
-        sCnt = 0; sFail = 0; sSeen = 0; sVer = 0; sCmax = INFINITY; sCslot = 0; sLeaves = 0;
+        sFail = 0;
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // pass 1: candidate leaves (Eq. 5 not out) and their lower bounds
-    if (Rv > 0.f) {
+    for (;;) {
+        if (tid == 0) sQ = atomicAdd(A.workCtr, 1);
+        __syncthreads();
+        const int a = sQ;
+        if (a >= A.na) break;
+        if (!BF_CHECK(a >= 0, 7, a)) break;
+        // fresh barriers for every query (no copy is in flight here)
+        if (tid == 0) {
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[0])) : "memory");
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[1])) : "memory");
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        phase[0] = phase[1] = 0u;
+        const int q = A.act[a];
+        const Thr T = A.thr[a];
+        const float lov = T.lov;
+        const float Rv = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
+        for (int i = tid; i < ld; i += BF_THREADS) qs[i] = A.Qd[(int64_t)q * ld + i];
+        if (tid < PM_MP) sq[tid] = A.qp32[(int64_t)q * PM_MP + tid];
+        if (tid < PM_MAX_PIVOTS) sp[tid] = A.qpiv[(int64_t)q * PM_MAX_PIVOTS + tid];
+        for (int e = tid; e < KP; e += BF_THREADS) { vals[e] = INFINITY; idxs[e] = -1; }
+        if (tid == 0) { sSeen = 0; sVer = 0; sCmax = INFINITY; sCslot = 0; sLeaves = 0; }
+        __syncthreads();
+        // pass 1: leaf bounds; per-warp nearest centre
+        float myMin = INFINITY;
+        int myMinL = -1;
         for (int64_t base = (int64_t)warp * 32; base < L; base += 32 * (BF_THREADS / 32)) {
             const int64_t l = base + lane;
             bool cand = false;
-            if (l < L) cand = leaf_class(sq, sp, s, Rv, Rv, meta + l * PM_LEAF_STRIDE) != CL_OUT;
+            if (l < L) {
+                if (Rv > 0.f) cand = leaf_class(sq, sp, s, Rv, Rv, A.meta + l * PM_LEAF_STRIDE) != CL_OUT;
+                if (!cand) lbS[l] = INFINITY;
+            }
             unsigned bits = __ballot_sync(0xffffffffu, cand);
             while (bits) {
                 const int src = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int64_t ll = base + src;
-                const float *mu = leafMu + ll * ld;
+                const float *mu = A.leafMu + ll * ld;
                 float acc = 0.f;
                 for (int i = lane; i < ld; i += 32) {
                     float t = __fsub_rn(qs[i], mu[i]);
                     acc = __fmaf_rn(t, t, acc);
                 }
                 for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                const float dc = __fsqrt_rn(acc);
                 if (lane == 0) {
-                    // sort key: distance to the leaf centre (home leaves first)
-                    int slot = atomicAdd(&sCnt, 1);
-                    if (slot < BF_LCAP) { lbv[slot] = __fsqrt_rn(acc); lid[slot] = (int)ll; }
+                    dcS[ll] = dc;
+                    lbS[ll] = __fsub_rn(__fmul_rn(dc, lbSlack), A.leafRx[ll]);
                 }
+                if (dc < myMin) { myMin = dc; myMinL = (int)ll; }
             }
         }
-    }
-    __syncthreads();
-    const int nc = min(sCnt, BF_LCAP);
-    const bool sorted = sCnt <= BF_LCAP;
-    if (!sorted && tid == 0) atomicOr(errFlag, 256);   // more candidate leaves than fit
-    // bitonic sort of (lb, leaf id)
-    int P = 1;
-    while (P < nc) P <<= 1;
-    for (int i = nc + tid; i < P; i += BF_THREADS) { lbv[i] = INFINITY; lid[i] = 0x7fffffff; }
-    __syncthreads();
-    for (int k2 = 2; k2 <= P; k2 <<= 1)
-        for (int j = k2 >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < P; i += BF_THREADS) {
-                int ixj = i ^ j;
-                if (ixj > i) {
-                    bool up = (i & k2) == 0;
-                    bool gt = lbv[i] > lbv[ixj] || (lbv[i] == lbv[ixj] && lid[i] > lid[ixj]);
-                    if (gt == up) {
-                        float tv = lbv[i]; lbv[i] = lbv[ixj]; lbv[ixj] = tv;
-                        int ti = lid[i]; lid[i] = lid[ixj]; lid[ixj] = ti;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    // lower bounds of the sorted leaves, in parallel, in place of the sort
-    // keys (the walk below is serial)
-    for (int e = tid; e < nc; e += BF_THREADS)
-        lbv[e] = __fsub_rn(__fmul_rn(lbv[e], lbSlack), leafRx[lid[e]]);
-    __syncthreads();
-    // pass 2: visit leaves in order of lb; inside a leaf, chunks (<= 32
-    // points) whose own ball bound excludes them are skipped too
-    uint32_t phase[2] = {0u, 0u};
-    const int nDch = (ld + dch - 1) / dch;
-    const int pp = tid >> 3, g = tid & 7;
-    for (int e = 0; e < nc; e++) {
-        const int l = lid[e];
-        // lower bound of every member's distance: ||q - mu_l|| - Rx_l
-        const float lb = lbv[e];
-        const float cm = sCmax;
-        if (lb > 0.f && (double)lb * lb * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv)) continue;
-        if (tid == 0) sLeaves++;
-        const unsigned char cl = leaf_class(sq, sp, s, Rv, Rv, meta + (int64_t)l * PM_LEAF_STRIDE);
-        const int cb = leafChunk[l];
-        const int nch = min(leafChunk[l + 1] - cb, BF_MAXCH);
-        if (tid == 0 && leafChunk[l + 1] - cb > BF_MAXCH) atomicOr(errFlag, 512);
-        // chunk bounds and candidate masks, one warp per chunk
-        for (int ci = warp; ci < nch; ci += BF_THREADS / 32) {
-            const int c = cb + ci;
-            const int64_t r0 = chunkOff[c];
-            const int rows = (int)(chunkOff[c + 1] - r0);
-            const float *mu = chunkMu + (int64_t)c * ld;
-            float acc = 0.f;
-            for (int i = lane; i < ld; i += 32) {
-                float t = __fsub_rn(qs[i], mu[i]);
-                acc = __fmaf_rn(t, t, acc);
-            }
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            const float lbc = __fsub_rn(__fmul_rn(__fsqrt_rn(acc), lbSlack), chunkRx[c]);
-            const bool alive = !(lbc > 0.f && (double)lbc * lbc * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv));
-            bool cand = false;
-            if (alive && lane < rows)
-                cand = cl == CL_FULL || pm_pd2_32(O32 + (r0 + lane) * PM_MP, sq) <= lov;
-            unsigned m = __ballot_sync(0xffffffffu, cand);
-            if (lane == 0) cmask[ci] = m;
+        if (lane == 0) { wMinD[warp] = myMin; wMinL[warp] = myMinL; }
+        __syncthreads();
+        if (tid == 0) {
+            float bd = INFINITY;
+            int bl = -1;
+            for (int w = 0; w < BF_THREADS / 32; w++)
+                if (wMinD[w] < bd || (wMinD[w] == bd && wMinL[w] >= 0 && wMinL[w] < bl)) { bd = wMinD[w]; bl = wMinL[w]; }
+            sHome = bl;
+            sHomeD = bd;
         }
         __syncthreads();
-        int nextC = 0;
-        while (nextC < nch && cmask[nextC] == 0u) nextC++;
-        int job = 0;   // running job counter selects the stage
-        auto issue = [&](int ci, int dc, int stage) {
-            if (tid == 0) {
-                const int64_t r0 = chunkOff[cb + ci];
-                const int rows = (int)(chunkOff[cb + ci + 1] - r0);
-                const int w = min(dch, ld - dc * dch);
-                fence_async_shared();
-                mbar_expect_tx(&bar[stage], (uint32_t)(rows * w * 4));
-                for (int r = 0; r < rows; r++)
-                    bulk_g2s(xs + (stage * BF_ROWS + r) * rs, X + (r0 + r) * ld + dc * dch, (uint32_t)(w * 4),
-                             &bar[stage]);
+
+        // verifies the candidates of leaf l (all threads)
+        auto visit = [&](int l) -> bool {
+            if (!BF_CHECK(l >= 0 && l < L, 1, l)) return true;
+            const float cm = sCmax;
+            if (tid == 0) { sLeaves++; lbS[l] = INFINITY; }
+            const unsigned char cl = leaf_class(sq, sp, s, Rv, Rv, A.meta + (int64_t)l * PM_LEAF_STRIDE);
+            const int cb = A.leafChunk[l];
+            const int nch = min(A.leafChunk[l + 1] - cb, BF_MAXCH);
+            if (tid == 0 && A.leafChunk[l + 1] - cb > BF_MAXCH) atomicOr(A.errFlag, 512);
+            for (int ci = warp; ci < nch; ci += BF_THREADS / 32) {
+                const int c = cb + ci;
+                const int64_t r0 = A.chunkOff[c];
+                int rows = (int)(A.chunkOff[c + 1] - r0);
+                if (!BF_CHECK(rows >= 1 && rows <= BF_ROWS && r0 >= 0 && r0 + rows <= A.n, 2, rows)) rows = 0;
+                const float *mu = A.chunkMu + (int64_t)c * ld;
+                float acc = 0.f;
+                for (int i = lane; i < ld; i += 32) {
+                    float t = __fsub_rn(qs[i], mu[i]);
+                    acc = __fmaf_rn(t, t, acc);
+                }
+                for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                const float lbc = __fsub_rn(__fmul_rn(__fsqrt_rn(acc), lbSlack), A.chunkRx[c]);
+                const bool alive = !(lbc > 0.f && (double)lbc * lbc * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv));
+                bool cand = false;
+                if (alive && lane < rows)
+                    cand = cl == CL_FULL || pm_pd2_32(A.O32 + (r0 + lane) * PM_MP, sq) <= lov;
+                unsigned m = __ballot_sync(0xffffffffu, cand);
+                if (lane == 0) cmask[ci] = rows > 0 ? m : 0u;
             }
+            __syncthreads();
+            int nextC = 0;
+            while (nextC < nch && cmask[nextC] == 0u) nextC++;
+            int job = 0;
+            auto issue = [&](int ci, int dc, int stage) {
+                if (tid == 0) {
+                    const int64_t r0 = A.chunkOff[cb + ci];
+                    const int rows = (int)(A.chunkOff[cb + ci + 1] - r0);
+                    const int w = min(dch, ld - dc * dch);
+                    fence_async_shared();
+                    mbar_expect_tx(&bar[stage], (uint32_t)(rows * w * 4));
+                    for (int r = 0; r < rows; r++)
+                        bulk_g2s(xs + (stage * BF_ROWS + r) * rs, A.X + (r0 + r) * ld + dc * dch, (uint32_t)(w * 4),
+                                 &bar[stage]);
+                }
+            };
+            if (nextC < nch) issue(nextC, 0, 0);
+            for (int ci = nextC; ci < nch;) {
+                const unsigned m = cmask[ci];
+                const int64_t r0 = A.chunkOff[cb + ci];
+                const int rows = (int)(A.chunkOff[cb + ci + 1] - r0);
+                float acc = 0.f;
+                int cn = ci + 1;
+                while (cn < nch && cmask[cn] == 0u) cn++;
+                for (int dc = 0; dc < nDch; dc++) {
+                    const int stage = job & 1;
+                    if (dc + 1 < nDch) issue(ci, dc + 1, stage ^ 1);
+                    else if (cn < nch) issue(cn, 0, stage ^ 1);
+                    bool ok = mbar_wait_bounded(&bar[stage], phase[stage]);
+                    if (!ok) atomicOr(&sFail, 1);
+                    phase[stage] ^= 1u;
+                    const int w = min(dch, ld - dc * dch);
+                    if (pp < rows && ((m >> pp) & 1u)) {
+                        const float *xr = xs + (stage * BF_ROWS + pp) * rs;
+                        const float *qr = qs + dc * dch;
+                        for (int i = g; i < w; i += 8) {
+                            float t = __fsub_rn(qr[i], xr[i]);
+                            acc = __fmaf_rn(t, t, acc);
+                        }
+                    }
+                    __syncthreads();
+                    if (sFail) return false;
+                    job++;
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+                if (g == 0) dist[pp] = (pp < rows && ((m >> pp) & 1u)) ? acc : INFINITY;
+                __syncthreads();
+                if (warp == 0) {
+                    float cmx = sCmax;
+                    int csl = sCslot;
+                    const float v = dist[lane];
+                    unsigned bits = __ballot_sync(0xffffffffu, v < cmx);
+                    while (bits) {
+                        const int src = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const float val = __shfl_sync(0xffffffffu, v, src);
+                        topk_insert_warp(vals, idxs, KP, cmx, csl, val, (int)(r0 + src), lane);
+                    }
+                    if (lane == 0) {
+                        sCmax = cmx;
+                        sCslot = csl;
+                        sSeen += __popc(m);
+                        sVer += __popc(m);
+                    }
+                }
+                __syncthreads();
+                ci = cn;
+            }
+            return true;
         };
-        if (nextC < nch) issue(nextC, 0, 0);
-        for (int ci = nextC; ci < nch;) {
-            const unsigned m = cmask[ci];
-            const int64_t r0 = chunkOff[cb + ci];
-            const int rows = (int)(chunkOff[cb + ci + 1] - r0);
-            float acc = 0.f;
-            int cn = ci + 1;
-            while (cn < nch && cmask[cn] == 0u) cn++;
-            for (int dc = 0; dc < nDch; dc++) {
-                const int stage = job & 1;
-                // prefetch the next job into the other stage
-                if (dc + 1 < nDch) issue(ci, dc + 1, stage ^ 1);
-                else if (cn < nch) issue(cn, 0, stage ^ 1);
-                bool ok = mbar_wait_bounded(&bar[stage], phase[stage]);
-                if (!ok) atomicOr(&sFail, 1);
-                phase[stage] ^= 1u;
-                const int w = min(dch, ld - dc * dch);
-                if (pp < rows && ((m >> pp) & 1u)) {
-                    const float *xr = xs + (stage * BF_ROWS + pp) * rs;
-                    const float *qr = qs + dc * dch;
-                    for (int i = g; i < w; i += 8) {
-                        float t = __fsub_rn(qr[i], xr[i]);
-                        acc = __fmaf_rn(t, t, acc);
-                    }
-                }
-                __syncthreads();
-                if (sFail) goto fail;
-                job++;
-            }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            if (g == 0) dist[pp] = (pp < rows && ((m >> pp) & 1u)) ? acc : INFINITY;
+
+        bool ok = true;
+        if (sHome >= 0) ok = visit(sHome);
+        if (tid == 0) BF_CHECK(sHome >= -1 && sHome < L, 6, sHome);
+        // filtering passes: leaves whose bound admits them, nearest centre first
+        while (ok) {
+            if (tid == 0) sCnt = 0;
             __syncthreads();
-            if (warp == 0) {
-                float cmx = sCmax;
-                int csl = sCslot;
-                const float v = dist[lane];
-                unsigned bits = __ballot_sync(0xffffffffu, v < cmx);
-                while (bits) {
-                    const int src = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const float val = __shfl_sync(0xffffffffu, v, src);
-                    topk_insert_warp(vals, idxs, KP, cmx, csl, val, (int)(r0 + src), lane);
-                }
-                if (lane == 0) {
-                    sCmax = cmx;
-                    sCslot = csl;
-                    sSeen += __popc(m);
-                    sVer += __popc(m);
-                }
+            const float cm = sCmax;
+            for (int64_t l = tid; l < L; l += BF_THREADS) {
+                const float lb = lbS[l];
+                if (!(lb < INFINITY)) continue;
+                if (lb > 0.f && (double)lb * lb * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv)) continue;
+                const int slot = atomicAdd(&sCnt, 1);
+                if (slot < BF_SURV) { svk[slot] = dcS[l]; svi[slot] = (int)l; }
             }
             __syncthreads();
-            ci = cn;
-        }
-    }
-    // band-in points (FP64-resolved members just inside the radius)
-    if (warp == 0) {
-        const int nIn = min(inN[a], BCAP);
-        float cmx = sCmax;
-        int csl = sCslot;
-        for (int e = 0; e < nIn; e++) {
-            const int pos = inPos[(int64_t)a * BCAP + e];
-            const float *xr = X + (int64_t)pos * ld;
-            float acc = 0.f;
-            for (int i = lane; i < ld; i += 32) {
-                float t = __fsub_rn(qs[i], xr[i]);
-                acc = __fmaf_rn(t, t, acc);
-            }
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            topk_insert_warp(vals, idxs, KP, cmx, csl, acc, pos, lane);
-        }
-        if (lane == 0) { sCmax = cmx; sCslot = csl; sSeen += nIn; sVer += nIn; }
-    }
-    __syncthreads();
-    {
-        // guard set: sort the top-KP by FP32 d^2, then FP64 for {d^2 <= K32 (1 + 3 eps_v)}
-        float *gv = lbv;                 // reuse the leaf list area
-        int *gp = lid;
-        double *gd = (double *)(lid + 2048);
-        long long *gid = (long long *)(gd + GCAP);
-        int PK = 1;
-        while (PK < KP) PK <<= 1;
-        for (int i = tid; i < PK; i += BF_THREADS) {
-            gv[i] = i < KP ? vals[i] : INFINITY;
-            gp[i] = i < KP ? idxs[i] : 0x7fffffff;
-            if (!(gv[i] < INFINITY)) gp[i] = 0x7fffffff;
-        }
-        __syncthreads();
-        for (int k2 = 2; k2 <= PK; k2 <<= 1)
-            for (int j = k2 >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < PK; i += BF_THREADS) {
-                    int ixj = i ^ j;
-                    if (ixj > i) {
-                        bool up = (i & k2) == 0;
-                        bool gt = gv[i] > gv[ixj] || (gv[i] == gv[ixj] && gp[i] > gp[ixj]);
-                        if (gt == up) {
-                            float tv = gv[i]; gv[i] = gv[ixj]; gv[ixj] = tv;
-                            int tp = gp[i]; gp[i] = gp[ixj]; gp[ixj] = tp;
+            const int total = sCnt;
+            if (total == 0) break;
+            const int ns = min(total, BF_SURV);
+            int P = 1;
+            while (P < ns) P <<= 1;
+            for (int i = ns + tid; i < P; i += BF_THREADS) { svk[i] = INFINITY; svi[i] = 0x7fffffff; }
+            __syncthreads();
+            for (int k2 = 2; k2 <= P; k2 <<= 1)
+                for (int j = k2 >> 1; j > 0; j >>= 1) {
+                    for (int i = tid; i < P; i += BF_THREADS) {
+                        int ixj = i ^ j;
+                        if (ixj > i) {
+                            bool up = (i & k2) == 0;
+                            bool gt = svk[i] > svk[ixj] || (svk[i] == svk[ixj] && svi[i] > svi[ixj]);
+                            if (gt == up) {
+                                float tv = svk[i]; svk[i] = svk[ixj]; svk[ixj] = tv;
+                                int ti = svi[i]; svi[i] = svi[ixj]; svi[ixj] = ti;
+                            }
                         }
                     }
+                    __syncthreads();
                 }
+            for (int e = 0; e < ns && ok; e++) {
+                const int l = svi[e];
+                const float lb = (l >= 0 && l < L) ? lbS[l] : INFINITY;
+                const float cmn = sCmax;
+                // every thread has its copy of lbS[l] and sCmax before visit()
+                // changes them, so all threads take the same branch below
                 __syncthreads();
+                if (tid == 0) BF_CHECK(l >= 0 && l < L, 3, l);
+                if (!(lb < INFINITY)) continue;
+                if (lb > 0.f && (double)lb * lb * (1.0 - epsv) > (double)cmn * (1.0 + 3.0 * epsv)) {
+                    if (tid == 0) lbS[l] = INFINITY;
+                    continue;
+                }
+                ok = visit(l);
             }
-        if (tid == 0) {
-            const float K32 = gv[k - 1];
-            const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
-            int G = 0;
-            while (G < KP && gv[G] <= thrv && gv[G] < INFINITY) G++;
-            // entries dropped from the top-KP are >= its final maximum
-            if (sSeen > KP && sCmax <= thrv) atomicOr(errFlag, 16);
-            sG = G;
+            __syncthreads();
+            if (total <= BF_SURV) break;
+        }
+        if (!ok) break;
+        // band-in points (FP64-resolved members just inside the radius)
+        if (warp == 0) {
+            const int nIn = min(A.inN[a], BCAP);
+            float cmx = sCmax;
+            int csl = sCslot;
+            for (int e = 0; e < nIn; e++) {
+                const int pos = A.inPos[(int64_t)a * BCAP + e];
+                if (!BF_CHECK(pos >= 0 && pos < A.n, 4, pos)) continue;
+                const float *xr = A.X + (int64_t)pos * ld;
+                float acc = 0.f;
+                for (int i = lane; i < ld; i += 32) {
+                    float t = __fsub_rn(qs[i], xr[i]);
+                    acc = __fmaf_rn(t, t, acc);
+                }
+                for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                topk_insert_warp(vals, idxs, KP, cmx, csl, acc, pos, lane);
+            }
+            if (lane == 0) { sCmax = cmx; sCslot = csl; sSeen += nIn; sVer += nIn; }
         }
         __syncthreads();
-        const int G = min(sG, GCAP);
-        int Pg = 1;
-        while (Pg < G) Pg <<= 1;
-        for (int e = tid; e < Pg; e += BF_THREADS) {
-            if (e < G) {
-                int p = gp[e];
-                gd[e] = pm_dist64(X + (int64_t)p * ld, qs, d);
-                gid[e] = perm[p];
-            } else {
-                gd[e] = INFINITY;
-                gid[e] = 0x7fffffffffffffffLL;
+        {
+            // guard set: sort the top-KP by FP32 d^2, then FP64 for {d^2 <= K32 (1 + 3 eps_v)}
+            float *gv = (float *)uarea;                // [512]
+            int *gp = (int *)(gv + 512);               // [512]
+            double *gd = (double *)(gp + 512);         // [GCAP]
+            long long *gid = (long long *)(gd + GCAP); // [GCAP]
+            int PK = 1;
+            while (PK < KP) PK <<= 1;
+            for (int i = tid; i < PK; i += BF_THREADS) {
+                gv[i] = i < KP ? vals[i] : INFINITY;
+                gp[i] = i < KP ? idxs[i] : 0x7fffffff;
+                if (!(gv[i] < INFINITY)) gp[i] = 0x7fffffff;
             }
-        }
-        __syncthreads();
-        for (int k2 = 2; k2 <= Pg; k2 <<= 1)
-            for (int j = k2 >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < Pg; i += BF_THREADS) {
-                    int ixj = i ^ j;
-                    if (ixj > i) {
-                        bool up = (i & k2) == 0;
-                        bool gt = gd[i] > gd[ixj] || (gd[i] == gd[ixj] && gid[i] > gid[ixj]);
-                        if (gt == up) {
-                            double td = gd[i]; gd[i] = gd[ixj]; gd[ixj] = td;
-                            long long ti = gid[i]; gid[i] = gid[ixj]; gid[ixj] = ti;
+            __syncthreads();
+            for (int k2 = 2; k2 <= PK; k2 <<= 1)
+                for (int j = k2 >> 1; j > 0; j >>= 1) {
+                    for (int i = tid; i < PK; i += BF_THREADS) {
+                        int ixj = i ^ j;
+                        if (ixj > i) {
+                            bool up = (i & k2) == 0;
+                            bool gt = gv[i] > gv[ixj] || (gv[i] == gv[ixj] && gp[i] > gp[ixj]);
+                            if (gt == up) {
+                                float tv = gv[i]; gv[i] = gv[ixj]; gv[ixj] = tv;
+                                int tp = gp[i]; gp[i] = gp[ixj]; gp[ixj] = tp;
+                            }
                         }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
+            if (tid == 0) {
+                const float K32 = gv[k - 1];
+                const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
+                int G = 0;
+                while (G < KP && gv[G] <= thrv && gv[G] < INFINITY) G++;
+                // entries dropped from the top-KP are >= its final maximum
+                if (sSeen > KP && sCmax <= thrv) atomicOr(A.errFlag, 16);
+                sG = G;
             }
-        for (int e = tid; e < k; e += BF_THREADS) {
-            const int64_t o = (int64_t)q * k + e;
-            if (e < G) {
-                double dv = gd[e];
-                float f = __double2float_rn(dv);
-                outIds[o] = gid[e];
-                outD[o] = f;
-                outErr[o] = (float)fabs((double)f - dv);
-            } else {
-                outIds[o] = -1;
-                outD[o] = INFINITY;
-                outErr[o] = 0.f;
+            __syncthreads();
+            const int G = min(sG, GCAP);
+            int Pg = 1;
+            while (Pg < G) Pg <<= 1;
+            for (int e = tid; e < Pg; e += BF_THREADS) {
+                if (e < G && BF_CHECK(gp[e] >= 0 && gp[e] < A.n, 5, gp[e])) {
+                    int p = gp[e];
+                    gd[e] = pm_dist64(A.X + (int64_t)p * ld, qs, d);
+                    gid[e] = A.perm[p];
+                } else {
+                    gd[e] = INFINITY;
+                    gid[e] = 0x7fffffffffffffffLL;
+                }
             }
-        }
-        if (tid == 0) {
-            dk[a] = G >= k ? gd[k - 1] : INFINITY;
-            atomicAdd(&fp64cnt[a], G);
-            nverOut[a] = sVer;
-            nleafOut[a] = sLeaves;
+            __syncthreads();
+            for (int k2 = 2; k2 <= Pg; k2 <<= 1)
+                for (int j = k2 >> 1; j > 0; j >>= 1) {
+                    for (int i = tid; i < Pg; i += BF_THREADS) {
+                        int ixj = i ^ j;
+                        if (ixj > i) {
+                            bool up = (i & k2) == 0;
+                            bool gt = gd[i] > gd[ixj] || (gd[i] == gd[ixj] && gid[i] > gid[ixj]);
+                            if (gt == up) {
+                                double td = gd[i]; gd[i] = gd[ixj]; gd[ixj] = td;
+                                long long ti = gid[i]; gid[i] = gid[ixj]; gid[ixj] = ti;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            for (int e = tid; e < k; e += BF_THREADS) {
+                const int64_t o = (int64_t)q * k + e;
+                if (e < G) {
+                    double dv = gd[e];
+                    float f = __double2float_rn(dv);
+                    A.outIds[o] = gid[e];
+                    A.outD[o] = f;
+                    A.outErr[o] = (float)fabs((double)f - dv);
+                } else {
+                    A.outIds[o] = -1;
+                    A.outD[o] = INFINITY;
+                    A.outErr[o] = 0.f;
+                }
+            }
+            if (tid == 0) {
+                A.dk[a] = G >= k ? gd[k - 1] : INFINITY;
+                atomicAdd(&A.fp64cnt[a], G);
+                A.nverOut[a] = sVer;
+                A.nleafOut[a] = sLeaves;
+            }
+            __syncthreads();
         }
     }
-    return;
-fail:
-    // a staged copy did not complete in time: record it, give copies still in
-    // flight a bounded time to land, and leave
-    if (tid == 0) {
-        atomicOr(errFlag, 128);
-        mbar_wait_bounded(&bar[0], phase[0]);
-        mbar_wait_bounded(&bar[1], phase[1]);
+    if (sFail) {
+        // a staged copy did not complete in time: record it, give copies still
+        // in flight a bounded time to land, and leave
+        if (tid == 0) {
+            atomicOr(A.errFlag, 128);
+            mbar_wait_bounded(&bar[0], phase[0]);
+            mbar_wait_bounded(&bar[1], phase[1]);
+        }
     }
 }
 
 size_t bestfirst_smem(int ld, int KP)
 {
     const int dch = ld < BF_DCH ? ld : BF_DCH;
-    size_t f = (size_t)2 * BF_ROWS * (dch + 8) + ld + 2 * BF_LCAP + 2 * (size_t)KP;
-    return (f * 4 + 127) & ~(size_t)127;
+    size_t f = (size_t)2 * BF_ROWS * (dch + 8) + ld + 2 * (size_t)KP;
+    size_t u = std::max<size_t>((size_t)BF_SURV * 8, 512 * 8 + (size_t)GCAP * 16);
+    return ((f * 4 + 15) & ~(size_t)15) + u + 128;
 }
 
 // Locality order: counting sort of queries by leaf key.
@@ -1022,6 +1117,9 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         return PMLSH_EINVAL;
     }
     PM_CUDA(cudaFuncSetAttribute(k_bestfirst, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+    int bfPerSM = 1;
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfPerSM, k_bestfirst, BF_THREADS, bsmem));
+    bfPerSM = std::max(1, bfPerSM);
 
     std::vector<int32_t> actH;
     actH.reserve(nq);
@@ -1106,12 +1204,23 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             PM_CUDA(cudaGetLastError());
         }
         // verification: best-first over candidate leaves, guard set, FP64
-        int *nverD = grow<int>(w.partSeen, (size_t)2 * na, s);
+        int *nverD = grow<int>(w.partSeen, (size_t)2 * na + 8, s);
+        const int bfGrid = std::max(1, std::min(na, bfPerSM * nsm));
+        float *bfScratch = grow<float>(w.partD, (size_t)bfGrid * 2 * L, s);
         if (s != PMLSH_OK) return s;
-        PM_LAUNCH("k_bestfirst", st, k_bestfirst<<<na, BF_THREADS, bsmem, st>>>(
-            act, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L, ix->O32, ix->X, Qd, ld, d, ix->leafMu,
-            ix->leafRx, ix->chunkOff, ix->leafChunk, ix->chunkMu, ix->chunkRx, KP, k, inN, inPos, ix->perm, oIds,
-            oD, oE, dk, fpc, nverD, nverD + na, errFlag));
+        PM_CUDA(cudaMemsetAsync(nverD + 2 * na, 0, 8 * sizeof(int), st));
+        {
+            BfArgs ba;
+            ba.act = act; ba.na = na; ba.thr = thr; ba.qp32 = qp32; ba.qpiv = qpiv; ba.s = ix->s;
+            ba.meta = ix->leafMeta; ba.off = ix->leafOff; ba.L = L; ba.O32 = ix->O32; ba.X = ix->X; ba.Qd = Qd;
+            ba.ld = ld; ba.d = d; ba.leafMu = ix->leafMu; ba.leafRx = ix->leafRx; ba.chunkOff = ix->chunkOff;
+            ba.leafChunk = ix->leafChunk; ba.chunkMu = ix->chunkMu; ba.chunkRx = ix->chunkRx; ba.KP = KP; ba.k = k;
+            ba.inN = inN; ba.inPos = inPos; ba.perm = ix->perm; ba.outIds = oIds; ba.outD = oD; ba.outErr = oE;
+            ba.dk = dk; ba.fp64cnt = fpc; ba.nverOut = nverD; ba.nleafOut = nverD + na; ba.errFlag = errFlag;
+            ba.workCtr = nverD + 2 * na; ba.scratch = bfScratch;
+            ba.dbg = nverD + 2 * na + 1; ba.n = n;
+            PM_LAUNCH("k_bestfirst", st, k_bestfirst<<<bfGrid, BF_THREADS, bsmem, st>>>(ba));
+        }
         PM_CUDA(cudaGetLastError());
         std::vector<double> dkH(na);
         std::vector<int> fpH(na), nvH(na), nlH(na);
@@ -1123,8 +1232,11 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         PM_CUDA(cudaMemcpyAsync(&errH, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
         if (errH) {
-            pm_set_error("internal capacity exceeded (code %d): too many points tied within one FP32 "
-                         "error band", errH);
+            int dbgH[3] = {0, 0, 0};
+            cudaMemcpy(dbgH, nverD + 2 * na + 1, sizeof(dbgH), cudaMemcpyDeviceToHost);
+            pm_set_error("internal error flags %d (index check %d value %d query %d); flags 2, 4, 8, 16, 32, "
+                         "64: more points tied within one FP32 error band than an internal capacity; 128: a "
+                         "staged copy timed out; 256/512: layout capacity", errH, dbgH[0], dbgH[1], dbgH[2]);
             return PMLSH_EINTERNAL;
         }
         // stop rules (Algorithm 2, with the readings of pmlsh.h)
