@@ -25,7 +25,7 @@ WORKLOADS = {
     "c3": dict(n=1_000_000, d=960, clusters=1000, sigma=1.0, aniso=True,
                nq=1000, k=10, c=1.5),
     # closest pairs with 20 planted near-duplicate pairs at distance 0.01
-    "c4": dict(n=100_000, d=512, clusters=500, sigma=1.0, planted=20,
+    "c4": dict(n=100_000, d=512, clusters=500, sigma=1.0, n_planted=20,
                planted_dist=0.01, k=10, c=1.5),
     # serving data set
     "c5": dict(n=2_000_000, d=256, clusters=2000, sigma=1.0, nq=4096, k=10,
@@ -105,8 +105,8 @@ def workload(name, seed=0, n=None, nq=None):
     X, Q, _, _ = mixture(w["n"], w["d"], w["clusters"], w.get("sigma", 1.0),
                          seed=seed, nq=w.get("nq", 0), aniso=w.get("aniso", False))
     planted = None
-    if w.get("planted"):
-        planted = plant_pairs(X, w["planted"], w["planted_dist"], seed=seed)
+    if w.get("n_planted"):
+        planted = plant_pairs(X, w["n_planted"], w["planted_dist"], seed=seed)
     return dict(X=X, Q=Q, planted=planted, **w)
 
 

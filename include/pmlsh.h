@@ -213,6 +213,50 @@ pmlsh_status pmlsh_knn(pmlsh_index *index, const float *Q, int64_t nq,
                        float *out_dists, float *out_err,
                        pmlsh_query_stats *stats, void *stream);
 
+/* ---------------------------------------------------- (c,k)-ACP query */
+
+typedef struct {
+    int k;            /* closest pairs to return, 1..min(n(n-1)/2, 1024) */
+    double c;         /* approximation ratio c > 1 (Definition 4) */
+    double alpha1;    /* Lemma 4; default 1/e; gives t by Eq. 9 when t <= 0 */
+    double alpha2;    /* budget fraction: T = ceil(alpha2 n (n-1)) + k when
+                         T <= 0; default 0.0024 (Sec. 7.1) */
+    int64_t T;        /* candidate-pair budget of Algorithm 4; <= 0: from alpha2 */
+    double gamma;     /* radius-filter factor (Sec. 6.3), > 0, may be +inf */
+    double t;         /* projected radius factor; <= 0: from alpha1 (Eq. 9) */
+} pmlsh_cp_opts;
+
+void pmlsh_cp_opts_default(pmlsh_cp_opts *o);
+
+typedef struct {
+    int64_t count;       /* verified pairs (Algorithm 4's count) */
+    double ub_self;      /* k-th distance after the leaf self-joins */
+    int64_t lca_nodes;   /* nodes returned by FindLCA */
+    int64_t nodes_done;  /* of those, nodes examined before count > T */
+    int64_t self_pairs;  /* pairs inside leaves */
+    int64_t fp64_checks; /* projected-distance decisions re-taken in FP64 */
+    double t;            /* t used */
+    int64_t T;           /* T used */
+} pmlsh_cp_stats;
+
+/* Algorithm 4 (radius filtering) with FindLCA (Algorithm 5) over the index's
+ * leaf hierarchy (pmlsh_export_layout): every pair inside a leaf is verified
+ * (count = their number, ub = k-th distance); R = gamma t ub; the maximal
+ * inner nodes with ball radius < R (FP64 bounding-box-midpoint balls of the
+ * projected points) are taken in ascending (radius, node id); for each, the
+ * pairs of its subtree that lie in different leaves and have projected
+ * distance < t ub (ub as the node starts) are verified, keeping only the
+ * T + 1 - count smallest by (projected distance, i, j) if count would pass
+ * T; ub is updated after each node; the loop ends once count > T.
+ * Outputs (host or device): out_pairs [k][2] original ids (i < j),
+ * out_dists [k] FP32 (FP64 distance rounded), stats or NULL.  Pairs sorted
+ * by (distance, i, j); missing entries are -1 / +inf.
+ * Errors: EINVAL (k, gamma, alpha), ENOMEM, ECUDA, EINTERNAL (more than 4096
+ * pairs tied inside one FP32 error band). */
+pmlsh_status pmlsh_closest_pair(pmlsh_index *index, const pmlsh_cp_opts *opts,
+                                int64_t *out_pairs, float *out_dists,
+                                pmlsh_cp_stats *stats, void *stream);
+
 /* ------------------------------------------------------------- profiling */
 
 /* Turns per-kernel timing on (1) or off (0), process-wide.  While on, every

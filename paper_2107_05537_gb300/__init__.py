@@ -43,6 +43,19 @@ class KnnOpts(ctypes.Structure):
                 ("stop_rule", ctypes.c_int)]
 
 
+class CpOpts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("c", ctypes.c_double), ("alpha1", ctypes.c_double),
+                ("alpha2", ctypes.c_double), ("T", ctypes.c_int64), ("gamma", ctypes.c_double),
+                ("t", ctypes.c_double)]
+
+
+class CpStats(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("ub_self", ctypes.c_double),
+                ("lca_nodes", ctypes.c_int64), ("nodes_done", ctypes.c_int64),
+                ("self_pairs", ctypes.c_int64), ("fp64_checks", ctypes.c_int64),
+                ("t", ctypes.c_double), ("T", ctypes.c_int64)]
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("n_cand", ctypes.c_int64), ("r_final", ctypes.c_double),
@@ -66,6 +79,8 @@ _SIGS = {
     "pmlsh_project_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_knn_opts_default": (None, [_P]),
     "pmlsh_knn": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_cp_opts_default": (None, [_P]),
+    "pmlsh_closest_pair": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pmlsh_profile": (ctypes.c_int, [ctypes.c_int]),
     "pmlsh_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
     "pmlsh_launch_count": (ctypes.c_longlong, []),
@@ -230,6 +245,20 @@ class Index:
             p64, p32 = o64.ctypes.data_as(ctypes.c_void_p), o32.ctypes.data_as(ctypes.c_void_p)
         _check(lib().pmlsh_project(self._h, qp, nq, p64, p32, _stream()))
         return o64, o32
+
+    def closest_pairs(self, k=10, c=1.5, alpha1=1 / math.e, alpha2=0.0024, T=0, gamma=3.0, t=0.0):
+        """Algorithm 4.  Returns dict(pairs [k,2] int64, dists [k] f32, stats)."""
+        o = CpOpts()
+        lib().pmlsh_cp_opts_default(ctypes.byref(o))
+        o.k, o.c, o.alpha1, o.alpha2, o.T, o.gamma, o.t = k, c, alpha1, alpha2, T, gamma, t
+        pairs = np.empty((k, 2), dtype=np.int64)
+        dists = np.empty(k, dtype=np.float32)
+        st = CpStats()
+        _check(lib().pmlsh_closest_pair(self._h, ctypes.byref(o), pairs.ctypes.data_as(ctypes.c_void_p),
+                                        dists.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st),
+                                        _stream()))
+        return dict(pairs=pairs, dists=dists,
+                    stats={f: getattr(st, f) for f, _ in CpStats._fields_})
 
     def knn(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
             precision=PMLSH_FP32_PLAIN, stop_rule=STOP_LITERAL, t=0.0, out=None,

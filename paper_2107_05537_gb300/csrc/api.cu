@@ -210,6 +210,34 @@ pmlsh_status pmlsh_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_
     return pm_knn(ix, Q, nq, &o, out_ids, out_dists, out_err, stats, (cudaStream_t)stream);
 }
 
+void pmlsh_cp_opts_default(pmlsh_cp_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->k = 10;
+    o->c = 1.5;
+    o->alpha1 = 0.36787944117144233;
+    o->alpha2 = 0.0024;   // Sec. 7.1
+    o->T = 0;
+    o->gamma = 3.0;
+    o->t = 0.0;
+}
+
+pmlsh_status pmlsh_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *opts, int64_t *out_pairs, float *out_dists,
+                                pmlsh_cp_stats *stats, void *stream)
+{
+    PM_CHECK(ix && opts && out_pairs && out_dists, "NULL argument");
+    const pmlsh_cp_opts &o = *opts;
+    const int64_t npairs = ix->n * (ix->n - 1) / 2;
+    PM_CHECK(ix->n >= 2, "closest pairs need n >= 2");
+    PM_CHECK(o.k >= 1 && o.k <= 1024 && o.k <= npairs, "k must be in 1..min(n(n-1)/2, 1024) (got %d)", o.k);
+    PM_CHECK(o.c > 1.0, "c must be > 1");
+    PM_CHECK(o.gamma > 0.0, "gamma must be > 0 (calibration by sampling is not provided)");
+    PM_CHECK(o.t > 0.0 || (o.alpha1 > 0.0 && o.alpha1 < 1.0), "alpha1 must be in (0,1)");
+    PM_CHECK(o.T > 0 || (o.alpha2 > 0.0 && o.alpha2 <= 1.0), "alpha2 must be in (0,1]");
+    return pm_closest_pair(ix, &o, out_pairs, out_dists, stats, (cudaStream_t)stream);
+}
+
 pmlsh_status pmlsh_project(pmlsh_index *ix, const float *Q, int64_t nq, double *out64, float *out32,
                            void *stream)
 {

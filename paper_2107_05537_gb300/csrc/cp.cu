@@ -1,0 +1,545 @@
+// (c,k)-ACP query path: Algorithm 4 (radius filtering) with FindLCA
+// (Algorithm 5) over the index's leaf hierarchy.
+//
+//   k_cp_selfjoin   every pair inside each leaf: FP32 squared distance
+//   k_node_ball     node balls (Sec. 4.1) in FP64, bounding-box midpoint and
+//                   largest distance, the same arithmetic as the oracle
+//   [host]          FindLCA: maximal inner nodes with radius < R = gamma t ub,
+//                   sorted by (radius, node id)
+//   k_cp_node_pairs cross-leaf pairs of a node's subtree with projected
+//                   distance < t ub (FP32 with a proven band, FP64 inside it)
+//   k_pair_*        exact top-k merges: radix select of an FP32 threshold,
+//                   guard set, FP64 distances, sort by (dist, i, j)
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pmlsh_impl.h"
+
+namespace {
+
+constexpr int PAIR_SORT_CAP = 4096;   // guard entries merged in one block
+
+struct PairCand {
+    float key;      // FP32 squared distance (original or projected space)
+    int32_t a, b;   // leaf-order positions, a < b in position order
+};
+
+// All pairs inside leaf l, FP32 squared distance by direct difference
+// (sequential over the row).  One block per leaf.
+__global__ void k_cp_selfjoin(const float *__restrict__ X, int ld, const int64_t *__restrict__ off,
+                              const int64_t *__restrict__ pairOff, PairCand *__restrict__ out)
+{
+    const int64_t l = blockIdx.x;
+    const int64_t p0 = off[l], s = off[l + 1] - p0;
+    const int64_t np = s * (s - 1) / 2;
+    for (int64_t e = threadIdx.x; e < np; e += blockDim.x) {
+        // e -> (i, j), i < j, row-major over the upper triangle
+        int64_t i = 0, rem = e;
+        while (rem >= s - 1 - i) { rem -= s - 1 - i; i++; }
+        const int64_t j = i + 1 + rem;
+        const float *x = X + (p0 + i) * ld, *y = X + (p0 + j) * ld;
+        float acc = 0.f;
+        for (int c = 0; c < ld; c++) {
+            float t = __fsub_rn(x[c], y[c]);
+            acc = __fmaf_rn(t, t, acc);
+        }
+        PairCand pc;
+        pc.key = acc;
+        pc.a = (int32_t)(p0 + i);
+        pc.b = (int32_t)(p0 + j);
+        out[pairOff[l] + e] = pc;
+    }
+}
+
+__device__ __forceinline__ double dmin_warp(double v)
+{
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double dmax_warp(double v)
+{
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Node ball in FP64: centre = midpoint of the bounding box of the node's
+// projected points, radius = largest FP64 distance to it.  One block (256
+// threads) per node.
+__global__ void k_node_ball(const double *__restrict__ O64, const int64_t *__restrict__ posLo,
+                            const int64_t *__restrict__ posHi, int m, double *__restrict__ rad)
+{
+    __shared__ double smn[8][PM_MP], smx[8][PM_MP], sro[PM_MP], srad[8];
+    const int e = blockIdx.x;
+    const int64_t a = posLo[e], b = posHi[e];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = 0; j < PM_MP; j++) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) {
+            double v = O64[p * PM_MP + j];
+            mn = fmin(mn, v);
+            mx = fmax(mx, v);
+        }
+        mn = dmin_warp(mn);
+        mx = dmax_warp(mx);
+        if (lane == 0) { smn[warp][j] = mn; smx[warp][j] = mx; }
+    }
+    __syncthreads();
+    if (threadIdx.x < PM_MP) {
+        int j = threadIdx.x;
+        double mn = smn[0][j], mx = smx[0][j];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            mn = fmin(mn, smn[w][j]);
+            mx = fmax(mx, smx[w][j]);
+        }
+        sro[j] = j < m ? __dmul_rn(0.5, __dadd_rn(mn, mx)) : 0.0;
+    }
+    __syncthreads();
+    double r = 0.0;
+    for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) r = fmax(r, pm_pdist64(O64 + p * PM_MP, sro, m));
+    r = dmax_warp(r);
+    if (lane == 0) srad[warp] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rr = srad[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) rr = fmax(rr, srad[w]);
+        rad[e] = rr;
+    }
+}
+
+// Cross-leaf pairs of positions [lo, hi) whose FP64 projected distance is
+// < Rt (strict, Algorithm 4).  FP32: |sqrt(d'^2_32) - d'_64| <= eps, so
+// d'^2_32 < loT is surely in, > hiT surely out, and the rest is decided in
+// FP64.  Thread per first position a; loops over b > a.
+__global__ void k_cp_node_pairs(const float *__restrict__ O32, const double *__restrict__ O64, int m,
+                                const int32_t *__restrict__ leafOfPos, int64_t lo, int64_t hi, float loT,
+                                float hiT, double Rt, PairCand *__restrict__ out, unsigned long long *cnt,
+                                unsigned long long cap, unsigned long long *fp64n)
+{
+    const int64_t a = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= hi) return;
+    float oa[PM_MP];
+#pragma unroll
+    for (int j = 0; j < PM_MP; j++) oa[j] = O32[a * PM_MP + j];
+    const int la = leafOfPos[a];
+    for (int64_t b = a + 1; b < hi; b++) {
+        if (leafOfPos[b] == la) continue;
+        const float v = pm_pd2_32(oa, O32 + b * PM_MP);
+        bool in = v < loT;
+        if (!in && v <= hiT) {
+            atomicAdd(fp64n, 1ull);
+            in = pm_pdist64(O64 + a * PM_MP, O64 + b * PM_MP, m) < Rt;
+        }
+        if (in) {
+            unsigned long long slot = atomicAdd(cnt, 1ull);
+            if (slot < cap) {
+                PairCand pc;
+                pc.key = v;
+                pc.a = (int32_t)a;
+                pc.b = (int32_t)b;
+                out[slot] = pc;
+            }
+        }
+    }
+}
+
+// Original-space FP32 squared distances of candidate pairs (overwrites key).
+__global__ void k_pair_dist32(const float *__restrict__ X, int ld, PairCand *__restrict__ p, int64_t n)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float *x = X + (int64_t)p[e].a * ld, *y = X + (int64_t)p[e].b * ld;
+    float acc = 0.f;
+    for (int c = 0; c < ld; c++) {
+        float t = __fsub_rn(x[c], y[c]);
+        acc = __fmaf_rn(t, t, acc);
+    }
+    p[e].key = acc;
+}
+
+// Histogram of key bits [sh, sh+w) among keys whose bits above sh+w equal
+// `prefix` (radix select pass over a global buffer).
+__global__ void k_pair_hist(const PairCand *__restrict__ p, int64_t n, int sh, int w, unsigned int hiMask,
+                            unsigned int prefix, unsigned int *__restrict__ hist)
+{
+    __shared__ unsigned int h[2048];
+    for (int i = threadIdx.x; i < (1 << w); i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        unsigned int k = __float_as_uint(p[e].key);
+        if ((k & hiMask) == (prefix & hiMask)) atomicAdd(&h[(k >> sh) & ((1u << w) - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (1 << w); i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// Entries with key <= thr, appended to `out` with FP64 distance (original or
+// projected space) and original ids (i < j).
+struct PairExact {
+    double dist;
+    int64_t i, j;
+    int32_t a, b;   // positions
+};
+
+__global__ void k_pair_collect(const PairCand *__restrict__ p, int64_t n, float thr, const float *__restrict__ X,
+                               int ld, int d, const double *__restrict__ O64, int m, int useProj,
+                               const int32_t *__restrict__ perm, PairExact *__restrict__ out,
+                               unsigned long long *cnt, unsigned long long cap)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const PairCand c = p[e];
+    if (!(c.key <= thr)) return;
+    unsigned long long slot = atomicAdd(cnt, 1ull);
+    if (slot >= cap) return;
+    PairExact x;
+    x.dist = useProj ? pm_pdist64(O64 + (int64_t)c.a * PM_MP, O64 + (int64_t)c.b * PM_MP, m)
+                     : pm_dist64(X + (int64_t)c.a * ld, X + (int64_t)c.b * ld, d);
+    int64_t ia = perm[c.a], ib = perm[c.b];
+    x.i = ia < ib ? ia : ib;
+    x.j = ia < ib ? ib : ia;
+    x.a = c.a;
+    x.b = c.b;
+    out[slot] = x;
+}
+
+__device__ __forceinline__ bool pe_less(const PairExact &x, const PairExact &y)
+{
+    if (x.dist != y.dist) return x.dist < y.dist;
+    if (x.i != y.i) return x.i < y.i;
+    return x.j < y.j;
+}
+
+// One block: sorts n (<= PAIR_SORT_CAP) entries by (dist, i, j) in place.
+__global__ void k_pair_sort(PairExact *__restrict__ v, int n)
+{
+    extern __shared__ __align__(16) unsigned char psm[];
+    PairExact *s = (PairExact *)psm;
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        if (i < n) s[i] = v[i];
+        else { s[i].dist = INFINITY; s[i].i = 0x7fffffffffffffffLL; s[i].j = 0x7fffffffffffffffLL; s[i].a = s[i].b = -1; }
+    }
+    __syncthreads();
+    for (int k2 = 2; k2 <= P; k2 <<= 1)
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool up = (i & k2) == 0;
+                    if (pe_less(s[ixj], s[i]) == up) {
+                        PairExact t = s[i]; s[i] = s[ixj]; s[ixj] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = s[i];
+}
+
+template <class T> pmlsh_status dalloc(T **p, size_t count)
+{
+    PM_CUDA(cudaMalloc((void **)p, std::max<size_t>(1, count) * sizeof(T)));
+    return PMLSH_OK;
+}
+
+struct DevPtrs {
+    std::vector<void *> ps;
+    ~DevPtrs() { for (void *p : ps) cudaFree(p); }
+    template <class T> pmlsh_status get(T **p, size_t n)
+    {
+        PM_TRY(dalloc(p, n));
+        ps.push_back(*p);
+        return PMLSH_OK;
+    }
+};
+
+// Radix select over a device pair buffer: the rank-th smallest FP32 key
+// (1-based).  Three passes of 11/11/10 bits.
+pmlsh_status pair_kth(const PairCand *p, int64_t n, int64_t rank, unsigned int *hist, float *out, cudaStream_t st)
+{
+    unsigned int prefix = 0;
+    int64_t need = rank;
+    const int shifts[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+    std::vector<unsigned int> hh(2048);
+    for (int pass = 0; pass < 3; pass++) {
+        const int sh = shifts[pass], w = widths[pass];
+        const unsigned int hiMask = pass == 0 ? 0u : (0xffffffffu << (sh + w));
+        PM_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 2048, st));
+        int grid = (int)std::min<int64_t>(1024, (n + 255) / 256);
+        PM_LAUNCH("k_pair_hist", st, k_pair_hist<<<std::max(1, grid), 256, 0, st>>>(p, n, sh, w, hiMask, prefix, hist));
+        PM_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(unsigned int) * (1u << w), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        int64_t acc = 0;
+        int bin = 0;
+        for (; bin < (1 << w); bin++) {
+            if (acc + (int64_t)hh[bin] >= need) break;
+            acc += hh[bin];
+        }
+        need -= acc;
+        prefix |= (unsigned int)bin << sh;
+    }
+    float f;
+    std::memcpy(&f, &prefix, sizeof(f));
+    *out = f;
+    return PMLSH_OK;
+}
+
+// Exact top-k merge: the current list `top` (sorted by (dist, i, j), FP64
+// distances, size kc <= k) and the candidate buffer p[0, n) with FP32
+// original-space squared distances.  A candidate can enter only if its FP32
+// value is <= min(K32 (1 + 3 eps_v), D_k^2 (1 + 3 eps_v)) (K32: k-th smallest
+// FP32 candidate value, D_k: current k-th distance); those are recomputed in
+// FP64 and sorted with the current list.
+struct TopK {
+    std::vector<PairExact> v;   // host copy, sorted
+};
+
+pmlsh_status pair_merge(TopK &top, int k, const PairCand *p, int64_t n, const pmlsh_index *ix, unsigned int *hist,
+                        PairExact *scratch, unsigned long long *cnt, cudaStream_t st)
+{
+    if (n <= 0) return PMLSH_OK;
+    const double epsv = (double)(ix->ld + 8) * 0x1.0p-24;
+    double thr = INFINITY;
+    if (n >= k) {
+        float K32;
+        PM_TRY(pair_kth(p, n, k, hist, &K32, st));
+        thr = (double)K32 * (1.0 + 3.0 * epsv) + 1e-36;
+    }
+    if ((int)top.v.size() >= k) {
+        double Dk = top.v[k - 1].dist;
+        thr = std::min(thr, Dk * Dk * (1.0 + 3.0 * epsv) + 1e-36);
+    }
+    float thr32 = std::isinf(thr) ? INFINITY : (float)thr;
+    if (!std::isinf(thr) && (double)thr32 < thr) thr32 = nextafterf(thr32, INFINITY);
+    PM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    const unsigned long long cap = PAIR_SORT_CAP - (unsigned long long)top.v.size();
+    PM_LAUNCH("k_pair_collect", st, k_pair_collect<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        p, n, thr32, ix->X, ix->ld, ix->d, ix->O64, ix->m, 0, ix->perm, scratch + top.v.size(), cnt, cap));
+    PM_CUDA(cudaGetLastError());
+    unsigned long long got = 0;
+    PM_CUDA(cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    if (got > cap) {
+        pm_set_error("closest pairs: %llu candidates tied inside the FP32 guard band (capacity %llu)", got, cap);
+        return PMLSH_EINTERNAL;
+    }
+    const int tot = (int)(top.v.size() + got);
+    if (!top.v.empty())
+        PM_CUDA(cudaMemcpyAsync(scratch, top.v.data(), top.v.size() * sizeof(PairExact), cudaMemcpyHostToDevice, st));
+    int P = 1;
+    while (P < tot) P <<= 1;
+    PM_LAUNCH("k_pair_sort", st, k_pair_sort<<<1, 1024, (size_t)P * sizeof(PairExact), st>>>(scratch, tot));
+    PM_CUDA(cudaGetLastError());
+    const int keep = std::min(tot, k);
+    top.v.resize(keep);
+    PM_CUDA(cudaMemcpyAsync(top.v.data(), scratch, keep * sizeof(PairExact), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    return PMLSH_OK;
+}
+
+// Keeps the `need` candidates with the smallest (FP64 projected distance,
+// i, j) of p[0, n) (the count > T cut of Algorithm 4).
+pmlsh_status pair_truncate(PairCand *p, int64_t n, int64_t need, const pmlsh_index *ix, unsigned int *hist,
+                           PairExact *scratch, unsigned long long *cnt, int64_t *nOut, cudaStream_t st)
+{
+    if (need >= n) { *nOut = n; return PMLSH_OK; }
+    if (need <= 0) { *nOut = 0; return PMLSH_OK; }
+    // FP32 projected keys: |sqrt(key) - d'_64| <= eps(d'); select the need-th
+    // and resolve the band around it in FP64
+    float K;
+    PM_TRY(pair_kth(p, n, need, hist, &K, st));
+    const double tau = std::sqrt((double)K);
+    const double eps = 0x1.0p-22 * ix->maxNorm + 0x1.0p-19 * tau + 1e-300;
+    const float hiK = (float)((tau + 2 * eps) * (tau + 2 * eps));
+    PM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    PM_LAUNCH("k_pair_collect", st, k_pair_collect<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        p, n, nextafterf(hiK, INFINITY), ix->X, ix->ld, ix->d, ix->O64, ix->m, 1, ix->perm, scratch, cnt,
+        PAIR_SORT_CAP));
+    unsigned long long got = 0;
+    PM_CUDA(cudaMemcpyAsync(&got, cnt, sizeof(got), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    if (got > PAIR_SORT_CAP) {
+        pm_set_error("closest pairs: %llu candidates tied at the count > T cut (capacity %d)", got, PAIR_SORT_CAP);
+        return PMLSH_EINTERNAL;
+    }
+    int P = 1;
+    while (P < (int)got) P <<= 1;
+    PM_LAUNCH("k_pair_sort", st, k_pair_sort<<<1, 1024, (size_t)P * sizeof(PairExact), st>>>(scratch, (int)got));
+    std::vector<PairExact> v(got);
+    PM_CUDA(cudaMemcpyAsync(v.data(), scratch, got * sizeof(PairExact), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    const int64_t keep = std::min<int64_t>(need, (int64_t)got);
+    std::vector<PairCand> kept(keep);
+    for (int64_t e = 0; e < keep; e++) {
+        kept[e].key = 0.f;
+        kept[e].a = v[e].a;
+        kept[e].b = v[e].b;
+    }
+    PM_CUDA(cudaMemcpyAsync(p, kept.data(), keep * sizeof(PairCand), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    *nOut = keep;
+    return PMLSH_OK;
+}
+
+}  // namespace
+
+pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
+                             pmlsh_cp_stats *stats, cudaStream_t st)
+{
+    const int64_t n = ix->n, L = ix->L;
+    const int k = o->k;
+    const double t = o->t > 0.0 ? o->t : std::sqrt(pm_chi2_upper_quantile(o->alpha1, ix->m));
+    const double gamma = o->gamma;
+    const int64_t T = o->T > 0 ? o->T : (int64_t)std::ceil(o->alpha2 * (double)n * (double)(n - 1) - 1e-9) + k;
+    DevPtrs mem;
+    // 1. self-join of every leaf
+    std::vector<int64_t> pairOff(L + 1, 0);
+    for (int64_t l = 0; l < L; l++) {
+        int64_t s = ix->leafOffH[l + 1] - ix->leafOffH[l];
+        pairOff[l + 1] = pairOff[l] + s * (s - 1) / 2;
+    }
+    const int64_t nSelf = pairOff[L];
+    int64_t *dPairOff;
+    PairCand *pairs;
+    unsigned int *hist;
+    PairExact *scratch;
+    unsigned long long *cnt;
+    PM_TRY(mem.get(&dPairOff, L + 1));
+    PM_TRY(mem.get(&pairs, (size_t)std::max<int64_t>(nSelf, 1)));
+    PM_TRY(mem.get(&hist, 2048));
+    PM_TRY(mem.get(&scratch, PAIR_SORT_CAP));
+    PM_TRY(mem.get(&cnt, 4));
+    PM_CUDA(cudaMemcpyAsync(dPairOff, pairOff.data(), (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaFuncSetAttribute(k_pair_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(PAIR_SORT_CAP * sizeof(PairExact))));
+    if (nSelf > 0) {
+        PM_LAUNCH("k_cp_selfjoin", st, k_cp_selfjoin<<<(unsigned)L, 128, 0, st>>>(ix->X, ix->ld, ix->leafOff, dPairOff, pairs));
+        PM_CUDA(cudaGetLastError());
+    }
+    TopK top;
+    PM_TRY(pair_merge(top, k, pairs, nSelf, ix, hist, scratch, cnt, st));
+    int64_t count = nSelf;
+    double ub = (int)top.v.size() >= k ? top.v[k - 1].dist : INFINITY;
+    const double ubSelf = ub;
+    const double R = gamma * t * ub;
+    // 2. node balls (FP64) and FindLCA (Algorithm 5) over the hierarchy
+    const int64_t N = (int64_t)ix->nodeLo.size();
+    std::vector<int64_t> pLo(N), pHi(N);
+    for (int64_t e = 0; e < N; e++) {
+        pLo[e] = ix->leafOffH[ix->nodeLo[e]];
+        pHi[e] = ix->leafOffH[ix->nodeHi[e]];
+    }
+    int64_t *dLo, *dHi;
+    double *dRad;
+    PM_TRY(mem.get(&dLo, N));
+    PM_TRY(mem.get(&dHi, N));
+    PM_TRY(mem.get(&dRad, N));
+    PM_CUDA(cudaMemcpyAsync(dLo, pLo.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemcpyAsync(dHi, pHi.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_LAUNCH("k_node_ball", st, k_node_ball<<<(unsigned)N, 256, 0, st>>>(ix->O64, dLo, dHi, ix->m, dRad));
+    PM_CUDA(cudaGetLastError());
+    std::vector<double> rad(N);
+    PM_CUDA(cudaMemcpyAsync(rad.data(), dRad, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    std::vector<int64_t> A;
+    {
+        std::vector<int64_t> stack{0};
+        while (!stack.empty()) {
+            int64_t e = stack.back();
+            stack.pop_back();
+            if (ix->nodeLeft[e] < 0) continue;             // leaf nodes are never inserted
+            if (rad[e] < R) { A.push_back(e); continue; }
+            stack.push_back(ix->nodeRight[e]);             // visit left first (order is irrelevant:
+            stack.push_back(ix->nodeLeft[e]);              // A is sorted below)
+        }
+        std::sort(A.begin(), A.end(), [&rad](int64_t x, int64_t y) { return rad[x] < rad[y] || (rad[x] == rad[y] && x < y); });
+    }
+    // leaf of each position
+    int32_t *dLeafOf;
+    PM_TRY(mem.get(&dLeafOf, n));
+    {
+        std::vector<int32_t> lof(n);
+        for (int64_t l = 0; l < L; l++)
+            for (int64_t p = ix->leafOffH[l]; p < ix->leafOffH[l + 1]; p++) lof[p] = (int32_t)l;
+        PM_CUDA(cudaMemcpyAsync(dLeafOf, lof.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    // 3. nodes in ascending radius while count <= T
+    int64_t nodesDone = 0, fp64 = 0;
+    PairCand *cand = nullptr;
+    size_t candCap = 0;
+    for (size_t ai = 0; ai < A.size() && count <= T; ai++) {
+        const int64_t e = A[ai];
+        const int64_t lo = pLo[e], hi = pHi[e];
+        const double Rt = t * ub;
+        int64_t ncand = 0;
+        for (int attempt = 0; attempt < 2; attempt++) {
+            if (!cand) {
+                candCap = std::max<size_t>(candCap, (size_t)1 << 20);
+                PM_TRY(mem.get(&cand, candCap));
+            }
+            PM_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+            float loT = -1.f, hiT = INFINITY;
+            if (!std::isinf(Rt)) {
+                const double eps = 0x1.0p-22 * ix->maxNorm + 0x1.0p-19 * Rt + 1e-300;
+                loT = Rt - eps > 0 ? (float)((Rt - eps) * (Rt - eps)) : -1.f;
+                if ((double)loT > (Rt - eps) * (Rt - eps)) loT = nextafterf(loT, -INFINITY);
+                hiT = (float)((Rt + eps) * (Rt + eps));
+                if ((double)hiT < (Rt + eps) * (Rt + eps)) hiT = nextafterf(hiT, INFINITY);
+            } else {
+                loT = INFINITY;   // every pair is a candidate
+                hiT = INFINITY;
+            }
+            PM_LAUNCH("k_cp_node_pairs", st, k_cp_node_pairs<<<(unsigned)((hi - lo + 127) / 128), 128, 0, st>>>(
+                ix->O32, ix->O64, ix->m, dLeafOf, lo, hi, loT, hiT, Rt, cand, cnt, candCap, cnt + 1));
+            PM_CUDA(cudaGetLastError());
+            unsigned long long hc[2];
+            PM_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaStreamSynchronize(st));
+            fp64 += (int64_t)hc[1];
+            if (hc[0] <= candCap) { ncand = (int64_t)hc[0]; break; }
+            // grow and redo this node
+            candCap = (size_t)hc[0];
+            cand = nullptr;
+            if (attempt == 1) {
+                pm_set_error("closest pairs: candidate buffer growth failed");
+                return PMLSH_EINTERNAL;
+            }
+        }
+        int64_t keep = ncand;
+        if (count + ncand > T) PM_TRY(pair_truncate(cand, ncand, T + 1 - count, ix, hist, scratch, cnt, &keep, st));
+        if (keep > 0) {
+            PM_LAUNCH("k_pair_dist32", st, k_pair_dist32<<<(unsigned)((keep + 255) / 256), 256, 0, st>>>(ix->X, ix->ld, cand, keep));
+            PM_TRY(pair_merge(top, k, cand, keep, ix, hist, scratch, cnt, st));
+        }
+        count += keep;
+        ub = (int)top.v.size() >= k ? top.v[k - 1].dist : INFINITY;
+        nodesDone++;
+    }
+    // results
+    std::vector<int64_t> op((size_t)2 * k, -1);
+    std::vector<float> od(k, INFINITY);
+    for (int e = 0; e < k && e < (int)top.v.size(); e++) {
+        op[2 * e] = top.v[e].i;
+        op[2 * e + 1] = top.v[e].j;
+        od[e] = (float)top.v[e].dist;
+    }
+    PM_CUDA(cudaMemcpy(out_pairs, op.data(), op.size() * sizeof(int64_t),
+                       pm_is_device_ptr(out_pairs) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    PM_CUDA(cudaMemcpy(out_dists, od.data(), od.size() * sizeof(float),
+                       pm_is_device_ptr(out_dists) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    if (stats) {
+        stats->count = count;
+        stats->ub_self = ubSelf;
+        stats->lca_nodes = (int64_t)A.size();
+        stats->nodes_done = nodesDone;
+        stats->self_pairs = nSelf;
+        stats->fp64_checks = fp64;
+        stats->t = t;
+        stats->T = T;
+    }
+    return PMLSH_OK;
+}

@@ -130,6 +130,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq,
                     const pmlsh_knn_opts *o, int64_t *ids, float *dists,
                     float *err, pmlsh_query_stats *stats, cudaStream_t st);
 
+// Closest pairs (cp.cu)
+pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
+                             pmlsh_cp_stats *stats, cudaStream_t st);
+
 // Parameters (params.cpp)
 double pm_chi2_sf(double x, int m);
 double pm_chi2_upper_quantile(double alpha, int m);

@@ -356,12 +356,13 @@ def _bisect_layout(X, leaf):
 
 
 def test_cp_all_pairs_budget_is_exact_kcp():
-    # T >= n(n-1)/2 and gamma = inf: every cross-leaf pair is examined, so the
-    # answer is the exact k closest pairs (the NLJ result).
+    # T >= n(n-1)/2, gamma = inf and a t so large that every pair passes the
+    # projected filter: every cross-leaf pair is examined, so the answer is
+    # the exact k closest pairs (the NLJ result).
     X = datagen.gaussian(150, 6, seed=5)
     A = oracle.gen_projection(3, 4, 6).astype(np.float32)
     lay = _bisect_layout(X, 8)
-    r = oracle.cp_radius_filter(X, A, lay, 12, 4.0, math.inf, 150 * 149 // 2)
+    r = oracle.cp_radius_filter(X, A, lay, 12, 1e6, math.inf, 150 * 149 // 2)
     ep, ed = oracle.exact_kcp(X, 12)
     assert r["pairs"].tolist() == ep.tolist()
     assert np.array_equal(r["dists"], ed)
