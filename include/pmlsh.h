@@ -257,6 +257,62 @@ pmlsh_status pmlsh_closest_pair(pmlsh_index *index, const pmlsh_cp_opts *opts,
                                 int64_t *out_pairs, float *out_dists,
                                 pmlsh_cp_stats *stats, void *stream);
 
+/* ------------------------------------------------------------- serving */
+
+/* Continuous batching over one resident index.  `slots` worker threads, each
+ * with its own CUDA stream and scratch buffers, take the oldest waiting
+ * request plus every later waiting request with identical query options (up
+ * to max_batch_queries rows and within mem_budget_bytes of estimated device
+ * scratch; a batch over the budget runs alone) and run them as one
+ * pmlsh_knn batch, so requests that arrive while others run are admitted as
+ * slots and memory free up and their work overlaps on the device.  Each
+ * request's results equal pmlsh_knn's on that request alone. */
+typedef struct pmlsh_server pmlsh_server;
+
+typedef struct {
+    int slots;                  /* concurrent batches (streams); default 3 */
+    int64_t max_batch_queries;  /* rows per batch; default 16384 */
+    int64_t mem_budget_bytes;   /* device scratch across slots; default 8 GiB */
+} pmlsh_serve_opts;
+
+typedef struct {
+    int64_t submitted, completed, queries, batches;
+    int64_t deferred;     /* times a slot waited for memory */
+    int64_t canceled;     /* requests cancelled by pmlsh_serve_stop */
+    int64_t queue_depth;  /* requests waiting now */
+    double p50_ms, p99_ms, mean_ms;  /* submit -> completion latency */
+    double qps;           /* queries / (last completion - first submission) */
+} pmlsh_server_stats;
+
+void pmlsh_serve_opts_default(pmlsh_serve_opts *o);
+
+/* Starts the worker threads on the current device.  The index must outlive
+ * the server.  Errors: EINVAL, ENOMEM. */
+pmlsh_status pmlsh_serve_create(pmlsh_index *index, const pmlsh_serve_opts *opts,
+                                pmlsh_server **out);
+
+/* Queues Q [nq][d] (host memory, copied before return) with `opts` and
+ * returns a ticket.  Errors: EINVAL (options as pmlsh_knn, nq < 1, device
+ * pointer), ENOMEM, ECANCELED (server stopping). */
+pmlsh_status pmlsh_serve_submit(pmlsh_server *s, const float *Q, int64_t nq,
+                                const pmlsh_knn_opts *opts, uint64_t *ticket);
+
+/* Waits up to timeout_ms (< 0: no limit) for the ticket and copies its
+ * results to host buffers ids [nq][k], dists [nq][k].  ETIMEOUT leaves the
+ * ticket valid; any other return consumes it.  ECANCELED: cancelled by
+ * pmlsh_serve_stop.  The query path's own errors are passed through. */
+pmlsh_status pmlsh_serve_wait(pmlsh_server *s, uint64_t ticket, int64_t *ids,
+                              float *dists, int timeout_ms);
+
+/* Stops accepting requests, cancels the ones not yet started (their waits
+ * return ECANCELED), lets running batches finish, joins the workers. */
+pmlsh_status pmlsh_serve_stop(pmlsh_server *s);
+
+pmlsh_status pmlsh_serve_stats(pmlsh_server *s, pmlsh_server_stats *out);
+
+/* pmlsh_serve_stop, then frees the server. */
+pmlsh_status pmlsh_serve_destroy(pmlsh_server *s);
+
 /* ------------------------------------------------------------- profiling */
 
 /* Turns per-kernel timing on (1) or off (0), process-wide.  While on, every

@@ -56,6 +56,17 @@ class CpStats(ctypes.Structure):
                 ("t", ctypes.c_double), ("T", ctypes.c_int64)]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_batch_queries", ctypes.c_int64),
+                ("mem_budget_bytes", ctypes.c_int64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "queries", "batches",
+                                               "deferred", "canceled", "queue_depth")] + \
+               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "qps")]
+
+
 class QueryStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("n_cand", ctypes.c_int64), ("r_final", ctypes.c_double),
@@ -81,6 +92,13 @@ _SIGS = {
     "pmlsh_knn": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
     "pmlsh_cp_opts_default": (None, [_P]),
     "pmlsh_closest_pair": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "pmlsh_serve_opts_default": (None, [_P]),
+    "pmlsh_serve_create": (ctypes.c_int, [_P, _P, _P]),
+    "pmlsh_serve_submit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "pmlsh_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int]),
+    "pmlsh_serve_stop": (ctypes.c_int, [_P]),
+    "pmlsh_serve_stats": (ctypes.c_int, [_P, _P]),
+    "pmlsh_serve_destroy": (ctypes.c_int, [_P]),
     "pmlsh_profile": (ctypes.c_int, [ctypes.c_int]),
     "pmlsh_profile_read": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
     "pmlsh_launch_count": (ctypes.c_longlong, []),
@@ -306,3 +324,58 @@ class Index:
                 nver=np.array([s.n_verified for s in stats[:nq]], dtype=np.int64),
                 leaves=np.array([s.leaves_visited for s in stats[:nq]], dtype=np.int32))
         return res
+
+
+class Server:
+    """Continuous-batching server over an Index (see pmlsh_serve_* in pmlsh.h)."""
+
+    def __init__(self, index, slots=3, max_batch_queries=16384, mem_budget_bytes=8 << 30):
+        L = lib()
+        o = ServeOpts()
+        L.pmlsh_serve_opts_default(ctypes.byref(o))
+        o.slots, o.max_batch_queries, o.mem_budget_bytes = slots, max_batch_queries, mem_budget_bytes
+        h = ctypes.c_void_p()
+        _check(L.pmlsh_serve_create(index._h, ctypes.byref(o), ctypes.byref(h)))
+        self._h, self.index, self._k = h, index, {}
+
+    def submit(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
+               stop_rule=STOP_LITERAL, t=0.0):
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        o = KnnOpts()
+        lib().pmlsh_knn_opts_default(ctypes.byref(o))
+        o.k, o.c, o.alpha1, o.beta, o.r_min, o.stop_rule, o.t = k, c, alpha1, beta, r_min, stop_rule, t
+        tk = ctypes.c_uint64()
+        _check(lib().pmlsh_serve_submit(self._h, Q.ctypes.data_as(ctypes.c_void_p), Q.shape[0],
+                                        ctypes.byref(o), ctypes.byref(tk)))
+        self._k[tk.value] = (Q.shape[0], k)
+        return tk.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        nq, k = self._k.get(ticket, (1, 1))
+        ids = np.empty((nq, k), dtype=np.int64)
+        dd = np.empty((nq, k), dtype=np.float32)
+        rc = lib().pmlsh_serve_wait(self._h, ticket, ids.ctypes.data_as(ctypes.c_void_p),
+                                    dd.ctypes.data_as(ctypes.c_void_p), int(timeout_ms))
+        if rc != 3:
+            self._k.pop(ticket, None)
+        _check(rc)
+        return ids, dd
+
+    def stats(self):
+        s = ServeStats()
+        _check(lib().pmlsh_serve_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServeStats._fields_}
+
+    def stop(self):
+        _check(lib().pmlsh_serve_stop(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pmlsh_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

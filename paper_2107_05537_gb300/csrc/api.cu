@@ -32,6 +32,26 @@ bool pm_is_device_ptr(const void *p)
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+pmlsh_status pm_allow_max_dyn_smem(const void *func)
+{
+    cudaFuncAttributes fa;
+    PM_CUDA(cudaFuncGetAttributes(&fa, func));
+    const int v = pm_max_smem_optin() - (int)fa.sharedSizeBytes;
+    PM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    return PMLSH_OK;
+}
+
+int pm_max_smem_optin()
+{
+    int dev = 0, v = 48 * 1024;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        v = 48 * 1024;
+    }
+    return v;
+}
+
 #define PM_CHECK(cond, ...)                                                    \
     do {                                                                       \
         if (!(cond)) {                                                         \

@@ -642,7 +642,11 @@ void pm_free_index(pmlsh_index *ix)
     cudaFree(ix->leafChunk);
     cudaFree(ix->chunkMu);
     cudaFree(ix->chunkRx);
-    KnnWork &w = ix->work;
+    pm_release_work(ix->work);
+}
+
+void pm_release_work(KnnWork &w)
+{
     DevBuf *bufs[] = {&w.Qd, &w.qp32, &w.qp64, &w.qnorm, &w.qpiv, &w.order, &w.keys,
                       &w.keys2, &w.vals2, &w.sortTmp, &w.qstate, &w.thr, &w.blkCnt,
                       &w.blkLeaves, &w.cntSure, &w.cntBand, &w.bandQ, &w.bandPos,

@@ -414,8 +414,7 @@ pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *o
     PM_TRY(mem.get(&scratch, PAIR_SORT_CAP));
     PM_TRY(mem.get(&cnt, 4));
     PM_CUDA(cudaMemcpyAsync(dPairOff, pairOff.data(), (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    PM_CUDA(cudaFuncSetAttribute(k_pair_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(PAIR_SORT_CAP * sizeof(PairExact))));
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_pair_sort));
     if (nSelf > 0) {
         PM_LAUNCH("k_cp_selfjoin", st, k_cp_selfjoin<<<(unsigned)L, 128, 0, st>>>(ix->X, ix->ld, ix->leafOff, dPairOff, pairs));
         PM_CUDA(cudaGetLastError());

@@ -1025,12 +1025,12 @@ pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, 
 
 pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn_opts *o,
                     int64_t *ids, float *dists, float *err, pmlsh_query_stats *stats,
-                    cudaStream_t st)
+                    cudaStream_t st, KnnWork *work)
 {
     const int64_t n = ix->n;
     const int d = ix->d, ld = ix->ld, m = ix->m, k = o->k;
     const int64_t L = ix->L;
-    KnnWork &w = ix->work;
+    KnnWork &w = work ? *work : ix->work;
     // parameters (Eq. 9; budget of Algorithm 2; r_min rule of Sec. 5.2)
     const double t = o->t > 0.0 ? o->t : std::sqrt(pm_chi2_upper_quantile(o->alpha1, m));
     const int64_t B = pmlsh_budget(n, o->beta, k);
@@ -1116,7 +1116,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         pm_set_error("d = %d is too large for the verification kernel's shared memory", d);
         return PMLSH_EINVAL;
     }
-    PM_CUDA(cudaFuncSetAttribute(k_bestfirst, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_bestfirst));
     int bfPerSM = 1;
     PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfPerSM, k_bestfirst, BF_THREADS, bsmem));
     bfPerSM = std::max(1, bfPerSM);

@@ -126,9 +126,14 @@ pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, 
                              double *out64, float *out32, int ostride, cudaStream_t st);
 
 // Query path (knn.cu)
+// `work`: scratch buffers for this call (NULL: the index's own); calls on
+// one index may run concurrently on different streams with different
+// workspaces (the index itself is read-only during queries).
 pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq,
                     const pmlsh_knn_opts *o, int64_t *ids, float *dists,
-                    float *err, pmlsh_query_stats *stats, cudaStream_t st);
+                    float *err, pmlsh_query_stats *stats, cudaStream_t st,
+                    KnnWork *work = nullptr);
+void pm_release_work(KnnWork &w);
 
 // Closest pairs (cp.cu)
 pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
@@ -143,6 +148,14 @@ uint64_t pm_splitmix64(uint64_t seed, uint64_t i);
 void pm_gaussian_projection(uint64_t seed, int m, int d, float *A);
 
 bool pm_is_device_ptr(const void *p);
+
+// Largest shared memory a block may opt in to on the current device.
+int pm_max_smem_optin();
+// Raises `func`'s dynamic shared-memory limit to the largest the device
+// allows next to its static shared memory.  The limit is one setting per
+// function shared by every caller (and every thread), so it is never set to
+// a single call's own need.
+pmlsh_status pm_allow_max_dyn_smem(const void *func);
 
 // Launch bookkeeping (prof.cpp): counts every launch; brackets it with CUDA
 // events while profiling is enabled.

@@ -1,0 +1,117 @@
+"""Continuous-batching server (pmlsh_serve_*): every request's result equals
+pmlsh_knn on that request alone, whether it ran alone or batched with others
+of uneven size and k; timeouts, cancellation and memory admission behave."""
+import math
+import threading
+
+import numpy as np
+import pytest
+
+import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2107_05537_gb300 as pm  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def served():
+    X, Q, _, _ = datagen.mixture(20_000, 64, 40, (0.5, 2.0), seed=11, nq=6000)
+    ix = pm.Index(torch.from_numpy(X).cuda(), leaf_size=128)
+    yield ix, Q
+    ix.close()
+
+
+def _requests(Q, count, seed):
+    rng = np.random.default_rng(seed)
+    reqs, at = [], 0
+    for _ in range(count):
+        size = int(np.exp(rng.uniform(0, math.log(300))))
+        k = int(rng.choice([1, 10, 50]))
+        rows = Q[at % len(Q): at % len(Q) + size]
+        if len(rows) == 0:
+            rows = Q[:size]
+        at += size
+        reqs.append((np.ascontiguousarray(rows), k))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix(served):
+    ix, Q = served
+    reqs = _requests(Q, 48, seed=1)
+    srv = pm.Server(ix, slots=3, max_batch_queries=2048)
+    tickets = [None] * len(reqs)
+
+    def client(part):
+        for i in range(part, len(reqs), 4):
+            tickets[i] = srv.submit(reqs[i][0], k=reqs[i][1])
+    threads = [threading.Thread(target=client, args=(p,)) for p in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    outs = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["queries"] == sum(len(r) for r, _ in reqs)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    for (rows, k), (ids, dd) in zip(reqs, outs):
+        alone = ix.knn(rows, k=k, with_stats=False)
+        assert np.array_equal(ids, alone["ids"])
+        assert np.array_equal(dd, alone["dists"])
+
+
+def test_tiny_memory_budget_runs_batches_one_at_a_time(served):
+    ix, Q = served
+    reqs = _requests(Q, 12, seed=2)
+    srv = pm.Server(ix, slots=3, mem_budget_bytes=1)
+    tickets = [srv.submit(r, k=k) for r, k in reqs]
+    outs = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    for (rows, k), (ids, _) in zip(reqs, outs):
+        assert np.array_equal(ids, ix.knn(rows, k=k, with_stats=False)["ids"])
+
+
+def test_timeout_cancel_and_stop(served):
+    ix, Q = served
+    srv = pm.Server(ix, slots=1, max_batch_queries=64)
+    big = srv.submit(Q[:3000], k=50)
+    smalls = [srv.submit(Q[3000 + 10 * i: 3010 + 10 * i], k=10) for i in range(20)]
+    # an immediate wait either finds the result or times out, leaving the ticket valid
+    try:
+        srv.wait(smalls[-1], timeout_ms=0)
+        waited = True
+    except pm.PmlshError as e:
+        assert e.code == 3   # ETIMEOUT
+        waited = False
+    srv.stop()
+    outcomes = []
+    for t in [big] + smalls[:-1] + ([] if waited else [smalls[-1]]):
+        try:
+            srv.wait(t, timeout_ms=60_000)
+            outcomes.append("ok")
+        except pm.PmlshError as e:
+            assert e.code == 5   # ECANCELED
+            outcomes.append("cancelled")
+    assert "ok" in outcomes   # the running batch finished
+    st = srv.stats()
+    assert st["canceled"] == outcomes.count("cancelled")
+    with pytest.raises(pm.PmlshError) as e:
+        srv.submit(Q[:4], k=1)
+    assert e.value.code == 5
+    srv.close()
+
+
+def test_invalid_requests_rejected(served):
+    ix, Q = served
+    srv = pm.Server(ix, slots=1)
+    with pytest.raises(pm.PmlshError):
+        srv.submit(Q[:4], k=0)
+    with pytest.raises(pm.PmlshError):
+        srv.submit(Q[:4], k=10, c=0.9)
+    with pytest.raises(pm.PmlshError):
+        srv.wait(123456)
+    srv.close()
