@@ -220,7 +220,7 @@ def main():
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     del Xd
-    prec = pm.PMLSH_BF16_RERANK if args.precision == "bf16" else pm.PMLSH_FP32_PLAIN
+    prec = pm.PMLSH_BF16_TENSOR if args.precision == "bf16" else pm.PMLSH_FP32_PLAIN
     Qd = torch.from_numpy(Q).cuda()
     ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
     dd = torch.empty((nq, K), dtype=torch.float32, device="cuda")

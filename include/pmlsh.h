@@ -78,8 +78,9 @@ typedef struct {
                            FP32, host or device; NULL = draw from `seed` */
     int64_t rmin_pairs; /* pairs sampled for the distance distribution F of
                            Sec. 5.2 (r_min rule); 0 = default 10000 */
-    int bf16_shadow;    /* 1 = also keep a BF16 copy of the leaf-centred
-                           points for the BF16_RERANK verification mode */
+    int bf16_shadow;    /* 1 (default) = also keep the tensor-core operand of
+                           the projected points (BF16 hi/lo split, 100 bytes
+                           per point) that PMLSH_BF16_TENSOR needs */
 } pmlsh_build_opts;
 
 /* Fills `o` with the defaults above. */
@@ -161,7 +162,7 @@ pmlsh_status pmlsh_project_noalloc(const pmlsh_index *index, const float *Q,
 
 /* ------------------------------------------------------- (c,k)-ANN query */
 
-enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_RERANK = 1 };
+enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_TENSOR = 1 };
 enum { PMLSH_STOP_LITERAL = 0, PMLSH_STOP_BC_CONSISTENT = 1 };
 
 typedef struct {
@@ -173,8 +174,14 @@ typedef struct {
     double r_min;     /* first radius; <= 0: the Sec. 5.2 rule (r* with
                          F(rstar) = (beta n + k)/n on the sampled distance
                          distribution, r_min = rstar / c) */
-    int precision;    /* PMLSH_FP32_PLAIN or PMLSH_BF16_RERANK; both return
-                         the same ids and distances */
+    int precision;    /* how the range rounds count projected distances:
+                         PMLSH_FP32_PLAIN on the CUDA cores; PMLSH_BF16_TENSOR
+                         on the tensor cores (q'.o' from a three-product
+                         BF16 split, FP32 accumulate), every pair whose
+                         decision that value cannot settle is recomputed
+                         exactly.  Both return the same ids, distances and
+                         statistics.  BF16_TENSOR needs an index built with
+                         bf16_shadow = 1 (else PMLSH_EINVAL) */
     double t;         /* projected radius factor of Lemma 4; <= 0: t from
                          alpha1 by Eq. 9 (t = sqrt(chi^2_{alpha1}(m))) */
     int stop_rule;    /* PMLSH_STOP_LITERAL: stop rule 1 tested at the loop

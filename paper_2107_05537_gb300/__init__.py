@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpmlsh.so")
 
 PMLSH_FP32_PLAIN = 0
-PMLSH_BF16_RERANK = 1
+PMLSH_BF16_TENSOR = 1
 STOP_LITERAL = 0
 STOP_BC_CONSISTENT = 1
 
@@ -191,11 +191,13 @@ def launch_count():
 class Index:
     """A PM-LSH index resident on the current CUDA device."""
 
-    def __init__(self, X, m=15, s=5, leaf_size=256, seed=0, proj=None, rmin_pairs=10000):
+    def __init__(self, X, m=15, s=5, leaf_size=256, seed=0, proj=None, rmin_pairs=10000,
+                 bf16_shadow=True):
         L = lib()
         o = BuildOpts()
         L.pmlsh_build_opts_default(ctypes.byref(o))
         o.m, o.s, o.leaf_size, o.seed, o.rmin_pairs = m, s, leaf_size, seed, rmin_pairs
+        o.bf16_shadow = 1 if bf16_shadow else 0
         keep = []
         if proj is not None:
             pa, pp = _as_f32(proj)

@@ -97,7 +97,7 @@ void pmlsh_build_opts_default(pmlsh_build_opts *o)
     o->seed = 0;
     o->proj = nullptr;
     o->rmin_pairs = 10000;
-    o->bf16_shadow = 0;
+    o->bf16_shadow = 1;
 }
 
 void pmlsh_knn_opts_default(pmlsh_knn_opts *o)
@@ -131,6 +131,7 @@ pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opt
     PM_CHECK(o.leaf_size >= 16 && o.leaf_size <= 1024, "leaf_size must be 0 or 16..1024 (got %d)",
              o.leaf_size);
     PM_CHECK(o.rmin_pairs >= 0, "rmin_pairs must be >= 0");
+    PM_CHECK(o.bf16_shadow == 0 || o.bf16_shadow == 1, "bf16_shadow must be 0 or 1");
     pmlsh_index *ix = new (std::nothrow) pmlsh_index();
     if (!ix) {
         pm_set_error("host allocation failed");
@@ -225,8 +226,10 @@ pmlsh_status pmlsh_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_
     PM_CHECK(std::isfinite(o.t), "t must be finite");
     PM_CHECK(o.stop_rule == PMLSH_STOP_LITERAL || o.stop_rule == PMLSH_STOP_BC_CONSISTENT,
              "unknown stop_rule %d", o.stop_rule);
-    PM_CHECK(o.precision == PMLSH_FP32_PLAIN, "precision mode %d is not available in this build",
-             o.precision);
+    PM_CHECK(o.precision == PMLSH_FP32_PLAIN || o.precision == PMLSH_BF16_TENSOR,
+             "unknown precision mode %d", o.precision);
+    PM_CHECK(o.precision != PMLSH_BF16_TENSOR || ix->Bsplit != nullptr,
+             "PMLSH_BF16_TENSOR needs an index built with bf16_shadow = 1");
     return pm_knn(ix, Q, nq, &o, out_ids, out_dists, out_err, stats, (cudaStream_t)stream);
 }
 

@@ -7,6 +7,8 @@
 #include <cstring>
 #include <numeric>
 
+#include <cuda_bf16.h>
+
 #include "pmlsh_impl.h"
 
 namespace {
@@ -214,6 +216,37 @@ __global__ void k_leaf_orig(const float *__restrict__ X, const int64_t *__restri
         for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = fmax(r, sred[w]);
         r = fmax(r, sred[0]);
         rx[l] = __double2float_ru(r * (1.0 + 1e-6) + 1e-30);
+    }
+}
+
+// Tensor-core operand of the projected points: per point the 48 BF16 values
+// [hi(o') | hi(o') | lo(o')] (hi = o' rounded to BF16, lo = the rest rounded),
+// stored leaf by leaf (each leaf starts at a row that is a multiple of 16,
+// padding rows are zero) in the no-swizzle K-major canonical layout of the
+// tcgen05 matrix descriptor: 8-row x 8-element core matrices of 128 bytes,
+// row group g, K group kg at byte ((g * 6 + kg) * 8 + row % 8) * 16.  Also
+// the FP32 squared norms ||o'||^2 of the FP32 coordinates, same rows.
+__global__ void k_build_bsplit(const float *__restrict__ O32, const int64_t *__restrict__ off,
+                               const int64_t *__restrict__ bOff, int64_t L, uint16_t *__restrict__ B,
+                               float *__restrict__ norms)
+{
+    const int64_t l = blockIdx.x;
+    const int64_t p0 = off[l], s = off[l + 1] - p0, r0 = bOff[l];
+    for (int64_t r = threadIdx.x; r < s; r += blockDim.x) {
+        const float *o = O32 + (p0 + r) * PM_MP;
+        const int64_t R = r0 + r, g = R >> 3, i = R & 7;
+        double nn = 0.0;
+        for (int j = 0; j < PM_MP; j++) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(o[j]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(o[j] - __bfloat162float(hi));
+            const uint16_t hb = __bfloat16_as_ushort(hi), lb = __bfloat16_as_ushort(lo);
+            const int k0 = j, k1 = 16 + j, k2 = 32 + j;
+            B[((g * 6 + (k0 >> 3)) * 8 + i) * 8 + (k0 & 7)] = hb;
+            B[((g * 6 + (k1 >> 3)) * 8 + i) * 8 + (k1 & 7)] = hb;
+            B[((g * 6 + (k2 >> 3)) * 8 + i) * 8 + (k2 & 7)] = lb;
+            nn += (double)o[j] * (double)o[j];
+        }
+        norms[R] = (float)nn;
     }
 }
 
@@ -642,6 +675,9 @@ void pm_free_index(pmlsh_index *ix)
     cudaFree(ix->leafChunk);
     cudaFree(ix->chunkMu);
     cudaFree(ix->chunkRx);
+    cudaFree(ix->bOff);
+    cudaFree(ix->Bsplit);
+    cudaFree(ix->bNorm);
     pm_release_work(ix->work);
 }
 
@@ -862,6 +898,24 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
     PM_TRY(dalloc(&ix->leafRx, (size_t)L));
     PM_LAUNCH("k_leaf_orig", st, k_leaf_orig<<<(unsigned)L, 256, 0, st>>>(ix->X, ix->leafOff, ld, ix->leafMu, ix->leafRx));
     PM_CUDA(cudaGetLastError());
+    // tensor-core operand of the projected points (leaf-padded rows)
+    if (o->bf16_shadow) {
+        std::vector<int64_t> bo(L + 1, 0);
+        for (int64_t l = 0; l < L; l++) {
+            int64_t s = ix->leafOffH[l + 1] - ix->leafOffH[l];
+            bo[l + 1] = bo[l] + (s + 15) / 16 * 16;
+        }
+        ix->bOffH = bo;
+        const int64_t rows = bo[L];
+        PM_TRY(dalloc(&ix->bOff, L + 1));
+        PM_TRY(dalloc(&ix->Bsplit, (size_t)rows * 48));
+        PM_TRY(dalloc(&ix->bNorm, (size_t)rows));
+        PM_CUDA(cudaMemcpyAsync(ix->bOff, bo.data(), (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        PM_CUDA(cudaMemsetAsync(ix->Bsplit, 0, (size_t)rows * 48 * sizeof(uint16_t), st));
+        PM_CUDA(cudaMemsetAsync(ix->bNorm, 0, (size_t)rows * sizeof(float), st));
+        PM_LAUNCH("k_build_bsplit", st, k_build_bsplit<<<(unsigned)L, 128, 0, st>>>(ix->O32, ix->leafOff, ix->bOff, L, ix->Bsplit, ix->bNorm));
+        PM_CUDA(cudaGetLastError());
+    }
     // chunks of <= 32 points inside the leaves, with their own balls
     const int64_t C = (int64_t)ix->chunkOffH.size() - 1;
     ix->nChunks = C;

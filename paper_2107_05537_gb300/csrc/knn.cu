@@ -20,6 +20,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "pmlsh_impl.h"
 
 namespace {
@@ -129,28 +131,29 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 // Block b of the active list (QB queries) x 128 leaves: leaf classification,
 // whole-leaf counts, and the block's leaf list (leaves not out for some
 // query of the block, under the out-radius).
+template <int QBT>
 __global__ void __launch_bounds__(128)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, int64_t L,
         int *__restrict__ cntSure, int *__restrict__ blkCnt, int *__restrict__ blkLeaves)
 {
-    __shared__ float sq[QB][PM_MP];
-    __shared__ float sp[QB][PM_MAX_PIVOTS];
-    __shared__ float sRin[QB], sRout[QB];
-    __shared__ int sCnt[QB];
+    __shared__ float sq[QBT][PM_MP];
+    __shared__ float sp[QBT][PM_MAX_PIVOTS];
+    __shared__ float sRin[QBT], sRout[QBT];
+    __shared__ int sCnt[QBT];
     const int b = blockIdx.y;
-    const int a0 = b * QB;
-    const int nb = min(QB, na - a0);
-    for (int e = threadIdx.x; e < QB * PM_MP; e += blockDim.x) {
+    const int a0 = b * QBT;
+    const int nb = min(QBT, na - a0);
+    for (int e = threadIdx.x; e < QBT * PM_MP; e += blockDim.x) {
         int qq = e / PM_MP, j = e % PM_MP;
         sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
     }
-    for (int e = threadIdx.x; e < QB * PM_MAX_PIVOTS; e += blockDim.x) {
+    for (int e = threadIdx.x; e < QBT * PM_MAX_PIVOTS; e += blockDim.x) {
         int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
         sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
     }
-    for (int qq = threadIdx.x; qq < QB; qq += blockDim.x) {
+    for (int qq = threadIdx.x; qq < QBT; qq += blockDim.x) {
         if (qq < nb) {
             Thr T = thr[a0 + qq];
             sRin[qq] = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
@@ -963,6 +966,258 @@ size_t bestfirst_smem(int ld, int KP)
     return ((f * 4 + 15) & ~(size_t)15) + u + 128;
 }
 
+// ---------------------------------------- tensor-core range count (tcgen05)
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major: start address,
+// leading byte offset (between core matrices adjacent in K), stride byte
+// offset (between 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, shape M x N.
+__device__ __forceinline__ uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int TC_Q = 128;        // queries per tile (MMA M, TMEM lanes)
+constexpr int TC_N = 256;        // points per tile at most (MMA N, TMEM columns)
+constexpr int TC_K = 48;         // [hi | lo | hi] . [hi | hi | lo] of 16 coordinates
+constexpr int TC_ROWB = TC_K * 2;  // bytes per operand row
+
+// Range count of one round on the tensor cores.  Per query block of 128 and
+// per leaf of its list: D = 128 x N accumulators of q' . o' (BF16 split of the
+// FP32 coordinates, three products, FP32 accumulate) in TMEM; the epilogue
+// forms d'^2 ~ ||o'||^2 + ||q'||^2 - 2 q'.o' for queries whose Eq. 5 class is
+// partial.  With E bounding |d'^2 ~ - pm_pd2_32| (split and accumulation
+// error, the FP32 computation's own error), d'^2 ~ <= lo - E is surely
+// in, > hi + E surely out, and in between pm_pd2_32 decides exactly as the
+// CUDA-core count does; counts and band lists are therefore identical.
+// Leaf tiles arrive by one TMA bulk copy each (operand rows + norms).
+__global__ void __launch_bounds__(TC_Q)
+k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
+           const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
+           const float *__restrict__ meta, const int64_t *__restrict__ off, const float *__restrict__ O32,
+           const int64_t *__restrict__ bOff, const uint16_t *__restrict__ Bsplit, const float *__restrict__ bNorm,
+           const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, int64_t L, double maxNorm,
+           int *__restrict__ cntSure, int *__restrict__ cntBand, int *__restrict__ bandN, int bandCap,
+           int *__restrict__ bandA, int *__restrict__ bandPos, int *__restrict__ errFlag)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char *sA = tsm;                              // [128 rows][48] canonical, 12 KB
+    unsigned char *sB = tsm + TC_Q * TC_ROWB;             // [256 rows][48] canonical, 24 KB
+    float *sNorm = (float *)(sB + TC_N * TC_ROWB);        // [256]
+    __shared__ __align__(8) uint64_t barLoad, barMma;
+    __shared__ uint32_t sTmem;
+    __shared__ int sFail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int b = blockIdx.x, S = gridDim.y, sidx = blockIdx.y;
+    const int a0 = b * TC_Q;
+    const int nb = min(TC_Q, na - a0);
+    const bool valid = tid < nb;
+    const int a = a0 + tid;
+    // this thread's query
+    float qv[PM_MP], qpv[PM_MAX_PIVOTS];
+    float lo = -1.f, hi = -1.f, Rin = -1.f, Rout = -1.f, nq = 0.f, E = 0.f;
+    if (valid) {
+        const int q = act[a];
+        double nn = 0.0;
+        for (int j = 0; j < PM_MP; j++) {
+            qv[j] = qp32[(int64_t)q * PM_MP + j];
+            nn += (double)qv[j] * (double)qv[j];
+        }
+        for (int i = 0; i < PM_MAX_PIVOTS; i++) qpv[i] = qpiv[(int64_t)q * PM_MAX_PIVOTS + i];
+        const Thr T = thr[a];
+        lo = T.lo;
+        hi = T.hi;
+        Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
+        Rout = __fsqrt_rn(T.hi);
+        nq = (float)nn;
+        const double qn = sqrt(nn);
+        // Error of d'^2~ against the exact d'^2: the split drops lo*lo and
+        // the two rounding residues, each <= 2^-16 |q_j| |o_j|, so the three
+        // products miss q'.o' by <= 3 * 2^-16 ||q'|| ||o'|| (Cauchy-Schwarz);
+        // the FP32 accumulation of 48 exact products adds <= 128 * 2^-23 of
+        // the same (a loose bound whatever the adder's alignment); the norms
+        // and the final fma are rounded to FP32 (2^-24 each); pm_pd2_32 is
+        // within 2^-20 of the exact value.  Everything is taken 1.25 times.
+        E = (float)(1.25 * (2.0 * (3.0 * 0x1.0p-16 + 128.0 * 0x1.0p-23) * qn * maxNorm +
+                            0x1.0p-22 * (nn + maxNorm * maxNorm) + 0x1.0p-18 * (double)T.hi) + 1e-30);
+    } else {
+        for (int j = 0; j < PM_MP; j++) qv[j] = 0.f;
+        for (int i = 0; i < PM_MAX_PIVOTS; i++) qpv[i] = 0.f;
+    }
+    // A operand row `tid`: [hi | lo | hi]
+    {
+        const int g = tid >> 3, i = tid & 7;
+        uint16_t *A16 = (uint16_t *)sA;
+        for (int j = 0; j < PM_MP; j++) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(qv[j]);
+            const __nv_bfloat16 l = __float2bfloat16_rn(qv[j] - __bfloat162float(h));
+            const uint16_t hb = __bfloat16_as_ushort(h), lb = __bfloat16_as_ushort(l);
+            const int k0 = j, k1 = 16 + j, k2 = 32 + j;
+            A16[((g * 6 + (k0 >> 3)) * 8 + i) * 8 + (k0 & 7)] = hb;
+            A16[((g * 6 + (k1 >> 3)) * 8 + i) * 8 + (k1 & 7)] = lb;
+            A16[((g * 6 + (k2 >> 3)) * 8 + i) * 8 + (k2 & 7)] = hb;
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTmem)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        sFail = 0;
+        mbar_init(&barLoad, 1);
+        mbar_init(&barMma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_shared();   // A (generic stores) visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sTmem;
+    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phLoad = 0, phMma = 0;
+    bool ldOut = false, mmaOut = false;   // thread 0: copy / MMA not yet seen complete
+    int sure = 0, band = 0;
+    const int nl = blkCnt[b];
+    for (int li = sidx; li < nl; li += S) {
+        const int l = blkLeaves[(int64_t)b * L + li];
+        const unsigned char cl =
+            valid ? leaf_class(qv, qpv, s, Rin, Rout, meta + (int64_t)l * PM_LEAF_STRIDE) : CL_OUT;
+        if (!__syncthreads_or(cl == CL_PART)) continue;
+        const int64_t p0 = off[l], size = off[l + 1] - p0;
+        for (int64_t t0 = 0; t0 < size; t0 += TC_N) {
+            const int rows = (int)min((int64_t)TC_N, size - t0);
+            const int N = (rows + 15) & ~15;
+            const int64_t R0 = bOff[l] + t0;
+            if (tid == 0) {
+                fence_async_shared();
+                mbar_expect_tx(&barLoad, (uint32_t)(N * TC_ROWB + N * 4));
+                bulk_g2s(sB, Bsplit + R0 * TC_K, (uint32_t)(N * TC_ROWB), &barLoad);
+                bulk_g2s(sNorm, bNorm + R0, (uint32_t)(N * 4), &barLoad);
+                ldOut = true;
+            }
+            if (mbar_wait_bounded(&barLoad, phLoad)) {
+                phLoad ^= 1u;
+                ldOut = false;
+            } else {
+                atomicOr(&sFail, 1);
+            }
+            __syncthreads();
+            if (sFail) break;
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t idesc = umma_idesc_bf16(TC_Q, N);
+                const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+                for (int ks = 0; ks < TC_K / 16; ks++) {
+                    const uint64_t ad = umma_sdesc(aBase + ks * 256, 128, 6 * 128);
+                    const uint64_t bd = umma_sdesc(bBase + ks * 256, 128, 6 * 128);
+                    umma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+                umma_commit(&barMma);
+                mmaOut = true;
+            }
+            if (mbar_wait_bounded(&barMma, phMma)) {
+                phMma ^= 1u;
+                mmaOut = false;
+            } else {
+                atomicOr(&sFail, 1);
+            }
+            __syncthreads();
+            if (sFail) break;
+            tc_fence_after();
+            const bool part = cl == CL_PART;
+            // tcgen05.ld is warp-collective: the column loop is warp-uniform
+            if (__any_sync(0xffffffffu, part)) {
+                const float loS = lo - E, hiS = hi + E;
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    __syncwarp();
+                    tmem_ld16(tlane + (uint32_t)c0, v);
+                    if (!part) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int col = c0 + j;
+                        if (col >= rows) break;
+                        const float vt = __fmaf_rn(-2.f, v[j], __fadd_rn(sNorm[col], nq));
+                        if (vt <= loS) { sure++; continue; }
+                        if (vt > hiS) continue;
+                        const int64_t pos = p0 + t0 + col;
+                        const float ex = pm_pd2_32(O32 + pos * PM_MP, qv);
+                        if (ex <= lo) sure++;
+                        else if (ex <= hi) {
+                            band++;
+                            const int e = atomicAdd(bandN, 1);
+                            if (e < bandCap) { bandA[e] = a; bandPos[e] = (int)pos; }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (sFail) break;
+    }
+    if (valid) {
+        if (sure) atomicAdd(&cntSure[a], sure);
+        if (band) atomicAdd(&cntBand[a], band);
+    }
+    if (tid == 0 && sFail) {
+        atomicOr(errFlag, 128);
+        // nothing may land in shared memory or TMEM after the CTA leaves
+        if (ldOut) mbar_wait_bounded(&barLoad, phLoad);
+        if (mmaOut) mbar_wait_bounded(&barMma, phMma);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    }
+}
+
+size_t count_tc_smem() { return (size_t)TC_Q * TC_ROWB + (size_t)TC_N * TC_ROWB + TC_N * 4 + 1024; }
+
 // Locality order: counting sort of queries by leaf key.
 __global__ void k_hist(const unsigned int *__restrict__ key, int64_t nq, int *__restrict__ h)
 {
@@ -1121,6 +1376,12 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfPerSM, k_bestfirst, BF_THREADS, bsmem));
     bfPerSM = std::max(1, bfPerSM);
 
+    const bool tensor = o->precision == PMLSH_BF16_TENSOR;
+    // the tensor-core count holds 256 TMEM columns per CTA: at most two CTAs
+    // per SM, enforced through the shared-memory request
+    const size_t tcSmem = std::max<size_t>(count_tc_smem(), 100 * 1024);
+    if (tensor) PM_TRY(pm_allow_max_dyn_smem((const void *)k_count_tc));
+
     std::vector<int32_t> actH;
     actH.reserve(nq);
     for (int round = 0; round < 100000; round++) {
@@ -1130,24 +1391,38 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         const int na = (int)actH.size();
         if (na == 0) break;
         const int nblk = (na + QB - 1) / QB;
+        const int nblkT = (na + TC_Q - 1) / TC_Q;
+        const int nlist = tensor ? nblkT : nblk;
         PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        int *blkCnt = grow<int>(w.blkCnt, nblk, s);
-        int *blkLeaves = grow<int>(w.blkLeaves, (size_t)nblk * L, s);
+        int *blkCnt = grow<int>(w.blkCnt, nlist, s);
+        int *blkLeaves = grow<int>(w.blkLeaves, (size_t)nlist * L, s);
         if (s != PMLSH_OK) return s;
-        PM_CUDA(cudaMemsetAsync(blkCnt, 0, nblk * sizeof(int), st));
+        PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(cntSure, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(cntBand, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(inTrue, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(inN, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(fpc, 0, (nq + 8) * sizeof(int), st));
         PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
-        dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblk);
-        PM_LAUNCH("k_class", st, k_class<<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
-                                    cntSure, blkCnt, blkLeaves));
-        int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
-        PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                                    ix->leafOff, ix->O32, blkCnt, blkLeaves, L,
-                                                    cntSure, cntBand, bandN, bandCap, bandA, bandPos));
+        if (!tensor) {
+            dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblk);
+            PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
+                                        cntSure, blkCnt, blkLeaves));
+            int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
+            PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
+                                                        ix->leafOff, ix->O32, blkCnt, blkLeaves, L,
+                                                        cntSure, cntBand, bandN, bandCap, bandA, bandPos));
+        } else {
+            // 128-query blocks: leaf lists per block, then the tensor-core count
+            dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblkT);
+            PM_LAUNCH("k_class", st, k_class<TC_Q><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
+                                          cntSure, blkCnt, blkLeaves));
+            int splitC = std::max(1, std::min(128, (2 * nsm + nblkT - 1) / nblkT));
+            PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_Q, tcSmem, st>>>(
+                                        act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, ix->O32,
+                                        ix->bOff, ix->Bsplit, ix->bNorm, blkCnt, blkLeaves, L, ix->maxNorm,
+                                        cntSure, cntBand, bandN, bandCap, bandA, bandPos, errFlag));
+        }
         // FP64 band resolution (grid sized by the capacity; empty threads exit)
         {
             int hBand = 0;

@@ -23,7 +23,7 @@ E = math.e
 
 
 def _run_both(X, Q, A, k, c=1.5, beta=0.2809, r_min=None, stop_rule=0, leaf=64, s=5, m=None,
-              t=None, device_inputs=True):
+              t=None, device_inputs=True, precision=0):
     m = A.shape[0] if m is None else m
     ix = pm.Index(torch.from_numpy(X).cuda() if device_inputs else X, m=m, s=s, leaf_size=leaf,
                   proj=A)
@@ -35,7 +35,7 @@ def _run_both(X, Q, A, k, c=1.5, beta=0.2809, r_min=None, stop_rule=0, leaf=64, 
     ref = oracle.knn(X, A, Q, k, c, tt, B, rmin, stop_rule)
     Qin = torch.from_numpy(Q).cuda() if device_inputs else Q
     got = ix.knn(Qin, k=k, c=c, beta=beta, r_min=r_min if r_min is not None else 0.0,
-                 stop_rule=stop_rule, t=tt)
+                 stop_rule=stop_rule, t=tt, precision=precision)
     torch.cuda.synchronize()
     ix.close()
     return got, ref
@@ -214,3 +214,98 @@ def test_query_projection_entry_point(c1):
     h64, h32 = ix.project(Q[:7])
     assert np.array_equal(h64, ref[:7])
     ix.close()
+
+
+# ------------------------------------------- tensor-core range counts
+
+TENSOR = pm.PMLSH_BF16_TENSOR
+
+
+@pytest.mark.parametrize("stop_rule", [0, 1])
+def test_c1_parity_tensor(c1, stop_rule):
+    X, Q, A = c1
+    got, ref = _run_both(X, Q, A, k=10, stop_rule=stop_rule, precision=TENSOR)
+    _assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("n,d,m,leaf,s,k,nq", [
+    (1000 + 17, 37, 15, 64, 5, 7, 33),     # ragged n and d
+    (300, 8, 3, 16, 0, 1, 129),            # m = 3, one query past a 128-query tile
+    (50, 20, 16, 64, 5, 50, 1),            # n < leaf size, k = n, one query
+    (2500, 64, 15, 1024, 8, 20, 257),      # leaves of 1024 points: four 256-row tiles
+])
+def test_shapes_and_edges_tensor(n, d, m, leaf, s, k, nq):
+    X, Q, _, _ = datagen.mixture(n, d, 7, 1.0, seed=n, nq=nq)
+    A = oracle.gen_projection(11, m, d).astype(np.float32)
+    for rmin in (None, 0.5):
+        got, ref = _run_both(X, Q, A, k=k, leaf=leaf, s=s, r_min=rmin, beta=0.1, precision=TENSOR)
+        _assert_parity(got, ref)
+
+
+def test_tensor_rule2_multiround_and_duplicates(c1):
+    X, Q, A = c1
+    got, ref = _run_both(X, Q[:40], A, k=10, r_min=200.0, precision=TENSOR)
+    _assert_parity(got, ref)
+    got, ref = _run_both(X, Q[:50], A, k=5, beta=0.01, r_min=2.0, precision=TENSOR)
+    _assert_parity(got, ref)
+    base, Qd, _, _ = datagen.mixture(25, 16, 5, 1.0, seed=3, nq=20)
+    Xd = np.repeat(base, 40, axis=0)
+    Ad = oracle.gen_projection(5, 15, 16).astype(np.float32)
+    got, ref = _run_both(Xd, Qd, Ad, k=30, beta=0.02, leaf=32, precision=TENSOR)
+    _assert_parity(got, ref)
+
+
+def test_tensor_far_from_origin():
+    # a common offset of 1000 makes ||o'||^2 + ||q'||^2 - 2 q'.o' cancel
+    # heavily: far more pairs fall back to the exact test, results unchanged
+    X, Q, _, _ = datagen.mixture(3000, 32, 10, 1.0, seed=21, nq=200)
+    X = X + np.float32(1000.0)
+    Q = Q + np.float32(1000.0)
+    A = oracle.gen_projection(4, 15, 32).astype(np.float32)
+    got, ref = _run_both(X, Q, A, k=10, precision=TENSOR)
+    _assert_parity(got, ref)
+
+
+def test_tensor_trace_equals_fp32_path(c1):
+    # identical counts and band lists: every statistic of the two modes agrees
+    X, Q, A = c1
+    ix = pm.Index(torch.from_numpy(X).cuda(), proj=A, leaf_size=128)
+    a = ix.knn(Q, k=10, precision=pm.PMLSH_FP32_PLAIN)
+    b = ix.knn(Q, k=10, precision=TENSOR)
+    ix.close()
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["dists"], b["dists"])
+    for key in ("rounds", "rule", "ncand", "r", "fp64"):
+        assert np.array_equal(a["stats"][key], b["stats"][key]), key
+
+
+def test_tensor_needs_the_split_operand(c1):
+    X, Q, A = c1
+    ix = pm.Index(X, proj=A, bf16_shadow=False)
+    with pytest.raises(pm.PmlshError):
+        ix.knn(Q[:4], k=3, precision=TENSOR)
+    assert ix.knn(Q[:4], k=3)["ids"].shape == (4, 3)
+    ix.close()
+
+
+@pytest.mark.slow
+def test_c2_full_size_sampled_parity_tensor():
+    w = datagen.workload("c2")
+    X, Q = w["X"], w["Q"]
+    A = oracle.gen_projection(2, 15, 128).astype(np.float32)
+    ix = pm.Index(torch.from_numpy(X).cuda(), proj=A, leaf_size=256)
+    Qd = torch.from_numpy(Q).cuda()
+    got = ix.knn(Qd, k=50, c=1.5, beta=0.2809, precision=TENSOR)
+    plain = ix.knn(Qd, k=50, c=1.5, beta=0.2809)
+    torch.cuda.synchronize()
+    ix.close()
+    assert torch.equal(got["ids"], plain["ids"]) and torch.equal(got["dists"], plain["dists"])
+    for key in ("rounds", "rule", "ncand", "r", "fp64"):
+        assert np.array_equal(got["stats"][key], plain["stats"][key]), key
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(len(Q), size=32, replace=False))
+    t, _, _ = oracle.params(15, 1.5, 1 / E)
+    ref = oracle.knn(X, A, Q[sample], 50, 1.5, t, oracle.budget(len(X), 0.2809, 50),
+                     oracle.rmin_auto(X, 0.2809, 50, 1.5, 3), 0)
+    sub = dict(ids=got["ids"][sample], dists=got["dists"][sample], err=got["err"][sample],
+               stats={k2: v[sample] for k2, v in got["stats"].items()})
+    _assert_parity(sub, ref)
