@@ -3,10 +3,13 @@
 // One round of Algorithm 2 for every still-active query is a fixed sequence
 // of kernels:
 //   k_thresholds   radius R = t r and the FP32 classification thresholds
-//   k_class        Eq. 5 leaf test for (query block x leaf); builds each query
-//                  block's list of leaves and counts whole-leaf members
+//   k_class        Eq. 5 leaf test for (query block x leaf); counts whole-leaf
+//                  members and lists, per query block, the leaves that some
+//                  query covers partially, with the bit mask of those queries
 //   k_count        per-point test in partially covered leaves; points whose
-//                  FP32 distance is inside the error band go to a band list
+//   (k_count_tc)   FP32 distance is inside the error band go to a band list
+//                  (k_count_tc: the same decisions from tensor-core dot
+//                  products, PMLSH_BF16_TENSOR)
 //   k_band64       FP64 decision for band points (equal to the FP64 oracle)
 //   [host]         |S_i| per query -> which queries reach the budget B
 //   k_collect,     for budget queries: the B nearest in projected space
@@ -128,16 +131,19 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 
 // ------------------------------------------------------------ range round
 
-// Block b of the active list (QB queries) x 128 leaves: leaf classification,
-// whole-leaf counts, and the block's leaf list (leaves not out for some
-// query of the block, under the out-radius).
+// Block b of the active list (QBT queries) x 128 leaves: leaf classification
+// and whole-leaf counts.  Leaves that some query of the block covers only
+// partially are listed for the block, each with the QBT-bit mask of those
+// queries (bit qq of word qq / 32).
 template <int QBT>
 __global__ void __launch_bounds__(128)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, int64_t L,
-        int *__restrict__ cntSure, int *__restrict__ blkCnt, int *__restrict__ blkLeaves)
+        int *__restrict__ cntSure, int *__restrict__ blkCnt, int *__restrict__ blkLeaves,
+        uint32_t *__restrict__ blkMask)
 {
+    constexpr int W = QBT / 32;
     __shared__ float sq[QBT][PM_MP];
     __shared__ float sp[QBT][PM_MAX_PIVOTS];
     __shared__ float sRin[QBT], sRout[QBT];
@@ -163,41 +169,54 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     }
     __syncthreads();
     const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool any = false;
+    uint32_t mw[W];
+    bool anyPart = false;
+#pragma unroll
+    for (int w = 0; w < W; w++) mw[w] = 0u;
     if (l < L) {
         float Mv[PM_LEAF_STRIDE];
 #pragma unroll
         for (int j = 0; j < PM_LEAF_STRIDE; j++) Mv[j] = meta[l * PM_LEAF_STRIDE + j];
-        int cnt = (int)(off[l + 1] - off[l]);
-        for (int qq = 0; qq < nb; qq++) {
-            unsigned char c = leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv);
-            if (c != CL_OUT) any = true;
-            if (c == CL_FULL) atomicAdd(&sCnt[qq], cnt);
+        const int cnt = (int)(off[l + 1] - off[l]);
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            uint32_t bits = 0u;
+            for (int j = 0; j < 32; j++) {
+                const int qq = w * 32 + j;
+                if (qq >= nb) break;
+                const unsigned char c = leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv);
+                if (c == CL_FULL) atomicAdd(&sCnt[qq], cnt);
+                bits |= (uint32_t)(c == CL_PART) << j;
+            }
+            mw[w] = bits;
+            anyPart |= bits != 0u;
         }
     }
-    if (any) {
-        int slot = atomicAdd(&blkCnt[b], 1);
-        blkLeaves[(int64_t)b * L + slot] = (int)l;
+    if (anyPart) {
+        const int slot = atomicAdd(&blkCnt[b], 1);
+        const int64_t e = (int64_t)b * L + slot;
+        blkLeaves[e] = (int)l;
+#pragma unroll
+        for (int w = 0; w < W; w++) blkMask[e * W + w] = mw[w];
     }
     __syncthreads();
     for (int qq = threadIdx.x; qq < nb; qq += blockDim.x)
         if (sCnt[qq]) atomicAdd(&cntSure[a0 + qq], sCnt[qq]);
 }
 
-// Per-point test in partially covered leaves.  Grid (block, split).
+// Per-point test in partially covered leaves (the queries of the block's
+// list mask).  Grid (block, split).
 __global__ void __launch_bounds__(256)
 k_count(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
-        const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
-        const float *__restrict__ meta, const int64_t *__restrict__ off, const float *__restrict__ O32,
-        const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, int64_t L,
+        const float *__restrict__ qp32, const int64_t *__restrict__ off, const float *__restrict__ O32,
+        const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves,
+        const uint32_t *__restrict__ blkMask, int64_t L,
         int *__restrict__ cntSure, int *__restrict__ cntBand,
         int *__restrict__ bandN, int bandCap, int *__restrict__ bandA, int *__restrict__ bandPos)
 {
     __shared__ float sq[QB][PM_MP];
-    __shared__ float sp[QB][PM_MAX_PIVOTS];
-    __shared__ float sRin[QB], sRout[QB], sLo[QB], sHi[QB];
+    __shared__ float sLo[QB], sHi[QB];
     __shared__ int sSure[QB], sBand[QB];
-    __shared__ unsigned long long sPart;
     const int b = blockIdx.x;
     const int a0 = b * QB;
     const int nb = min(QB, na - a0);
@@ -205,35 +224,22 @@ k_count(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         int qq = e / PM_MP, j = e % PM_MP;
         sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
     }
-    for (int e = threadIdx.x; e < QB * PM_MAX_PIVOTS; e += blockDim.x) {
-        int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
-        sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
-    }
     for (int qq = threadIdx.x; qq < QB; qq += blockDim.x) {
         if (qq < nb) {
             Thr T = thr[a0 + qq];
-            sRin[qq] = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
-            sRout[qq] = __fsqrt_rn(T.hi);
             sLo[qq] = T.lo;
             sHi[qq] = T.hi;
         }
         sSure[qq] = 0;
         sBand[qq] = 0;
     }
+    __syncthreads();
     const int nl = blkCnt[b];
     for (int li = blockIdx.y; li < nl; li += gridDim.y) {
-        const int l = blkLeaves[(int64_t)b * L + li];
-        __syncthreads();
-        if (threadIdx.x == 0) sPart = 0ull;
-        __syncthreads();
-        if (threadIdx.x < nb) {
-            unsigned char c = leaf_class(sq[threadIdx.x], sp[threadIdx.x], s, sRin[threadIdx.x],
-                                         sRout[threadIdx.x], meta + (int64_t)l * PM_LEAF_STRIDE);
-            if (c == CL_PART) atomicOr(&sPart, 1ull << threadIdx.x);
-        }
-        __syncthreads();
-        const unsigned long long part = sPart;
-        if (!part) continue;
+        const int64_t e = (int64_t)b * L + li;
+        const int l = blkLeaves[e];
+        const unsigned long long part =
+            ((unsigned long long)blkMask[e * 2 + 1] << 32) | (unsigned long long)blkMask[e * 2];
         const int64_t p0 = off[l], p1 = off[l + 1];
         for (int64_t base = p0; base < p1; base += blockDim.x) {
             const int64_t pos = base + threadIdx.x;
@@ -255,10 +261,10 @@ k_count(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                     if (bb) atomicAdd(&sBand[qq], __popc(bb));
                 }
                 if (band) {
-                    int e = atomicAdd(bandN, 1);
-                    if (e < bandCap) {
-                        bandA[e] = a0 + qq;
-                        bandPos[e] = (int)pos;
+                    int e2 = atomicAdd(bandN, 1);
+                    if (e2 < bandCap) {
+                        bandA[e2] = a0 + qq;
+                        bandPos[e2] = (int)pos;
                     }
                 }
             }
@@ -1003,220 +1009,327 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+// 32 lanes x 1 FP32 accumulator column (this warp's lane quarter).
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr)
 {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return r;
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int TC_Q = 128;        // queries per tile (MMA M, TMEM lanes)
-constexpr int TC_N = 256;        // points per tile at most (MMA N, TMEM columns)
-constexpr int TC_K = 48;         // [hi | lo | hi] . [hi | hi | lo] of 16 coordinates
+constexpr int TC_QN = 256;         // queries per block: MMA N, TMEM columns per buffer
+constexpr int TC_PM = 128;         // points per tile: MMA M, TMEM lanes
+constexpr int TC_K = 48;           // [hi | hi | lo] . [hi | lo | hi] of 16 coordinates
 constexpr int TC_ROWB = TC_K * 2;  // bytes per operand row
+constexpr int TC_STAGES = 4;       // point tiles in flight
+constexpr int TC_THREADS = 320;    // warp 0 loads, warp 1 MMA, warps 2-9 epilogue
+constexpr int TC_MW = TC_QN / 32;  // mask words per list entry
+// dynamic shared memory: query operand, point-tile ring, per-query data
+constexpr int TC_OFF_A = TC_QN * TC_ROWB;                              // 24 KB
+constexpr int TC_OFF_QP = TC_OFF_A + TC_STAGES * TC_PM * TC_ROWB;      // + 48 KB
+constexpr int TC_OFF_PAR = TC_OFF_QP + TC_QN * PM_MP * 4;              // + 16 KB
+constexpr int TC_OFF_LH = TC_OFF_PAR + TC_QN * 16;
+constexpr int TC_OFF_CNT = TC_OFF_LH + TC_QN * 8;
+constexpr int TC_SMEM = TC_OFF_CNT + 2 * TC_QN * 4;
+// at most one CTA per SM (the CTA holds all 512 TMEM columns)
+constexpr int TC_SMEM_REQ = 120 * 1024;
+static_assert(TC_SMEM <= TC_SMEM_REQ, "tensor-count shared memory");
 
-// Range count of one round on the tensor cores.  Per query block of 128 and
-// per leaf of its list: D = 128 x N accumulators of q' . o' (BF16 split of the
-// FP32 coordinates, three products, FP32 accumulate) in TMEM; the epilogue
-// forms d'^2 ~ ||o'||^2 + ||q'||^2 - 2 q'.o' for queries whose Eq. 5 class is
-// partial.  With E bounding |d'^2 ~ - pm_pd2_32| (split and accumulation
-// error, the FP32 computation's own error), d'^2 ~ <= lo - E is surely
-// in, > hi + E surely out, and in between pm_pd2_32 decides exactly as the
-// CUDA-core count does; counts and band lists are therefore identical.
-// Leaf tiles arrive by one TMA bulk copy each (operand rows + norms).
-__global__ void __launch_bounds__(TC_Q)
+// Waits for phase `ph` of `bar`, giving up on the iteration limit or when
+// another role has already failed (fail != 0).
+__device__ __forceinline__ bool mbar_wait_or_fail(uint64_t *bar, uint32_t ph, volatile int *fail)
+{
+    for (int it = 0; it < (1 << 22); it++) {
+        if (mbar_try_wait(bar, ph)) return true;
+        if ((it & 255) == 255 && *fail) return false;
+    }
+    return false;
+}
+
+// Range count of one round on the tensor cores, point-major: for a block of
+// up to 256 queries and each listed leaf (tiles of 128 points), TMEM holds
+// the 128 x 256 dot products q'.o' of a BF16 split of the FP32 coordinates
+// (three products, FP32 accumulate).  Only the columns of queries that cover
+// the leaf partially are read.  With E bounding |d'^2~ - pm_pd2_32| for
+// d'^2~ = ||o'||^2 + ||q'||^2 - 2 q'.o' (split and accumulation error, FP32
+// rounding of the norms, the CUDA-core computation's own error), d'^2~ <=
+// lo - E is surely in, > hi + E surely out, and in between pm_pd2_32 decides
+// exactly as k_count does: counts and band lists equal k_count's.
+//
+// Roles: warp 0 streams point tiles into a 4-stage ring with TMA bulk copies,
+// warp 1 issues tcgen05.mma into one of two TMEM accumulators, warps 2-5 and
+// 6-9 (one warp per TMEM lane quarter each) read even and odd tiles.  Every
+// wait is bounded; on a timeout the CTA records error bit 128, lets the
+// copies and MMAs it issued complete and frees its TMEM.
+__global__ void __launch_bounds__(TC_THREADS, 1)
 k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
-           const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
-           const float *__restrict__ meta, const int64_t *__restrict__ off, const float *__restrict__ O32,
+           const float *__restrict__ qp32, const int64_t *__restrict__ off, const float *__restrict__ O32,
            const int64_t *__restrict__ bOff, const uint16_t *__restrict__ Bsplit, const float *__restrict__ bNorm,
-           const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, int64_t L, double maxNorm,
-           int *__restrict__ cntSure, int *__restrict__ cntBand, int *__restrict__ bandN, int bandCap,
-           int *__restrict__ bandA, int *__restrict__ bandPos, int *__restrict__ errFlag)
+           const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, const uint32_t *__restrict__ blkMask,
+           int64_t L, double maxNorm, int *__restrict__ cntSure, int *__restrict__ cntBand,
+           int *__restrict__ bandN, int bandCap, int *__restrict__ bandA, int *__restrict__ bandPos,
+           int *__restrict__ errFlag)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char *sA = tsm;                              // [128 rows][48] canonical, 12 KB
-    unsigned char *sB = tsm + TC_Q * TC_ROWB;             // [256 rows][48] canonical, 24 KB
-    float *sNorm = (float *)(sB + TC_N * TC_ROWB);        // [256]
-    __shared__ __align__(8) uint64_t barLoad, barMma;
+    unsigned char *sQ = tsm;
+    unsigned char *sA = tsm + TC_OFF_A;
+    float *sQp = (float *)(tsm + TC_OFF_QP);
+    float4 *sPar = (float4 *)(tsm + TC_OFF_PAR);   // ||q'||^2, lo - E, hi + E
+    float2 *sLH = (float2 *)(tsm + TC_OFF_LH);     // lo, hi
+    int *sCntS = (int *)(tsm + TC_OFF_CNT);
+    int *sCntB = sCntS + TC_QN;
+    __shared__ __align__(8) uint64_t barFull[TC_STAGES], barEmpty[TC_STAGES], barTFull[2], barTEmpty[2];
     __shared__ uint32_t sTmem;
     __shared__ int sFail;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ int sIssued[TC_STAGES], sSeenFull[TC_STAGES], sCommitted[2], sSeenT[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x, S = gridDim.y, sidx = blockIdx.y;
-    const int a0 = b * TC_Q;
-    const int nb = min(TC_Q, na - a0);
-    const bool valid = tid < nb;
-    const int a = a0 + tid;
-    // this thread's query
-    float qv[PM_MP], qpv[PM_MAX_PIVOTS];
-    float lo = -1.f, hi = -1.f, Rin = -1.f, Rout = -1.f, nq = 0.f, E = 0.f;
-    if (valid) {
-        const int q = act[a];
-        double nn = 0.0;
-        for (int j = 0; j < PM_MP; j++) {
-            qv[j] = qp32[(int64_t)q * PM_MP + j];
-            nn += (double)qv[j] * (double)qv[j];
+    const int a0 = b * TC_QN;
+    const int nb = min(TC_QN, na - a0);
+    const int Nq = (nb + 15) & ~15;
+    volatile int *vFail = &sFail;
+
+    // query operand [hi | lo | hi], per-query thresholds and error bound
+    if (tid < TC_QN) {
+        const int j = tid;
+        float qv[PM_MP];
+        float4 par = make_float4(0.f, -INFINITY, -INFINITY, 0.f);
+        float2 lh = make_float2(-INFINITY, -INFINITY);
+        if (j < nb) {
+            const int q = act[a0 + j];
+            double nn = 0.0;
+            for (int c = 0; c < PM_MP; c++) {
+                qv[c] = qp32[(int64_t)q * PM_MP + c];
+                nn += (double)qv[c] * (double)qv[c];
+            }
+            const Thr T = thr[a0 + j];
+            const double qn = sqrt(nn);
+            // split: lo*lo and both rounding residues dropped, each <= 2^-16
+            // |q_c| |o_c|, so <= 3 * 2^-16 ||q'|| ||o'|| (Cauchy-Schwarz); the
+            // FP32 accumulation of 48 exact products <= 128 * 2^-23 of the
+            // same, whatever the adder's alignment; norms, their sum and the
+            // final fma rounded to FP32; pm_pd2_32 within 18 * 2^-24 relative.
+            // Everything is taken 1.25 times.
+            const double E = 1.25 * (2.0 * (3.0 * 0x1.0p-16 + 128.0 * 0x1.0p-23) * qn * maxNorm +
+                                     0x1.0p-22 * (nn + maxNorm * maxNorm) + 0x1.0p-18 * (double)T.hi) + 1e-30;
+            par = make_float4((float)nn, (float)((double)T.lo - E), (float)((double)T.hi + E), 0.f);
+            lh = make_float2(T.lo, T.hi);
+        } else {
+            for (int c = 0; c < PM_MP; c++) qv[c] = 0.f;
         }
-        for (int i = 0; i < PM_MAX_PIVOTS; i++) qpv[i] = qpiv[(int64_t)q * PM_MAX_PIVOTS + i];
-        const Thr T = thr[a];
-        lo = T.lo;
-        hi = T.hi;
-        Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
-        Rout = __fsqrt_rn(T.hi);
-        nq = (float)nn;
-        const double qn = sqrt(nn);
-        // Error of d'^2~ against the exact d'^2: the split drops lo*lo and
-        // the two rounding residues, each <= 2^-16 |q_j| |o_j|, so the three
-        // products miss q'.o' by <= 3 * 2^-16 ||q'|| ||o'|| (Cauchy-Schwarz);
-        // the FP32 accumulation of 48 exact products adds <= 128 * 2^-23 of
-        // the same (a loose bound whatever the adder's alignment); the norms
-        // and the final fma are rounded to FP32 (2^-24 each); pm_pd2_32 is
-        // within 2^-20 of the exact value.  Everything is taken 1.25 times.
-        E = (float)(1.25 * (2.0 * (3.0 * 0x1.0p-16 + 128.0 * 0x1.0p-23) * qn * maxNorm +
-                            0x1.0p-22 * (nn + maxNorm * maxNorm) + 0x1.0p-18 * (double)T.hi) + 1e-30);
-    } else {
-        for (int j = 0; j < PM_MP; j++) qv[j] = 0.f;
-        for (int i = 0; i < PM_MAX_PIVOTS; i++) qpv[i] = 0.f;
-    }
-    // A operand row `tid`: [hi | lo | hi]
-    {
-        const int g = tid >> 3, i = tid & 7;
-        uint16_t *A16 = (uint16_t *)sA;
-        for (int j = 0; j < PM_MP; j++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(qv[j]);
-            const __nv_bfloat16 l = __float2bfloat16_rn(qv[j] - __bfloat162float(h));
+        sPar[j] = par;
+        sLH[j] = lh;
+        sCntS[j] = 0;
+        sCntB[j] = 0;
+        const int g = j >> 3, i = j & 7;
+        uint16_t *Q16 = (uint16_t *)sQ;
+        for (int c = 0; c < PM_MP; c++) {
+            sQp[j * PM_MP + c] = qv[c];
+            const __nv_bfloat16 h = __float2bfloat16_rn(qv[c]);
+            const __nv_bfloat16 l = __float2bfloat16_rn(qv[c] - __bfloat162float(h));
             const uint16_t hb = __bfloat16_as_ushort(h), lb = __bfloat16_as_ushort(l);
-            const int k0 = j, k1 = 16 + j, k2 = 32 + j;
-            A16[((g * 6 + (k0 >> 3)) * 8 + i) * 8 + (k0 & 7)] = hb;
-            A16[((g * 6 + (k1 >> 3)) * 8 + i) * 8 + (k1 & 7)] = lb;
-            A16[((g * 6 + (k2 >> 3)) * 8 + i) * 8 + (k2 & 7)] = hb;
+            const int k0 = c, k1 = 16 + c, k2 = 32 + c;
+            Q16[((g * 6 + (k0 >> 3)) * 8 + i) * 8 + (k0 & 7)] = hb;
+            Q16[((g * 6 + (k1 >> 3)) * 8 + i) * 8 + (k1 & 7)] = lb;
+            Q16[((g * 6 + (k2 >> 3)) * 8 + i) * 8 + (k2 & 7)] = hb;
         }
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTmem)),
-                     "r"(TC_N)
+                     "r"(2 * TC_QN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
+    if (tid == 32) {
         sFail = 0;
-        mbar_init(&barLoad, 1);
-        mbar_init(&barMma, 1);
+        for (int st = 0; st < TC_STAGES; st++) {
+            mbar_init(&barFull[st], 1);
+            mbar_init(&barEmpty[st], 1);
+            sIssued[st] = 0;
+            sSeenFull[st] = 0;
+        }
+        for (int t = 0; t < 2; t++) {
+            mbar_init(&barTFull[t], 1);
+            mbar_init(&barTEmpty[t], 4);
+            sCommitted[t] = 0;
+            sSeenT[t] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    fence_async_shared();   // A (generic stores) visible to the tensor core
+    fence_async_shared();   // query operand (generic stores) -> tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sTmem;
-    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t phLoad = 0, phMma = 0;
-    bool ldOut = false, mmaOut = false;   // thread 0: copy / MMA not yet seen complete
-    int sure = 0, band = 0;
     const int nl = blkCnt[b];
-    for (int li = sidx; li < nl; li += S) {
-        const int l = blkLeaves[(int64_t)b * L + li];
-        const unsigned char cl =
-            valid ? leaf_class(qv, qpv, s, Rin, Rout, meta + (int64_t)l * PM_LEAF_STRIDE) : CL_OUT;
-        if (!__syncthreads_or(cl == CL_PART)) continue;
-        const int64_t p0 = off[l], size = off[l + 1] - p0;
-        for (int64_t t0 = 0; t0 < size; t0 += TC_N) {
-            const int rows = (int)min((int64_t)TC_N, size - t0);
-            const int N = (rows + 15) & ~15;
-            const int64_t R0 = bOff[l] + t0;
-            if (tid == 0) {
-                fence_async_shared();
-                mbar_expect_tx(&barLoad, (uint32_t)(N * TC_ROWB + N * 4));
-                bulk_g2s(sB, Bsplit + R0 * TC_K, (uint32_t)(N * TC_ROWB), &barLoad);
-                bulk_g2s(sNorm, bNorm + R0, (uint32_t)(N * 4), &barLoad);
-                ldOut = true;
-            }
-            if (mbar_wait_bounded(&barLoad, phLoad)) {
-                phLoad ^= 1u;
-                ldOut = false;
-            } else {
-                atomicOr(&sFail, 1);
-            }
-            __syncthreads();
-            if (sFail) break;
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t idesc = umma_idesc_bf16(TC_Q, N);
-                const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
-                for (int ks = 0; ks < TC_K / 16; ks++) {
-                    const uint64_t ad = umma_sdesc(aBase + ks * 256, 128, 6 * 128);
-                    const uint64_t bd = umma_sdesc(bBase + ks * 256, 128, 6 * 128);
-                    umma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+    const int64_t lbase = (int64_t)b * L;
+
+    if (warp == 0) {
+        // ---- TMA producer
+        if (lane == 0) {
+            int i = 0;
+            int issued[TC_STAGES] = {0, 0, 0, 0};
+            for (int li = sidx; li < nl && !*vFail; li += S) {
+                const int l = blkLeaves[lbase + li];
+                const int64_t size = off[l + 1] - off[l], r0 = bOff[l];
+                for (int64_t t0 = 0; t0 < size; t0 += TC_PM, i++) {
+                    const int st = i % TC_STAGES;
+                    if (!mbar_wait_or_fail(&barEmpty[st], ((i / TC_STAGES) & 1) ^ 1, vFail)) {
+                        atomicOr(&sFail, 1);
+                        break;
+                    }
+                    const int rows = (int)min((int64_t)TC_PM, size - t0);
+                    const uint32_t bytes = (uint32_t)(((rows + 15) & ~15) * TC_ROWB);
+                    mbar_expect_tx(&barFull[st], bytes);
+                    bulk_g2s(sA + st * (TC_PM * TC_ROWB), Bsplit + (r0 + t0) * TC_K, bytes, &barFull[st]);
+                    issued[st]++;
                 }
-                umma_commit(&barMma);
-                mmaOut = true;
+                if (*vFail) break;
             }
-            if (mbar_wait_bounded(&barMma, phMma)) {
-                phMma ^= 1u;
-                mmaOut = false;
-            } else {
-                atomicOr(&sFail, 1);
-            }
-            __syncthreads();
-            if (sFail) break;
-            tc_fence_after();
-            const bool part = cl == CL_PART;
-            // tcgen05.ld is warp-collective: the column loop is warp-uniform
-            if (__any_sync(0xffffffffu, part)) {
-                const float loS = lo - E, hiS = hi + E;
-                for (int c0 = 0; c0 < N; c0 += 16) {
-                    float v[16];
-                    __syncwarp();
-                    tmem_ld16(tlane + (uint32_t)c0, v);
-                    if (!part) continue;
+            for (int st = 0; st < TC_STAGES; st++) sIssued[st] = issued[st];
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            int i = 0;
+            int seen[TC_STAGES] = {0, 0, 0, 0};
+            int committed[2] = {0, 0};
+            const uint32_t idesc = umma_idesc_bf16(TC_PM, Nq);
+            const uint32_t qBase = smem_u32(sQ);
+            for (int li = sidx; li < nl && !*vFail; li += S) {
+                const int l = blkLeaves[lbase + li];
+                const int64_t size = off[l + 1] - off[l];
+                for (int64_t t0 = 0; t0 < size; t0 += TC_PM, i++) {
+                    const int st = i % TC_STAGES, tb = i & 1;
+                    if (!mbar_wait_or_fail(&barFull[st], (i / TC_STAGES) & 1, vFail)) {
+                        atomicOr(&sFail, 1);
+                        break;
+                    }
+                    seen[st]++;
+                    if (!mbar_wait_or_fail(&barTEmpty[tb], ((i >> 1) & 1) ^ 1, vFail)) {
+                        atomicOr(&sFail, 1);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t aBase = smem_u32(sA + st * (TC_PM * TC_ROWB));
 #pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int col = c0 + j;
-                        if (col >= rows) break;
-                        const float vt = __fmaf_rn(-2.f, v[j], __fadd_rn(sNorm[col], nq));
-                        if (vt <= loS) { sure++; continue; }
-                        if (vt > hiS) continue;
-                        const int64_t pos = p0 + t0 + col;
-                        const float ex = pm_pd2_32(O32 + pos * PM_MP, qv);
-                        if (ex <= lo) sure++;
-                        else if (ex <= hi) {
-                            band++;
-                            const int e = atomicAdd(bandN, 1);
-                            if (e < bandCap) { bandA[e] = a; bandPos[e] = (int)pos; }
+                    for (int ks = 0; ks < TC_K / 16; ks++) {
+                        const uint64_t ad = umma_sdesc(aBase + ks * 256, 128, 6 * 128);
+                        const uint64_t bd = umma_sdesc(qBase + ks * 256, 128, 6 * 128);
+                        umma_bf16(tmem + (uint32_t)(tb * TC_QN), ad, bd, idesc, ks > 0 ? 1u : 0u);
+                    }
+                    umma_commit(&barEmpty[st]);
+                    umma_commit(&barTFull[tb]);
+                    committed[tb]++;
+                }
+                if (*vFail) break;
+            }
+            for (int st = 0; st < TC_STAGES; st++) sSeenFull[st] = seen[st];
+            sCommitted[0] = committed[0];
+            sCommitted[1] = committed[1];
+        }
+    } else {
+        // ---- epilogue: group g reads the tiles i with i % 2 == g from TMEM buffer g
+        const int g = (warp - 2) >> 2, qd = warp & 3;
+        const uint32_t taddr = tmem + (uint32_t)(g * TC_QN) + ((uint32_t)(qd * 32) << 16);
+        int i = 0, seenT = 0;
+        for (int li = sidx; li < nl && !*vFail; li += S) {
+            const int l = blkLeaves[lbase + li];
+            const int64_t p0 = off[l], size = off[l + 1] - p0, r0 = bOff[l];
+            const uint32_t mwl = lane < TC_MW ? blkMask[(lbase + li) * TC_MW + lane] : 0u;
+            for (int64_t t0 = 0; t0 < size; t0 += TC_PM, i++) {
+                if ((i & 1) != g) continue;
+                if (!mbar_wait_or_fail(&barTFull[g], (i >> 1) & 1, vFail)) {
+                    atomicOr(&sFail, 1);
+                    break;
+                }
+                seenT++;
+                tc_fence_after();
+                const int rows = (int)min((int64_t)TC_PM, size - t0);
+                if (qd * 32 < rows) {
+                    const int lrow = qd * 32 + lane;
+                    const bool vrow = lrow < rows;
+                    const int64_t pos = p0 + t0 + lrow;
+                    const float no = vrow ? bNorm[r0 + t0 + lrow] : 0.f;
+                    for (int w = 0; w < TC_MW; w++) {
+                        uint32_t bits = __shfl_sync(0xffffffffu, mwl, w);
+                        while (bits) {
+                            // up to four columns per TMEM wait
+                            int jj[4];
+                            float v[4];
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                jj[u] = bits ? w * 32 + __ffs(bits) - 1 : -1;
+                                bits &= bits - 1;
+                            }
+                            __syncwarp();
+#pragma unroll
+                            for (int u = 0; u < 4; u++)
+                                if (jj[u] >= 0) v[u] = __uint_as_float(tmem_ld1(taddr + (uint32_t)jj[u]));
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const int j = jj[u];
+                                if (j < 0) break;
+                                const float4 P = sPar[j];
+                                const float vt = __fmaf_rn(-2.f, v[u], __fadd_rn(no, P.x));
+                                const bool sure = vrow && vt <= P.y;
+                                const bool maybe = vrow && !sure && vt <= P.z;
+                                const unsigned bs = __ballot_sync(0xffffffffu, sure);
+                                if (lane == 0 && bs) atomicAdd(&sCntS[j], __popc(bs));
+                                if (__any_sync(0xffffffffu, maybe) && maybe) {
+                                    const float ex = pm_pd2_32(O32 + pos * PM_MP, sQp + j * PM_MP);
+                                    const float2 lh = sLH[j];
+                                    if (ex <= lh.x) {
+                                        atomicAdd(&sCntS[j], 1);
+                                    } else if (ex <= lh.y) {
+                                        atomicAdd(&sCntB[j], 1);
+                                        const int e = atomicAdd(bandN, 1);
+                                        if (e < bandCap) {
+                                            bandA[e] = a0 + j;
+                                            bandPos[e] = (int)pos;
+                                        }
+                                    }
+                                }
+                            }
                         }
                     }
                 }
+                __syncwarp();
+                tc_fence_before();
+                if (lane == 0) mbar_arrive(&barTEmpty[g]);
             }
-            tc_fence_before();
-            __syncthreads();
+            if (*vFail) break;
         }
-        if (sFail) break;
+        if (lane == 0) atomicMax(&sSeenT[g], seenT);
     }
-    if (valid) {
-        if (sure) atomicAdd(&cntSure[a], sure);
-        if (band) atomicAdd(&cntBand[a], band);
+    __syncthreads();
+    if (tid < nb) {
+        if (sCntS[tid]) atomicAdd(&cntSure[a0 + tid], sCntS[tid]);
+        if (sCntB[tid]) atomicAdd(&cntBand[a0 + tid], sCntB[tid]);
     }
     if (tid == 0 && sFail) {
         atomicOr(errFlag, 128);
-        // nothing may land in shared memory or TMEM after the CTA leaves
-        if (ldOut) mbar_wait_bounded(&barLoad, phLoad);
-        if (mmaOut) mbar_wait_bounded(&barMma, phMma);
+        // nothing may land in shared memory or TMEM after the CTA leaves:
+        // wait (bounded) for the last copy and MMA not yet seen complete
+        for (int st = 0; st < TC_STAGES; st++)
+            if (sIssued[st] > sSeenFull[st]) mbar_wait_bounded(&barFull[st], (uint32_t)((sIssued[st] - 1) & 1));
+        for (int t = 0; t < 2; t++)
+            if (sCommitted[t] > sSeenT[t]) mbar_wait_bounded(&barTFull[t], (uint32_t)((sCommitted[t] - 1) & 1));
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_QN) : "memory");
     }
 }
-
-size_t count_tc_smem() { return (size_t)TC_Q * TC_ROWB + (size_t)TC_N * TC_ROWB + TC_N * 4 + 1024; }
 
 // Locality order: counting sort of queries by leaf key.
 __global__ void k_hist(const unsigned int *__restrict__ key, int64_t nq, int *__restrict__ h)
@@ -1377,9 +1490,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     bfPerSM = std::max(1, bfPerSM);
 
     const bool tensor = o->precision == PMLSH_BF16_TENSOR;
-    // the tensor-core count holds 256 TMEM columns per CTA: at most two CTAs
-    // per SM, enforced through the shared-memory request
-    const size_t tcSmem = std::max<size_t>(count_tc_smem(), 100 * 1024);
+    // the tensor-core count holds all 512 TMEM columns of its SM; its
+    // shared-memory request keeps a second CTA off the SM
     if (tensor) PM_TRY(pm_allow_max_dyn_smem((const void *)k_count_tc));
 
     std::vector<int32_t> actH;
@@ -1391,11 +1503,13 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         const int na = (int)actH.size();
         if (na == 0) break;
         const int nblk = (na + QB - 1) / QB;
-        const int nblkT = (na + TC_Q - 1) / TC_Q;
+        const int nblkT = (na + TC_QN - 1) / TC_QN;
         const int nlist = tensor ? nblkT : nblk;
+        const int mwords = tensor ? TC_MW : QB / 32;
         PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         int *blkCnt = grow<int>(w.blkCnt, nlist, s);
         int *blkLeaves = grow<int>(w.blkLeaves, (size_t)nlist * L, s);
+        uint32_t *blkMask = grow<uint32_t>(w.blkMask, (size_t)nlist * L * mwords, s);
         if (s != PMLSH_OK) return s;
         PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(cntSure, 0, na * sizeof(int), st));
@@ -1407,21 +1521,21 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         if (!tensor) {
             dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblk);
             PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
-                                        cntSure, blkCnt, blkLeaves));
+                                        cntSure, blkCnt, blkLeaves, blkMask));
             int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
-            PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                                        ix->leafOff, ix->O32, blkCnt, blkLeaves, L,
+            PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->leafOff, ix->O32,
+                                                        blkCnt, blkLeaves, blkMask, L,
                                                         cntSure, cntBand, bandN, bandCap, bandA, bandPos));
         } else {
-            // 128-query blocks: leaf lists per block, then the tensor-core count
+            // 256-query blocks: leaf lists with masks, then the tensor-core count
             dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblkT);
-            PM_LAUNCH("k_class", st, k_class<TC_Q><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
-                                          cntSure, blkCnt, blkLeaves));
-            int splitC = std::max(1, std::min(128, (2 * nsm + nblkT - 1) / nblkT));
-            PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_Q, tcSmem, st>>>(
-                                        act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, ix->O32,
-                                        ix->bOff, ix->Bsplit, ix->bNorm, blkCnt, blkLeaves, L, ix->maxNorm,
-                                        cntSure, cntBand, bandN, bandCap, bandA, bandPos, errFlag));
+            PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
+                                           cntSure, blkCnt, blkLeaves, blkMask));
+            int splitC = std::max(1, std::min(256, (4 * nsm + nblkT - 1) / nblkT));
+            PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_THREADS, TC_SMEM_REQ, st>>>(
+                                        act, na, thr, qp32, ix->leafOff, ix->O32, ix->bOff, ix->Bsplit, ix->bNorm,
+                                        blkCnt, blkLeaves, blkMask, L, ix->maxNorm, cntSure, cntBand,
+                                        bandN, bandCap, bandA, bandPos, errFlag));
         }
         // FP64 band resolution (grid sized by the capacity; empty threads exit)
         {

@@ -56,7 +56,7 @@ struct DevBuf {
 // demand, reused across calls).
 struct KnnWork {
     DevBuf Qd, qp32, qp64, qnorm, qpiv, order, keys, keys2, vals2, sortTmp;
-    DevBuf qstate, thr, blkCnt, blkLeaves, cntSure, cntBand, bandQ, bandPos,
+    DevBuf qstate, thr, blkCnt, blkLeaves, blkMask, cntSure, cntBand, bandQ, bandPos,
         bandIn, bandCnt;
     DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
     DevBuf selBuf, selOff, selCnt, selTau;
