@@ -133,14 +133,15 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 
 // Block b of the active list (QBT queries) x 128 leaves: leaf classification
 // and whole-leaf counts.  Leaves that some query of the block covers only
-// partially are listed for the block, each with the QBT-bit mask of those
-// queries (bit qq of word qq / 32).
+// partially are listed for the block as {leaf, first position, size, first
+// tensor-operand row}, each with the QBT-bit mask of those queries (bit qq
+// of word qq / 32).
 template <int QBT>
 __global__ void __launch_bounds__(128)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
-        const float *__restrict__ meta, const int64_t *__restrict__ off, int64_t L,
-        int *__restrict__ cntSure, int *__restrict__ blkCnt, int *__restrict__ blkLeaves,
+        const float *__restrict__ meta, const int64_t *__restrict__ off, const int64_t *__restrict__ bOff,
+        int64_t L, int *__restrict__ cntSure, int *__restrict__ blkCnt, int4 *__restrict__ blkEnt,
         uint32_t *__restrict__ blkMask)
 {
     constexpr int W = QBT / 32;
@@ -195,7 +196,7 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     if (anyPart) {
         const int slot = atomicAdd(&blkCnt[b], 1);
         const int64_t e = (int64_t)b * L + slot;
-        blkLeaves[e] = (int)l;
+        blkEnt[e] = make_int4((int)l, (int)off[l], (int)(off[l + 1] - off[l]), bOff ? (int)bOff[l] : 0);
 #pragma unroll
         for (int w = 0; w < W; w++) blkMask[e * W + w] = mw[w];
     }
@@ -208,8 +209,8 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
 // list mask).  Grid (block, split).
 __global__ void __launch_bounds__(256)
 k_count(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
-        const float *__restrict__ qp32, const int64_t *__restrict__ off, const float *__restrict__ O32,
-        const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves,
+        const float *__restrict__ qp32, const float *__restrict__ O32,
+        const int *__restrict__ blkCnt, const int4 *__restrict__ blkEnt,
         const uint32_t *__restrict__ blkMask, int64_t L,
         int *__restrict__ cntSure, int *__restrict__ cntBand,
         int *__restrict__ bandN, int bandCap, int *__restrict__ bandA, int *__restrict__ bandPos)
@@ -237,10 +238,10 @@ k_count(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     const int nl = blkCnt[b];
     for (int li = blockIdx.y; li < nl; li += gridDim.y) {
         const int64_t e = (int64_t)b * L + li;
-        const int l = blkLeaves[e];
+        const int4 ent = blkEnt[e];
         const unsigned long long part =
             ((unsigned long long)blkMask[e * 2 + 1] << 32) | (unsigned long long)blkMask[e * 2];
-        const int64_t p0 = off[l], p1 = off[l + 1];
+        const int64_t p0 = ent.y, p1 = (int64_t)ent.y + ent.z;
         for (int64_t base = p0; base < p1; base += blockDim.x) {
             const int64_t pos = base + threadIdx.x;
             const bool valid = pos < p1;
@@ -1028,11 +1029,13 @@ constexpr int TC_PM = 128;         // points per tile: MMA M, TMEM lanes
 constexpr int TC_K = 48;           // [hi | hi | lo] . [hi | lo | hi] of 16 coordinates
 constexpr int TC_ROWB = TC_K * 2;  // bytes per operand row
 constexpr int TC_STAGES = 4;       // point tiles in flight
-constexpr int TC_THREADS = 320;    // warp 0 loads, warp 1 MMA, warps 2-9 epilogue
+constexpr int TC_EPI = 16;         // epilogue warps: 2 TMEM buffers x 2 halves x 4 lane quarters
+constexpr int TC_THREADS = 32 * (2 + TC_EPI);
 constexpr int TC_MW = TC_QN / 32;  // mask words per list entry
-// dynamic shared memory: query operand, point-tile ring, per-query data
+// dynamic shared memory: query operand, point-tile ring, norms ring, per-query data
 constexpr int TC_OFF_A = TC_QN * TC_ROWB;                              // 24 KB
-constexpr int TC_OFF_QP = TC_OFF_A + TC_STAGES * TC_PM * TC_ROWB;      // + 48 KB
+constexpr int TC_OFF_NO = TC_OFF_A + TC_STAGES * TC_PM * TC_ROWB;      // + 48 KB
+constexpr int TC_OFF_QP = TC_OFF_NO + TC_STAGES * TC_PM * 4;           // + 2 KB
 constexpr int TC_OFF_PAR = TC_OFF_QP + TC_QN * PM_MP * 4;              // + 16 KB
 constexpr int TC_OFF_LH = TC_OFF_PAR + TC_QN * 16;
 constexpr int TC_OFF_CNT = TC_OFF_LH + TC_QN * 8;
@@ -1062,16 +1065,19 @@ __device__ __forceinline__ bool mbar_wait_or_fail(uint64_t *bar, uint32_t ph, vo
 // lo - E is surely in, > hi + E surely out, and in between pm_pd2_32 decides
 // exactly as k_count does: counts and band lists equal k_count's.
 //
-// Roles: warp 0 streams point tiles into a 4-stage ring with TMA bulk copies,
-// warp 1 issues tcgen05.mma into one of two TMEM accumulators, warps 2-5 and
-// 6-9 (one warp per TMEM lane quarter each) read even and odd tiles.  Every
-// wait is bounded; on a timeout the CTA records error bit 128, lets the
-// copies and MMAs it issued complete and frees its TMEM.
+// Roles: warp 0 streams point tiles and their norms into a 4-stage ring with
+// TMA bulk copies, warp 1 issues tcgen05.mma into one of two TMEM
+// accumulators (even / odd tiles), and 16 epilogue warps read them: per
+// accumulator two halves of four warps (one per TMEM lane quarter), the
+// halves taking alternate partial columns.  The epilogue releases both the
+// accumulator and the ring stage.  Every wait is bounded; on a timeout the
+// CTA records error bit 128, lets the copies and MMAs it issued complete and
+// frees its TMEM.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
-           const float *__restrict__ qp32, const int64_t *__restrict__ off, const float *__restrict__ O32,
-           const int64_t *__restrict__ bOff, const uint16_t *__restrict__ Bsplit, const float *__restrict__ bNorm,
-           const int *__restrict__ blkCnt, const int *__restrict__ blkLeaves, const uint32_t *__restrict__ blkMask,
+           const float *__restrict__ qp32, const float *__restrict__ O32,
+           const uint16_t *__restrict__ Bsplit, const float *__restrict__ bNorm,
+           const int *__restrict__ blkCnt, const int4 *__restrict__ blkEnt, const uint32_t *__restrict__ blkMask,
            int64_t L, double maxNorm, int *__restrict__ cntSure, int *__restrict__ cntBand,
            int *__restrict__ bandN, int bandCap, int *__restrict__ bandA, int *__restrict__ bandPos,
            int *__restrict__ errFlag)
@@ -1079,6 +1085,7 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char *sQ = tsm;
     unsigned char *sA = tsm + TC_OFF_A;
+    float *sNo = (float *)(tsm + TC_OFF_NO);
     float *sQp = (float *)(tsm + TC_OFF_QP);
     float4 *sPar = (float4 *)(tsm + TC_OFF_PAR);   // ||q'||^2, lo - E, hi + E
     float2 *sLH = (float2 *)(tsm + TC_OFF_LH);     // lo, hi
@@ -1150,13 +1157,13 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         sFail = 0;
         for (int st = 0; st < TC_STAGES; st++) {
             mbar_init(&barFull[st], 1);
-            mbar_init(&barEmpty[st], 1);
+            mbar_init(&barEmpty[st], TC_EPI / 2);
             sIssued[st] = 0;
             sSeenFull[st] = 0;
         }
         for (int t = 0; t < 2; t++) {
             mbar_init(&barTFull[t], 1);
-            mbar_init(&barTEmpty[t], 4);
+            mbar_init(&barTEmpty[t], TC_EPI / 2);
             sCommitted[t] = 0;
             sSeenT[t] = 0;
         }
@@ -1175,22 +1182,23 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         if (lane == 0) {
             int i = 0;
             int issued[TC_STAGES] = {0, 0, 0, 0};
+            int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
             for (int li = sidx; li < nl && !*vFail; li += S) {
-                const int l = blkLeaves[lbase + li];
-                const int64_t size = off[l + 1] - off[l], r0 = bOff[l];
-                for (int64_t t0 = 0; t0 < size; t0 += TC_PM, i++) {
+                const int4 ent = nxt;
+                if (li + S < nl) nxt = blkEnt[lbase + li + S];
+                for (int t0 = 0; t0 < ent.z; t0 += TC_PM, i++) {
                     const int st = i % TC_STAGES;
                     if (!mbar_wait_or_fail(&barEmpty[st], ((i / TC_STAGES) & 1) ^ 1, vFail)) {
                         atomicOr(&sFail, 1);
                         break;
                     }
-                    const int rows = (int)min((int64_t)TC_PM, size - t0);
-                    const uint32_t bytes = (uint32_t)(((rows + 15) & ~15) * TC_ROWB);
-                    mbar_expect_tx(&barFull[st], bytes);
-                    bulk_g2s(sA + st * (TC_PM * TC_ROWB), Bsplit + (r0 + t0) * TC_K, bytes, &barFull[st]);
+                    const int nr = (min(TC_PM, ent.z - t0) + 15) & ~15;
+                    const int64_t r = (int64_t)ent.w + t0;
+                    mbar_expect_tx(&barFull[st], (uint32_t)(nr * (TC_ROWB + 4)));
+                    bulk_g2s(sA + st * (TC_PM * TC_ROWB), Bsplit + r * TC_K, (uint32_t)(nr * TC_ROWB), &barFull[st]);
+                    bulk_g2s(sNo + st * TC_PM, bNorm + r, (uint32_t)(nr * 4), &barFull[st]);
                     issued[st]++;
                 }
-                if (*vFail) break;
             }
             for (int st = 0; st < TC_STAGES; st++) sIssued[st] = issued[st];
         }
@@ -1202,10 +1210,11 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
             int committed[2] = {0, 0};
             const uint32_t idesc = umma_idesc_bf16(TC_PM, Nq);
             const uint32_t qBase = smem_u32(sQ);
+            int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
             for (int li = sidx; li < nl && !*vFail; li += S) {
-                const int l = blkLeaves[lbase + li];
-                const int64_t size = off[l + 1] - off[l];
-                for (int64_t t0 = 0; t0 < size; t0 += TC_PM, i++) {
+                const int4 ent = nxt;
+                if (li + S < nl) nxt = blkEnt[lbase + li + S];
+                for (int t0 = 0; t0 < ent.z; t0 += TC_PM, i++) {
                     const int st = i % TC_STAGES, tb = i & 1;
                     if (!mbar_wait_or_fail(&barFull[st], (i / TC_STAGES) & 1, vFail)) {
                         atomicOr(&sFail, 1);
@@ -1224,41 +1233,65 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                         const uint64_t bd = umma_sdesc(qBase + ks * 256, 128, 6 * 128);
                         umma_bf16(tmem + (uint32_t)(tb * TC_QN), ad, bd, idesc, ks > 0 ? 1u : 0u);
                     }
-                    umma_commit(&barEmpty[st]);
                     umma_commit(&barTFull[tb]);
                     committed[tb]++;
                 }
-                if (*vFail) break;
             }
             for (int st = 0; st < TC_STAGES; st++) sSeenFull[st] = seen[st];
             sCommitted[0] = committed[0];
             sCommitted[1] = committed[1];
         }
     } else {
-        // ---- epilogue: group g reads the tiles i with i % 2 == g from TMEM buffer g
-        const int g = (warp - 2) >> 2, qd = warp & 3;
-        const uint32_t taddr = tmem + (uint32_t)(g * TC_QN) + ((uint32_t)(qd * 32) << 16);
+        // ---- epilogue: warps of accumulator tb read the tiles i with
+        // i % 2 == tb; half h takes the partial columns of rank parity h
+        const int e = warp - 2, tb = e >> 3, h = (e >> 2) & 1, qd = warp & 3;
+        const uint32_t taddr = tmem + (uint32_t)(tb * TC_QN) + ((uint32_t)(qd * 32) << 16);
         int i = 0, seenT = 0;
+        int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
+        uint32_t mnxt = (sidx < nl && lane < TC_MW) ? blkMask[(lbase + sidx) * TC_MW + lane] : 0u;
         for (int li = sidx; li < nl && !*vFail; li += S) {
-            const int l = blkLeaves[lbase + li];
-            const int64_t p0 = off[l], size = off[l + 1] - p0, r0 = bOff[l];
-            const uint32_t mwl = lane < TC_MW ? blkMask[(lbase + li) * TC_MW + lane] : 0u;
-            for (int64_t t0 = 0; t0 < size; t0 += TC_PM, i++) {
-                if ((i & 1) != g) continue;
-                if (!mbar_wait_or_fail(&barTFull[g], (i >> 1) & 1, vFail)) {
+            const int4 ent = nxt;
+            const uint32_t mwl = mnxt;
+            if (li + S < nl) {
+                nxt = blkEnt[lbase + li + S];
+                mnxt = lane < TC_MW ? blkMask[(lbase + li + S) * TC_MW + lane] : 0u;
+            }
+            for (int t0 = 0; t0 < ent.z; t0 += TC_PM, i++) {
+                if ((i & 1) != tb) continue;
+                if (!mbar_wait_or_fail(&barTFull[tb], (i >> 1) & 1, vFail)) {
                     atomicOr(&sFail, 1);
                     break;
                 }
                 seenT++;
                 tc_fence_after();
-                const int rows = (int)min((int64_t)TC_PM, size - t0);
+                const int st = i % TC_STAGES;
+                // the stage's norms came by TMA: observe that copy's completion
+                // (already reached; the stage is not refilled before this tile
+                // releases it)
+                if (!mbar_wait_or_fail(&barFull[st], (i / TC_STAGES) & 1, vFail)) {
+                    atomicOr(&sFail, 1);
+                    break;
+                }
+                const int rows = min(TC_PM, ent.z - t0);
                 if (qd * 32 < rows) {
                     const int lrow = qd * 32 + lane;
                     const bool vrow = lrow < rows;
-                    const int64_t pos = p0 + t0 + lrow;
-                    const float no = vrow ? bNorm[r0 + t0 + lrow] : 0.f;
+                    const int64_t pos = (int64_t)ent.y + t0 + lrow;
+                    const float no = sNo[st * TC_PM + lrow];
+                    uint32_t cpar = 0u;   // parity of the partial columns before this word
                     for (int w = 0; w < TC_MW; w++) {
-                        uint32_t bits = __shfl_sync(0xffffffffu, mwl, w);
+                        const uint32_t all = __shfl_sync(0xffffffffu, mwl, w);
+                        // prefix parity: bit c = parity of the set bits at or below c
+                        uint32_t px = all;
+                        px ^= px << 1;
+                        px ^= px << 2;
+                        px ^= px << 4;
+                        px ^= px << 8;
+                        px ^= px << 16;
+                        px ^= cpar;
+                        cpar ^= (uint32_t)0 - (uint32_t)(__popc(all) & 1);
+                        // odd ranks (px bit 1) to half 0, even ranks to half 1
+                        uint32_t bits = all & (h ? ~px : px);
                         while (bits) {
                             // up to four columns per TMEM wait
                             int jj[4];
@@ -1290,10 +1323,10 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                                         atomicAdd(&sCntS[j], 1);
                                     } else if (ex <= lh.y) {
                                         atomicAdd(&sCntB[j], 1);
-                                        const int e = atomicAdd(bandN, 1);
-                                        if (e < bandCap) {
-                                            bandA[e] = a0 + j;
-                                            bandPos[e] = (int)pos;
+                                        const int e2 = atomicAdd(bandN, 1);
+                                        if (e2 < bandCap) {
+                                            bandA[e2] = a0 + j;
+                                            bandPos[e2] = (int)pos;
                                         }
                                     }
                                 }
@@ -1303,11 +1336,13 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                 }
                 __syncwarp();
                 tc_fence_before();
-                if (lane == 0) mbar_arrive(&barTEmpty[g]);
+                if (lane == 0) {
+                    mbar_arrive(&barTEmpty[tb]);
+                    mbar_arrive(&barEmpty[st]);
+                }
             }
-            if (*vFail) break;
         }
-        if (lane == 0) atomicMax(&sSeenT[g], seenT);
+        if (lane == 0) atomicMax(&sSeenT[tb], seenT);
     }
     __syncthreads();
     if (tid < nb) {
@@ -1508,7 +1543,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         const int mwords = tensor ? TC_MW : QB / 32;
         PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         int *blkCnt = grow<int>(w.blkCnt, nlist, s);
-        int *blkLeaves = grow<int>(w.blkLeaves, (size_t)nlist * L, s);
+        int4 *blkEnt = grow<int4>(w.blkLeaves, (size_t)nlist * L, s);
         uint32_t *blkMask = grow<uint32_t>(w.blkMask, (size_t)nlist * L * mwords, s);
         if (s != PMLSH_OK) return s;
         PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
@@ -1520,21 +1555,21 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
         if (!tensor) {
             dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblk);
-            PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
-                                        cntSure, blkCnt, blkLeaves, blkMask));
+            PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff,
+                                        nullptr, L, cntSure, blkCnt, blkEnt, blkMask));
             int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
-            PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->leafOff, ix->O32,
-                                                        blkCnt, blkLeaves, blkMask, L,
+            PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->O32,
+                                                        blkCnt, blkEnt, blkMask, L,
                                                         cntSure, cntBand, bandN, bandCap, bandA, bandPos));
         } else {
             // 256-query blocks: leaf lists with masks, then the tensor-core count
             dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblkT);
-            PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L,
-                                           cntSure, blkCnt, blkLeaves, blkMask));
+            PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff,
+                                           ix->bOff, L, cntSure, blkCnt, blkEnt, blkMask));
             int splitC = std::max(1, std::min(256, (4 * nsm + nblkT - 1) / nblkT));
             PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_THREADS, TC_SMEM_REQ, st>>>(
-                                        act, na, thr, qp32, ix->leafOff, ix->O32, ix->bOff, ix->Bsplit, ix->bNorm,
-                                        blkCnt, blkLeaves, blkMask, L, ix->maxNorm, cntSure, cntBand,
+                                        act, na, thr, qp32, ix->O32, ix->Bsplit, ix->bNorm,
+                                        blkCnt, blkEnt, blkMask, L, ix->maxNorm, cntSure, cntBand,
                                         bandN, bandCap, bandA, bandPos, errFlag));
         }
         // FP64 band resolution (grid sized by the capacity; empty threads exit)
