@@ -1024,25 +1024,63 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int TC_QN = 256;         // queries per block: MMA N, TMEM columns per buffer
-constexpr int TC_PM = 128;         // points per tile: MMA M, TMEM lanes
-constexpr int TC_K = 48;           // [hi | hi | lo] . [hi | lo | hi] of 16 coordinates
+// 16 consecutive FP32 accumulator columns of this warp's lane quarter.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int TC_QN = 256;         // queries per block
+constexpr int TC_MT = 128;         // compacted queries per MMA (M, TMEM lanes)
+constexpr int TC_NT = 128;         // points per job at most (N)
+constexpr int TC_K = 48;           // [hi | lo | hi] . [hi | hi | lo] of 16 coordinates
 constexpr int TC_ROWB = TC_K * 2;  // bytes per operand row
-constexpr int TC_STAGES = 4;       // point tiles in flight
-constexpr int TC_EPI = 16;         // epilogue warps: 2 TMEM buffers x 2 halves x 4 lane quarters
-constexpr int TC_THREADS = 32 * (2 + TC_EPI);
+constexpr int TC_SO = 4;           // operand stages (released when the MMA completes)
+constexpr int TC_SJ = 8;           // job slots: norms, rank -> query map (released by the epilogue)
+constexpr int TC_EPI = 16;         // epilogue warps: 2 TMEM buffers x 2 M-tiles x 4 lane quarters
+constexpr int TC_THREADS = 32 * (2 + 4 + TC_EPI);   // loader, MMA, 4 builder warps, epilogue
 constexpr int TC_MW = TC_QN / 32;  // mask words per list entry
-// dynamic shared memory: query operand, point-tile ring, norms ring, per-query data
-constexpr int TC_OFF_A = TC_QN * TC_ROWB;                              // 24 KB
-constexpr int TC_OFF_NO = TC_OFF_A + TC_STAGES * TC_PM * TC_ROWB;      // + 48 KB
-constexpr int TC_OFF_QP = TC_OFF_NO + TC_STAGES * TC_PM * 4;           // + 2 KB
-constexpr int TC_OFF_PAR = TC_OFF_QP + TC_QN * PM_MP * 4;              // + 16 KB
-constexpr int TC_OFF_LH = TC_OFF_PAR + TC_QN * 16;
-constexpr int TC_OFF_CNT = TC_OFF_LH + TC_QN * 8;
-constexpr int TC_SMEM = TC_OFF_CNT + 2 * TC_QN * 4;
-// at most one CTA per SM (the CTA holds all 512 TMEM columns)
-constexpr int TC_SMEM_REQ = 120 * 1024;
-static_assert(TC_SMEM <= TC_SMEM_REQ, "tensor-count shared memory");
+constexpr int TC_MAYBE = 1024;     // pairs inside the error band staged per CTA
+// dynamic shared memory
+constexpr int TC_ASZ = 2 * TC_MT * TC_ROWB;                    // two M-tiles per stage, 24 KB
+constexpr int TC_BSZ = TC_NT * TC_ROWB;                        // 12 KB
+constexpr int TC_JSZ = TC_NT * 4 + TC_QN * 4;                  // norms + map, 1.5 KB
+constexpr int TC_OFF_B = TC_SO * TC_ASZ;
+constexpr int TC_OFF_J = TC_OFF_B + TC_SO * TC_BSZ;
+constexpr int TC_OFF_QR = TC_OFF_J + TC_SJ * TC_JSZ;           // query rows [256][96 B]
+constexpr int TC_OFF_PAR = TC_OFF_QR + TC_QN * TC_ROWB;
+constexpr int TC_OFF_MAY = TC_OFF_PAR + TC_QN * 16;
+constexpr int TC_OFF_CNT = TC_OFF_MAY + TC_MAYBE * 8;
+constexpr int TC_SMEM = TC_OFF_CNT + TC_QN * 4;
+static_assert(TC_SMEM <= 220 * 1024, "tensor-count shared memory");
+
+// The CUDA-core count's decision for one pair: 1 surely in (<= lo), 2 in
+// the band (<= hi), 0 out.
+__device__ __forceinline__ int exact_class(const float *o, const float *q, float lo, float hi)
+{
+    const float ex = pm_pd2_32(o, q);
+    return ex <= lo ? 1 : (ex <= hi ? 2 : 0);
+}
+
+// OR of `p` over the 128 threads of named barrier 1 (the operand builders).
+__device__ __forceinline__ bool bar1_or_128(bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
 
 // Waits for phase `ph` of `bar`, giving up on the iteration limit or when
 // another role has already failed (fail != 0).
@@ -1055,59 +1093,58 @@ __device__ __forceinline__ bool mbar_wait_or_fail(uint64_t *bar, uint32_t ph, vo
     return false;
 }
 
-// Range count of one round on the tensor cores, point-major: for a block of
-// up to 256 queries and each listed leaf (tiles of 128 points), TMEM holds
-// the 128 x 256 dot products q'.o' of a BF16 split of the FP32 coordinates
-// (three products, FP32 accumulate).  Only the columns of queries that cover
-// the leaf partially are read.  With E bounding |d'^2~ - pm_pd2_32| for
-// d'^2~ = ||o'||^2 + ||q'||^2 - 2 q'.o' (split and accumulation error, FP32
-// rounding of the norms, the CUDA-core computation's own error), d'^2~ <=
-// lo - E is surely in, > hi + E surely out, and in between pm_pd2_32 decides
-// exactly as k_count does: counts and band lists equal k_count's.
+// Range count of one round on the tensor cores.  A job is a listed leaf (or
+// its next 128 points) of a block of up to 256 queries: the queries that
+// cover the leaf partially are compacted into one or two 128-row operands,
+// and TMEM receives their dot products q'.o' with the leaf's points (BF16
+// split of the FP32 coordinates, three products, FP32 accumulate).  A lane
+// of the epilogue is a query: with E bounding |d'^2~ - pm_pd2_32| for d'^2~ =
+// ||o'||^2 + ||q'||^2 - 2 q'.o' (split and accumulation error, FP32 rounding
+// of the norms, the CUDA-core computation's own error), d'^2~ <= lo - E is
+// surely in and > hi + E surely out; the pairs in between go to a recheck
+// list that k_recheck decides exactly as k_count does.  Counts and band
+// lists therefore equal k_count's.
 //
-// Roles: warp 0 streams point tiles and their norms into a 4-stage ring with
-// TMA bulk copies, warp 1 issues tcgen05.mma into one of two TMEM
-// accumulators (even / odd tiles), and 16 epilogue warps read them: per
-// accumulator two halves of four warps (one per TMEM lane quarter), the
-// halves taking alternate partial columns.  The epilogue releases both the
-// accumulator and the ring stage.  Every wait is bounded; on a timeout the
-// CTA records error bit 128, lets the copies and MMAs it issued complete and
-// frees its TMEM.
+// Roles: warp 0 streams point tiles (operand ring) and their norms (job
+// ring) with TMA bulk copies, warps 2-5 build the compacted query operand
+// and the job's rank -> query map, warp 1 issues tcgen05.mma into one of two
+// TMEM buffers (even / odd jobs) and releases the operand stages on
+// completion, 16 epilogue warps (buffer x M-tile x lane quarter) read TMEM
+// and release the buffer and the job slot.  Every wait is bounded; on a
+// timeout the CTA records error bit 128, waits (bounded) for the copies and
+// MMAs it issued and frees its TMEM.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
-           const float *__restrict__ qp32, const float *__restrict__ O32,
-           const uint16_t *__restrict__ Bsplit, const float *__restrict__ bNorm,
+           const float *__restrict__ qp32, const uint16_t *__restrict__ Bsplit, const float *__restrict__ bNorm,
            const int *__restrict__ blkCnt, const int4 *__restrict__ blkEnt, const uint32_t *__restrict__ blkMask,
-           int64_t L, double maxNorm, int *__restrict__ cntSure, int *__restrict__ cntBand,
-           int *__restrict__ bandN, int bandCap, int *__restrict__ bandA, int *__restrict__ bandPos,
-           int *__restrict__ errFlag)
+           int64_t L, double maxNorm, int *__restrict__ cntSure, int *__restrict__ recheckN, int recheckCap,
+           int2 *__restrict__ recheck, int *__restrict__ errFlag)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char *sQ = tsm;
-    unsigned char *sA = tsm + TC_OFF_A;
-    float *sNo = (float *)(tsm + TC_OFF_NO);
-    float *sQp = (float *)(tsm + TC_OFF_QP);
+    unsigned char *sA = tsm;
+    unsigned char *sB = tsm + TC_OFF_B;
+    unsigned char *sJ = tsm + TC_OFF_J;
+    unsigned char *sQr = tsm + TC_OFF_QR;
     float4 *sPar = (float4 *)(tsm + TC_OFF_PAR);   // ||q'||^2, lo - E, hi + E
-    float2 *sLH = (float2 *)(tsm + TC_OFF_LH);     // lo, hi
+    int2 *sMay = (int2 *)(tsm + TC_OFF_MAY);
     int *sCntS = (int *)(tsm + TC_OFF_CNT);
-    int *sCntB = sCntS + TC_QN;
-    __shared__ __align__(8) uint64_t barFull[TC_STAGES], barEmpty[TC_STAGES], barTFull[2], barTEmpty[2];
+    __shared__ __align__(8) uint64_t barBFull[TC_SO], barBEmpty[TC_SO], barAFull[TC_SO], barAEmpty[TC_SO];
+    __shared__ __align__(8) uint64_t barJFull[TC_SJ], barJEmpty[TC_SJ], barTFull[2], barTEmpty[2];
     __shared__ uint32_t sTmem;
-    __shared__ int sFail;
-    __shared__ int sIssued[TC_STAGES], sSeenFull[TC_STAGES], sCommitted[2], sSeenT[2];
+    __shared__ int sFail, sMayN, sMayBase;
+    __shared__ int sNpart[TC_SJ];
+    __shared__ int sIssB[TC_SO], sSeenB[TC_SO], sIssJ[TC_SJ], sSeenJ[TC_SJ], sCommitted[2], sSeenT[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.x, S = gridDim.y, sidx = blockIdx.y;
     const int a0 = b * TC_QN;
     const int nb = min(TC_QN, na - a0);
-    const int Nq = (nb + 15) & ~15;
     volatile int *vFail = &sFail;
 
-    // query operand [hi | lo | hi], per-query thresholds and error bound
+    // query rows [hi | lo | hi], per-query thresholds and error bound
     if (tid < TC_QN) {
         const int j = tid;
         float qv[PM_MP];
         float4 par = make_float4(0.f, -INFINITY, -INFINITY, 0.f);
-        float2 lh = make_float2(-INFINITY, -INFINITY);
         if (j < nb) {
             const int q = act[a0 + j];
             double nn = 0.0;
@@ -1126,40 +1163,42 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
             const double E = 1.25 * (2.0 * (3.0 * 0x1.0p-16 + 128.0 * 0x1.0p-23) * qn * maxNorm +
                                      0x1.0p-22 * (nn + maxNorm * maxNorm) + 0x1.0p-18 * (double)T.hi) + 1e-30;
             par = make_float4((float)nn, (float)((double)T.lo - E), (float)((double)T.hi + E), 0.f);
-            lh = make_float2(T.lo, T.hi);
         } else {
             for (int c = 0; c < PM_MP; c++) qv[c] = 0.f;
         }
         sPar[j] = par;
-        sLH[j] = lh;
         sCntS[j] = 0;
-        sCntB[j] = 0;
-        const int g = j >> 3, i = j & 7;
-        uint16_t *Q16 = (uint16_t *)sQ;
+        uint16_t *row = (uint16_t *)(sQr + j * TC_ROWB);
         for (int c = 0; c < PM_MP; c++) {
-            sQp[j * PM_MP + c] = qv[c];
             const __nv_bfloat16 h = __float2bfloat16_rn(qv[c]);
             const __nv_bfloat16 l = __float2bfloat16_rn(qv[c] - __bfloat162float(h));
-            const uint16_t hb = __bfloat16_as_ushort(h), lb = __bfloat16_as_ushort(l);
-            const int k0 = c, k1 = 16 + c, k2 = 32 + c;
-            Q16[((g * 6 + (k0 >> 3)) * 8 + i) * 8 + (k0 & 7)] = hb;
-            Q16[((g * 6 + (k1 >> 3)) * 8 + i) * 8 + (k1 & 7)] = lb;
-            Q16[((g * 6 + (k2 >> 3)) * 8 + i) * 8 + (k2 & 7)] = hb;
+            row[c] = __bfloat16_as_ushort(h);
+            row[16 + c] = __bfloat16_as_ushort(l);
+            row[32 + c] = __bfloat16_as_ushort(h);
         }
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTmem)),
-                     "r"(2 * TC_QN)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 32) {
+    if (tid == 0) {
         sFail = 0;
-        for (int st = 0; st < TC_STAGES; st++) {
-            mbar_init(&barFull[st], 1);
-            mbar_init(&barEmpty[st], TC_EPI / 2);
-            sIssued[st] = 0;
-            sSeenFull[st] = 0;
+        sMayN = 0;
+        for (int st = 0; st < TC_SO; st++) {
+            mbar_init(&barBFull[st], 1);
+            mbar_init(&barBEmpty[st], 1);
+            mbar_init(&barAFull[st], 1);
+            mbar_init(&barAEmpty[st], 1);
+            sIssB[st] = 0;
+            sSeenB[st] = 0;
+        }
+        for (int s = 0; s < TC_SJ; s++) {
+            mbar_init(&barJFull[s], 2);   // loader (norms, with tx) + builders (map)
+            mbar_init(&barJEmpty[s], TC_EPI / 2);
+            sIssJ[s] = 0;
+            sSeenJ[s] = 0;
         }
         for (int t = 0; t < 2; t++) {
             mbar_init(&barTFull[t], 1);
@@ -1169,7 +1208,6 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    fence_async_shared();   // query operand (generic stores) -> tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -1178,191 +1216,270 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     const int64_t lbase = (int64_t)b * L;
 
     if (warp == 0) {
-        // ---- TMA producer
+        // ---- TMA loader: points into the operand ring, norms into the job slot
         if (lane == 0) {
             int i = 0;
-            int issued[TC_STAGES] = {0, 0, 0, 0};
             int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
             for (int li = sidx; li < nl && !*vFail; li += S) {
                 const int4 ent = nxt;
                 if (li + S < nl) nxt = blkEnt[lbase + li + S];
-                for (int t0 = 0; t0 < ent.z; t0 += TC_PM, i++) {
-                    const int st = i % TC_STAGES;
-                    if (!mbar_wait_or_fail(&barEmpty[st], ((i / TC_STAGES) & 1) ^ 1, vFail)) {
+                for (int t0 = 0; t0 < ent.z; t0 += TC_NT, i++) {
+                    const int so = i % TC_SO, sj = i % TC_SJ;
+                    if (!mbar_wait_or_fail(&barBEmpty[so], ((i / TC_SO) & 1) ^ 1, vFail) ||
+                        !mbar_wait_or_fail(&barJEmpty[sj], ((i / TC_SJ) & 1) ^ 1, vFail)) {
                         atomicOr(&sFail, 1);
                         break;
                     }
-                    const int nr = (min(TC_PM, ent.z - t0) + 15) & ~15;
+                    const int nr = (min(TC_NT, ent.z - t0) + 15) & ~15;
                     const int64_t r = (int64_t)ent.w + t0;
-                    mbar_expect_tx(&barFull[st], (uint32_t)(nr * (TC_ROWB + 4)));
-                    bulk_g2s(sA + st * (TC_PM * TC_ROWB), Bsplit + r * TC_K, (uint32_t)(nr * TC_ROWB), &barFull[st]);
-                    bulk_g2s(sNo + st * TC_PM, bNorm + r, (uint32_t)(nr * 4), &barFull[st]);
-                    issued[st]++;
+                    mbar_expect_tx(&barBFull[so], (uint32_t)(nr * TC_ROWB));
+                    bulk_g2s(sB + so * TC_BSZ, Bsplit + r * TC_K, (uint32_t)(nr * TC_ROWB), &barBFull[so]);
+                    sIssB[so]++;
+                    mbar_expect_tx(&barJFull[sj], (uint32_t)(nr * 4));
+                    bulk_g2s(sJ + sj * TC_JSZ, bNorm + r, (uint32_t)(nr * 4), &barJFull[sj]);
+                    sIssJ[sj]++;
                 }
             }
-            for (int st = 0; st < TC_STAGES; st++) sIssued[st] = issued[st];
         }
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
             int i = 0;
-            int seen[TC_STAGES] = {0, 0, 0, 0};
-            int committed[2] = {0, 0};
-            const uint32_t idesc = umma_idesc_bf16(TC_PM, Nq);
-            const uint32_t qBase = smem_u32(sQ);
             int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
             for (int li = sidx; li < nl && !*vFail; li += S) {
                 const int4 ent = nxt;
                 if (li + S < nl) nxt = blkEnt[lbase + li + S];
-                for (int t0 = 0; t0 < ent.z; t0 += TC_PM, i++) {
-                    const int st = i % TC_STAGES, tb = i & 1;
-                    if (!mbar_wait_or_fail(&barFull[st], (i / TC_STAGES) & 1, vFail)) {
+                for (int t0 = 0; t0 < ent.z; t0 += TC_NT, i++) {
+                    const int so = i % TC_SO, tb = i & 1;
+                    const uint32_t ph = (i / TC_SO) & 1;
+                    if (!mbar_wait_or_fail(&barBFull[so], ph, vFail)) {
                         atomicOr(&sFail, 1);
                         break;
                     }
-                    seen[st]++;
-                    if (!mbar_wait_or_fail(&barTEmpty[tb], ((i >> 1) & 1) ^ 1, vFail)) {
+                    sSeenB[so]++;
+                    if (!mbar_wait_or_fail(&barAFull[so], ph, vFail) ||
+                        !mbar_wait_or_fail(&barTEmpty[tb], ((i >> 1) & 1) ^ 1, vFail)) {
                         atomicOr(&sFail, 1);
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t aBase = smem_u32(sA + st * (TC_PM * TC_ROWB));
+                    const int N = (min(TC_NT, ent.z - t0) + 15) & ~15;
+                    const uint32_t idesc = umma_idesc_bf16(TC_MT, N);
+                    const int nmt = sNpart[i % TC_SJ] > TC_MT ? 2 : 1;
+                    const uint32_t bBase = smem_u32(sB + so * TC_BSZ);
+                    for (int mt = 0; mt < nmt; mt++) {
+                        const uint32_t aBase = smem_u32(sA + so * TC_ASZ + mt * (TC_MT * TC_ROWB));
 #pragma unroll
-                    for (int ks = 0; ks < TC_K / 16; ks++) {
-                        const uint64_t ad = umma_sdesc(aBase + ks * 256, 128, 6 * 128);
-                        const uint64_t bd = umma_sdesc(qBase + ks * 256, 128, 6 * 128);
-                        umma_bf16(tmem + (uint32_t)(tb * TC_QN), ad, bd, idesc, ks > 0 ? 1u : 0u);
+                        for (int ks = 0; ks < TC_K / 16; ks++) {
+                            const uint64_t ad = umma_sdesc(aBase + ks * 256, 128, 6 * 128);
+                            const uint64_t bd = umma_sdesc(bBase + ks * 256, 128, 6 * 128);
+                            umma_bf16(tmem + (uint32_t)(tb * 256 + mt * TC_NT), ad, bd, idesc, ks > 0 ? 1u : 0u);
+                        }
                     }
+                    umma_commit(&barBEmpty[so]);
+                    umma_commit(&barAEmpty[so]);
                     umma_commit(&barTFull[tb]);
-                    committed[tb]++;
+                    sCommitted[tb]++;
                 }
             }
-            for (int st = 0; st < TC_STAGES; st++) sSeenFull[st] = seen[st];
-            sCommitted[0] = committed[0];
-            sCommitted[1] = committed[1];
         }
-    } else {
-        // ---- epilogue: warps of accumulator tb read the tiles i with
-        // i % 2 == tb; half h takes the partial columns of rank parity h
-        const int e = warp - 2, tb = e >> 3, h = (e >> 2) & 1, qd = warp & 3;
-        const uint32_t taddr = tmem + (uint32_t)(tb * TC_QN) + ((uint32_t)(qd * 32) << 16);
-        int i = 0, seenT = 0;
+    } else if (warp < 6) {
+        // ---- operand builders (128 threads): compact the partial queries;
+        // every decision is uniform over the builders (named barrier 1)
+        const int t = tid - 64, wb = warp - 2;
+        int i = 0;
         int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
         uint32_t mnxt = (sidx < nl && lane < TC_MW) ? blkMask[(lbase + sidx) * TC_MW + lane] : 0u;
-        for (int li = sidx; li < nl && !*vFail; li += S) {
+        for (int li = sidx; li < nl; li += S) {
             const int4 ent = nxt;
             const uint32_t mwl = mnxt;
             if (li + S < nl) {
                 nxt = blkEnt[lbase + li + S];
                 mnxt = lane < TC_MW ? blkMask[(lbase + li + S) * TC_MW + lane] : 0u;
             }
-            for (int t0 = 0; t0 < ent.z; t0 += TC_PM, i++) {
+            // builder warp wb handles queries j = t (word wb) and t + 128
+            // (word wb + 4); prefix popcounts of the mask words by shuffles
+            const uint32_t pc = lane < TC_MW ? (uint32_t)__popc(mwl) : 0u;
+            uint32_t inc = pc;
+#pragma unroll
+            for (int o = 1; o < TC_MW; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t excl = inc - pc;
+            const int npart = (int)__shfl_sync(0xffffffffu, inc, TC_MW - 1);
+            const uint32_t wA = __shfl_sync(0xffffffffu, mwl, wb), wB = __shfl_sync(0xffffffffu, mwl, wb + 4);
+            const int preA = (int)__shfl_sync(0xffffffffu, excl, wb), preB = (int)__shfl_sync(0xffffffffu, excl, wb + 4);
+            const uint32_t below = (1u << lane) - 1u;
+            bool failed = false;
+            for (int t0 = 0; t0 < ent.z; t0 += TC_NT, i++) {
+                const int so = i % TC_SO, sj = i % TC_SJ;
+                const bool bad = !mbar_wait_or_fail(&barAEmpty[so], ((i / TC_SO) & 1) ^ 1, vFail) ||
+                                 !mbar_wait_or_fail(&barJEmpty[sj], ((i / TC_SJ) & 1) ^ 1, vFail);
+                if (bar1_or_128(bad || *vFail != 0)) {
+                    failed = true;
+                    break;
+                }
+                int *map = (int *)(sJ + sj * TC_JSZ + TC_NT * 4);
+                if ((wA >> lane) & 1u) map[preA + __popc(wA & below)] = t;
+                if ((wB >> lane) & 1u) map[preB + __popc(wB & below)] = t + 128;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                // operand rows: rank r -> M-tile r / 128, row r % 128
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    const int r = t + hh * 128;
+                    if (r < npart) {
+                        const uint4 *src = (const uint4 *)(sQr + map[r] * TC_ROWB);
+                        unsigned char *dst = sA + so * TC_ASZ + hh * (TC_MT * TC_ROWB);
+                        const int g = t >> 3, ii = t & 7;
+#pragma unroll
+                        for (int kg = 0; kg < 6; kg++) *(uint4 *)(dst + ((g * 6 + kg) * 8 + ii) * 16) = src[kg];
+                    }
+                }
+                if (t == 0) sNpart[sj] = npart;
+                fence_async_shared();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (t == 0) {
+                    mbar_arrive(&barAFull[so]);
+                    mbar_arrive(&barJFull[sj]);
+                }
+            }
+            if (failed) {
+                if (t == 0) atomicOr(&sFail, 1);
+                break;
+            }
+        }
+    } else {
+        // ---- epilogue: warp (buffer tb, M-tile mt, lane quarter qd); wait
+        // outcomes are made uniform over the warp before any warp-collective
+        // TMEM load
+        const int e = warp - 6, tb = e >> 3, mt = (e >> 2) & 1, qd = warp & 3;
+        const uint32_t taddr = tmem + (uint32_t)(tb * 256 + mt * TC_NT) + ((uint32_t)(qd * 32) << 16);
+        int i = 0, seenT = 0;
+        int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
+        for (int li = sidx; li < nl; li += S) {
+            if (__any_sync(0xffffffffu, *vFail != 0)) break;
+            const int4 ent = nxt;
+            if (li + S < nl) nxt = blkEnt[lbase + li + S];
+            bool failed = false;
+            for (int t0 = 0; t0 < ent.z; t0 += TC_NT, i++) {
                 if ((i & 1) != tb) continue;
-                if (!mbar_wait_or_fail(&barTFull[tb], (i >> 1) & 1, vFail)) {
-                    atomicOr(&sFail, 1);
+                const int sj = i % TC_SJ;
+                if (!__all_sync(0xffffffffu, mbar_wait_or_fail(&barTFull[tb], (i >> 1) & 1, vFail))) {
+                    failed = true;
                     break;
                 }
                 seenT++;
-                tc_fence_after();
-                const int st = i % TC_STAGES;
-                // the stage's norms came by TMA: observe that copy's completion
-                // (already reached; the stage is not refilled before this tile
-                // releases it)
-                if (!mbar_wait_or_fail(&barFull[st], (i / TC_STAGES) & 1, vFail)) {
-                    atomicOr(&sFail, 1);
+                if (!__all_sync(0xffffffffu, mbar_wait_or_fail(&barJFull[sj], (i / TC_SJ) & 1, vFail))) {
+                    failed = true;
                     break;
                 }
-                const int rows = min(TC_PM, ent.z - t0);
-                if (qd * 32 < rows) {
-                    const int lrow = qd * 32 + lane;
-                    const bool vrow = lrow < rows;
-                    const int64_t pos = (int64_t)ent.y + t0 + lrow;
-                    const float no = sNo[st * TC_PM + lrow];
-                    uint32_t cpar = 0u;   // parity of the partial columns before this word
-                    for (int w = 0; w < TC_MW; w++) {
-                        const uint32_t all = __shfl_sync(0xffffffffu, mwl, w);
-                        // prefix parity: bit c = parity of the set bits at or below c
-                        uint32_t px = all;
-                        px ^= px << 1;
-                        px ^= px << 2;
-                        px ^= px << 4;
-                        px ^= px << 8;
-                        px ^= px << 16;
-                        px ^= cpar;
-                        cpar ^= (uint32_t)0 - (uint32_t)(__popc(all) & 1);
-                        // odd ranks (px bit 1) to half 0, even ranks to half 1
-                        uint32_t bits = all & (h ? ~px : px);
-                        while (bits) {
-                            // up to four columns per TMEM wait
-                            int jj[4];
-                            float v[4];
+                if (lane == 0) atomicMax(&sSeenJ[sj], i / TC_SJ + 1);
+                tc_fence_after();
+                const int npart = sNpart[sj];
+                const int rows = min(TC_NT, ent.z - t0);
+                const int rank0 = mt * TC_MT + qd * 32;
+                if (rank0 < npart) {
+                    const int rank = rank0 + lane;
+                    const bool valid = rank < npart;
+                    const float *no = (const float *)(sJ + sj * TC_JSZ);
+                    const int j = valid ? ((const int *)(sJ + sj * TC_JSZ + TC_NT * 4))[rank] : 0;
+                    float4 P = sPar[j];
+                    if (!valid) P.y = P.z = -INFINITY;   // never undecided (stale rows may hold inf)
+                    int sure = 0;
+                    for (int c0 = 0; c0 < rows; c0 += 16) {
+                        float v[16];
+                        __syncwarp();
+                        tmem_ld16(taddr + (uint32_t)c0, v);
+                        const int lim = rows - c0;
 #pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                jj[u] = bits ? w * 32 + __ffs(bits) - 1 : -1;
-                                bits &= bits - 1;
-                            }
-                            __syncwarp();
-#pragma unroll
-                            for (int u = 0; u < 4; u++)
-                                if (jj[u] >= 0) v[u] = __uint_as_float(tmem_ld1(taddr + (uint32_t)jj[u]));
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                const int j = jj[u];
-                                if (j < 0) break;
-                                const float4 P = sPar[j];
-                                const float vt = __fmaf_rn(-2.f, v[u], __fadd_rn(no, P.x));
-                                const bool sure = vrow && vt <= P.y;
-                                const bool maybe = vrow && !sure && vt <= P.z;
-                                const unsigned bs = __ballot_sync(0xffffffffu, sure);
-                                if (lane == 0 && bs) atomicAdd(&sCntS[j], __popc(bs));
-                                if (__any_sync(0xffffffffu, maybe) && maybe) {
-                                    const float ex = pm_pd2_32(O32 + pos * PM_MP, sQp + j * PM_MP);
-                                    const float2 lh = sLH[j];
-                                    if (ex <= lh.x) {
-                                        atomicAdd(&sCntS[j], 1);
-                                    } else if (ex <= lh.y) {
-                                        atomicAdd(&sCntB[j], 1);
-                                        const int e2 = atomicAdd(bandN, 1);
-                                        if (e2 < bandCap) {
-                                            bandA[e2] = a0 + j;
-                                            bandPos[e2] = (int)pos;
-                                        }
+                        for (int c = 0; c < 16; c++) {
+                            if (c < lim) {
+                                const float vt = __fmaf_rn(-2.f, v[c], __fadd_rn(no[c0 + c], P.x));
+                                sure += vt <= P.y ? 1 : 0;
+                                if (vt > P.y && vt <= P.z) {
+                                    // inside the error band: decided exactly later
+                                    const int2 rec = make_int2(a0 + j, ent.y + t0 + c0 + c);
+                                    const int m = atomicAdd(&sMayN, 1);
+                                    if (m < TC_MAYBE) {
+                                        sMay[m] = rec;
+                                    } else {
+                                        const int g = atomicAdd(recheckN, 1);
+                                        if (g < recheckCap) recheck[g] = rec;
                                     }
                                 }
                             }
                         }
                     }
+                    if (valid && sure) atomicAdd(&sCntS[j], sure);
                 }
                 __syncwarp();
                 tc_fence_before();
                 if (lane == 0) {
                     mbar_arrive(&barTEmpty[tb]);
-                    mbar_arrive(&barEmpty[st]);
+                    mbar_arrive(&barJEmpty[sj]);
                 }
+            }
+            if (failed) {
+                atomicOr(&sFail, 1);
+                break;
             }
         }
         if (lane == 0) atomicMax(&sSeenT[tb], seenT);
     }
     __syncthreads();
-    if (tid < nb) {
-        if (sCntS[tid]) atomicAdd(&cntSure[a0 + tid], sCntS[tid]);
-        if (sCntB[tid]) atomicAdd(&cntBand[a0 + tid], sCntB[tid]);
+    if (tid < nb && sCntS[tid]) atomicAdd(&cntSure[a0 + tid], sCntS[tid]);
+    {
+        // staged band pairs -> the recheck list
+        const int n = min(sMayN, TC_MAYBE);
+        if (tid == 0) sMayBase = n ? atomicAdd(recheckN, n) : 0;
+        __syncthreads();
+        for (int m = tid; m < n; m += blockDim.x)
+            if (sMayBase + m < recheckCap) recheck[sMayBase + m] = sMay[m];
     }
     if (tid == 0 && sFail) {
         atomicOr(errFlag, 128);
         // nothing may land in shared memory or TMEM after the CTA leaves:
-        // wait (bounded) for the last copy and MMA not yet seen complete
-        for (int st = 0; st < TC_STAGES; st++)
-            if (sIssued[st] > sSeenFull[st]) mbar_wait_bounded(&barFull[st], (uint32_t)((sIssued[st] - 1) & 1));
+        // wait (bounded) for the copies and MMAs not yet seen complete
+        for (int st = 0; st < TC_SO; st++)
+            if (sIssB[st] > sSeenB[st]) mbar_wait_bounded(&barBFull[st], (uint32_t)((sIssB[st] - 1) & 1));
+        for (int s = 0; s < TC_SJ; s++)
+            if (sIssJ[s] > sSeenJ[s]) mbar_wait_bounded(&barJFull[s], (uint32_t)((sIssJ[s] - 1) & 1));
         for (int t = 0; t < 2; t++)
             if (sCommitted[t] > sSeenT[t]) mbar_wait_bounded(&barTFull[t], (uint32_t)((sCommitted[t] - 1) & 1));
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_QN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// Exact decision of the pairs the tensor-core count left inside its error
+// band, in k_count's arithmetic: surely in -> count, band -> band list.
+__global__ void k_recheck(const int *__restrict__ recheckN, int recheckCap, const int2 *__restrict__ recheck,
+                          const int32_t *__restrict__ act, const Thr *__restrict__ thr,
+                          const float *__restrict__ qp32, const float *__restrict__ O32,
+                          int *__restrict__ cntSure, int *__restrict__ cntBand, int *__restrict__ bandN, int bandCap,
+                          int *__restrict__ bandA, int *__restrict__ bandPos)
+{
+    const int n = min(*recheckN, recheckCap);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int2 rec = recheck[e];
+        const int a = rec.x;
+        const Thr T = thr[a];
+        const int cls = exact_class(O32 + (int64_t)rec.y * PM_MP, qp32 + (int64_t)act[a] * PM_MP, T.lo, T.hi);
+        if (cls == 1) {
+            atomicAdd(&cntSure[a], 1);
+        } else if (cls == 2) {
+            atomicAdd(&cntBand[a], 1);
+            const int e2 = atomicAdd(bandN, 1);
+            if (e2 < bandCap) {
+                bandA[e2] = a;
+                bandPos[e2] = rec.y;
+            }
+        }
     }
 }
 
@@ -1507,6 +1624,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     if (s != PMLSH_OK) return s;
     int *bandN = fpc + nq;       // counters after the per-query array
     int *errFlag = fpc + nq + 1;
+    int *recheckN = fpc + nq + 2;
 
     int nsm = 148;
     {
@@ -1526,8 +1644,12 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
 
     const bool tensor = o->precision == PMLSH_BF16_TENSOR;
     // the tensor-core count holds all 512 TMEM columns of its SM; its
-    // shared-memory request keeps a second CTA off the SM
+    // shared memory (over half the SM's) keeps a second CTA off the SM
     if (tensor) PM_TRY(pm_allow_max_dyn_smem((const void *)k_count_tc));
+    // pairs the tensor-core count leaves inside its error band (8 M, 64 MB)
+    const int recheckCap = 1 << 23;
+    int2 *recheck = tensor ? grow<int2>(w.recheck, recheckCap, s) : nullptr;
+    if (s != PMLSH_OK) return s;
 
     std::vector<int32_t> actH;
     actH.reserve(nq);
@@ -1539,44 +1661,61 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         if (na == 0) break;
         const int nblk = (na + QB - 1) / QB;
         const int nblkT = (na + TC_QN - 1) / TC_QN;
-        const int nlist = tensor ? nblkT : nblk;
-        const int mwords = tensor ? TC_MW : QB / 32;
         PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        int *blkCnt = grow<int>(w.blkCnt, nlist, s);
-        int4 *blkEnt = grow<int4>(w.blkLeaves, (size_t)nlist * L, s);
-        uint32_t *blkMask = grow<uint32_t>(w.blkMask, (size_t)nlist * L * mwords, s);
-        if (s != PMLSH_OK) return s;
-        PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
-        PM_CUDA(cudaMemsetAsync(cntSure, 0, na * sizeof(int), st));
-        PM_CUDA(cudaMemsetAsync(cntBand, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(inTrue, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(inN, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(fpc, 0, (nq + 8) * sizeof(int), st));
         PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
-        if (!tensor) {
-            dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblk);
-            PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff,
-                                        nullptr, L, cntSure, blkCnt, blkEnt, blkMask));
-            int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
-            PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->O32,
-                                                        blkCnt, blkEnt, blkMask, L,
-                                                        cntSure, cntBand, bandN, bandCap, bandA, bandPos));
-        } else {
-            // 256-query blocks: leaf lists with masks, then the tensor-core count
-            dim3 gc((unsigned)((L + 127) / 128), (unsigned)nblkT);
-            PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff,
-                                           ix->bOff, L, cntSure, blkCnt, blkEnt, blkMask));
-            int splitC = std::max(1, std::min(256, (4 * nsm + nblkT - 1) / nblkT));
-            PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_THREADS, TC_SMEM_REQ, st>>>(
-                                        act, na, thr, qp32, ix->O32, ix->Bsplit, ix->bNorm,
-                                        blkCnt, blkEnt, blkMask, L, ix->maxNorm, cntSure, cntBand,
-                                        bandN, bandCap, bandA, bandPos, errFlag));
-        }
+        // range counts: leaf lists with the masks of partially covering
+        // queries, then the per-point count (CUDA cores or tensor cores)
+        auto count_phase = [&](bool tc) -> pmlsh_status {
+            const int nlist = tc ? nblkT : nblk;
+            const int mwords = tc ? TC_MW : QB / 32;
+            pmlsh_status s2 = PMLSH_OK;
+            int *blkCnt = grow<int>(w.blkCnt, nlist, s2);
+            int4 *blkEnt = grow<int4>(w.blkLeaves, (size_t)nlist * L, s2);
+            uint32_t *blkMask = grow<uint32_t>(w.blkMask, (size_t)nlist * L * mwords, s2);
+            if (s2 != PMLSH_OK) return s2;
+            PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(cntSure, 0, na * sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(cntBand, 0, na * sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(bandN, 0, sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(recheckN, 0, sizeof(int), st));
+            dim3 gc((unsigned)((L + 127) / 128), (unsigned)nlist);
+            if (!tc) {
+                PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
+                                            ix->leafOff, nullptr, L, cntSure, blkCnt, blkEnt, blkMask));
+                int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
+                PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->O32,
+                                            blkCnt, blkEnt, blkMask, L, cntSure, cntBand, bandN, bandCap,
+                                            bandA, bandPos));
+            } else {
+                PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
+                                               ix->leafOff, ix->bOff, L, cntSure, blkCnt, blkEnt, blkMask));
+                int splitC = std::max(1, std::min(256, (4 * nsm + nblkT - 1) / nblkT));
+                PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_THREADS, TC_SMEM, st>>>(
+                                            act, na, thr, qp32, ix->Bsplit, ix->bNorm, blkCnt, blkEnt, blkMask, L,
+                                            ix->maxNorm, cntSure, recheckN, recheckCap, recheck, errFlag));
+                PM_LAUNCH("k_recheck", st, k_recheck<<<4 * nsm, 256, 0, st>>>(recheckN, recheckCap, recheck, act, thr,
+                                            qp32, ix->O32, cntSure, cntBand, bandN, bandCap, bandA, bandPos));
+            }
+            PM_CUDA(cudaGetLastError());
+            return PMLSH_OK;
+        };
+        PM_TRY(count_phase(tensor));
         // FP64 band resolution (grid sized by the capacity; empty threads exit)
         {
-            int hBand = 0;
-            PM_CUDA(cudaMemcpyAsync(&hBand, bandN, sizeof(int), cudaMemcpyDeviceToHost, st));
+            int hN[3] = {0, 0, 0};   // bandN, errFlag, recheckN
+            PM_CUDA(cudaMemcpyAsync(hN, bandN, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
             PM_CUDA(cudaStreamSynchronize(st));
+            if (tensor && hN[2] > recheckCap) {
+                // more undecided pairs than the recheck list holds: count this
+                // round on the CUDA cores instead (same results)
+                PM_TRY(count_phase(false));
+                PM_CUDA(cudaMemcpyAsync(hN, bandN, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                PM_CUDA(cudaStreamSynchronize(st));
+            }
+            const int hBand = hN[0];
             if (hBand > bandCap) {
                 pm_set_error("more than %d projected distances fell inside the FP32 error band in one round", bandCap);
                 return PMLSH_EINTERNAL;
