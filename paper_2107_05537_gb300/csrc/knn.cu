@@ -1048,7 +1048,7 @@ constexpr int TC_SJ = 8;           // job slots: norms, rank -> query map (relea
 constexpr int TC_EPI = 16;         // epilogue warps: 2 TMEM buffers x 2 M-tiles x 4 lane quarters
 constexpr int TC_THREADS = 32 * (2 + 4 + TC_EPI);   // loader, MMA, 4 builder warps, epilogue
 constexpr int TC_MW = TC_QN / 32;  // mask words per list entry
-constexpr int TC_MAYBE = 1024;     // pairs inside the error band staged per CTA
+constexpr int TC_MAYBE = 224;      // pairs inside the error band staged per epilogue warp
 // dynamic shared memory
 constexpr int TC_ASZ = 2 * TC_MT * TC_ROWB;                    // two M-tiles per stage, 24 KB
 constexpr int TC_BSZ = TC_NT * TC_ROWB;                        // 12 KB
@@ -1058,9 +1058,9 @@ constexpr int TC_OFF_J = TC_OFF_B + TC_SO * TC_BSZ;
 constexpr int TC_OFF_QR = TC_OFF_J + TC_SJ * TC_JSZ;           // query rows [256][96 B]
 constexpr int TC_OFF_PAR = TC_OFF_QR + TC_QN * TC_ROWB;
 constexpr int TC_OFF_MAY = TC_OFF_PAR + TC_QN * 16;
-constexpr int TC_OFF_CNT = TC_OFF_MAY + TC_MAYBE * 8;
+constexpr int TC_OFF_CNT = TC_OFF_MAY + TC_EPI * TC_MAYBE * 8;
 constexpr int TC_SMEM = TC_OFF_CNT + TC_QN * 4;
-static_assert(TC_SMEM <= 220 * 1024, "tensor-count shared memory");
+static_assert(TC_SMEM <= 222 * 1024, "tensor-count shared memory");
 
 // The CUDA-core count's decision for one pair: 1 surely in (<= lo), 2 in
 // the band (<= hi), 0 out.
@@ -1068,6 +1068,20 @@ __device__ __forceinline__ int exact_class(const float *o, const float *q, float
 {
     const float ex = pm_pd2_32(o, q);
     return ex <= lo ? 1 : (ex <= hi ? 2 : 0);
+}
+
+// Appends this warp's staged pairs to the global recheck list (one atomic
+// per warp) and empties the stage.
+__device__ __forceinline__ void may_flush(int2 *stage, int &n, int lane, int *recheckN, int recheckCap,
+                                          int2 *recheck)
+{
+    int base = 0;
+    if (lane == 0 && n) base = atomicAdd(recheckN, n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int m = lane; m < n; m += 32)
+        if (base + m < recheckCap) recheck[base + m] = stage[m];
+    __syncwarp();
+    n = 0;
 }
 
 // OR of `p` over the 128 threads of named barrier 1 (the operand builders).
@@ -1131,7 +1145,7 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     __shared__ __align__(8) uint64_t barBFull[TC_SO], barBEmpty[TC_SO], barAFull[TC_SO], barAEmpty[TC_SO];
     __shared__ __align__(8) uint64_t barJFull[TC_SJ], barJEmpty[TC_SJ], barTFull[2], barTEmpty[2];
     __shared__ uint32_t sTmem;
-    __shared__ int sFail, sMayN, sMayBase;
+    __shared__ int sFail;
     __shared__ int sNpart[TC_SJ];
     __shared__ int sIssB[TC_SO], sSeenB[TC_SO], sIssJ[TC_SJ], sSeenJ[TC_SJ], sCommitted[2], sSeenT[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1185,7 +1199,6 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     }
     if (tid == 0) {
         sFail = 0;
-        sMayN = 0;
         for (int st = 0; st < TC_SO; st++) {
             mbar_init(&barBFull[st], 1);
             mbar_init(&barBEmpty[st], 1);
@@ -1355,6 +1368,8 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         // TMEM load
         const int e = warp - 6, tb = e >> 3, mt = (e >> 2) & 1, qd = warp & 3;
         const uint32_t taddr = tmem + (uint32_t)(tb * 256 + mt * TC_NT) + ((uint32_t)(qd * 32) << 16);
+        int2 *stage = sMay + e * TC_MAYBE;   // this warp's undecided pairs
+        int nstage = 0;                      // warp-uniform
         int i = 0, seenT = 0;
         int4 nxt = sidx < nl ? blkEnt[lbase + sidx] : make_int4(0, 0, 0, 0);
         for (int li = sidx; li < nl; li += S) {
@@ -1392,23 +1407,42 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                         __syncwarp();
                         tmem_ld16(taddr + (uint32_t)c0, v);
                         const int lim = rows - c0;
+                        uint32_t mb = 0u;   // columns inside the error band
 #pragma unroll
                         for (int c = 0; c < 16; c++) {
                             if (c < lim) {
                                 const float vt = __fmaf_rn(-2.f, v[c], __fadd_rn(no[c0 + c], P.x));
                                 sure += vt <= P.y ? 1 : 0;
-                                if (vt > P.y && vt <= P.z) {
-                                    // inside the error band: decided exactly later
-                                    const int2 rec = make_int2(a0 + j, ent.y + t0 + c0 + c);
-                                    const int m = atomicAdd(&sMayN, 1);
-                                    if (m < TC_MAYBE) {
-                                        sMay[m] = rec;
-                                    } else {
-                                        const int g = atomicAdd(recheckN, 1);
-                                        if (g < recheckCap) recheck[g] = rec;
-                                    }
-                                }
+                                mb |= (vt > P.y && vt <= P.z) ? (1u << c) : 0u;
                             }
+                        }
+                        if (__any_sync(0xffffffffu, mb != 0u)) {
+                            // warp-aggregated append to the stage (flushed when full)
+                            const int cnt = __popc(mb);
+                            int incl = cnt;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (lane >= o) incl += y;
+                            }
+                            const int total = __shfl_sync(0xffffffffu, incl, 31);
+                            if (nstage + total > TC_MAYBE) may_flush(stage, nstage, lane, recheckN, recheckCap, recheck);
+                            int at = nstage + incl - cnt;
+                            while (mb) {
+                                const int c = __ffs(mb) - 1;
+                                mb &= mb - 1;
+                                const int2 rec = make_int2(a0 + j, ent.y + t0 + c0 + c);
+                                if (at < TC_MAYBE) {
+                                    stage[at] = rec;
+                                } else {
+                                    // more than a full stage in one chunk (at most 512)
+                                    const int g = atomicAdd(recheckN, 1);
+                                    if (g < recheckCap) recheck[g] = rec;
+                                }
+                                at++;
+                            }
+                            nstage = min(TC_MAYBE, nstage + total);
+                            __syncwarp();
                         }
                     }
                     if (valid && sure) atomicAdd(&sCntS[j], sure);
@@ -1426,17 +1460,10 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
             }
         }
         if (lane == 0) atomicMax(&sSeenT[tb], seenT);
+        may_flush(stage, nstage, lane, recheckN, recheckCap, recheck);
     }
     __syncthreads();
     if (tid < nb && sCntS[tid]) atomicAdd(&cntSure[a0 + tid], sCntS[tid]);
-    {
-        // staged band pairs -> the recheck list
-        const int n = min(sMayN, TC_MAYBE);
-        if (tid == 0) sMayBase = n ? atomicAdd(recheckN, n) : 0;
-        __syncthreads();
-        for (int m = tid; m < n; m += blockDim.x)
-            if (sMayBase + m < recheckCap) recheck[sMayBase + m] = sMay[m];
-    }
     if (tid == 0 && sFail) {
         atomicOr(errFlag, 128);
         // nothing may land in shared memory or TMEM after the CTA leaves:
