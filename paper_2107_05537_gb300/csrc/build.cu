@@ -225,7 +225,8 @@ __global__ void k_leaf_orig(const float *__restrict__ X, const int64_t *__restri
 // padding rows are zero) in the no-swizzle K-major canonical layout of the
 // tcgen05 matrix descriptor: 8-row x 8-element core matrices of 128 bytes,
 // row group g, K group kg at byte ((g * 6 + kg) * 8 + row % 8) * 16.  Also
-// the FP32 squared norms ||o'||^2 of the FP32 coordinates, same rows.
+// the FP32 squared norms ||o'||^2 of the FP32 coordinates, same rows (NaN
+// on padding rows).
 __global__ void k_build_bsplit(const float *__restrict__ O32, const int64_t *__restrict__ off,
                                const int64_t *__restrict__ bOff, int64_t L, uint16_t *__restrict__ B,
                                float *__restrict__ norms)
@@ -912,7 +913,8 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
         PM_TRY(dalloc(&ix->bNorm, (size_t)rows));
         PM_CUDA(cudaMemcpyAsync(ix->bOff, bo.data(), (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
         PM_CUDA(cudaMemsetAsync(ix->Bsplit, 0, (size_t)rows * 48 * sizeof(uint16_t), st));
-        PM_CUDA(cudaMemsetAsync(ix->bNorm, 0, (size_t)rows * sizeof(float), st));
+        // padding rows: NaN norms, so that every comparison on them is false
+        PM_CUDA(cudaMemsetAsync(ix->bNorm, 0xFF, (size_t)rows * sizeof(float), st));
         PM_LAUNCH("k_build_bsplit", st, k_build_bsplit<<<(unsigned)L, 128, 0, st>>>(ix->O32, ix->leafOff, ix->bOff, L, ix->Bsplit, ix->bNorm));
         PM_CUDA(cudaGetLastError());
     }

@@ -1400,21 +1400,29 @@ k_count_tc(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                     const float *no = (const float *)(sJ + sj * TC_JSZ);
                     const int j = valid ? ((const int *)(sJ + sj * TC_JSZ + TC_NT * 4))[rank] : 0;
                     float4 P = sPar[j];
-                    if (!valid) P.y = P.z = -INFINITY;   // never undecided (stale rows may hold inf)
+                    if (!valid) P.y = P.z = __int_as_float(0x7fffffff);   // NaN: every comparison false
                     int sure = 0;
                     for (int c0 = 0; c0 < rows; c0 += 16) {
                         float v[16];
                         __syncwarp();
                         tmem_ld16(taddr + (uint32_t)c0, v);
-                        const int lim = rows - c0;
+                        // branch-free over the 16 columns: padding columns have
+                        // NaN norms, so neither test holds for them
+                        float nv[16];
+#pragma unroll
+                        for (int c4 = 0; c4 < 4; c4++) {
+                            const float4 n4 = *(const float4 *)(no + c0 + 4 * c4);
+                            nv[4 * c4] = n4.x;
+                            nv[4 * c4 + 1] = n4.y;
+                            nv[4 * c4 + 2] = n4.z;
+                            nv[4 * c4 + 3] = n4.w;
+                        }
                         uint32_t mb = 0u;   // columns inside the error band
 #pragma unroll
                         for (int c = 0; c < 16; c++) {
-                            if (c < lim) {
-                                const float vt = __fmaf_rn(-2.f, v[c], __fadd_rn(no[c0 + c], P.x));
-                                sure += vt <= P.y ? 1 : 0;
-                                mb |= (vt > P.y && vt <= P.z) ? (1u << c) : 0u;
-                            }
+                            const float vt = __fmaf_rn(-2.f, v[c], __fadd_rn(nv[c], P.x));
+                            sure += vt <= P.y ? 1 : 0;
+                            mb |= (vt > P.y && vt <= P.z) ? (1u << c) : 0u;
                         }
                         if (__any_sync(0xffffffffu, mb != 0u)) {
                             // warp-aggregated append to the stage (flushed when full)

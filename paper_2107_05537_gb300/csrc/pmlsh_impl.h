@@ -90,7 +90,7 @@ struct pmlsh_index {
     // tensor-core operand of the projected points: leaf-padded rows
     int64_t *bOff = nullptr;       // [L+1] first row of each leaf (multiple of 16)
     uint16_t *Bsplit = nullptr;    // BF16 [rows][48] in the UMMA canonical layout
-    float *bNorm = nullptr;        // [rows] ||o'||^2 (FP32 coordinates)
+    float *bNorm = nullptr;        // [rows] ||o'||^2 (FP32 coordinates), NaN on padding rows
     std::vector<int64_t> bOffH;
     std::vector<int64_t> chunkOffH;
     std::vector<int32_t> leafChunkH;
