@@ -129,6 +129,8 @@ def peaks():
 
 
 def traffic_record():
+    """DRAM bytes per query of each profiled kernel (ncu), with the hash of
+    the source file they were taken from: a changed source voids them."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             return json.load(f)
@@ -190,17 +192,86 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def source_sha(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def timed_steps(step, steps, flush, stream):
+    """K steps, L2 flushed before each, CUDA events on the launch stream."""
+    import torch
+    import paper_2107_05537_gb300 as pm
+    pm.profile(True)
+    pm.profile_read()
+    launches0 = pm.launch_count()
+    total_ms, nver, res = 0.0, 0, None
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        nver += int(res["stats"]["nver"].sum())
+    launches = pm.launch_count() - launches0
+    prof = pm.profile_read()
+    pm.profile(False)
+    return total_ms, nver, res, prof, launches
+
+
+def serve_leg(pm, ix, Q, prec, rate_qps, seconds, seed):
+    """Open-loop Poisson request stream through the continuous-batching
+    server: request sizes log-uniform in [1, 4096], k uniform in {1, 10, 100},
+    c = 1.5; returns the server's latency and throughput figures."""
+    import threading
+    rng = np.random.default_rng(seed)
+    mean_size = (4096 - 1) / math.log(4096)
+    reqs, t = [], 0.0
+    while t < seconds:
+        t += rng.exponential(mean_size / rate_qps)
+        size = int(np.exp(rng.uniform(0.0, math.log(4096.0))))
+        q0 = int(rng.integers(0, len(Q) - size + 1))
+        reqs.append((t, q0, size, int(rng.choice([1, 10, 100]))))
+    srv = pm.Server(ix, slots=3, max_batch_queries=16384)
+    tickets = []
+
+    def producer():
+        t0 = time.perf_counter()
+        for at, q0, size, k in reqs:
+            dt = at - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(Q[q0:q0 + size], k=k, c=C, beta=BETA, precision=prec))
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    for tk in tickets:
+        srv.wait(tk)
+    st = srv.stats()
+    srv.close()
+    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "qps": st["qps"], "requests": st["completed"], "queries": st["queries"],
+            "batches": st["batches"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--ref-queries", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rate", type=float, default=50_000.0)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -226,45 +297,46 @@ def main():
     dd = torch.empty((nq, K), dtype=torch.float32, device="cuda")
     er = torch.empty((nq, K), dtype=torch.float32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-
-    def step():
-        return ix.knn(Qd, k=K, c=C, alpha1=ALPHA1, beta=BETA, precision=prec,
-                      out=(ids, dd, er))
-
-    for _ in range(args.warmup):
-        res = step()
-    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+
+    def make_step(p):
+        return lambda: ix.knn(Qd, k=K, c=C, alpha1=ALPHA1, beta=BETA, precision=p, out=(ids, dd, er))
+
+    step = make_step(prec)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
     barrier(ws)
     torch.cuda.synchronize()
-    pm.profile(True)
-    pm.profile_read()
-    launches0 = pm.launch_count()
-    total_ms = 0.0
-    nver = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        nver += int(res["stats"]["nver"].sum())
-    launches = pm.launch_count() - launches0
-    prof = pm.profile_read()
-    pm.profile(False)
+    total_ms, nver, res, prof, launches = timed_steps(step, args.steps, flush, stream)
     barrier(ws)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     total_s = max_over_ranks(total_ms / 1000.0, ws)
     value = nq * args.steps * ws / total_s
     stats = res["stats"]
+    ids_main = ids.clone()
+
+    # the other precision on the same batch: same results, its own speed
+    other = None
+    if not args.no_fp32_compare:
+        op = pm.PMLSH_FP32_PLAIN if prec == pm.PMLSH_BF16_TENSOR else pm.PMLSH_BF16_TENSOR
+        ostep = make_step(op)
+        for _ in range(args.warmup):
+            ostep()
+        torch.cuda.synchronize()
+        barrier(ws)
+        oms, _, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream)
+        barrier(ws)
+        os_ = max_over_ranks(oms / 1000.0, ws)
+        other = {"precision": "fp32" if op == pm.PMLSH_FP32_PLAIN else "bf16",
+                 "value": nq * args.steps * ws / os_, "ms_per_step": os_ * 1000 / args.steps,
+                 "ids_identical": bool(torch.equal(ids, ids_main)),
+                 "kernels": {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in oprof.items()}}
+        ids.copy_(ids_main)
 
     # quality at the operating point: Eq. 11 / Eq. 12 on a query sample
     # against exact neighbours (plain PyTorch FP64 on the GPU)
@@ -307,31 +379,33 @@ def main():
     roof = None
     if dom:
         launches_dom, ms_dom = prof[dom]
-        avg_s = ms_dom / 1000.0 / launches_dom
-        props = torch.cuda.get_device_properties(torch.cuda.current_device())
-        nsm = props.multi_processor_count
-        smhz = pk.get("sm_max_mhz", 2070.0)
         tr = traffic_record().get(dom)
-        if dom == "k_verify":
-            # algorithmic work: 3 flops (sub, mul, add) per coordinate of every
-            # verified candidate; FP32 lanes: 128 per SM, 2 instructions
-            # (FSUB, FFMA) per coordinate
-            flops = nver / args.steps * d * 3.0 / launches_dom * args.steps
-            achieved = flops / avg_s / 1e12
-            peak = nsm * 128 * smhz * 1e6 / 2 * 3 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "kernel": dom,
-                    "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 instr x 3 flop per coordinate" % (nsm, smhz),
-                    "traffic": tr.get("bytes_per_launch") if tr else None}
-        else:
-            roof = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": None, "kernel": dom, "traffic": tr.get("bytes_per_launch") if tr else None}
+        traffic = None
+        if tr and tr.get("sha256") == source_sha(tr["source"]):
+            traffic = tr["dram_bytes_per_query"] * nq * args.steps / launches_dom
+        roof = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "kernel": dom, "traffic": traffic}
+        if dom == "k_bestfirst":
+            # algorithmic bytes: the original-space row of every verified
+            # candidate, the query rows, the k results (id, distance, error)
+            alg = nver * d * 4.0 + args.steps * nq * (d * 4.0 + K * 16.0)
+            achieved = alg / (ms_dom / 1000.0) / 1e9
+            roof.update({"achieved": achieved, "frac": achieved / pk["hbm_gbs"],
+                         "algorithmic_bytes_per_launch": alg / launches_dom,
+                         "avg_launch_ms": ms_dom / launches_dom})
         roof["kernels"] = {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in prof.items()}
         roof["peak_kind"] = pk_kind
 
+    # serving: open-loop Poisson stream on the resident index, both precisions
+    serve = None
+    if rank == 0 and args.serve_seconds > 0:
+        serve = {"rate_qps": args.serve_rate, "seconds": args.serve_seconds,
+                 "note": "resident 1M x 128 index; request sizes log-uniform [1,4096], k in {1,10,100}"}
+        for nm, p in (("bf16", pm.PMLSH_BF16_TENSOR), ("fp32", pm.PMLSH_FP32_PLAIN)):
+            serve[nm] = serve_leg(pm, ix, Q, p, args.serve_rate, args.serve_seconds, seed=5)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        import oracle
         A = ix.projection()
         cpu = cpu_baseline(X, Q, A)
 
@@ -350,7 +424,7 @@ def main():
                           "mean_verified": float(stats["nver"].mean()),
                           "mean_leaves_visited": float(stats["leaves"].mean()),
                           "rule_counts": np.bincount(stats["rule"], minlength=4).tolist()},
-                "build_s": build_s,
+                "build_s": build_s, "other_precision": other, "serve": serve,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
         print(json.dumps(line), flush=True)
     ix.close()

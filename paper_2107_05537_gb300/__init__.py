@@ -341,11 +341,12 @@ class Server:
         self._h, self.index, self._k = h, index, {}
 
     def submit(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
-               stop_rule=STOP_LITERAL, t=0.0):
+               stop_rule=STOP_LITERAL, t=0.0, precision=PMLSH_FP32_PLAIN):
         Q = np.ascontiguousarray(Q, dtype=np.float32)
         o = KnnOpts()
         lib().pmlsh_knn_opts_default(ctypes.byref(o))
         o.k, o.c, o.alpha1, o.beta, o.r_min, o.stop_rule, o.t = k, c, alpha1, beta, r_min, stop_rule, t
+        o.precision = precision
         tk = ctypes.c_uint64()
         _check(lib().pmlsh_serve_submit(self._h, Q.ctypes.data_as(ctypes.c_void_p), Q.shape[0],
                                         ctypes.byref(o), ctypes.byref(tk)))
