@@ -385,7 +385,7 @@ def main():
             traffic = tr["dram_bytes_per_query"] * nq * args.steps / launches_dom
         roof = {"bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": None, "kernel": dom, "traffic": traffic}
-        if dom == "k_bestfirst":
+        if dom == "k_verify":
             # algorithmic bytes: the original-space row of every verified
             # candidate, the query rows, the k results (id, distance, error)
             alg = nver * d * 4.0 + args.steps * nq * (d * 4.0 + K * 16.0)

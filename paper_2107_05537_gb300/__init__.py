@@ -74,6 +74,12 @@ class QueryStats(ctypes.Structure):
                 ("n_verified", ctypes.c_int64)]
 
 
+# numpy view of pmlsh_query_stats (same field offsets as the ctypes struct)
+_QSTATS_DT = np.dtype({"names": [f for f, _ in QueryStats._fields_],
+                       "formats": [np.dtype(t._type_) for _, t in QueryStats._fields_],
+                       "offsets": [getattr(QueryStats, f).offset for f, _ in QueryStats._fields_],
+                       "itemsize": ctypes.sizeof(QueryStats)})
+
 # name -> (restype, argtypes); the exported C ABI of include/pmlsh.h
 _P = ctypes.c_void_p
 _SIGS = {
@@ -317,14 +323,11 @@ class Index:
                                _stream()))
         res = dict(ids=ids, dists=dists, err=err)
         if with_stats:
+            sv = np.frombuffer(stats, dtype=_QSTATS_DT, count=nq) if nq else np.zeros(0, _QSTATS_DT)
             res["stats"] = dict(
-                rounds=np.array([s.rounds for s in stats[:nq]], dtype=np.int32),
-                rule=np.array([s.stop_rule for s in stats[:nq]], dtype=np.int32),
-                ncand=np.array([s.n_cand for s in stats[:nq]], dtype=np.int64),
-                r=np.array([s.r_final for s in stats[:nq]], dtype=np.float64),
-                fp64=np.array([s.fp64_checks for s in stats[:nq]], dtype=np.int32),
-                nver=np.array([s.n_verified for s in stats[:nq]], dtype=np.int64),
-                leaves=np.array([s.leaves_visited for s in stats[:nq]], dtype=np.int32))
+                rounds=sv["rounds"].copy(), rule=sv["stop_rule"].copy(),
+                ncand=sv["n_cand"].copy(), r=sv["r_final"].copy(), fp64=sv["fp64_checks"].copy(),
+                nver=sv["n_verified"].copy(), leaves=sv["leaves_visited"].copy())
         return res
 
 

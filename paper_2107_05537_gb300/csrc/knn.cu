@@ -14,10 +14,11 @@
 //   [host]         |S_i| per query -> which queries reach the budget B
 //   k_collect,     for budget queries: the B nearest in projected space
 //   k_select       (radix select, FP64 resolution of the band at the cut)
-//   k_bestfirst    exact FP32 distances of the candidates that can reach the
-//                  top-k (leaves visited in order of an original-space lower
-//                  bound, rows staged by TMA), guard set, FP64 distances,
-//                  exact top-k and the k-th distance for stop rule 1
+//   k_verify       one warp per query: exact FP32 distances of the candidates
+//                  that can reach the top-k (leaves visited best first by an
+//                  original-space lower bound, chunks of <= 32 points skipped
+//                  by their own), guard set, FP64 distances, exact top-k and
+//                  the k-th distance for stop rule 1
 //   [host]         stop rules, r <- c r for the rest
 #include <algorithm>
 #include <cmath>
@@ -32,7 +33,6 @@ namespace {
 constexpr int QB = 64;          // queries per block
 constexpr int BCAP = 256;       // band-in entries per query
 constexpr int SELBAND = 2048;   // band at the budget cut, per query
-constexpr int GCAP = 1024;      // guard set per query
 constexpr float SLACK = 1e-5f;  // relative slack of the conservative leaf tests
 
 enum : unsigned char { CL_OUT = 0, CL_FULL = 1, CL_PART = 2 };
@@ -499,47 +499,74 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t ph)
     return false;
 }
 
-constexpr int BF_THREADS = 256;
-constexpr int BF_ROWS = 32;     // points per staged chunk
-constexpr int BF_DCH = 256;     // dimensions per staged chunk
-constexpr int BF_MAXCH = 512;   // chunks per leaf (leaf size <= 1024, chunks >= 2 points)
-constexpr int BF_SURV = 1024;   // leaves sorted per filtering pass
+constexpr int VW_MAXWARPS = 16;               // queries in flight per block (one per warp)
+constexpr unsigned VW_FULL = 0xffffffffu;
 
-// Inserts `val` (position `pos`) into the per-query top-KP held in shared
-// memory if it beats the current maximum; called by one full warp.
-__device__ __forceinline__ void topk_insert_warp(float *vals, int *idxs, int KP, float &cmax, int &cslot,
-                                                 float val, int pos, int lane)
+// Squared FP32 distances ||q - x_v||^2 of up to 32 rows x_v, one per lane
+// (`p`: the lane's row, nullptr: none; the lane then gets 0).  Eight lanes
+// share a row and read its float4 columns g, g + 8, ..., so that every load
+// instruction of the warp covers whole 128-byte lines of four rows; the
+// eight partial sums are added by a butterfly.  Requires ld % 32 == 0 with
+// zero padding columns in q and in the rows.
+__device__ __forceinline__ float warp_d2(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
 {
-    if (!(val < cmax)) return;
-    if (lane == 0) {
-        vals[cslot] = val;
-        idxs[cslot] = pos;
+    const int grp = lane >> 3, g = lane & 7;
+    float keep = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 8; j++) {
+        const float4 *x4 = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 4 * j);
+        float acc = 0.f;
+        if (x4 != nullptr) {
+            for (int t = g; t < nf4; t += 8) {
+                const float4 x = __ldg(x4 + t);
+                const float4 qv = q4[t];
+                float u = __fsub_rn(qv.x, x.x);
+                acc = __fmaf_rn(u, u, acc);
+                u = __fsub_rn(qv.y, x.y);
+                acc = __fmaf_rn(u, u, acc);
+                u = __fsub_rn(qv.z, x.z);
+                acc = __fmaf_rn(u, u, acc);
+                u = __fsub_rn(qv.w, x.w);
+                acc = __fmaf_rn(u, u, acc);
+            }
+        }
+        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 1));
+        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 2));
+        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 4));
+        if (g == j) keep = acc;
     }
-    __syncwarp();
-    float best = -1.f;
-    int bs = 0;
-    for (int e = lane; e < KP; e += 32) {
-        float x = vals[e];
-        if (x > best) { best = x; bs = e; }
-    }
-    for (int o = 16; o; o >>= 1) {
-        float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int os = __shfl_xor_sync(0xffffffffu, bs, o);
-        if (ob > best || (ob == best && os < bs)) { best = ob; bs = os; }
-    }
-    cmax = best;
-    cslot = bs;
-    __syncwarp();
+    // lane (grp, g) holds row grp + 4 g
+    return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
 }
 
-struct BfArgs {
+// FP32 d'^2 of one projected row against q' (the arithmetic of pm_pd2_32:
+// sequential over the 16 coordinates, row minus query), float4 loads.
+__device__ __forceinline__ float pd2_row(const float *__restrict__ o, const float *__restrict__ qv)
+{
+    const float4 *o4 = (const float4 *)o;
+    float s = 0.f;
+#pragma unroll
+    for (int j4 = 0; j4 < PM_MP / 4; j4++) {
+        const float4 x = __ldg(o4 + j4);
+        float t = __fsub_rn(x.x, qv[4 * j4]);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(x.y, qv[4 * j4 + 1]);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(x.z, qv[4 * j4 + 2]);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(x.w, qv[4 * j4 + 3]);
+        s = __fmaf_rn(t, t, s);
+    }
+    return s;
+}
+
+struct VwArgs {
     const int32_t *act;
     int na;
     const Thr *thr;
     const float *qp32, *qpiv;
     int s;
     const float *meta;
-    const int64_t *off;
     int64_t L;
     const float *O32, *X, *Qd;
     int ld, d;
@@ -554,423 +581,274 @@ struct BfArgs {
     float *outD, *outErr;
     double *dk;
     int *fp64cnt, *nverOut, *nleafOut, *errFlag;
-    int *workCtr;        // next active query to take (persistent grid)
-    int *dbg;            // [4]: site, value, query of the first failed index check
-    int64_t n;           // points
-    float *scratch;      // [gridDim.x][2][L]: per-CTA leaf bounds and centre distances
+    int *workCtr;   // next active query to take (persistent warps)
+    int *dbg;       // [3]: site, value, query of the first failed index check
+    int64_t n;      // points
+    int2 *lists;    // [warps][L]: per-warp candidate leaves {leaf, lower bound bits}
 };
 
-// Persistent grid: each CTA takes active queries from a counter.  Per query,
-// the candidates are the points with FP32 d'^2 <= lov plus the FP64-resolved
-// band-in points, and only the top-k of the candidates matters (stop rule 1
-// tests the k-th smallest distance).  Pass 1 computes, for every leaf that
-// Eq. 5 does not exclude, the distance ||q - mu_l|| to its original-space
-// centre and the lower bound lb = ||q - mu_l|| - Rx_l of its members'
-// distances.  The leaf with the nearest centre is verified first; then the
-// leaves whose lb does not exclude them from the guard set
-// {d^2_32 <= K (1 + 3 eps_v)} (K the current KP-th smallest, an upper bound of
-// the k-th) are sorted by centre distance and verified, re-testing lb against
-// the tightening K; chunks of <= 32 points are skipped by their own bound.
-// Rows are staged by TMA bulk copies, 32 rows x 256 dimensions per stage,
-// double-buffered.  The result equals verifying every candidate.
-#define BF_CHECK(cond, site, val)                                              \
+// Shared memory of one warp: gd[KP] f64, gid[KP] i64, q[ld], vals[KP],
+// idxs[KP], gpos[KP], q'[16], pivot distances[8].
+__host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP)
+{
+    return (size_t)KP * 28 + (size_t)ld * 4 + 96;
+}
+
+#define VW_CHECK(cond, site, val)                                              \
     (((cond)) ? true                                                           \
               : (atomicCAS(&A.dbg[0], 0, (site)) == 0 ? (A.dbg[1] = (int)(val), A.dbg[2] = a, \
-                                                          atomicOr(A.errFlag, 1024), false)   \
-                                                       : (atomicOr(A.errFlag, 1024), false)))
+                                                         atomicOr(A.errFlag, 1024), false)    \
+                                                      : (atomicOr(A.errFlag, 1024), false)))
 
-__global__ void __launch_bounds__(BF_THREADS)
-k_bestfirst(BfArgs A)
+// Exact top-k of the candidate set, one warp per query (persistent warps
+// take active queries from a counter).  The candidates are the points with
+// FP32 d'^2 <= lov plus the FP64-resolved band-in points; only their k
+// nearest matter (stop rule 1 tests the k-th distance).
+//  1. The leaves that Eq. 5 does not exclude for radius sqrt(lov) are listed
+//     with the lower bound lb = ||q - mu_l|| - Rx_l of their members'
+//     distances (original-space leaf balls).
+//  2. Best first: the listed leaf with the smallest lb is visited while lb
+//     does not exclude it from the guard set {d^2_32 <= K (1 + 3 eps_v)},
+//     K the current KP-th smallest FP32 d^2 (an upper bound of the k-th);
+//     inside a leaf, chunks of <= 32 points are skipped by their own ball.
+//     Each candidate's FP32 d^2 is offered to a per-warp top-KP.
+//  3. Guard set: the entries of the top-KP within (1 + 3 eps_v) of its k-th
+//     value provably contain the exact k nearest; they are recomputed in
+//     FP64 and ranked by (FP64 distance, id).
+// The result equals verifying every candidate.
+__global__ void __launch_bounds__(32 * VW_MAXWARPS, 2)
+k_verify(VwArgs A)
 {
-    extern __shared__ __align__(128) unsigned char bsm[];
-    const int ld = A.ld, d = A.d, KP = A.KP, k = A.k, s = A.s;
+    extern __shared__ __align__(16) unsigned char vsm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int ld = A.ld, KP = A.KP, KPW = A.KP >> 5, k = A.k, s = A.s, nf4 = A.ld >> 2;
     const int64_t L = A.L;
-    const int dch = ld < BF_DCH ? ld : BF_DCH;
-    const int rs = dch + 8;                                  // staged row stride (floats)
-    float *xs = (float *)bsm;                                // [2][32][rs]
-    float *qs = xs + 2 * BF_ROWS * rs;                       // [ld]
-    float *vals = qs + ld;                                   // [KP]
-    int *idxs = (int *)(vals + KP);                          // [KP]
-    unsigned char *uarea = (unsigned char *)(idxs + KP);     // union: survivors / guard set
-    float *svk = (float *)uarea;                             // [BF_SURV]
-    int *svi = (int *)(svk + BF_SURV);                       // [BF_SURV]
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float sq[PM_MP], sp[PM_MAX_PIVOTS], dist[BF_ROWS];
-    __shared__ unsigned int cmask[BF_MAXCH];
-    __shared__ int sCnt, sFail, sSeen, sVer, sG, sLeaves, sQ, sHome;
-    __shared__ float sCmax, sHomeD;
-    __shared__ int sCslot;
-    __shared__ float wMinD[BF_THREADS / 32];
-    __shared__ int wMinL[BF_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *lbS = A.scratch + (int64_t)blockIdx.x * 2 * L;    // [L] lower bounds (INF: out or done)
-    float *dcS = lbS + L;                                    // [L] centre distances
+    unsigned char *wbase = vsm + (size_t)wib * verify_smem_warp(ld, KP);
+    double *gd = (double *)wbase;
+    long long *gid = (long long *)(gd + KP);
+    float *qs = (float *)(gid + KP);
+    float *vals = qs + ld;
+    int *idxs = (int *)(vals + KP);
+    int *gpos = idxs + KP;
+    float *sq = (float *)(gpos + KP);
+    float *sp = sq + PM_MP;
+    const float4 *q4 = (const float4 *)qs;
+    int2 *list = A.lists + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * L;
     const double epsv = (double)(ld + 8) * 0x1.0p-24;
+    const double lbMul = 1.0 - epsv, cutMul = 1.0 + 3.0 * epsv;
     const float lbSlack = 1.f - (float)((ld + 8) * 0x1.0p-24) - 1e-6f;
-    const int nDch = (ld + dch - 1) / dch;
-    const int pp = tid >> 3, g = tid & 7;
-    uint32_t phase[2] = {0u, 0u};
-    if (tid == 0) {
-        sFail = 0;
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
     for (;;) {
-        if (tid == 0) sQ = atomicAdd(A.workCtr, 1);
-        __syncthreads();
-        const int a = sQ;
+        int a = 0;
+        if (lane == 0) a = atomicAdd(A.workCtr, 1);
+        a = __shfl_sync(VW_FULL, a, 0);
         if (a >= A.na) break;
-        if (!BF_CHECK(a >= 0, 7, a)) break;
-        // fresh barriers for every query (no copy is in flight here)
-        if (tid == 0) {
-            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[0])) : "memory");
-            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar[1])) : "memory");
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        phase[0] = phase[1] = 0u;
+        if (!VW_CHECK(a >= 0, 7, a)) break;
         const int q = A.act[a];
         const Thr T = A.thr[a];
         const float lov = T.lov;
         const float Rv = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
-        for (int i = tid; i < ld; i += BF_THREADS) qs[i] = A.Qd[(int64_t)q * ld + i];
-        if (tid < PM_MP) sq[tid] = A.qp32[(int64_t)q * PM_MP + tid];
-        if (tid < PM_MAX_PIVOTS) sp[tid] = A.qpiv[(int64_t)q * PM_MAX_PIVOTS + tid];
-        for (int e = tid; e < KP; e += BF_THREADS) { vals[e] = INFINITY; idxs[e] = -1; }
-        if (tid == 0) { sSeen = 0; sVer = 0; sCmax = INFINITY; sCslot = 0; sLeaves = 0; }
-        __syncthreads();
-        // pass 1: leaf bounds; per-warp nearest centre
-        float myMin = INFINITY;
-        int myMinL = -1;
-        for (int64_t base = (int64_t)warp * 32; base < L; base += 32 * (BF_THREADS / 32)) {
-            const int64_t l = base + lane;
-            bool cand = false;
-            if (l < L) {
-                if (Rv > 0.f) cand = leaf_class(sq, sp, s, Rv, Rv, A.meta + l * PM_LEAF_STRIDE) != CL_OUT;
-                if (!cand) lbS[l] = INFINITY;
-            }
-            unsigned bits = __ballot_sync(0xffffffffu, cand);
+        for (int i = lane; i < ld; i += 32) qs[i] = A.Qd[(int64_t)q * ld + i];
+        if (lane < PM_MP) sq[lane] = A.qp32[(int64_t)q * PM_MP + lane];
+        if (lane < PM_MAX_PIVOTS) sp[lane] = A.qpiv[(int64_t)q * PM_MAX_PIVOTS + lane];
+        for (int e = lane; e < KP; e += 32) {
+            vals[e] = INFINITY;
+            idxs[e] = 0x7fffffff;
+        }
+        __syncwarp();
+        // top-KP state: lane owns slots lane, lane + 32, ...; cmax is the
+        // largest entry (the KP-th smallest so far), cslot its slot
+        float cmax = INFINITY, myMax = INFINITY;
+        int cslot = 0, mySlot = lane;
+        int seen = 0, leaves = 0;
+        auto pruned = [&](float lb) -> bool {
+            return lb > 0.f && (double)lb * lb * lbMul > (double)cmax * cutMul;
+        };
+        // offers the lanes' values (cand) to the top-KP, in lane order
+        auto offer = [&](bool cand, float v, int pos) {
+            unsigned bits = __ballot_sync(VW_FULL, cand && v < cmax);
             while (bits) {
                 const int src = __ffs(bits) - 1;
                 bits &= bits - 1;
-                const int64_t ll = base + src;
-                const float *mu = A.leafMu + ll * ld;
-                float acc = 0.f;
-                for (int i = lane; i < ld; i += 32) {
-                    float t = __fsub_rn(qs[i], mu[i]);
-                    acc = __fmaf_rn(t, t, acc);
+                const float val = __shfl_sync(VW_FULL, v, src);
+                const int ps = __shfl_sync(VW_FULL, pos, src);
+                if (!(val < cmax)) continue;
+                if (lane == (cslot & 31)) {
+                    vals[cslot] = val;
+                    idxs[cslot] = ps;
+                    float mm = -1.f;
+                    int ms = lane;
+                    for (int j = 0; j < KPW; j++) {
+                        const float x = vals[lane + 32 * j];
+                        if (x > mm) { mm = x; ms = lane + 32 * j; }
+                    }
+                    myMax = mm;
+                    mySlot = ms;
                 }
-                for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                const float dc = __fsqrt_rn(acc);
-                if (lane == 0) {
-                    dcS[ll] = dc;
-                    lbS[ll] = __fsub_rn(__fmul_rn(dc, lbSlack), A.leafRx[ll]);
+                __syncwarp();
+                float bm = myMax;
+                int bs = mySlot;
+                for (int o = 16; o; o >>= 1) {
+                    const float om = __shfl_xor_sync(VW_FULL, bm, o);
+                    const int os = __shfl_xor_sync(VW_FULL, bs, o);
+                    if (om > bm || (om == bm && os < bs)) { bm = om; bs = os; }
                 }
-                if (dc < myMin) { myMin = dc; myMinL = (int)ll; }
+                cmax = bm;
+                cslot = bs;
             }
-        }
-        if (lane == 0) { wMinD[warp] = myMin; wMinL[warp] = myMinL; }
-        __syncthreads();
-        if (tid == 0) {
-            float bd = INFINITY;
-            int bl = -1;
-            for (int w = 0; w < BF_THREADS / 32; w++)
-                if (wMinD[w] < bd || (wMinD[w] == bd && wMinL[w] >= 0 && wMinL[w] < bl)) { bd = wMinD[w]; bl = wMinL[w]; }
-            sHome = bl;
-            sHomeD = bd;
-        }
-        __syncthreads();
-
-        // verifies the candidates of leaf l (all threads)
-        auto visit = [&](int l) -> bool {
-            if (!BF_CHECK(l >= 0 && l < L, 1, l)) return true;
-            const float cm = sCmax;
-            if (tid == 0) { sLeaves++; lbS[l] = INFINITY; }
+        };
+        // verifies the candidates of leaf l
+        auto visit = [&](int l) {
+            leaves++;
             const unsigned char cl = leaf_class(sq, sp, s, Rv, Rv, A.meta + (int64_t)l * PM_LEAF_STRIDE);
-            const int cb = A.leafChunk[l];
-            const int nch = min(A.leafChunk[l + 1] - cb, BF_MAXCH);
-            if (tid == 0 && A.leafChunk[l + 1] - cb > BF_MAXCH) atomicOr(A.errFlag, 512);
-            for (int ci = warp; ci < nch; ci += BF_THREADS / 32) {
-                const int c = cb + ci;
-                const int64_t r0 = A.chunkOff[c];
-                int rows = (int)(A.chunkOff[c + 1] - r0);
-                if (!BF_CHECK(rows >= 1 && rows <= BF_ROWS && r0 >= 0 && r0 + rows <= A.n, 2, rows)) rows = 0;
-                const float *mu = A.chunkMu + (int64_t)c * ld;
-                float acc = 0.f;
-                for (int i = lane; i < ld; i += 32) {
-                    float t = __fsub_rn(qs[i], mu[i]);
-                    acc = __fmaf_rn(t, t, acc);
+            const int cb = A.leafChunk[l], ce = A.leafChunk[l + 1];
+            for (int c0 = cb; c0 < ce; c0 += 32) {
+                const int c = c0 + lane;
+                const bool vc = c < ce;
+                const float d2c = warp_d2(q4, vc ? A.chunkMu + (int64_t)c * ld : nullptr, nf4, lane);
+                const float lbc = vc ? __fsub_rn(__fmul_rn(__fsqrt_rn(d2c), lbSlack), A.chunkRx[c]) : INFINITY;
+                unsigned alive = __ballot_sync(VW_FULL, vc && !pruned(lbc));
+                while (alive) {
+                    const int src = __ffs(alive) - 1;
+                    alive &= alive - 1;
+                    if (pruned(__shfl_sync(VW_FULL, lbc, src))) continue;   // K fell since
+                    const int ci = c0 + src;
+                    const int64_t r0 = A.chunkOff[ci];
+                    int rows = (int)(A.chunkOff[ci + 1] - r0);
+                    if (!VW_CHECK(rows >= 1 && rows <= 32 && r0 >= 0 && r0 + rows <= A.n, 2, rows)) rows = 0;
+                    const bool cand = lane < rows && (cl == CL_FULL || pd2_row(A.O32 + (r0 + lane) * PM_MP, sq) <= lov);
+                    if (__ballot_sync(VW_FULL, cand) == 0u) continue;
+                    const float d2 = warp_d2(q4, cand ? A.X + (r0 + lane) * ld : nullptr, nf4, lane);
+                    seen += __popc(__ballot_sync(VW_FULL, cand));
+                    offer(cand, d2, (int)(r0 + lane));
                 }
-                for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                const float lbc = __fsub_rn(__fmul_rn(__fsqrt_rn(acc), lbSlack), A.chunkRx[c]);
-                const bool alive = !(lbc > 0.f && (double)lbc * lbc * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv));
-                bool cand = false;
-                if (alive && lane < rows)
-                    cand = cl == CL_FULL || pm_pd2_32(A.O32 + (r0 + lane) * PM_MP, sq) <= lov;
-                unsigned m = __ballot_sync(0xffffffffu, cand);
-                if (lane == 0) cmask[ci] = rows > 0 ? m : 0u;
             }
-            __syncthreads();
-            int nextC = 0;
-            while (nextC < nch && cmask[nextC] == 0u) nextC++;
-            int job = 0;
-            auto issue = [&](int ci, int dc, int stage) {
-                if (tid == 0) {
-                    const int64_t r0 = A.chunkOff[cb + ci];
-                    const int rows = (int)(A.chunkOff[cb + ci + 1] - r0);
-                    const int w = min(dch, ld - dc * dch);
-                    fence_async_shared();
-                    mbar_expect_tx(&bar[stage], (uint32_t)(rows * w * 4));
-                    for (int r = 0; r < rows; r++)
-                        bulk_g2s(xs + (stage * BF_ROWS + r) * rs, A.X + (r0 + r) * ld + dc * dch, (uint32_t)(w * 4),
-                                 &bar[stage]);
-                }
-            };
-            if (nextC < nch) issue(nextC, 0, 0);
-            for (int ci = nextC; ci < nch;) {
-                const unsigned m = cmask[ci];
-                const int64_t r0 = A.chunkOff[cb + ci];
-                const int rows = (int)(A.chunkOff[cb + ci + 1] - r0);
-                float acc = 0.f;
-                int cn = ci + 1;
-                while (cn < nch && cmask[cn] == 0u) cn++;
-                for (int dc = 0; dc < nDch; dc++) {
-                    const int stage = job & 1;
-                    if (dc + 1 < nDch) issue(ci, dc + 1, stage ^ 1);
-                    else if (cn < nch) issue(cn, 0, stage ^ 1);
-                    bool ok = mbar_wait_bounded(&bar[stage], phase[stage]);
-                    if (!ok) atomicOr(&sFail, 1);
-                    phase[stage] ^= 1u;
-                    const int w = min(dch, ld - dc * dch);
-                    if (pp < rows && ((m >> pp) & 1u)) {
-                        const float *xr = xs + (stage * BF_ROWS + pp) * rs;
-                        const float *qr = qs + dc * dch;
-                        for (int i = g; i < w; i += 8) {
-                            float t = __fsub_rn(qr[i], xr[i]);
-                            acc = __fmaf_rn(t, t, acc);
-                        }
-                    }
-                    __syncthreads();
-                    if (sFail) return false;
-                    job++;
-                }
-                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-                if (g == 0) dist[pp] = (pp < rows && ((m >> pp) & 1u)) ? acc : INFINITY;
-                __syncthreads();
-                if (warp == 0) {
-                    float cmx = sCmax;
-                    int csl = sCslot;
-                    const float v = dist[lane];
-                    unsigned bits = __ballot_sync(0xffffffffu, v < cmx);
-                    while (bits) {
-                        const int src = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const float val = __shfl_sync(0xffffffffu, v, src);
-                        topk_insert_warp(vals, idxs, KP, cmx, csl, val, (int)(r0 + src), lane);
-                    }
-                    if (lane == 0) {
-                        sCmax = cmx;
-                        sCslot = csl;
-                        sSeen += __popc(m);
-                        sVer += __popc(m);
-                    }
-                }
-                __syncthreads();
-                ci = cn;
-            }
-            return true;
         };
 
-        bool ok = true;
-        if (sHome >= 0) ok = visit(sHome);
-        if (tid == 0) BF_CHECK(sHome >= -1 && sHome < L, 6, sHome);
-        // filtering passes: leaves whose bound admits them, nearest centre first
-        while (ok) {
-            if (tid == 0) sCnt = 0;
-            __syncthreads();
-            const float cm = sCmax;
-            for (int64_t l = tid; l < L; l += BF_THREADS) {
-                const float lb = lbS[l];
-                if (!(lb < INFINITY)) continue;
-                if (lb > 0.f && (double)lb * lb * (1.0 - epsv) > (double)cm * (1.0 + 3.0 * epsv)) continue;
-                const int slot = atomicAdd(&sCnt, 1);
-                if (slot < BF_SURV) { svk[slot] = dcS[l]; svi[slot] = (int)l; }
+        // 1. candidate leaves and their lower bounds
+        int cnt = 0;
+        if (Rv > 0.f) {
+            for (int64_t b0 = 0; b0 < L; b0 += 32) {
+                const int64_t l = b0 + lane;
+                const bool in = l < L && leaf_class(sq, sp, s, Rv, Rv, A.meta + l * PM_LEAF_STRIDE) != CL_OUT;
+                const unsigned m = __ballot_sync(VW_FULL, in);
+                if (in) list[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2((int)l, 0);
+                cnt += __popc(m);
             }
-            __syncthreads();
-            const int total = sCnt;
-            if (total == 0) break;
-            const int ns = min(total, BF_SURV);
-            int P = 1;
-            while (P < ns) P <<= 1;
-            for (int i = ns + tid; i < P; i += BF_THREADS) { svk[i] = INFINITY; svi[i] = 0x7fffffff; }
-            __syncthreads();
-            for (int k2 = 2; k2 <= P; k2 <<= 1)
-                for (int j = k2 >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < P; i += BF_THREADS) {
-                        int ixj = i ^ j;
-                        if (ixj > i) {
-                            bool up = (i & k2) == 0;
-                            bool gt = svk[i] > svk[ixj] || (svk[i] == svk[ixj] && svi[i] > svi[ixj]);
-                            if (gt == up) {
-                                float tv = svk[i]; svk[i] = svk[ixj]; svk[ixj] = tv;
-                                int ti = svi[i]; svi[i] = svi[ixj]; svi[ixj] = ti;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            for (int e = 0; e < ns && ok; e++) {
-                const int l = svi[e];
-                const float lb = (l >= 0 && l < L) ? lbS[l] : INFINITY;
-                const float cmn = sCmax;
-                // every thread has its copy of lbS[l] and sCmax before visit()
-                // changes them, so all threads take the same branch below
-                __syncthreads();
-                if (tid == 0) BF_CHECK(l >= 0 && l < L, 3, l);
-                if (!(lb < INFINITY)) continue;
-                if (lb > 0.f && (double)lb * lb * (1.0 - epsv) > (double)cmn * (1.0 + 3.0 * epsv)) {
-                    if (tid == 0) lbS[l] = INFINITY;
-                    continue;
-                }
-                ok = visit(l);
-            }
-            __syncthreads();
-            if (total <= BF_SURV) break;
         }
-        if (!ok) break;
+        __syncwarp();
+        for (int e0 = 0; e0 < cnt; e0 += 32) {
+            const int e = e0 + lane;
+            const int l = e < cnt ? list[e].x : -1;
+            const float d2 = warp_d2(q4, l >= 0 ? A.leafMu + (int64_t)l * ld : nullptr, nf4, lane);
+            if (l >= 0) list[e].y = __float_as_int(__fsub_rn(__fmul_rn(__fsqrt_rn(d2), lbSlack), A.leafRx[l]));
+        }
+        __syncwarp();
+        // 2. best first over the listed leaves
+        for (;;) {
+            float bl = INFINITY;
+            int be = 0x7fffffff;
+            for (int e = lane; e < cnt; e += 32) {
+                const float lb = __int_as_float(list[e].y);
+                if (lb < bl) { bl = lb; be = e; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const float ob = __shfl_xor_sync(VW_FULL, bl, o);
+                const int oe = __shfl_xor_sync(VW_FULL, be, o);
+                if (ob < bl || (ob == bl && oe < be)) { bl = ob; be = oe; }
+            }
+            if (be == 0x7fffffff || pruned(bl)) break;
+            const int l = list[be].x;
+            __syncwarp();
+            if (lane == 0) list[be].y = __float_as_int(INFINITY);
+            __syncwarp();
+            if (!VW_CHECK(l >= 0 && l < L, 1, l)) break;
+            visit(l);
+        }
         // band-in points (FP64-resolved members just inside the radius)
-        if (warp == 0) {
-            const int nIn = min(A.inN[a], BCAP);
-            float cmx = sCmax;
-            int csl = sCslot;
-            for (int e = 0; e < nIn; e++) {
-                const int pos = A.inPos[(int64_t)a * BCAP + e];
-                if (!BF_CHECK(pos >= 0 && pos < A.n, 4, pos)) continue;
-                const float *xr = A.X + (int64_t)pos * ld;
-                float acc = 0.f;
-                for (int i = lane; i < ld; i += 32) {
-                    float t = __fsub_rn(qs[i], xr[i]);
-                    acc = __fmaf_rn(t, t, acc);
-                }
-                for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                topk_insert_warp(vals, idxs, KP, cmx, csl, acc, pos, lane);
-            }
-            if (lane == 0) { sCmax = cmx; sCslot = csl; sSeen += nIn; sVer += nIn; }
+        const int nIn = min(A.inN[a], BCAP);
+        for (int e0 = 0; e0 < nIn; e0 += 32) {
+            const int e = e0 + lane;
+            int pos = e < nIn ? A.inPos[(int64_t)a * BCAP + e] : -1;
+            if (e < nIn && !VW_CHECK(pos >= 0 && pos < A.n, 4, pos)) pos = -1;
+            const bool cand = pos >= 0;
+            const float d2 = warp_d2(q4, cand ? A.X + (int64_t)pos * ld : nullptr, nf4, lane);
+            seen += __popc(__ballot_sync(VW_FULL, cand));
+            offer(cand, d2, pos);
         }
-        __syncthreads();
-        {
-            // guard set: sort the top-KP by FP32 d^2, then FP64 for {d^2 <= K32 (1 + 3 eps_v)}
-            float *gv = (float *)uarea;                // [512]
-            int *gp = (int *)(gv + 512);               // [512]
-            double *gd = (double *)(gp + 512);         // [GCAP]
-            long long *gid = (long long *)(gd + GCAP); // [GCAP]
-            int PK = 1;
-            while (PK < KP) PK <<= 1;
-            for (int i = tid; i < PK; i += BF_THREADS) {
-                gv[i] = i < KP ? vals[i] : INFINITY;
-                gp[i] = i < KP ? idxs[i] : 0x7fffffff;
-                if (!(gv[i] < INFINITY)) gp[i] = 0x7fffffff;
+        __syncwarp();
+        // 3. guard set: the k-th smallest (value, position) of the top-KP
+        float kth = INFINITY;
+        int nfin = 0;
+        for (int j = 0; j < KPW; j++) {
+            const int e = lane + 32 * j;
+            const float v = vals[e];
+            const int p = idxs[e];
+            int rank = 0;
+            for (int f = 0; f < KP; f++) {
+                const float vf = vals[f];
+                rank += (vf < v || (vf == v && idxs[f] < p)) ? 1 : 0;
             }
-            __syncthreads();
-            for (int k2 = 2; k2 <= PK; k2 <<= 1)
-                for (int j = k2 >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < PK; i += BF_THREADS) {
-                        int ixj = i ^ j;
-                        if (ixj > i) {
-                            bool up = (i & k2) == 0;
-                            bool gt = gv[i] > gv[ixj] || (gv[i] == gv[ixj] && gp[i] > gp[ixj]);
-                            if (gt == up) {
-                                float tv = gv[i]; gv[i] = gv[ixj]; gv[ixj] = tv;
-                                int tp = gp[i]; gp[i] = gp[ixj]; gp[ixj] = tp;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            if (tid == 0) {
-                const float K32 = gv[k - 1];
-                const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
-                int G = 0;
-                while (G < KP && gv[G] <= thrv && gv[G] < INFINITY) G++;
-                // entries dropped from the top-KP are >= its final maximum
-                if (sSeen > KP && sCmax <= thrv) atomicOr(A.errFlag, 16);
-                sG = G;
-            }
-            __syncthreads();
-            const int G = min(sG, GCAP);
-            int Pg = 1;
-            while (Pg < G) Pg <<= 1;
-            for (int e = tid; e < Pg; e += BF_THREADS) {
-                if (e < G && BF_CHECK(gp[e] >= 0 && gp[e] < A.n, 5, gp[e])) {
-                    int p = gp[e];
-                    gd[e] = pm_dist64(A.X + (int64_t)p * ld, qs, d);
-                    gid[e] = A.perm[p];
-                } else {
-                    gd[e] = INFINITY;
-                    gid[e] = 0x7fffffffffffffffLL;
-                }
-            }
-            __syncthreads();
-            for (int k2 = 2; k2 <= Pg; k2 <<= 1)
-                for (int j = k2 >> 1; j > 0; j >>= 1) {
-                    for (int i = tid; i < Pg; i += BF_THREADS) {
-                        int ixj = i ^ j;
-                        if (ixj > i) {
-                            bool up = (i & k2) == 0;
-                            bool gt = gd[i] > gd[ixj] || (gd[i] == gd[ixj] && gid[i] > gid[ixj]);
-                            if (gt == up) {
-                                double td = gd[i]; gd[i] = gd[ixj]; gd[ixj] = td;
-                                long long ti = gid[i]; gid[i] = gid[ixj]; gid[ixj] = ti;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            for (int e = tid; e < k; e += BF_THREADS) {
-                const int64_t o = (int64_t)q * k + e;
-                if (e < G) {
-                    double dv = gd[e];
-                    float f = __double2float_rn(dv);
-                    A.outIds[o] = gid[e];
-                    A.outD[o] = f;
-                    A.outErr[o] = (float)fabs((double)f - dv);
-                } else {
-                    A.outIds[o] = -1;
-                    A.outD[o] = INFINITY;
-                    A.outErr[o] = 0.f;
-                }
-            }
-            if (tid == 0) {
-                A.dk[a] = G >= k ? gd[k - 1] : INFINITY;
-                atomicAdd(&A.fp64cnt[a], G);
-                A.nverOut[a] = sVer;
-                A.nleafOut[a] = sLeaves;
-            }
-            __syncthreads();
+            if (v < INFINITY && rank == k - 1) kth = v;
+            nfin += v < INFINITY ? 1 : 0;
         }
+        for (int o = 16; o; o >>= 1) {
+            nfin += __shfl_xor_sync(VW_FULL, nfin, o);
+            kth = fminf(kth, __shfl_xor_sync(VW_FULL, kth, o));
+        }
+        const float K32 = nfin >= k ? kth : INFINITY;
+        const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
+        // entries dropped from the top-KP are >= its final maximum
+        if (lane == 0 && seen > KP && cmax <= thrv) atomicOr(A.errFlag, 16);
+        int G = 0;
+        for (int j = 0; j < KPW; j++) {
+            const int e = lane + 32 * j;
+            const float v = vals[e];
+            const bool in = v <= thrv && v < INFINITY;
+            const unsigned m = __ballot_sync(VW_FULL, in);
+            if (in) gpos[G + __popc(m & ((1u << lane) - 1u))] = idxs[e];
+            G += __popc(m);
+        }
+        __syncwarp();
+        for (int e = lane; e < G; e += 32) {
+            const int p = gpos[e];
+            if (VW_CHECK(p >= 0 && p < A.n, 5, p)) {
+                gd[e] = pm_dist64(A.X + (int64_t)p * ld, qs, A.d);
+                gid[e] = A.perm[p];
+            } else {
+                gd[e] = INFINITY;
+                gid[e] = 0x7fffffffffffffffLL;
+            }
+        }
+        __syncwarp();
+        // rank by (FP64 distance, id); the k nearest are written in order
+        for (int e = lane; e < G; e += 32) {
+            const double dv = gd[e];
+            const long long iv = gid[e];
+            int rank = 0;
+            for (int f = 0; f < G; f++) rank += (gd[f] < dv || (gd[f] == dv && gid[f] < iv)) ? 1 : 0;
+            if (rank < k) {
+                const int64_t o = (int64_t)q * k + rank;
+                const float fv = __double2float_rn(dv);
+                A.outIds[o] = iv;
+                A.outD[o] = fv;
+                A.outErr[o] = (float)fabs((double)fv - dv);
+            }
+            if (rank == k - 1) A.dk[a] = dv;
+        }
+        for (int e = G + lane; e < k; e += 32) {
+            const int64_t o = (int64_t)q * k + e;
+            A.outIds[o] = -1;
+            A.outD[o] = INFINITY;
+            A.outErr[o] = 0.f;
+        }
+        if (lane == 0) {
+            if (G < k) A.dk[a] = INFINITY;
+            atomicAdd(&A.fp64cnt[a], G);
+            A.nverOut[a] = seen;
+            A.nleafOut[a] = leaves;
+        }
+        __syncwarp();
     }
-    if (sFail) {
-        // a staged copy did not complete in time: record it, give copies still
-        // in flight a bounded time to land, and leave
-        if (tid == 0) {
-            atomicOr(A.errFlag, 128);
-            mbar_wait_bounded(&bar[0], phase[0]);
-            mbar_wait_bounded(&bar[1], phase[1]);
-        }
-    }
-}
-
-size_t bestfirst_smem(int ld, int KP)
-{
-    const int dch = ld < BF_DCH ? ld : BF_DCH;
-    size_t f = (size_t)2 * BF_ROWS * (dch + 8) + ld + 2 * (size_t)KP;
-    size_t u = std::max<size_t>((size_t)BF_SURV * 8, 512 * 8 + (size_t)GCAP * 16);
-    return ((f * 4 + 15) & ~(size_t)15) + u + 128;
 }
 
 // ---------------------------------------- tensor-core range count (tcgen05)
@@ -1667,15 +1545,19 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
-    const size_t bsmem = bestfirst_smem(ld, KP);
-    if (bsmem > 227 * 1024) {
+    // verification: one warp per query, as many warps per block as shared
+    // memory allows (up to VW_MAXWARPS)
+    const size_t vwarp = verify_smem_warp(ld, KP);
+    const int vWarps = (int)std::min<size_t>(VW_MAXWARPS, (size_t)(227 * 1024) / vwarp);
+    if (vWarps < 1) {
         pm_set_error("d = %d is too large for the verification kernel's shared memory", d);
         return PMLSH_EINVAL;
     }
-    PM_TRY(pm_allow_max_dyn_smem((const void *)k_bestfirst));
-    int bfPerSM = 1;
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bfPerSM, k_bestfirst, BF_THREADS, bsmem));
-    bfPerSM = std::max(1, bfPerSM);
+    const size_t vsmem = (size_t)vWarps * vwarp;
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_verify));
+    int vPerSM = 1;
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vPerSM, k_verify, 32 * vWarps, vsmem));
+    vPerSM = std::max(1, vPerSM);
 
     const bool tensor = o->precision == PMLSH_BF16_TENSOR;
     // the tensor-core count holds all 512 TMEM columns of its SM; its
@@ -1803,21 +1685,20 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         }
         // verification: best-first over candidate leaves, guard set, FP64
         int *nverD = grow<int>(w.partSeen, (size_t)2 * na + 8, s);
-        const int bfGrid = std::max(1, std::min(na, bfPerSM * nsm));
-        float *bfScratch = grow<float>(w.partD, (size_t)bfGrid * 2 * L, s);
+        const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, vPerSM * nsm));
+        int2 *vLists = grow<int2>(w.partD, (size_t)vGrid * vWarps * L, s);
         if (s != PMLSH_OK) return s;
         PM_CUDA(cudaMemsetAsync(nverD + 2 * na, 0, 8 * sizeof(int), st));
         {
-            BfArgs ba;
-            ba.act = act; ba.na = na; ba.thr = thr; ba.qp32 = qp32; ba.qpiv = qpiv; ba.s = ix->s;
-            ba.meta = ix->leafMeta; ba.off = ix->leafOff; ba.L = L; ba.O32 = ix->O32; ba.X = ix->X; ba.Qd = Qd;
-            ba.ld = ld; ba.d = d; ba.leafMu = ix->leafMu; ba.leafRx = ix->leafRx; ba.chunkOff = ix->chunkOff;
-            ba.leafChunk = ix->leafChunk; ba.chunkMu = ix->chunkMu; ba.chunkRx = ix->chunkRx; ba.KP = KP; ba.k = k;
-            ba.inN = inN; ba.inPos = inPos; ba.perm = ix->perm; ba.outIds = oIds; ba.outD = oD; ba.outErr = oE;
-            ba.dk = dk; ba.fp64cnt = fpc; ba.nverOut = nverD; ba.nleafOut = nverD + na; ba.errFlag = errFlag;
-            ba.workCtr = nverD + 2 * na; ba.scratch = bfScratch;
-            ba.dbg = nverD + 2 * na + 1; ba.n = n;
-            PM_LAUNCH("k_bestfirst", st, k_bestfirst<<<bfGrid, BF_THREADS, bsmem, st>>>(ba));
+            VwArgs va;
+            va.act = act; va.na = na; va.thr = thr; va.qp32 = qp32; va.qpiv = qpiv; va.s = ix->s;
+            va.meta = ix->leafMeta; va.L = L; va.O32 = ix->O32; va.X = ix->X; va.Qd = Qd;
+            va.ld = ld; va.d = d; va.leafMu = ix->leafMu; va.leafRx = ix->leafRx; va.chunkOff = ix->chunkOff;
+            va.leafChunk = ix->leafChunk; va.chunkMu = ix->chunkMu; va.chunkRx = ix->chunkRx; va.KP = KP; va.k = k;
+            va.inN = inN; va.inPos = inPos; va.perm = ix->perm; va.outIds = oIds; va.outD = oD; va.outErr = oE;
+            va.dk = dk; va.fp64cnt = fpc; va.nverOut = nverD; va.nleafOut = nverD + na; va.errFlag = errFlag;
+            va.workCtr = nverD + 2 * na; va.dbg = nverD + 2 * na + 1; va.n = n; va.lists = vLists;
+            PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
         std::vector<double> dkH(na);
