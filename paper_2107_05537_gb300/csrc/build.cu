@@ -689,7 +689,8 @@ void pm_release_work(KnnWork &w)
                       &w.blkLeaves, &w.cntSure, &w.cntBand, &w.bandQ, &w.bandPos,
                       &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen, &w.bandInQ,
                       &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf,
-                      &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc};
+                      &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask,
+                      &w.recheck, &w.leafBits};
     for (DevBuf *b : bufs) b->release();
 }
 

@@ -135,14 +135,16 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 // and whole-leaf counts.  Leaves that some query of the block covers only
 // partially are listed for the block as {leaf, first position, size, first
 // tensor-operand row}, each with the QBT-bit mask of those queries (bit qq
-// of word qq / 32).
+// of word qq / 32).  Also, per query, the bit set of the leaves that Eq. 5
+// does not exclude (leafBits [active query][ceil(L / 32)]), which the
+// verification kernel walks instead of testing every leaf again.
 template <int QBT>
 __global__ void __launch_bounds__(128)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, const int64_t *__restrict__ bOff,
         int64_t L, int *__restrict__ cntSure, int *__restrict__ blkCnt, int4 *__restrict__ blkEnt,
-        uint32_t *__restrict__ blkMask)
+        uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32)
 {
     constexpr int W = QBT / 32;
     __shared__ float sq[QBT][PM_MP];
@@ -170,28 +172,31 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     }
     __syncthreads();
     const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool lv = l < L;
+    const int lane = threadIdx.x & 31;
     uint32_t mw[W];
     bool anyPart = false;
 #pragma unroll
     for (int w = 0; w < W; w++) mw[w] = 0u;
-    if (l < L) {
-        float Mv[PM_LEAF_STRIDE];
+    float Mv[PM_LEAF_STRIDE];
 #pragma unroll
-        for (int j = 0; j < PM_LEAF_STRIDE; j++) Mv[j] = meta[l * PM_LEAF_STRIDE + j];
-        const int cnt = (int)(off[l + 1] - off[l]);
+    for (int j = 0; j < PM_LEAF_STRIDE; j++) Mv[j] = lv ? meta[l * PM_LEAF_STRIDE + j] : 0.f;
+    const int cnt = lv ? (int)(off[l + 1] - off[l]) : 0;
 #pragma unroll
-        for (int w = 0; w < W; w++) {
-            uint32_t bits = 0u;
-            for (int j = 0; j < 32; j++) {
-                const int qq = w * 32 + j;
-                if (qq >= nb) break;
-                const unsigned char c = leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv);
-                if (c == CL_FULL) atomicAdd(&sCnt[qq], cnt);
-                bits |= (uint32_t)(c == CL_PART) << j;
-            }
-            mw[w] = bits;
-            anyPart |= bits != 0u;
+    for (int w = 0; w < W; w++) {
+        uint32_t bits = 0u;
+        for (int j = 0; j < 32; j++) {
+            const int qq = w * 32 + j;
+            if (qq >= nb) break;
+            const unsigned char c = lv ? leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv) : CL_OUT;
+            if (c == CL_FULL) atomicAdd(&sCnt[qq], cnt);
+            bits |= (uint32_t)(c == CL_PART) << j;
+            // per query: the warp's 32 leaves that Eq. 5 does not exclude
+            const uint32_t word = __ballot_sync(0xffffffffu, c != CL_OUT);
+            if (lane == 0 && (l >> 5) < W32) leafBits[(int64_t)(a0 + qq) * W32 + (l >> 5)] = word;
         }
+        mw[w] = bits;
+        anyPart |= bits != 0u;
     }
     if (anyPart) {
         const int slot = atomicAdd(&blkCnt[b], 1);
@@ -585,6 +590,8 @@ struct VwArgs {
     int *dbg;       // [3]: site, value, query of the first failed index check
     int64_t n;      // points
     int2 *lists;    // [warps][L]: per-warp candidate leaves {leaf, lower bound bits}
+    const uint32_t *leafBits;   // [na][W32]: leaves Eq. 5 does not exclude (k_class)
+    int W32;
 };
 
 // Shared memory of one warp: gd[KP] f64, gid[KP] i64, q[ld], vals[KP],
@@ -724,15 +731,29 @@ k_verify(VwArgs A)
             }
         };
 
-        // 1. candidate leaves and their lower bounds
+        // 1. candidate leaves (k_class's bit set for this round's radius,
+        // a superset of the leaves Eq. 5 keeps for sqrt(lov) <= its radius)
+        // and their lower bounds
         int cnt = 0;
         if (Rv > 0.f) {
-            for (int64_t b0 = 0; b0 < L; b0 += 32) {
-                const int64_t l = b0 + lane;
-                const bool in = l < L && leaf_class(sq, sp, s, Rv, Rv, A.meta + l * PM_LEAF_STRIDE) != CL_OUT;
-                const unsigned m = __ballot_sync(VW_FULL, in);
-                if (in) list[cnt + __popc(m & ((1u << lane) - 1u))] = make_int2((int)l, 0);
-                cnt += __popc(m);
+            const uint32_t *bits = A.leafBits + (int64_t)a * A.W32;
+            for (int w0 = 0; w0 < A.W32; w0 += 32) {
+                const int wi = w0 + lane;
+                uint32_t word = wi < A.W32 ? bits[wi] : 0u;
+                const int c = __popc(word);
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(VW_FULL, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                int at = cnt + incl - c;
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1u;
+                    const int64_t l = (int64_t)wi * 32 + b;
+                    if (l < L) list[at++] = make_int2((int)l, 0);
+                }
+                cnt += __shfl_sync(VW_FULL, incl, 31);
             }
         }
         __syncwarp();
@@ -1538,6 +1559,9 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     int *bandN = fpc + nq;       // counters after the per-query array
     int *errFlag = fpc + nq + 1;
     int *recheckN = fpc + nq + 2;
+    const int W32 = (int)((L + 31) / 32);
+    uint32_t *leafBits = grow<uint32_t>(w.leafBits, (size_t)nq * W32, s);
+    if (s != PMLSH_OK) return s;
 
     int nsm = 148;
     {
@@ -1601,14 +1625,14 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             dim3 gc((unsigned)((L + 127) / 128), (unsigned)nlist);
             if (!tc) {
                 PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                            ix->leafOff, nullptr, L, cntSure, blkCnt, blkEnt, blkMask));
+                                            ix->leafOff, nullptr, L, cntSure, blkCnt, blkEnt, blkMask, leafBits, W32));
                 int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
                 PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->O32,
                                             blkCnt, blkEnt, blkMask, L, cntSure, cntBand, bandN, bandCap,
                                             bandA, bandPos));
             } else {
                 PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                               ix->leafOff, ix->bOff, L, cntSure, blkCnt, blkEnt, blkMask));
+                                               ix->leafOff, ix->bOff, L, cntSure, blkCnt, blkEnt, blkMask, leafBits, W32));
                 int splitC = std::max(1, std::min(256, (4 * nsm + nblkT - 1) / nblkT));
                 PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_THREADS, TC_SMEM, st>>>(
                                             act, na, thr, qp32, ix->Bsplit, ix->bNorm, blkCnt, blkEnt, blkMask, L,
@@ -1698,6 +1722,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             va.inN = inN; va.inPos = inPos; va.perm = ix->perm; va.outIds = oIds; va.outD = oD; va.outErr = oE;
             va.dk = dk; va.fp64cnt = fpc; va.nverOut = nverD; va.nleafOut = nverD + na; va.errFlag = errFlag;
             va.workCtr = nverD + 2 * na; va.dbg = nverD + 2 * na + 1; va.n = n; va.lists = vLists;
+            va.leafBits = leafBits; va.W32 = W32;
             PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
