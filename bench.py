@@ -205,7 +205,7 @@ def timed_steps(step, steps, flush, stream):
     pm.profile(True)
     pm.profile_read()
     launches0 = pm.launch_count()
-    total_ms, nver, res = 0.0, 0, None
+    total_ms, res = 0.0, None
     for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -216,11 +216,10 @@ def timed_steps(step, steps, flush, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
-        nver += int(res["stats"]["nver"].sum())
     launches = pm.launch_count() - launches0
     prof = pm.profile_read()
     pm.profile(False)
-    return total_ms, nver, res, prof, launches
+    return total_ms, res, prof, launches
 
 
 def serve_leg(pm, ix, Q, prec, rate_qps, seconds, seed):
@@ -299,8 +298,12 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def make_step(p):
-        return lambda: ix.knn(Qd, k=K, c=C, alpha1=ALPHA1, beta=BETA, precision=p, out=(ids, dd, er))
+    # the timed call is the one a caller makes for results: ids, distances
+    # and error bounds, no per-query statistics (with statistics the exact
+    # |C| of every round is also counted; that form is timed beside it)
+    def make_step(p, with_stats=False):
+        return lambda: ix.knn(Qd, k=K, c=C, alpha1=ALPHA1, beta=BETA, precision=p, out=(ids, dd, er),
+                              with_stats=with_stats)
 
     step = make_step(prec)
     for _ in range(args.warmup):
@@ -311,14 +314,25 @@ def main():
         sampler.start()
     barrier(ws)
     torch.cuda.synchronize()
-    total_ms, nver, res, prof, launches = timed_steps(step, args.steps, flush, stream)
+    total_ms, res, prof, launches = timed_steps(step, args.steps, flush, stream)
     barrier(ws)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     total_s = max_over_ranks(total_ms / 1000.0, ws)
     value = nq * args.steps * ws / total_s
-    stats = res["stats"]
     ids_main = ids.clone()
+    dd_main = dd.clone()
+
+    # the same batch with per-query statistics (exact |C| per round): the
+    # trace, the verified rows behind the roofline, and its own speed
+    sstep = make_step(prec, with_stats=True)
+    sstep()
+    sms, sres, _, _ = timed_steps(sstep, args.steps, flush, stream)
+    stats = sres["stats"]
+    nver = int(stats["nver"].sum()) * args.steps
+    with_stats = {"value": nq * args.steps * ws / max_over_ranks(sms / 1000.0, ws),
+                  "ms_per_step": sms / args.steps,
+                  "ids_identical": bool(torch.equal(ids, ids_main) and torch.equal(dd, dd_main))}
 
     # the other precision on the same batch: same results, its own speed
     other = None
@@ -329,7 +343,7 @@ def main():
             ostep()
         torch.cuda.synchronize()
         barrier(ws)
-        oms, _, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream)
+        oms, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream)
         barrier(ws)
         os_ = max_over_ranks(oms / 1000.0, ws)
         other = {"precision": "fp32" if op == pm.PMLSH_FP32_PLAIN else "bf16",
@@ -360,14 +374,15 @@ def main():
         idh = torch.empty((nq, K), dtype=torch.int64).pin_memory()
         ddh = torch.empty((nq, K), dtype=torch.float32).pin_memory()
         erh = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-        ix.knn(Qh.numpy(), k=K, c=C, beta=BETA, precision=prec, out=(idh.numpy(), ddh.numpy(), erh.numpy()))
+        ix.knn(Qh.numpy(), k=K, c=C, beta=BETA, precision=prec, out=(idh.numpy(), ddh.numpy(), erh.numpy()),
+               with_stats=False)
         el = 0.0
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ix.knn(Qh.numpy(), k=K, c=C, beta=BETA, precision=prec,
-                   out=(idh.numpy(), ddh.numpy(), erh.numpy()))
+                   out=(idh.numpy(), ddh.numpy(), erh.numpy()), with_stats=False)
             el += time.perf_counter() - t0
         el = max_over_ranks(el, ws)
         e2e = {"value": nq * args.steps * ws / el, "unit": "queries/s",
@@ -424,7 +439,7 @@ def main():
                           "mean_verified": float(stats["nver"].mean()),
                           "mean_leaves_visited": float(stats["leaves"].mean()),
                           "rule_counts": np.bincount(stats["rule"], minlength=4).tolist()},
-                "build_s": build_s, "other_precision": other, "serve": serve,
+                "build_s": build_s, "with_stats": with_stats, "other_precision": other, "serve": serve,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
         print(json.dumps(line), flush=True)
     ix.close()

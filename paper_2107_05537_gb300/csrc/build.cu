@@ -690,7 +690,7 @@ void pm_release_work(KnnWork &w)
                       &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen, &w.bandInQ,
                       &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf,
                       &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask,
-                      &w.recheck, &w.leafBits};
+                      &w.recheck, &w.leafBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits};
     for (DevBuf *b : bufs) b->release();
 }
 

@@ -108,7 +108,7 @@ struct Thr {
     double R;      // t r (FP64, as in the oracle)
     float lo, hi;  // FP32 d'^2 <= lo: surely in; > hi: surely out
     float lov;     // verification threshold (lo, or the budget cut)
-    float pad;
+    float pad;     // 1: the budget selection listed this query's band-in points
 };
 
 __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const double *__restrict__ r,
@@ -137,20 +137,22 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 // tensor-operand row}, each with the QBT-bit mask of those queries (bit qq
 // of word qq / 32).  Also, per query, the bit set of the leaves that Eq. 5
 // does not exclude (leafBits [active query][ceil(L / 32)]), which the
-// verification kernel walks instead of testing every leaf again.
+// verification kernel walks instead of testing every leaf again, and the
+// sizes of the partially covered leaves (cntPart): with the whole-leaf
+// counts (cntSure) they bound |S_i| from below and above.
 template <int QBT>
 __global__ void __launch_bounds__(128)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, const int64_t *__restrict__ bOff,
         int64_t L, int *__restrict__ cntSure, int *__restrict__ blkCnt, int4 *__restrict__ blkEnt,
-        uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32)
+        uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32, int *__restrict__ cntPart)
 {
     constexpr int W = QBT / 32;
     __shared__ float sq[QBT][PM_MP];
     __shared__ float sp[QBT][PM_MAX_PIVOTS];
     __shared__ float sRin[QBT], sRout[QBT];
-    __shared__ int sCnt[QBT];
+    __shared__ int sCnt[QBT], sPart[QBT];
     const int b = blockIdx.y;
     const int a0 = b * QBT;
     const int nb = min(QBT, na - a0);
@@ -169,6 +171,7 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
             sRout[qq] = __fsqrt_rn(T.hi);
         }
         sCnt[qq] = 0;
+        sPart[qq] = 0;
     }
     __syncthreads();
     const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -189,7 +192,10 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
             const int qq = w * 32 + j;
             if (qq >= nb) break;
             const unsigned char c = lv ? leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv) : CL_OUT;
-            if (c == CL_FULL) atomicAdd(&sCnt[qq], cnt);
+            const int fullAdd = __reduce_add_sync(0xffffffffu, c == CL_FULL ? cnt : 0);
+            const int partAdd = __reduce_add_sync(0xffffffffu, c == CL_PART ? cnt : 0);
+            if (lane == 0 && fullAdd) atomicAdd(&sCnt[qq], fullAdd);
+            if (lane == 0 && partAdd) atomicAdd(&sPart[qq], partAdd);
             bits |= (uint32_t)(c == CL_PART) << j;
             // per query: the warp's 32 leaves that Eq. 5 does not exclude
             const uint32_t word = __ballot_sync(0xffffffffu, c != CL_OUT);
@@ -206,8 +212,10 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         for (int w = 0; w < W; w++) blkMask[e * W + w] = mw[w];
     }
     __syncthreads();
-    for (int qq = threadIdx.x; qq < nb; qq += blockDim.x)
+    for (int qq = threadIdx.x; qq < nb; qq += blockDim.x) {
         if (sCnt[qq]) atomicAdd(&cntSure[a0 + qq], sCnt[qq]);
+        if (sPart[qq]) atomicAdd(&cntPart[a0 + qq], sPart[qq]);
+    }
 }
 
 // Per-point test in partially covered leaves (the queries of the block's
@@ -455,6 +463,7 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
         atomicAdd(&fp64cnt[a], nband);
         Thr T = thr[a];
         T.lov = LO > 0.f ? __uint_as_float(__float_as_uint(LO) - 1u) : -1.f;  // v <= lov  <=>  v < LO
+        T.pad = 1.f;   // the band-in points of this query are listed (inPos)
         thr[a] = T;
     }
 }
@@ -592,6 +601,9 @@ struct VwArgs {
     int2 *lists;    // [warps][L]: per-warp candidate leaves {leaf, lower bound bits}
     const uint32_t *leafBits;   // [na][W32]: leaves Eq. 5 does not exclude (k_class)
     int W32;
+    const double *O64, *qp64;   // FP64 projected points and queries
+    int m;
+    int inlineBand;             // 1: decide FP32 band points in FP64 here (no exact count ran)
 };
 
 // Shared memory of one warp: gd[KP] f64, gid[KP] i64, q[ld], vals[KP],
@@ -609,8 +621,11 @@ __host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP)
 
 // Exact top-k of the candidate set, one warp per query (persistent warps
 // take active queries from a counter).  The candidates are the points with
-// FP32 d'^2 <= lov plus the FP64-resolved band-in points; only their k
-// nearest matter (stop rule 1 tests the k-th distance).
+// FP32 d'^2 <= lov plus the FP64-resolved band-in points: listed by the
+// exact count or the budget selection, or (inlineBand, when neither ran for
+// the query) decided here for the points of the visited leaves with
+// lov < d'^2 <= hi by the FP64 test of k_band64.  Only their k nearest
+// matter (stop rule 1 tests the k-th distance).
 //  1. The leaves that Eq. 5 does not exclude for radius sqrt(lov) are listed
 //     with the lower bound lb = ||q - mu_l|| - Rx_l of their members'
 //     distances (original-space leaf balls).
@@ -654,6 +669,9 @@ k_verify(VwArgs A)
         const Thr T = A.thr[a];
         const float lov = T.lov;
         const float Rv = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
+        const bool inl = A.inlineBand != 0 && T.pad == 0.f;
+        const float Rout = inl ? __fsqrt_rn(T.hi) : Rv;   // leaves beyond hold no candidate
+        int nfp = 0;                                       // FP64 decisions (this lane)
         for (int i = lane; i < ld; i += 32) qs[i] = A.Qd[(int64_t)q * ld + i];
         if (lane < PM_MP) sq[lane] = A.qp32[(int64_t)q * PM_MP + lane];
         if (lane < PM_MAX_PIVOTS) sp[lane] = A.qpiv[(int64_t)q * PM_MAX_PIVOTS + lane];
@@ -706,7 +724,7 @@ k_verify(VwArgs A)
         // verifies the candidates of leaf l
         auto visit = [&](int l) {
             leaves++;
-            const unsigned char cl = leaf_class(sq, sp, s, Rv, Rv, A.meta + (int64_t)l * PM_LEAF_STRIDE);
+            const unsigned char cl = leaf_class(sq, sp, s, Rv, Rout, A.meta + (int64_t)l * PM_LEAF_STRIDE);
             const int cb = A.leafChunk[l], ce = A.leafChunk[l + 1];
             for (int c0 = cb; c0 < ce; c0 += 32) {
                 const int c = c0 + lane;
@@ -722,7 +740,20 @@ k_verify(VwArgs A)
                     const int64_t r0 = A.chunkOff[ci];
                     int rows = (int)(A.chunkOff[ci + 1] - r0);
                     if (!VW_CHECK(rows >= 1 && rows <= 32 && r0 >= 0 && r0 + rows <= A.n, 2, rows)) rows = 0;
-                    const bool cand = lane < rows && (cl == CL_FULL || pd2_row(A.O32 + (r0 + lane) * PM_MP, sq) <= lov);
+                    bool cand = false;
+                    if (lane < rows) {
+                        if (cl == CL_FULL) {
+                            cand = true;
+                        } else {
+                            const float pd = pd2_row(A.O32 + (r0 + lane) * PM_MP, sq);
+                            cand = pd <= lov;
+                            if (!cand && inl && pd <= T.hi) {
+                                // inside the FP32 error band: k_band64's FP64 test
+                                cand = pm_pdist64(A.O64 + (r0 + lane) * PM_MP, A.qp64 + (int64_t)q * PM_MP, A.m) <= T.R;
+                                nfp++;
+                            }
+                        }
+                    }
                     if (__ballot_sync(VW_FULL, cand) == 0u) continue;
                     const float d2 = warp_d2(q4, cand ? A.X + (r0 + lane) * ld : nullptr, nf4, lane);
                     seen += __popc(__ballot_sync(VW_FULL, cand));
@@ -735,7 +766,7 @@ k_verify(VwArgs A)
         // a superset of the leaves Eq. 5 keeps for sqrt(lov) <= its radius)
         // and their lower bounds
         int cnt = 0;
-        if (Rv > 0.f) {
+        if (Rv > 0.f || inl) {
             const uint32_t *bits = A.leafBits + (int64_t)a * A.W32;
             for (int w0 = 0; w0 < A.W32; w0 += 32) {
                 const int wi = w0 + lane;
@@ -862,9 +893,10 @@ k_verify(VwArgs A)
             A.outD[o] = INFINITY;
             A.outErr[o] = 0.f;
         }
+        for (int o = 16; o; o >>= 1) nfp += __shfl_xor_sync(VW_FULL, nfp, o);
         if (lane == 0) {
             if (G < k) A.dk[a] = INFINITY;
-            atomicAdd(&A.fp64cnt[a], G);
+            atomicAdd(&A.fp64cnt[a], G + nfp);
             A.nverOut[a] = seen;
             A.nleafOut[a] = leaves;
         }
@@ -908,15 +940,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-
-// 32 lanes x 1 FP32 accumulator column (this warp's lane quarter).
-__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr)
-{
-    uint32_t r;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    return r;
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -1417,6 +1440,17 @@ __global__ void k_recheck(const int *__restrict__ recheckN, int recheckCap, cons
     }
 }
 
+// Sub-batch of the active queries (the ones whose exact range count is
+// needed): their query ids and round thresholds.
+__global__ void k_gather_sub(const int *__restrict__ idx, int n2, const int32_t *__restrict__ act,
+                             const Thr *__restrict__ thr, int32_t *__restrict__ act2, Thr *__restrict__ thr2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    act2[i] = act[idx[i]];
+    thr2[i] = thr[idx[i]];
+}
+
 // Locality order: counting sort of queries by leaf key.
 __global__ void k_hist(const unsigned int *__restrict__ key, int64_t nq, int *__restrict__ h)
 {
@@ -1548,6 +1582,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     Thr *thr = grow<Thr>(w.thr, nq, s);
     int *cntSure = grow<int>(w.cntSure, nq, s);
     int *cntBand = grow<int>(w.cntBand, nq, s);
+    int *cntPart = grow<int>(w.cntPart, nq, s);
     int *inTrue = grow<int>(w.bandCnt, nq, s);
     int *inN = grow<int>(w.bandIn, nq, s);
     int *inPos = grow<int>(w.bandInQ, (size_t)nq * BCAP, s);
@@ -1600,17 +1635,24 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             if (!done[orderH[i]]) actH.push_back(orderH[i]);
         const int na = (int)actH.size();
         if (na == 0) break;
-        const int nblk = (na + QB - 1) / QB;
-        const int nblkT = (na + TC_QN - 1) / TC_QN;
         PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         PM_CUDA(cudaMemsetAsync(inTrue, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(inN, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(fpc, 0, (nq + 8) * sizeof(int), st));
         PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
-        // range counts: leaf lists with the masks of partially covering
-        // queries, then the per-point count (CUDA cores or tensor cores)
-        auto count_phase = [&](bool tc) -> pmlsh_status {
-            const int nlist = tc ? nblkT : nblk;
+        // leaf classification (Eq. 5): bounds of |S_i|, leaf lists with the
+        // masks of partially covering queries, per-query leaf bit sets.  The
+        // phases run on the active batch or on a gathered sub-batch (io).
+        struct CountIO {
+            const int32_t *act;
+            int na;
+            const Thr *thr;
+            int *cntSure, *cntPart, *cntBand, *inTrue, *inN, *inPos, *fpc;
+            uint32_t *leafBits;
+        };
+        const int64_t Tdec = std::min<int64_t>(B, n);
+        auto class_phase = [&](bool tc, const CountIO &io) -> pmlsh_status {
+            const int nlist = tc ? (io.na + TC_QN - 1) / TC_QN : (io.na + QB - 1) / QB;
             const int mwords = tc ? TC_MW : QB / 32;
             pmlsh_status s2 = PMLSH_OK;
             int *blkCnt = grow<int>(w.blkCnt, nlist, s2);
@@ -1618,41 +1660,61 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             uint32_t *blkMask = grow<uint32_t>(w.blkMask, (size_t)nlist * L * mwords, s2);
             if (s2 != PMLSH_OK) return s2;
             PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(cntSure, 0, na * sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(cntBand, 0, na * sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(io.cntSure, 0, io.na * sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(io.cntPart, 0, io.na * sizeof(int), st));
+            PM_CUDA(cudaMemsetAsync(io.cntBand, 0, io.na * sizeof(int), st));
             PM_CUDA(cudaMemsetAsync(bandN, 0, sizeof(int), st));
             PM_CUDA(cudaMemsetAsync(recheckN, 0, sizeof(int), st));
             dim3 gc((unsigned)((L + 127) / 128), (unsigned)nlist);
+            if (!tc)
+                PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(io.act, io.na, io.thr, qp32, qpiv, ix->s,
+                                            ix->leafMeta, ix->leafOff, nullptr, L, io.cntSure, blkCnt, blkEnt,
+                                            blkMask, io.leafBits, W32, io.cntPart));
+            else
+                PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(io.act, io.na, io.thr, qp32, qpiv, ix->s,
+                                               ix->leafMeta, ix->leafOff, ix->bOff, L, io.cntSure, blkCnt, blkEnt,
+                                               blkMask, io.leafBits, W32, io.cntPart));
+            PM_CUDA(cudaGetLastError());
+            return PMLSH_OK;
+        };
+        // the per-point count in the partially covered leaves (CUDA cores
+        // or tensor cores), points inside the FP32 error band listed
+        auto point_count = [&](bool tc, const CountIO &io) -> pmlsh_status {
+            const int nlist = tc ? (io.na + TC_QN - 1) / TC_QN : (io.na + QB - 1) / QB;
+            const int *blkCnt = w.blkCnt.as<int>();
+            const int4 *blkEnt = w.blkLeaves.as<int4>();
+            const uint32_t *blkMask = w.blkMask.as<uint32_t>();
             if (!tc) {
-                PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                            ix->leafOff, nullptr, L, cntSure, blkCnt, blkEnt, blkMask, leafBits, W32));
-                int splitC = std::max(1, std::min(64, (4 * nsm + nblk - 1) / nblk));
-                PM_LAUNCH("k_count", st, k_count<<<dim3(nblk, splitC), 256, 0, st>>>(act, na, thr, qp32, ix->O32,
-                                            blkCnt, blkEnt, blkMask, L, cntSure, cntBand, bandN, bandCap,
-                                            bandA, bandPos));
+                int splitC = std::max(1, std::min(64, (4 * nsm + nlist - 1) / nlist));
+                PM_LAUNCH("k_count", st, k_count<<<dim3(nlist, splitC), 256, 0, st>>>(io.act, io.na, io.thr, qp32,
+                                            ix->O32, blkCnt, blkEnt, blkMask, L, io.cntSure, io.cntBand, bandN,
+                                            bandCap, bandA, bandPos));
             } else {
-                PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(act, na, thr, qp32, qpiv, ix->s, ix->leafMeta,
-                                               ix->leafOff, ix->bOff, L, cntSure, blkCnt, blkEnt, blkMask, leafBits, W32));
-                int splitC = std::max(1, std::min(256, (4 * nsm + nblkT - 1) / nblkT));
-                PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nblkT, splitC), TC_THREADS, TC_SMEM, st>>>(
-                                            act, na, thr, qp32, ix->Bsplit, ix->bNorm, blkCnt, blkEnt, blkMask, L,
-                                            ix->maxNorm, cntSure, recheckN, recheckCap, recheck, errFlag));
-                PM_LAUNCH("k_recheck", st, k_recheck<<<4 * nsm, 256, 0, st>>>(recheckN, recheckCap, recheck, act, thr,
-                                            qp32, ix->O32, cntSure, cntBand, bandN, bandCap, bandA, bandPos));
+                int splitC = std::max(1, std::min(256, (4 * nsm + nlist - 1) / nlist));
+                PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nlist, splitC), TC_THREADS, TC_SMEM, st>>>(
+                                            io.act, io.na, io.thr, qp32, ix->Bsplit, ix->bNorm, blkCnt, blkEnt,
+                                            blkMask, L, ix->maxNorm, io.cntSure, recheckN, recheckCap, recheck,
+                                            errFlag));
+                PM_LAUNCH("k_recheck", st, k_recheck<<<4 * nsm, 256, 0, st>>>(recheckN, recheckCap, recheck, io.act,
+                                            io.thr, qp32, ix->O32, io.cntSure, io.cntBand, bandN, bandCap, bandA,
+                                            bandPos));
             }
             PM_CUDA(cudaGetLastError());
             return PMLSH_OK;
         };
-        PM_TRY(count_phase(tensor));
-        // FP64 band resolution (grid sized by the capacity; empty threads exit)
-        {
+        // exact count: per-point test, FP64 band resolution; host copies of
+        // the sure, band and band-in counts
+        auto exact_count = [&](const CountIO &io, std::vector<int> &es, std::vector<int> &eb,
+                               std::vector<int> &ein) -> pmlsh_status {
+            PM_TRY(point_count(tensor, io));
             int hN[3] = {0, 0, 0};   // bandN, errFlag, recheckN
             PM_CUDA(cudaMemcpyAsync(hN, bandN, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
             PM_CUDA(cudaStreamSynchronize(st));
             if (tensor && hN[2] > recheckCap) {
                 // more undecided pairs than the recheck list holds: count this
                 // round on the CUDA cores instead (same results)
-                PM_TRY(count_phase(false));
+                PM_TRY(class_phase(false, io));
+                PM_TRY(point_count(false, io));
                 PM_CUDA(cudaMemcpyAsync(hN, bandN, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
                 PM_CUDA(cudaStreamSynchronize(st));
             }
@@ -1661,17 +1723,70 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 pm_set_error("more than %d projected distances fell inside the FP32 error band in one round", bandCap);
                 return PMLSH_EINTERNAL;
             }
+            // (grid sized by the capacity; empty threads exit)
             if (hBand > 0)
-                PM_LAUNCH("k_band64", st, k_band64<<<(hBand + 255) / 256, 256, 0, st>>>(bandN, bandCap, bandA, bandPos, act, thr,
-                                                             ix->O64, qp64, m, inTrue, inN, inPos, fpc,
-                                                             errFlag));
-        }
-        PM_CUDA(cudaGetLastError());
-        std::vector<int> hs(na), hb(na), hin(na);
+                PM_LAUNCH("k_band64", st, k_band64<<<(hBand + 255) / 256, 256, 0, st>>>(bandN, bandCap, bandA, bandPos,
+                                                             io.act, io.thr, ix->O64, qp64, m, io.inTrue, io.inN,
+                                                             io.inPos, io.fpc, errFlag));
+            PM_CUDA(cudaGetLastError());
+            es.resize(io.na);
+            eb.resize(io.na);
+            ein.resize(io.na);
+            PM_CUDA(cudaMemcpyAsync(es.data(), io.cntSure, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaMemcpyAsync(eb.data(), io.cntBand, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaMemcpyAsync(ein.data(), io.inTrue, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaStreamSynchronize(st));
+            return PMLSH_OK;
+        };
+        const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits};
+        PM_TRY(class_phase(tensor, full));
+        std::vector<int> hs(na), hp(na), hb(na, 0), hin(na, 0);
         PM_CUDA(cudaMemcpyAsync(hs.data(), cntSure, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(hb.data(), cntBand, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(hin.data(), inTrue, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(hp.data(), cntPart, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
+        // The decisions of Algorithm 2 compare |S_i| only with min(B, n)
+        // (rule 2: |S_i| >= B; rule 3: |S_i| = n).  Whole-leaf counts bound
+        // |S_i| from below and whole partial leaves from above.  The exact
+        // count runs for every query when the caller asks for the statistics
+        // (|C| is one of them), else only for the queries whose bounds
+        // straddle min(B, n); for the rest the verification decides the FP32
+        // band points it meets in FP64 itself.
+        const bool needExact = stats != nullptr;
+        // hb: points with FP32 d'^2 <= hi beyond the sure ones (the budget
+        // selection's capacity); without the exact count, the partial leaves
+        std::vector<int32_t> ambH;
+        if (needExact) {
+            PM_TRY(exact_count(full, hs, hb, hin));
+        } else {
+            for (int a = 0; a < na; a++) {
+                hb[a] = hp[a];
+                if (hs[a] < Tdec && (int64_t)hs[a] + hp[a] >= Tdec) ambH.push_back(a);
+            }
+        }
+        if (!ambH.empty()) {
+            // exact count of the sub-batch whose bounds straddle min(B, n)
+            const int na2 = (int)ambH.size();
+            int *sub = grow<int>(w.subIdx, (size_t)na2 * (12 + BCAP), s);
+            Thr *thr2 = grow<Thr>(w.subThr, na2, s);
+            uint32_t *bits2 = grow<uint32_t>(w.subBits, (size_t)na2 * W32, s);
+            if (s != PMLSH_OK) return s;
+            int *amb = sub, *act2 = sub + na2, *s2Sure = sub + 2 * na2, *s2Part = sub + 3 * na2,
+                *s2Band = sub + 4 * na2, *s2In = sub + 5 * na2, *s2InN = sub + 6 * na2, *s2Fp = sub + 7 * na2,
+                *s2InPos = sub + 12 * na2;
+            PM_CUDA(cudaMemcpyAsync(amb, ambH.data(), na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            PM_CUDA(cudaMemsetAsync(s2In, 0, 3 * (size_t)na2 * sizeof(int), st));   // inTrue, inN, fp64
+            PM_LAUNCH("k_gather_sub", st, k_gather_sub<<<(na2 + 255) / 256, 256, 0, st>>>(amb, na2, act, thr, act2, thr2));
+            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2};
+            PM_TRY(class_phase(tensor, subIO));
+            std::vector<int> es, eb, ein;
+            PM_TRY(exact_count(subIO, es, eb, ein));
+            for (int i = 0; i < na2; i++) {
+                const int a = ambH[i];
+                hs[a] = es[i];
+                hb[a] = eb[i];
+                hin[a] = ein[i];
+            }
+        }
         // which queries reached the budget (rule 2)
         std::vector<int32_t> selH;
         std::vector<int64_t> selOffH;
@@ -1723,6 +1838,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             va.dk = dk; va.fp64cnt = fpc; va.nverOut = nverD; va.nleafOut = nverD + na; va.errFlag = errFlag;
             va.workCtr = nverD + 2 * na; va.dbg = nverD + 2 * na + 1; va.n = n; va.lists = vLists;
             va.leafBits = leafBits; va.W32 = W32;
+            va.O64 = ix->O64; va.qp64 = qp64; va.m = m; va.inlineBand = needExact ? 0 : 1;
             PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
@@ -1760,7 +1876,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 r[q] = o->c * r[q];
             } else {
                 r[q] = o->c * r[q];
-                if (count[a] > 0 && dkH[a] <= o->c * r[q]) { done[q] = 1; rule[q] = 1; continue; }
+                // dk is finite only when C holds at least k points
+                if (dkH[a] <= o->c * r[q]) { done[q] = 1; rule[q] = 1; continue; }
             }
             changed = true;
         }
@@ -1798,3 +1915,4 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     if (!idev || !ddev) PM_CUDA(cudaStreamSynchronize(st));
     return PMLSH_OK;
 }
+

@@ -60,7 +60,7 @@ struct KnnWork {
         bandIn, bandCnt;
     DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
     DevBuf selBuf, selOff, selCnt, selTau;
-    DevBuf active, misc, recheck, leafBits;
+    DevBuf active, misc, recheck, leafBits, cntPart, subIdx, subThr, subBits;
 };
 
 struct pmlsh_index {

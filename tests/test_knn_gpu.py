@@ -23,7 +23,7 @@ E = math.e
 
 
 def _run_both(X, Q, A, k, c=1.5, beta=0.2809, r_min=None, stop_rule=0, leaf=64, s=5, m=None,
-              t=None, device_inputs=True, precision=0):
+              t=None, device_inputs=True, precision=0, with_stats=True):
     m = A.shape[0] if m is None else m
     ix = pm.Index(torch.from_numpy(X).cuda() if device_inputs else X, m=m, s=s, leaf_size=leaf,
                   proj=A)
@@ -35,7 +35,7 @@ def _run_both(X, Q, A, k, c=1.5, beta=0.2809, r_min=None, stop_rule=0, leaf=64, 
     ref = oracle.knn(X, A, Q, k, c, tt, B, rmin, stop_rule)
     Qin = torch.from_numpy(Q).cuda() if device_inputs else Q
     got = ix.knn(Qin, k=k, c=c, beta=beta, r_min=r_min if r_min is not None else 0.0,
-                 stop_rule=stop_rule, t=tt, precision=precision)
+                 stop_rule=stop_rule, t=tt, precision=precision, with_stats=with_stats)
     torch.cuda.synchronize()
     ix.close()
     return got, ref
@@ -296,9 +296,12 @@ def test_c2_full_size_sampled_parity_tensor():
     Qd = torch.from_numpy(Q).cuda()
     got = ix.knn(Qd, k=50, c=1.5, beta=0.2809, precision=TENSOR)
     plain = ix.knn(Qd, k=50, c=1.5, beta=0.2809)
+    fast = ix.knn(Qd, k=50, c=1.5, beta=0.2809, precision=TENSOR, with_stats=False)
     torch.cuda.synchronize()
     ix.close()
     assert torch.equal(got["ids"], plain["ids"]) and torch.equal(got["dists"], plain["dists"])
+    assert torch.equal(got["ids"], fast["ids"]) and torch.equal(got["dists"], fast["dists"])
+    assert torch.equal(got["err"], fast["err"])
     for key in ("rounds", "rule", "ncand", "r", "fp64"):
         assert np.array_equal(got["stats"][key], plain["stats"][key]), key
     rng = np.random.default_rng(1)
@@ -309,3 +312,61 @@ def test_c2_full_size_sampled_parity_tensor():
     sub = dict(ids=got["ids"][sample], dists=got["dists"][sample], err=got["err"][sample],
                stats={k2: v[sample] for k2, v in got["stats"].items()})
     _assert_parity(sub, ref)
+
+
+# Without statistics the exact range count runs only where the bounds of
+# |S_i| from whole leaves straddle min(B, n); band points of the visited
+# leaves are then decided in FP64 by the verification.  Results are the
+# oracle's in every regime: rule 1 (bounds far below B), a radius whose
+# lower bound already reaches B (rule 2 without a count), bounds that
+# straddle B (the exact count runs), several rounds, rule 3 (B > n).
+@pytest.mark.parametrize("precision", [pm.PMLSH_FP32_PLAIN, pm.PMLSH_BF16_TENSOR])
+@pytest.mark.parametrize("kw", [
+    dict(k=10),
+    dict(k=10, r_min=200.0),
+    dict(k=5, beta=0.01, r_min=2.0),
+    dict(k=5, beta=0.01, r_min=2.0, stop_rule=1),
+    dict(k=10, beta=0.05, r_min=8.0),
+    dict(k=10, beta=1.0, r_min=400.0),
+])
+def test_no_stats_path_parity(c1, precision, kw):
+    X, Q, A = c1
+    got, ref = _run_both(X, Q[:64], A, precision=precision, with_stats=False, **kw)
+    assert got.get("stats") is None
+    _assert_parity(got, ref, trace=False)
+
+
+@pytest.mark.parametrize("n,d,m,leaf,s,k", [
+    (1000 + 17, 37, 15, 64, 5, 7),
+    (300, 8, 3, 16, 0, 1),
+    (50, 20, 16, 64, 5, 50),
+])
+def test_no_stats_path_shapes(n, d, m, leaf, s, k):
+    X, Q, _, _ = datagen.mixture(n, d, 7, 1.0, seed=n, nq=33)
+    A = oracle.gen_projection(11, m, d).astype(np.float32)
+    for rmin in (None, 0.5):
+        got, ref = _run_both(X, Q, A, k=k, leaf=leaf, s=s, r_min=rmin, beta=0.1, with_stats=False)
+        _assert_parity(got, ref, trace=False)
+
+
+def test_no_stats_path_sub_batch_of_straddling_queries(c1):
+    # radii for which some queries' bounds straddle B and others do not: the
+    # exact count runs on a gathered sub-batch (k_gather_sub), results equal
+    # the oracle's, and the sweep also covers rounds without any count
+    X, Q, A = c1
+    seen_sub, seen_none = [], []
+    # projected clusters of this workload lie ~600 apart with radius ~45, so
+    # the counts of different queries cross B = 510 at r of about 80-120
+    for beta, rmin in ((0.05, 3.0), (0.05, 60.0), (0.05, 80.0), (0.05, 100.0), (0.05, 120.0),
+                       (0.2809, 3.0)):
+        pm.profile(True)
+        pm.profile_read()
+        got, ref = _run_both(X, Q[:64], A, k=10, beta=beta, r_min=rmin, with_stats=False)
+        prof = pm.profile_read()
+        pm.profile(False)
+        _assert_parity(got, ref, trace=False)
+        if "k_gather_sub" in prof:
+            seen_sub.append((beta, rmin))
+        if "k_count" not in prof and "k_count_tc" not in prof:
+            seen_none.append((beta, rmin))
+    assert seen_sub and seen_none, (seen_sub, seen_none)
