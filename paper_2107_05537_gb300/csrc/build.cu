@@ -650,6 +650,65 @@ struct Bisect {
     }
 };
 
+// Orthonormalises the columns of V [d][K] (FP64, column c at V[j * K + c])
+// by modified Gram-Schmidt, twice; a column that vanishes becomes zero.
+void orthonormalize(std::vector<double> &V, int d, int K)
+{
+    for (int pass = 0; pass < 2; pass++)
+        for (int c = 0; c < K; c++) {
+            for (int b = 0; b < c; b++) {
+                double dot = 0.0;
+                for (int j = 0; j < d; j++) dot += V[(size_t)j * K + b] * V[(size_t)j * K + c];
+                for (int j = 0; j < d; j++) V[(size_t)j * K + c] -= dot * V[(size_t)j * K + b];
+            }
+            double nn = 0.0;
+            for (int j = 0; j < d; j++) nn += V[(size_t)j * K + c] * V[(size_t)j * K + c];
+            const double inv = nn > 1e-24 ? 1.0 / std::sqrt(nn) : 0.0;
+            for (int j = 0; j < d; j++) V[(size_t)j * K + c] *= inv;
+        }
+}
+
+// PM_PCA leading principal directions of the leaf centres (rows of P,
+// [PM_PCA][ld], zero padding columns), by subspace iteration from a seeded
+// start.  Any rows that are orthonormal make ||P v|| <= ||v||, so the
+// iteration count affects only how tight that bound is; rows beyond the
+// rank of the centres (or beyond d) are zero.
+void leaf_pca(const std::vector<float> &mu, int64_t L, int ld, int d, uint64_t seed, std::vector<double> &P)
+{
+    const int K = PM_PCA;
+    std::vector<double> mean(d, 0.0);
+    for (int64_t l = 0; l < L; l++)
+        for (int j = 0; j < d; j++) mean[j] += mu[(size_t)l * ld + j];
+    for (int j = 0; j < d; j++) mean[j] /= (double)L;
+    std::vector<double> V((size_t)d * K), W((size_t)d * K), T((size_t)K);
+    for (size_t i = 0; i < V.size(); i++)
+        V[i] = (double)(pm_splitmix64(seed, i) >> 11) * 0x1.0p-52 - 1.0;
+    orthonormalize(V, d, K);
+    for (int it = 0; it < 5; it++) {
+        std::fill(W.begin(), W.end(), 0.0);
+        for (int64_t l = 0; l < L; l++) {
+            const float *m = mu.data() + (size_t)l * ld;
+            // T = (mu_l - mean) . V, then W += (mu_l - mean) T
+            std::fill(T.begin(), T.end(), 0.0);
+            for (int j = 0; j < d; j++) {
+                const double x = m[j] - mean[j];
+                const double *v = V.data() + (size_t)j * K;
+                for (int c = 0; c < K; c++) T[c] += x * v[c];
+            }
+            for (int j = 0; j < d; j++) {
+                const double x = m[j] - mean[j];
+                double *w = W.data() + (size_t)j * K;
+                for (int c = 0; c < K; c++) w[c] += x * T[c];
+            }
+        }
+        V.swap(W);
+        orthonormalize(V, d, K);
+    }
+    P.assign((size_t)K * ld, 0.0);
+    for (int c = 0; c < K && c < d; c++)
+        for (int j = 0; j < d; j++) P[(size_t)c * ld + j] = V[(size_t)j * K + c];
+}
+
 template <class T> pmlsh_status dalloc(T **p, size_t count)
 {
     PM_CUDA(cudaMalloc((void **)p, std::max<size_t>(1, count) * sizeof(T)));
@@ -672,6 +731,8 @@ void pm_free_index(pmlsh_index *ix)
     cudaFree(ix->treeV);
     cudaFree(ix->leafMu);
     cudaFree(ix->leafRx);
+    cudaFree(ix->pcaP);
+    cudaFree(ix->leafPmu);
     cudaFree(ix->chunkOff);
     cudaFree(ix->leafChunk);
     cudaFree(ix->chunkMu);
@@ -690,7 +751,7 @@ void pm_release_work(KnnWork &w)
                       &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen, &w.bandInQ,
                       &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf,
                       &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask,
-                      &w.recheck, &w.leafBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits};
+                      &w.recheck, &w.leafBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
     for (DevBuf *b : bufs) b->release();
 }
 
@@ -900,6 +961,34 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
     PM_TRY(dalloc(&ix->leafRx, (size_t)L));
     PM_LAUNCH("k_leaf_orig", st, k_leaf_orig<<<(unsigned)L, 256, 0, st>>>(ix->X, ix->leafOff, ld, ix->leafMu, ix->leafRx));
     PM_CUDA(cudaGetLastError());
+    // principal directions of the leaf centres: a cheap exact lower bound
+    // ||P (q - mu)|| <= ||q - mu|| for the verification's leaf order
+    {
+        std::vector<float> muH((size_t)L * ld);
+        PM_CUDA(cudaMemcpyAsync(muH.data(), ix->leafMu, muH.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> P;
+        leaf_pca(muH, L, ld, d, ix->seed + 5, P);
+        std::vector<float> pmu((size_t)L * PM_PCA);
+        double muMax = 0.0;
+        for (int64_t l = 0; l < L; l++) {
+            const float *m = muH.data() + (size_t)l * ld;
+            double nn = 0.0;
+            for (int j = 0; j < d; j++) nn += (double)m[j] * m[j];
+            muMax = std::max(muMax, std::sqrt(nn));
+            for (int r = 0; r < PM_PCA; r++) {
+                double s = 0.0;
+                for (int j = 0; j < d; j++) s += P[(size_t)r * ld + j] * (double)m[j];
+                pmu[(size_t)l * PM_PCA + r] = (float)s;
+            }
+        }
+        ix->muMax = muMax;
+        PM_TRY(dalloc(&ix->pcaP, P.size()));
+        PM_TRY(dalloc(&ix->leafPmu, pmu.size()));
+        PM_CUDA(cudaMemcpyAsync(ix->pcaP, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        PM_CUDA(cudaMemcpyAsync(ix->leafPmu, pmu.data(), pmu.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+    }
     // tensor-core operand of the projected points (leaf-padded rows)
     if (o->bf16_shadow) {
         std::vector<int64_t> bo(L + 1, 0);

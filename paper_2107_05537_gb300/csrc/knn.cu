@@ -53,10 +53,15 @@ __device__ __forceinline__ unsigned char leaf_class(const float *q, const float 
     float rr = M[16];
     float ro = __fmul_rn(Rout, hi_f);
     if (__fsub_rn(__fmul_rn(dc, lo_f), rr) > ro) return CL_OUT;
-    for (int i = 0; i < s; i++) {
-        float dq = qpiv[i];
-        if (__fsub_rn(__fmul_rn(dq, lo_f), M[32 + i]) > ro) return CL_OUT;
-        if (__fsub_rn(M[24 + i], __fmul_rn(dq, hi_f)) > ro) return CL_OUT;
+    // unrolled over the largest pivot count, so that a register copy of M
+    // is indexed by constants
+#pragma unroll
+    for (int i = 0; i < PM_MAX_PIVOTS; i++) {
+        if (i < s) {
+            float dq = qpiv[i];
+            if (__fsub_rn(__fmul_rn(dq, lo_f), M[32 + i]) > ro) return CL_OUT;
+            if (__fsub_rn(M[24 + i], __fmul_rn(dq, hi_f)) > ro) return CL_OUT;
+        }
     }
     if (Rin > 0.f && __fadd_rn(__fmul_rn(dc, hi_f), rr) <= __fmul_rn(Rin, lo_f)) return CL_FULL;
     return CL_PART;
@@ -101,6 +106,40 @@ __global__ void k_query_aux(const double *__restrict__ qp64, const float *__rest
     qnorm[q] = sqrt(nn);
     for (int i = 0; i < PM_MAX_PIVOTS; i++)
         qpiv[q * PM_MAX_PIVOTS + i] = i < s ? sqrtf(pm_pd2_32(qp32 + q * PM_MP, piv + i * PM_MP)) : 0.f;
+}
+
+// Query coordinates along the leaf centres' principal directions (FP64
+// sums rounded to FP32) and ||q|| (FP64, rounded up to FP32).  One warp per
+// query.
+__global__ void k_query_pca(const float *__restrict__ Qd, int64_t nq, int ld, const double *__restrict__ P,
+                            float *__restrict__ qpca, float *__restrict__ qnx)
+{
+    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= nq) return;
+    double acc[PM_PCA];
+#pragma unroll
+    for (int r = 0; r < PM_PCA; r++) acc[r] = 0.0;
+    double nn = 0.0;
+    for (int j = lane; j < ld; j += 32) {
+        const double x = (double)Qd[q * ld + j];
+        nn = fma(x, x, nn);
+#pragma unroll
+        for (int r = 0; r < PM_PCA; r++) acc[r] = fma(P[(int64_t)r * ld + j], x, acc[r]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        nn += __shfl_xor_sync(0xffffffffu, nn, o);
+#pragma unroll
+        for (int r = 0; r < PM_PCA; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    }
+    if (lane < PM_PCA) {
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < PM_PCA; r++) v = lane == r ? acc[r] : v;
+        qpca[q * PM_PCA + lane] = (float)v;
+    }
+    if (lane == 0) qnx[q] = __double2float_ru(sqrt(nn));
 }
 
 // Per-round thresholds for the active queries.
@@ -513,7 +552,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t ph)
     return false;
 }
 
-constexpr int VW_MAXWARPS = 16;               // queries in flight per block (one per warp)
+constexpr int VW_MAXWARPS = 8;                // queries in flight per block (one per warp)
+constexpr int VW_MINBLOCKS = 4;               // blocks per SM the register budget allows
 constexpr unsigned VW_FULL = 0xffffffffu;
 
 // Squared FP32 distances ||q - x_v||^2 of up to 32 rows x_v, one per lane
@@ -595,22 +635,26 @@ struct VwArgs {
     float *outD, *outErr;
     double *dk;
     int *fp64cnt, *nverOut, *nleafOut, *errFlag;
-    int *workCtr;   // next active query to take (persistent warps)
+    int *workCtr;   // next entry of `order` to take (persistent warps)
+    const int *order;   // [na] active queries, the costliest first
     int *dbg;       // [3]: site, value, query of the first failed index check
     int64_t n;      // points
     int2 *lists;    // [warps][L]: per-warp candidate leaves {leaf, lower bound bits}
     const uint32_t *leafBits;   // [na][W32]: leaves Eq. 5 does not exclude (k_class)
     int W32;
     const double *O64, *qp64;   // FP64 projected points and queries
+    const float *leafPmu;       // [L][PM_PCA] leaf centres along the principal directions
+    const float *qpca, *qnx;    // [nq][PM_PCA] queries along them, [nq] ||q|| (rounded up)
+    float muMax;                // max ||mu_l|| (rounded up)
     int m;
     int inlineBand;             // 1: decide FP32 band points in FP64 here (no exact count ran)
 };
 
 // Shared memory of one warp: gd[KP] f64, gid[KP] i64, q[ld], vals[KP],
-// idxs[KP], gpos[KP], q'[16], pivot distances[8].
+// idxs[KP], gpos[KP], q'[16], pivot distances[8], P q [PM_PCA].
 __host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP)
 {
-    return (size_t)KP * 28 + (size_t)ld * 4 + 96;
+    return (size_t)KP * 28 + (size_t)ld * 4 + 96 + PM_PCA * 4;
 }
 
 #define VW_CHECK(cond, site, val)                                              \
@@ -638,7 +682,7 @@ __host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP)
 //     value provably contain the exact k nearest; they are recomputed in
 //     FP64 and ranked by (FP64 distance, id).
 // The result equals verifying every candidate.
-__global__ void __launch_bounds__(32 * VW_MAXWARPS, 2)
+__global__ void __launch_bounds__(32 * VW_MAXWARPS, VW_MINBLOCKS)
 k_verify(VwArgs A)
 {
     extern __shared__ __align__(16) unsigned char vsm[];
@@ -654,6 +698,7 @@ k_verify(VwArgs A)
     int *gpos = idxs + KP;
     float *sq = (float *)(gpos + KP);
     float *sp = sq + PM_MP;
+    float *sPq = sp + PM_MAX_PIVOTS;
     const float4 *q4 = (const float4 *)qs;
     int2 *list = A.lists + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * L;
     const double epsv = (double)(ld + 8) * 0x1.0p-24;
@@ -664,6 +709,7 @@ k_verify(VwArgs A)
         if (lane == 0) a = atomicAdd(A.workCtr, 1);
         a = __shfl_sync(VW_FULL, a, 0);
         if (a >= A.na) break;
+        a = A.order[a];
         if (!VW_CHECK(a >= 0, 7, a)) break;
         const int q = A.act[a];
         const Thr T = A.thr[a];
@@ -675,11 +721,13 @@ k_verify(VwArgs A)
         for (int i = lane; i < ld; i += 32) qs[i] = A.Qd[(int64_t)q * ld + i];
         if (lane < PM_MP) sq[lane] = A.qp32[(int64_t)q * PM_MP + lane];
         if (lane < PM_MAX_PIVOTS) sp[lane] = A.qpiv[(int64_t)q * PM_MAX_PIVOTS + lane];
+        if (lane < PM_PCA) sPq[lane] = A.qpca[(int64_t)q * PM_PCA + lane];
         for (int e = lane; e < KP; e += 32) {
             vals[e] = INFINITY;
             idxs[e] = 0x7fffffff;
         }
         __syncwarp();
+        auto D2 = [&](const float *p) -> float { return warp_d2(q4, p, nf4, lane); };
         // top-KP state: lane owns slots lane, lane + 32, ...; cmax is the
         // largest entry (the KP-th smallest so far), cslot its slot
         float cmax = INFINITY, myMax = INFINITY;
@@ -729,7 +777,7 @@ k_verify(VwArgs A)
             for (int c0 = cb; c0 < ce; c0 += 32) {
                 const int c = c0 + lane;
                 const bool vc = c < ce;
-                const float d2c = warp_d2(q4, vc ? A.chunkMu + (int64_t)c * ld : nullptr, nf4, lane);
+                const float d2c = D2(vc ? A.chunkMu + (int64_t)c * ld : nullptr);
                 const float lbc = vc ? __fsub_rn(__fmul_rn(__fsqrt_rn(d2c), lbSlack), A.chunkRx[c]) : INFINITY;
                 unsigned alive = __ballot_sync(VW_FULL, vc && !pruned(lbc));
                 while (alive) {
@@ -755,7 +803,7 @@ k_verify(VwArgs A)
                         }
                     }
                     if (__ballot_sync(VW_FULL, cand) == 0u) continue;
-                    const float d2 = warp_d2(q4, cand ? A.X + (r0 + lane) * ld : nullptr, nf4, lane);
+                    const float d2 = D2(cand ? A.X + (r0 + lane) * ld : nullptr);
                     seen += __popc(__ballot_sync(VW_FULL, cand));
                     offer(cand, d2, (int)(r0 + lane));
                 }
@@ -788,14 +836,37 @@ k_verify(VwArgs A)
             }
         }
         __syncwarp();
+        // cheap bounds first: ||P q - P mu|| <= ||q - mu|| for the
+        // orthonormal rows P (FP32 roundings of P q, P mu and the sum covered
+        // by the slack); an entry {-(l + 1), bound} holds a cheap bound,
+        // {l, bound} the full one
+        const float pSlack = __fmul_rn(0x1.0p-20f, __fadd_rn(A.qnx[q], A.muMax));
         for (int e0 = 0; e0 < cnt; e0 += 32) {
             const int e = e0 + lane;
-            const int l = e < cnt ? list[e].x : -1;
-            const float d2 = warp_d2(q4, l >= 0 ? A.leafMu + (int64_t)l * ld : nullptr, nf4, lane);
-            if (l >= 0) list[e].y = __float_as_int(__fsub_rn(__fmul_rn(__fsqrt_rn(d2), lbSlack), A.leafRx[l]));
+            if (e < cnt) {
+                const int l = list[e].x;
+                const float4 *pm4 = (const float4 *)(A.leafPmu + (int64_t)l * PM_PCA);
+                float s2 = 0.f;
+#pragma unroll
+                for (int r4 = 0; r4 < PM_PCA / 4; r4++) {
+                    const float4 pmv = __ldg(pm4 + r4);
+                    float u = __fsub_rn(sPq[4 * r4], pmv.x);
+                    s2 = __fmaf_rn(u, u, s2);
+                    u = __fsub_rn(sPq[4 * r4 + 1], pmv.y);
+                    s2 = __fmaf_rn(u, u, s2);
+                    u = __fsub_rn(sPq[4 * r4 + 2], pmv.z);
+                    s2 = __fmaf_rn(u, u, s2);
+                    u = __fsub_rn(sPq[4 * r4 + 3], pmv.w);
+                    s2 = __fmaf_rn(u, u, s2);
+                }
+                const float lbp = __fsub_rn(__fsub_rn(__fmul_rn(__fsqrt_rn(s2), 1.f - 0x1.0p-18f), pSlack), A.leafRx[l]);
+                list[e] = make_int2(-l - 1, __float_as_int(lbp));
+            }
         }
         __syncwarp();
-        // 2. best first over the listed leaves
+        // 2. best first over the listed leaves: an entry with a cheap bound
+        // gets its full bound (original-space leaf ball) when it comes first
+        // and goes back on the list; one with the full bound is visited
         for (;;) {
             float bl = INFINITY;
             int be = 0x7fffffff;
@@ -809,12 +880,58 @@ k_verify(VwArgs A)
                 if (ob < bl || (ob == bl && oe < be)) { bl = ob; be = oe; }
             }
             if (be == 0x7fffffff || pruned(bl)) break;
-            const int l = list[be].x;
+            const int x = list[be].x;
             __syncwarp();
+            if (x < 0) {
+                // the first entry has a cheap bound: full bounds for it and up
+                // to 31 more cheap entries with bounds near it, in one pass
+                const float lim = fmaxf(bl, 0.f) + 16.f;
+                int ref = -1, nb = 0;   // lane i refines entry ref (slot i)
+                for (int e0 = 0; e0 < cnt && nb < 32; e0 += 32) {
+                    const int e = e0 + lane;
+                    bool pick = false;
+                    if (e < cnt) {
+                        const int2 v = list[e];
+                        pick = v.x < 0 && (e == be || __int_as_float(v.y) <= lim);
+                    }
+                    const unsigned m = __ballot_sync(VW_FULL, pick);
+                    if (lane >= nb && lane < nb + __popc(m)) ref = e0 + (int)__fns(m, 0, lane - nb + 1);
+                    nb = min(32, nb + __popc(m));
+                }
+                // the first entry itself, if 32 earlier ones crowded it out
+                if (__ballot_sync(VW_FULL, ref == be) == 0u && lane == 31) ref = be;
+                int lr = ref >= 0 ? -list[ref].x - 1 : -1;
+                if (__any_sync(VW_FULL, ref >= 0 && !(lr >= 0 && lr < L))) {
+                    if (ref >= 0 && !(lr >= 0 && lr < L)) VW_CHECK(false, 10, lr);
+                    break;
+                }
+                const float d2 = D2(ref >= 0 ? A.leafMu + (int64_t)lr * ld : nullptr);
+                __syncwarp();
+                if (ref >= 0)
+                    list[ref] = make_int2(lr, __float_as_int(__fsub_rn(__fmul_rn(__fsqrt_rn(d2), lbSlack), A.leafRx[lr])));
+                __syncwarp();
+                continue;
+            }
             if (lane == 0) list[be].y = __float_as_int(INFINITY);
             __syncwarp();
-            if (!VW_CHECK(l >= 0 && l < L, 1, l)) break;
-            visit(l);
+            if (!VW_CHECK(x < L, 1, x)) break;
+            visit(x);
+            // drop the entries whose bound the tighter K now excludes
+            if (cnt > 96 && cmax < INFINITY) {
+                int kept = 0;
+                for (int e0 = 0; e0 < cnt; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int2 v = e < cnt ? list[e] : make_int2(0, __float_as_int(INFINITY));
+                    const float lb = __int_as_float(v.y);
+                    const bool keep = e < cnt && lb < INFINITY && !pruned(lb);
+                    const unsigned m = __ballot_sync(VW_FULL, keep);
+                    __syncwarp();
+                    if (keep) list[kept + __popc(m & ((1u << lane) - 1u))] = v;
+                    kept += __popc(m);
+                }
+                cnt = kept;
+                __syncwarp();
+            }
         }
         // band-in points (FP64-resolved members just inside the radius)
         const int nIn = min(A.inN[a], BCAP);
@@ -823,7 +940,7 @@ k_verify(VwArgs A)
             int pos = e < nIn ? A.inPos[(int64_t)a * BCAP + e] : -1;
             if (e < nIn && !VW_CHECK(pos >= 0 && pos < A.n, 4, pos)) pos = -1;
             const bool cand = pos >= 0;
-            const float d2 = warp_d2(q4, cand ? A.X + (int64_t)pos * ld : nullptr, nf4, lane);
+            const float d2 = D2(cand ? A.X + (int64_t)pos * ld : nullptr);
             seen += __popc(__ballot_sync(VW_FULL, cand));
             offer(cand, d2, pos);
         }
@@ -1550,6 +1667,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     float *qpiv = grow<float>(w.qpiv, (size_t)nq * PM_MAX_PIVOTS, s);
     unsigned int *key = grow<unsigned int>(w.keys, nq, s);
     int32_t *order = grow<int32_t>(w.order, nq, s);
+    float *qpca = grow<float>(w.qpca, (size_t)nq * (PM_PCA + 1), s);
+    float *qnx = qpca + (size_t)nq * PM_PCA;
     int *hist = grow<int>(w.keys2, L + 1, s);
     double *rq = grow<double>(w.qstate, nq, s);
     int64_t *oIds = grow<int64_t>(w.outIds, (size_t)nq * k, s);
@@ -1559,6 +1678,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     PM_TRY(pm_project_rows(ix, Q, nq, Qd, qp64, qp32, PM_MP, st));
     const unsigned gq = (unsigned)((nq + 255) / 256);
     PM_LAUNCH("k_query_aux", st, k_query_aux<<<gq, 256, 0, st>>>(qp64, qp32, nq, ix->piv32, ix->s, qnorm, qpiv));
+    PM_LAUNCH("k_query_pca", st, k_query_pca<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(Qd, nq, ld, ix->pcaP,
+                                                                                              qpca, qnx));
     PM_LAUNCH("k_leaf_key", st, k_leaf_key<<<gq, 256, 0, st>>>(qp32, nq, ix->treeI, ix->treeV, key));
     PM_CUDA(cudaMemsetAsync(hist, 0, (L + 1) * sizeof(int), st));
     PM_LAUNCH("k_hist", st, k_hist<<<gq, 256, 0, st>>>(key, nq, hist));
@@ -1822,8 +1943,27 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                           qnorm, ix->O64, qp64, m, ix->perm, inN, inPos, fpc, errFlag));
             PM_CUDA(cudaGetLastError());
         }
-        // verification: best-first over candidate leaves, guard set, FP64
-        int *nverD = grow<int>(w.partSeen, (size_t)2 * na + 8, s);
+        // verification: best-first over candidate leaves, guard set, FP64.
+        // Work order: the queries with the most range candidates (their
+        // upper bound) first, so that the long ones do not finish last;
+        // locality order inside each of 32 logarithmic cost classes.
+        int *nverD = grow<int>(w.partSeen, (size_t)3 * na + 8, s);
+        int *vOrder = nverD + 2 * na + 8;
+        {
+            std::vector<int32_t> cls(na);
+            int64_t hist[33] = {0};
+            for (int a = 0; a < na; a++) {
+                const int64_t c = (int64_t)hs[a] + hb[a] + 1;
+                int b = 0;
+                while (b < 31 && (c >> (b + 1)) > 0) b++;
+                cls[a] = 31 - b;   // costliest class first
+                hist[cls[a] + 1]++;
+            }
+            for (int b = 0; b < 32; b++) hist[b + 1] += hist[b];
+            std::vector<int32_t> ord(na);
+            for (int a = 0; a < na; a++) ord[hist[cls[a]]++] = a;
+            PM_CUDA(cudaMemcpyAsync(vOrder, ord.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
         const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, vPerSM * nsm));
         int2 *vLists = grow<int2>(w.partD, (size_t)vGrid * vWarps * L, s);
         if (s != PMLSH_OK) return s;
@@ -1837,8 +1977,11 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             va.inN = inN; va.inPos = inPos; va.perm = ix->perm; va.outIds = oIds; va.outD = oD; va.outErr = oE;
             va.dk = dk; va.fp64cnt = fpc; va.nverOut = nverD; va.nleafOut = nverD + na; va.errFlag = errFlag;
             va.workCtr = nverD + 2 * na; va.dbg = nverD + 2 * na + 1; va.n = n; va.lists = vLists;
+            va.order = vOrder;
             va.leafBits = leafBits; va.W32 = W32;
             va.O64 = ix->O64; va.qp64 = qp64; va.m = m; va.inlineBand = needExact ? 0 : 1;
+            va.leafPmu = ix->leafPmu; va.qpca = qpca; va.qnx = qnx;
+            va.muMax = (float)(ix->muMax * (1.0 + 1e-6)) + 1e-30f;
             PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());

@@ -18,6 +18,7 @@
 #define PM_LEAF_STRIDE 40
 #define PM_MAX_PIVOTS 8
 #define PM_MAX_K 256
+#define PM_PCA 16
 
 // Thread-local error reporting.
 void pm_set_error(const char *fmt, ...);
@@ -60,7 +61,7 @@ struct KnnWork {
         bandIn, bandCnt;
     DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
     DevBuf selBuf, selOff, selCnt, selTau;
-    DevBuf active, misc, recheck, leafBits, cntPart, subIdx, subThr, subBits;
+    DevBuf active, misc, recheck, leafBits, cntPart, subIdx, subThr, subBits, qpca;
 };
 
 struct pmlsh_index {
@@ -80,6 +81,11 @@ struct pmlsh_index {
     float *piv32 = nullptr;      // [PM_MAX_PIVOTS][16]
     float *leafMu = nullptr;     // [L][ld] original-space leaf centre (FP32)
     float *leafRx = nullptr;     // [L] radius around leafMu (rounded up)
+    // principal directions of the leaf centres (orthonormal rows) and the
+    // centres' coordinates along them: ||P q - P mu|| <= ||q - mu||
+    double *pcaP = nullptr;      // [PM_PCA][ld] FP64
+    float *leafPmu = nullptr;    // [L][PM_PCA] P mu (FP64 rounded to FP32)
+    double muMax = 0.0;          // max ||mu_l|| (FP64)
     // chunks: consecutive runs of <= 32 points inside a leaf, with their own
     // original-space balls
     int64_t nChunks = 0;
