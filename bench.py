@@ -198,14 +198,20 @@ def source_sha(rel):
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def timed_steps(step, steps, flush, stream):
-    """K steps, L2 flushed before each, CUDA events on the launch stream."""
+def timed_steps(step, steps, flush, stream, tag):
+    """K steps, L2 flushed before each, CUDA events on the launch stream.
+    The steps run inside the NVTX range `tag` (a profiler can select them)."""
     import torch
     import paper_2107_05537_gb300 as pm
     pm.profile(True)
     pm.profile_read()
     launches0 = pm.launch_count()
     total_ms, res = 0.0, None
+    try:
+        torch.cuda.nvtx.range_push(tag)
+        nvtx = True
+    except Exception:
+        nvtx = False
     for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -216,6 +222,8 @@ def timed_steps(step, steps, flush, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     launches = pm.launch_count() - launches0
     prof = pm.profile_read()
     pm.profile(False)
@@ -314,7 +322,7 @@ def main():
         sampler.start()
     barrier(ws)
     torch.cuda.synchronize()
-    total_ms, res, prof, launches = timed_steps(step, args.steps, flush, stream)
+    total_ms, res, prof, launches = timed_steps(step, args.steps, flush, stream, "timed_main")
     barrier(ws)
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
@@ -327,7 +335,7 @@ def main():
     # trace, the verified rows behind the roofline, and its own speed
     sstep = make_step(prec, with_stats=True)
     sstep()
-    sms, sres, _, _ = timed_steps(sstep, args.steps, flush, stream)
+    sms, sres, _, _ = timed_steps(sstep, args.steps, flush, stream, "timed_stats")
     stats = sres["stats"]
     nver = int(stats["nver"].sum()) * args.steps
     with_stats = {"value": nq * args.steps * ws / max_over_ranks(sms / 1000.0, ws),
@@ -343,7 +351,7 @@ def main():
             ostep()
         torch.cuda.synchronize()
         barrier(ws)
-        oms, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream)
+        oms, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream, "timed_other")
         barrier(ws)
         os_ = max_over_ranks(oms / 1000.0, ws)
         other = {"precision": "fp32" if op == pm.PMLSH_FP32_PLAIN else "bf16",
