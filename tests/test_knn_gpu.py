@@ -370,3 +370,31 @@ def test_no_stats_path_sub_batch_of_straddling_queries(c1):
         if "k_count" not in prof and "k_count_tc" not in prof:
             seen_none.append((beta, rmin))
     assert seen_sub and seen_none, (seen_sub, seen_none)
+
+
+@pytest.mark.slow
+def test_c3_full_size_sampled_parity():
+    # high-dimensional workload: n = 10^6, d = 960, anisotropic clusters;
+    # all 1,000 queries on the GPU for three (c, k) settings, a query sample
+    # against the oracle, and the statistics-free path against the full one
+    w = datagen.workload("c3")
+    X, Q = w["X"], w["Q"]
+    A = oracle.gen_projection(2, 15, X.shape[1]).astype(np.float32)
+    ix = pm.Index(torch.from_numpy(X).cuda(), proj=A, leaf_size=256)
+    torch.cuda.synchronize()
+    Qd = torch.from_numpy(Q).cuda()
+    O = oracle.project(X, A)
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(len(Q), size=12, replace=False))
+    for c, k in ((1.2, 1), (1.5, 10), (2.0, 100)):
+        got = ix.knn(Qd, k=k, c=c, beta=0.2809, precision=TENSOR)
+        fast = ix.knn(Qd, k=k, c=c, beta=0.2809, with_stats=False)
+        torch.cuda.synchronize()
+        assert torch.equal(got["ids"], fast["ids"]) and torch.equal(got["dists"], fast["dists"])
+        t, _, _ = oracle.params(15, c, 1 / E)
+        ref = oracle.knn(X, A, Q[sample], k, c, t, oracle.budget(len(X), 0.2809, k),
+                         oracle.rmin_auto(X, 0.2809, k, c, 3), 0, Oproj=O)
+        sub = dict(ids=got["ids"][sample], dists=got["dists"][sample], err=got["err"][sample],
+                   stats={k2: v[sample] for k2, v in got["stats"].items()})
+        _assert_parity(sub, ref)
+    ix.close()

@@ -115,3 +115,51 @@ def test_invalid_requests_rejected(served):
     with pytest.raises(pm.PmlshError):
         srv.wait(123456)
     srv.close()
+
+
+@pytest.mark.slow
+def test_c5_serving_full_size():
+    # serving workload: n = 2*10^6, d = 256 resident; an open-loop stream of
+    # requests of log-uniform size in [1, 4096] with k in {1, 10, 100} from
+    # four client threads; every result equals pmlsh_knn on that request
+    # alone, and a query sample equals the oracle's
+    import time
+    import oracle
+    w = datagen.workload("c5")
+    X, Q = w["X"], w["Q"]
+    ix = pm.Index(torch.from_numpy(X).cuda(), leaf_size=256)
+    rng = np.random.default_rng(7)
+    reqs = []
+    for _ in range(40):
+        size = int(np.exp(rng.uniform(0.0, math.log(4096.0))))
+        q0 = int(rng.integers(0, len(Q) - size + 1))
+        reqs.append((np.ascontiguousarray(Q[q0:q0 + size]), int(rng.choice([1, 10, 100]))))
+    srv = pm.Server(ix, slots=3)
+    tickets = [None] * len(reqs)
+
+    def client(part):
+        for i in range(part, len(reqs), 4):
+            time.sleep(0.002)
+            tickets[i] = srv.submit(reqs[i][0], k=reqs[i][1], precision=pm.PMLSH_BF16_TENSOR)
+    threads = [threading.Thread(target=client, args=(p,)) for p in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    outs = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+    for (rows, k), (ids, dd) in zip(reqs, outs):
+        alone = ix.knn(rows, k=k, with_stats=False)
+        assert np.array_equal(ids, alone["ids"]) and np.array_equal(dd, alone["dists"])
+    # a sample of the requests' queries against the oracle
+    A = ix.projection()
+    rows, k = reqs[0]
+    sel = rows[:4]
+    t, _, _ = oracle.params(15, 1.5, 1 / math.e)
+    ref = oracle.knn(X, A, sel, k, 1.5, t, oracle.budget(len(X), 0.2809, k),
+                     oracle.rmin_auto(X, 0.2809, k, 1.5, 3), 0)
+    assert np.array_equal(outs[0][0][:4], ref["ids"])
+    assert np.array_equal(outs[0][1][:4], ref["dists"].astype(np.float32))
+    ix.close()
