@@ -220,6 +220,22 @@ pmlsh_status pmlsh_knn(pmlsh_index *index, const float *Q, int64_t nq,
                        float *out_dists, float *out_err,
                        pmlsh_query_stats *stats, void *stream);
 
+/* Algorithm 1, the (r,c)-BC query (Sec. 5.1), for nq queries Q [nq][d]
+ * (FP32, host or device) at one radius r > 0.  Per query, C is the closed
+ * range set {o : ||o',q'|| <= t r} (no budget cut); if |C| >= beta n + 1
+ * (as an integer: pmlsh_budget(n, beta, 1)) or the point of C nearest to q
+ * lies within c r, that point is returned, else nothing (id -1, distance
+ * +inf).  From `opts` the call uses c, alpha1 (or t), beta and precision;
+ * k, r_min and stop_rule are ignored.  Outputs (host or device): out_ids
+ * [nq] int64 original ids, out_dists [nq] FP32 (the FP64 distance rounded),
+ * stats [nq] or NULL (rounds = 1, stop_rule 2: |C| >= beta n + 1, 1: within
+ * c r, 0: nothing; n_cand = |C|).  Ties by smaller id.  Errors: EINVAL (NULL
+ * pointers, r <= 0, options as pmlsh_knn), ENOMEM, ECUDA, EINTERNAL. */
+pmlsh_status pmlsh_rcbc(pmlsh_index *index, const float *Q, int64_t nq,
+                        double r, const pmlsh_knn_opts *opts, int64_t *out_ids,
+                        float *out_dists, pmlsh_query_stats *stats,
+                        void *stream);
+
 /* ---------------------------------------------------- (c,k)-ACP query */
 
 typedef struct {

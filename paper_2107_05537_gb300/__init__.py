@@ -96,6 +96,7 @@ _SIGS = {
     "pmlsh_project_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_knn_opts_default": (None, [_P]),
     "pmlsh_knn": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_rcbc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P, _P]),
     "pmlsh_cp_opts_default": (None, [_P]),
     "pmlsh_closest_pair": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pmlsh_serve_opts_default": (None, [_P]),
@@ -285,6 +286,29 @@ class Index:
                                         _stream()))
         return dict(pairs=pairs, dists=dists,
                     stats={f: getattr(st, f) for f, _ in CpStats._fields_})
+
+    def rcbc(self, Q, r, c=1.5, alpha1=1 / math.e, beta=0.2809, precision=PMLSH_FP32_PLAIN, t=0.0,
+             with_stats=True):
+        """Algorithm 1 ((r,c)-BC) at radius r.  Returns dict(ids [nq] int64,
+        dists [nq] f32, stats) in numpy (host) form; -1 / inf for "nothing"."""
+        qa, qp = _as_f32(Q)
+        nq = int(qa.shape[0])
+        o = KnnOpts()
+        lib().pmlsh_knn_opts_default(ctypes.byref(o))
+        o.c, o.alpha1, o.beta, o.precision, o.t = c, alpha1, beta, precision, t
+        ids = np.empty(nq, dtype=np.int64)
+        dists = np.empty(nq, dtype=np.float32)
+        stats = (QueryStats * max(1, nq))() if with_stats else None
+        _check(lib().pmlsh_rcbc(self._h, qp, nq, float(r), ctypes.byref(o),
+                                ids.ctypes.data_as(ctypes.c_void_p), dists.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.cast(stats, ctypes.c_void_p) if stats is not None else None,
+                                _stream()))
+        res = dict(ids=ids, dists=dists)
+        if with_stats:
+            sv = np.frombuffer(stats, dtype=_QSTATS_DT, count=nq) if nq else np.zeros(0, _QSTATS_DT)
+            res["stats"] = dict(rule=sv["stop_rule"].copy(), ncand=sv["n_cand"].copy(),
+                                rounds=sv["rounds"].copy())
+        return res
 
     def knn(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
             precision=PMLSH_FP32_PLAIN, stop_rule=STOP_LITERAL, t=0.0, out=None,

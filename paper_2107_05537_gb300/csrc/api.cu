@@ -233,6 +233,30 @@ pmlsh_status pmlsh_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_
     return pm_knn(ix, Q, nq, &o, out_ids, out_dists, out_err, stats, (cudaStream_t)stream);
 }
 
+pmlsh_status pmlsh_rcbc(pmlsh_index *ix, const float *Q, int64_t nq, double r, const pmlsh_knn_opts *opts,
+                        int64_t *out_ids, float *out_dists, pmlsh_query_stats *stats, void *stream)
+{
+    PM_CHECK(ix != nullptr, "index is NULL");
+    PM_CHECK(opts != nullptr, "opts is NULL");
+    PM_CHECK(nq >= 0, "nq must be >= 0");
+    if (nq == 0) return PMLSH_OK;
+    PM_CHECK(Q && out_ids && out_dists, "NULL argument");
+    PM_CHECK(r > 0.0 && std::isfinite(r), "r must be > 0 and finite (got %g)", r);
+    pmlsh_knn_opts o = *opts;
+    PM_CHECK(o.c > 1.0 && std::isfinite(o.c), "c must be > 1 (got %g)", o.c);
+    PM_CHECK(o.alpha1 > 0.0 && o.alpha1 < 1.0, "alpha1 must be in (0,1)");
+    PM_CHECK(o.beta > 0.0 && o.beta <= 1.0, "beta must be in (0,1]");
+    PM_CHECK(std::isfinite(o.t), "t must be finite");
+    PM_CHECK(o.precision == PMLSH_FP32_PLAIN || o.precision == PMLSH_BF16_TENSOR,
+             "unknown precision mode %d", o.precision);
+    PM_CHECK(o.precision != PMLSH_BF16_TENSOR || ix->Bsplit != nullptr,
+             "PMLSH_BF16_TENSOR needs an index built with bf16_shadow = 1");
+    o.k = 1;
+    o.r_min = r;
+    o.stop_rule = PMLSH_STOP_LITERAL;
+    return pm_knn(ix, Q, nq, &o, out_ids, out_dists, nullptr, stats, (cudaStream_t)stream, nullptr, true);
+}
+
 void pmlsh_cp_opts_default(pmlsh_cp_opts *o)
 {
     if (!o) return;

@@ -1557,6 +1557,20 @@ __global__ void k_recheck(const int *__restrict__ recheckN, int recheckCap, cons
     }
 }
 
+// Empties the results of the listed queries (-1, +inf, 0).
+__global__ void k_clear_results(const int32_t *__restrict__ qs, int nn, int k, int64_t *__restrict__ ids,
+                                float *__restrict__ dd, float *__restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    for (int e = 0; e < k; e++) {
+        const int64_t o = (int64_t)qs[i] * k + e;
+        ids[o] = -1;
+        dd[o] = INFINITY;
+        err[o] = 0.f;
+    }
+}
+
 // Sub-batch of the active queries (the ones whose exact range count is
 // needed): their query ids and round thresholds.
 __global__ void k_gather_sub(const int *__restrict__ idx, int n2, const int32_t *__restrict__ act,
@@ -1630,7 +1644,7 @@ pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, 
 
 pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn_opts *o,
                     int64_t *ids, float *dists, float *err, pmlsh_query_stats *stats,
-                    cudaStream_t st, KnnWork *work)
+                    cudaStream_t st, KnnWork *work, bool rcbc)
 {
     const int64_t n = ix->n;
     const int d = ix->d, ld = ix->ld, m = ix->m, k = o->k;
@@ -1638,7 +1652,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     KnnWork &w = work ? *work : ix->work;
     // parameters (Eq. 9; budget of Algorithm 2; r_min rule of Sec. 5.2)
     const double t = o->t > 0.0 ? o->t : std::sqrt(pm_chi2_upper_quantile(o->alpha1, m));
-    const int64_t B = pmlsh_budget(n, o->beta, k);
+    // Algorithm 2: |C| >= beta n + k; Algorithm 1: |C| >= beta n + 1
+    const int64_t B = pmlsh_budget(n, o->beta, rcbc ? 1 : k);
     double rmin = o->r_min;
     if (!(rmin > 0.0)) {
         const std::vector<double> &v = ix->distSample;
@@ -1915,7 +1930,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         int64_t selTotal = 0;
         for (int a = 0; a < na; a++) {
             count[a] = (int64_t)hs[a] + hin[a];
-            if (count[a] >= B) {
+            if (count[a] >= B && !rcbc) {   // Algorithm 1 keeps the whole range set
                 selH.push_back(a);
                 selOffH.push_back(selTotal);
                 selTotal += (int64_t)hs[a] + hb[a];
@@ -2011,6 +2026,14 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             const bool budget = count[a] >= B;
             nver[q] += nvH[a];
             nleaf[q] += nlH[a];
+            if (rcbc) {
+                // Algorithm 1: the nearest candidate if |C| >= beta n + 1 or it
+                // lies within c r, else nothing
+                done[q] = 1;
+                ncand[q] = count[a];
+                rule[q] = budget ? 2 : (dkH[a] <= o->c * r[q] ? 1 : 0);
+                continue;
+            }
             if (budget) { done[q] = 1; rule[q] = 2; ncand[q] = B; continue; }
             ncand[q] = count[a];
             if (count[a] == n) { done[q] = 1; rule[q] = 3; continue; }
@@ -2029,6 +2052,19 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         if (round == 99999) {
             pm_set_error("Algorithm 2 did not stop within 100000 rounds");
             return PMLSH_EINTERNAL;
+        }
+    }
+    if (rcbc) {
+        // queries whose answer is "nothing": -1 / +inf
+        std::vector<int32_t> none;
+        for (int64_t q = 0; q < nq; q++)
+            if (rule[q] == 0) none.push_back((int32_t)q);
+        if (!none.empty()) {
+            int32_t *noneD = grow<int32_t>(w.keys, none.size(), s);
+            if (s != PMLSH_OK) return s;
+            PM_CUDA(cudaMemcpyAsync(noneD, none.data(), none.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            PM_LAUNCH("k_clear_results", st, k_clear_results<<<(unsigned)((none.size() + 255) / 256), 256, 0, st>>>(
+                                                  noneD, (int)none.size(), k, oIds, oD, oE));
         }
     }
     // results

@@ -140,10 +140,14 @@ pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, 
 // `work`: scratch buffers for this call (NULL: the index's own); calls on
 // one index may run concurrently on different streams with different
 // workspaces (the index itself is read-only during queries).
+// `rcbc`: Algorithm 1 instead of Algorithm 2: one round at r = o->r_min
+// with k = 1, no budget cut of the range set, the budget beta n + 1; the
+// nearest candidate is kept if |C| >= beta n + 1 or it lies within c r,
+// else the result is -1 / +inf (stats: stop_rule 2, 1 or 0).
 pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq,
                     const pmlsh_knn_opts *o, int64_t *ids, float *dists,
                     float *err, pmlsh_query_stats *stats, cudaStream_t st,
-                    KnnWork *work = nullptr);
+                    KnnWork *work = nullptr, bool rcbc = false);
 void pm_release_work(KnnWork &w);
 
 // Closest pairs (cp.cu)
