@@ -593,6 +593,32 @@ __device__ __forceinline__ float warp_d2(const float4 *__restrict__ q4, const fl
     return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
 }
 
+// FP32 -> FP64 re-encoded with integer operations (exact, equal to the
+// conversion instruction), so that the widening does not occupy the FP64
+// pipe; zeros are re-encoded too, subnormals, infinities and NaNs use the
+// conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+// pm_dist64 (FP64 sequential sum of (x_i - y_i)^2, separate multiply and
+// add, correctly rounded sqrt) with the inputs widened by f2d_exact.
+__device__ __forceinline__ double dist64_widen(const float *x, const float *y, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; i++) {
+        const double t = __dsub_rn(f2d_exact(x[i]), f2d_exact(y[i]));
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return __dsqrt_rn(s);
+}
+
 // FP32 d'^2 of one projected row against q' (the arithmetic of pm_pd2_32:
 // sequential over the 16 coordinates, row minus query), float4 loads.
 __device__ __forceinline__ float pd2_row(const float *__restrict__ o, const float *__restrict__ qv)
@@ -702,7 +728,10 @@ k_verify(VwArgs A)
     const float4 *q4 = (const float4 *)qs;
     int2 *list = A.lists + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * L;
     const double epsv = (double)(ld + 8) * 0x1.0p-24;
-    const double lbMul = 1.0 - epsv, cutMul = 1.0 + 3.0 * epsv;
+    // the bound test in FP32 with directed rounding: lb^2 (1 - eps_v) rounded
+    // down against K (1 + 3 eps_v) rounded up, so it prunes only what the
+    // exact test prunes
+    const float lbMulF = __double2float_rd(1.0 - epsv), cutMulF = __double2float_ru(1.0 + 3.0 * epsv);
     const float lbSlack = 1.f - (float)((ld + 8) * 0x1.0p-24) - 1e-6f;
     for (;;) {
         int a = 0;
@@ -734,7 +763,7 @@ k_verify(VwArgs A)
         int cslot = 0, mySlot = lane;
         int seen = 0, leaves = 0;
         auto pruned = [&](float lb) -> bool {
-            return lb > 0.f && (double)lb * lb * lbMul > (double)cmax * cutMul;
+            return lb > 0.f && __fmul_rd(__fmul_rd(lb, lb), lbMulF) > __fmul_ru(cmax, cutMulF);
         };
         // offers the lanes' values (cand) to the top-KP, in lane order
         auto offer = [&](bool cand, float v, int pos) {
@@ -779,14 +808,15 @@ k_verify(VwArgs A)
                 const bool vc = c < ce;
                 const float d2c = D2(vc ? A.chunkMu + (int64_t)c * ld : nullptr);
                 const float lbc = vc ? __fsub_rn(__fmul_rn(__fsqrt_rn(d2c), lbSlack), A.chunkRx[c]) : INFINITY;
+                // the chunks' row ranges, one chunk per lane
+                const long long cOff = vc ? A.chunkOff[c] : 0, cEnd = vc ? A.chunkOff[c + 1] : 0;
                 unsigned alive = __ballot_sync(VW_FULL, vc && !pruned(lbc));
                 while (alive) {
                     const int src = __ffs(alive) - 1;
                     alive &= alive - 1;
                     if (pruned(__shfl_sync(VW_FULL, lbc, src))) continue;   // K fell since
-                    const int ci = c0 + src;
-                    const int64_t r0 = A.chunkOff[ci];
-                    int rows = (int)(A.chunkOff[ci + 1] - r0);
+                    const int64_t r0 = __shfl_sync(VW_FULL, cOff, src);
+                    int rows = (int)(__shfl_sync(VW_FULL, cEnd, src) - r0);
                     if (!VW_CHECK(rows >= 1 && rows <= 32 && r0 >= 0 && r0 + rows <= A.n, 2, rows)) rows = 0;
                     bool cand = false;
                     if (lane < rows) {
@@ -981,7 +1011,7 @@ k_verify(VwArgs A)
         for (int e = lane; e < G; e += 32) {
             const int p = gpos[e];
             if (VW_CHECK(p >= 0 && p < A.n, 5, p)) {
-                gd[e] = pm_dist64(A.X + (int64_t)p * ld, qs, A.d);
+                gd[e] = dist64_widen(A.X + (int64_t)p * ld, qs, A.d);
                 gid[e] = A.perm[p];
             } else {
                 gd[e] = INFINITY;
