@@ -38,7 +38,7 @@ def workload_desc(nq):
     return ("c-ANN, n=1,000,000 d=128 FP32, Gaussian mixture of 1,000 clusters "
             "(centres N(0,100 I), sigma U[0.5,2]), %d queries from the same mixture, "
             "m=15, c=1.5, k=50, beta=0.2809, alpha1=1/e, r_min by the Sec. 5.2 rule, "
-            "seed 0" % nq)
+            "leaf size autotuned, seed 0" % nq)
 
 
 def dist_setup():
@@ -273,6 +273,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--leaf-size", type=int, default=0, help="leaf capacity M; 0 = autotuned by pmlsh_build")
     ap.add_argument("--ref-queries", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -294,7 +295,7 @@ def main():
     nq, d = Q.shape
     Xd = torch.from_numpy(X).cuda()
     t0 = time.perf_counter()
-    ix = pm.Index(Xd, m=M_PROJ, leaf_size=256, seed=0)
+    ix = pm.Index(Xd, m=M_PROJ, leaf_size=args.leaf_size, seed=0)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     del Xd
@@ -438,6 +439,8 @@ def main():
                 "ms_per_step": total_s * 1000 / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_desc(nq), "precision": args.precision,
+                           "leaf_size": ix.leaf_size,
+                           "leaf_size_choice": "autotuned over 128/256/512" if args.leaf_size == 0 else "fixed",
                            "l2": "flushed between steps (512 MB write)",
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "gpu_launches": launches,

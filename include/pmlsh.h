@@ -69,7 +69,12 @@ int64_t pmlsh_budget(int64_t n, double beta, int64_t k);
 typedef struct {
     int m;              /* number of projections (Eq. 3), 1..16; default 15 */
     int s;              /* number of global pivots (Sec. 4.1), 0..8; default 5 */
-    int leaf_size;      /* leaf capacity M (points per leaf); 0 = default 256 */
+    int leaf_size;      /* leaf capacity M (points per leaf), 16..1024;
+                           default 256; 0 = autotuned: the index is built
+                           for M = 128, 256 and 512, pmlsh_knn with the
+                           default options is timed on up to 1,024 rows of X
+                           (an even stride) as queries, and the fastest index
+                           is kept (pmlsh_index_info reports its M) */
     int cp_leaf_size;   /* unused by pmlsh_build; see pmlsh_cp_opts */
     uint64_t seed;      /* the projection uses stream seed+2 of the
                            counter-based SplitMix64 generator with the

@@ -114,24 +114,12 @@ void pmlsh_knn_opts_default(pmlsh_knn_opts *o)
     o->stop_rule = PMLSH_STOP_LITERAL;
 }
 
-pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opts *opts, void *stream,
-                         pmlsh_index **out)
+namespace {
+
+// One index over X with the options as given (leaf_size 16..1024).
+pmlsh_status build_one(const float *X, int64_t n, int d, const pmlsh_build_opts &o, cudaStream_t st,
+                       pmlsh_index **out)
 {
-    PM_CHECK(out != nullptr, "out is NULL");
-    *out = nullptr;
-    PM_CHECK(X != nullptr, "X is NULL");
-    PM_CHECK(n >= 1 && n < (int64_t)1 << 31, "n must be in 1..2^31-1 (got %lld)", (long long)n);
-    PM_CHECK(d >= 1 && d <= 65536, "d must be in 1..65536 (got %d)", d);
-    pmlsh_build_opts o;
-    if (opts) o = *opts;
-    else pmlsh_build_opts_default(&o);
-    if (o.leaf_size == 0) o.leaf_size = 256;
-    PM_CHECK(o.m >= 1 && o.m <= PM_MP, "m must be in 1..16 (got %d)", o.m);
-    PM_CHECK(o.s >= 0 && o.s <= PM_MAX_PIVOTS, "s must be in 0..8 (got %d)", o.s);
-    PM_CHECK(o.leaf_size >= 16 && o.leaf_size <= 1024, "leaf_size must be 0 or 16..1024 (got %d)",
-             o.leaf_size);
-    PM_CHECK(o.rmin_pairs >= 0, "rmin_pairs must be >= 0");
-    PM_CHECK(o.bf16_shadow == 0 || o.bf16_shadow == 1, "bf16_shadow must be 0 or 1");
     pmlsh_index *ix = new (std::nothrow) pmlsh_index();
     if (!ix) {
         pm_set_error("host allocation failed");
@@ -144,7 +132,7 @@ pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opt
     ix->s = std::min<int64_t>(o.s, (n + o.leaf_size - 1) / o.leaf_size);
     ix->M = o.leaf_size;
     ix->seed = o.seed;
-    pmlsh_status s = pm_build_index(ix, X, pm_is_device_ptr(X), &o, (cudaStream_t)stream);
+    pmlsh_status s = pm_build_index(ix, X, pm_is_device_ptr(X), &o, st);
     if (s != PMLSH_OK) {
         pm_free_index(ix);
         delete ix;
@@ -152,6 +140,99 @@ pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opt
     }
     *out = ix;
     return PMLSH_OK;
+}
+
+// Leaf-size autotuner: builds the index for each candidate capacity, times
+// pmlsh_knn with the default options (k = 10, c = 1.5, beta = 0.2809, no
+// statistics) on up to 1,024 rows of X taken at an even stride as queries
+// (best of two runs after one warm-up), and keeps the fastest index.
+pmlsh_status build_autotuned(const float *X, int64_t n, int d, pmlsh_build_opts o, cudaStream_t st,
+                             pmlsh_index **out)
+{
+    static const int cand[] = {128, 256, 512};
+    const int64_t nq = std::min<int64_t>(n, 1024);
+    const int64_t stride = n / nq;
+    std::vector<float> Qs((size_t)nq * d);
+    PM_CUDA(cudaMemcpy2DAsync(Qs.data(), (size_t)d * sizeof(float), X, (size_t)stride * d * sizeof(float),
+                              (size_t)d * sizeof(float), (size_t)nq,
+                              pm_is_device_ptr(X) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    int64_t *ids = nullptr;
+    float *dd = nullptr;
+    PM_CUDA(cudaMalloc(&ids, (size_t)nq * 10 * sizeof(int64_t)));
+    if (cudaMalloc(&dd, (size_t)nq * 10 * sizeof(float)) != cudaSuccess) {
+        cudaFree(ids);
+        pm_set_error("device allocation failed");
+        return PMLSH_ENOMEM;
+    }
+    struct Bufs { int64_t *a; float *b; ~Bufs() { cudaFree(a); cudaFree(b); } } bufs{ids, dd};
+    pmlsh_knn_opts ko;
+    pmlsh_knn_opts_default(&ko);
+    ko.k = (int)std::min<int64_t>(10, n);
+    pmlsh_index *best = nullptr;
+    float bestMs = INFINITY;
+    for (int M : cand) {
+        if (M > n && best) break;
+        o.leaf_size = M;
+        pmlsh_index *ix = nullptr;
+        pmlsh_status s = build_one(X, n, d, o, st, &ix);
+        if (s != PMLSH_OK) {
+            if (best) pmlsh_free(best);
+            return s;
+        }
+        float ms = INFINITY;
+        for (int rep = 0; rep < 3 && s == PMLSH_OK; rep++) {
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+            s = pm_knn(ix, Qs.data(), nq, &ko, ids, dd, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float el = INFINITY;
+            cudaEventElapsedTime(&el, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rep > 0) ms = std::min(ms, el);
+        }
+        if (s != PMLSH_OK) {
+            pmlsh_free(ix);
+            if (best) pmlsh_free(best);
+            return s;
+        }
+        if (ms < bestMs) {
+            if (best) pmlsh_free(best);
+            best = ix;
+            bestMs = ms;
+        } else {
+            pmlsh_free(ix);
+        }
+    }
+    *out = best;
+    return PMLSH_OK;
+}
+
+}  // namespace
+
+pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opts *opts, void *stream,
+                         pmlsh_index **out)
+{
+    PM_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    PM_CHECK(X != nullptr, "X is NULL");
+    PM_CHECK(n >= 1 && n < (int64_t)1 << 31, "n must be in 1..2^31-1 (got %lld)", (long long)n);
+    PM_CHECK(d >= 1 && d <= 65536, "d must be in 1..65536 (got %d)", d);
+    pmlsh_build_opts o;
+    if (opts) o = *opts;
+    else pmlsh_build_opts_default(&o);
+    PM_CHECK(o.m >= 1 && o.m <= PM_MP, "m must be in 1..16 (got %d)", o.m);
+    PM_CHECK(o.s >= 0 && o.s <= PM_MAX_PIVOTS, "s must be in 0..8 (got %d)", o.s);
+    PM_CHECK(o.leaf_size == 0 || (o.leaf_size >= 16 && o.leaf_size <= 1024),
+             "leaf_size must be 0 or 16..1024 (got %d)", o.leaf_size);
+    PM_CHECK(o.rmin_pairs >= 0, "rmin_pairs must be >= 0");
+    PM_CHECK(o.bf16_shadow == 0 || o.bf16_shadow == 1, "bf16_shadow must be 0 or 1");
+    if (o.leaf_size == 0) return build_autotuned(X, n, d, o, (cudaStream_t)stream, out);
+    return build_one(X, n, d, o, (cudaStream_t)stream, out);
 }
 
 void pmlsh_free(pmlsh_index *index)

@@ -398,3 +398,17 @@ def test_c3_full_size_sampled_parity():
                    stats={k2: v[sample] for k2, v in got["stats"].items()})
         _assert_parity(sub, ref)
     ix.close()
+
+
+def test_autotuned_leaf_size(c1):
+    # leaf_size = 0: the build times each candidate capacity and keeps one;
+    # results do not depend on the layout
+    X, Q, A = c1
+    ix = pm.Index(torch.from_numpy(X).cuda(), proj=A, leaf_size=0)
+    assert ix.leaf_size in (128, 256, 512)
+    t, _, _ = oracle.params(15, 1.5, 1 / E)
+    ref = oracle.knn(X, A, Q, 10, 1.5, t, oracle.budget(len(X), 0.2809, 10),
+                     oracle.rmin_auto(X, 0.2809, 10, 1.5, 3), 0)
+    got = ix.knn(torch.from_numpy(Q).cuda(), k=10, t=t)
+    _assert_parity(got, ref)
+    ix.close()
