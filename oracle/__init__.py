@@ -68,6 +68,8 @@ def lib():
                                p, p, p]
         L.orc_exact_knn.restype = i32
         L.orc_exact_knn.argtypes = [p, i64, i32, p, i64, i64, p, p]
+        L.orc_cp_bnb.restype = i32
+        L.orc_cp_bnb.argtypes = [p, p, i64, i32, i32, i64, i64, p, p]
         L.orc_exact_kcp.restype = i32
         L.orc_exact_kcp.argtypes = [p, i64, i32, i64, p, p]
         L.orc_node_ball.argtypes = [p, i32, p, i64, i64, p, p]
@@ -186,6 +188,22 @@ def rcbc(X, A32, Q, r, c, t, Bbc, Oproj=None):
     lib().orc_rcbc(_ptr(X), _ptr(Oproj), n, d, _ptr(A32), m, _ptr(Q), nq,
                    r, c, t, Bbc, _ptr(ids), _ptr(dd), _ptr(nc))
     return ids, dd, nc
+
+
+def cp_bnb(X, A32, T, k, Oproj=None):
+    """Algorithm 3: the T pairs nearest in the projected space, verified;
+    returns (pairs [k,2] int64 with i < j, FP64 distances [k])."""
+    X, A32 = _f32(X), _f32(A32)
+    n, d = X.shape
+    m = A32.shape[0]
+    if Oproj is None:
+        Oproj = project(X, A32)
+    Oproj = np.ascontiguousarray(Oproj, dtype=np.float64)
+    pairs = np.empty((k, 2), dtype=np.int64)
+    dd = np.empty(k, dtype=np.float64)
+    if lib().orc_cp_bnb(_ptr(X), _ptr(Oproj), n, d, m, int(T), int(k), _ptr(pairs), _ptr(dd)):
+        raise ValueError("bad arguments")
+    return pairs, dd
 
 
 def exact_knn(X, Q, k):

@@ -28,6 +28,8 @@
  *   orc_rcbc .............. Algorithm 1, (r,c)-BC
  *   orc_exact_knn ......... Definition 2 with c = 1 (brute force ground truth)
  *   orc_exact_kcp ......... Definition 4 with c = 1 (nested-loop join, NLJ)
+ *   orc_cp_bnb ............ Algorithm 3 (branch and bound): the T pairs nearest
+ *                           in the projected space, verified, top k
  *   orc_cp_radius_filter .. Algorithm 4 with FindLCA (Algorithm 5) on a given
  *                           hierarchy of leaves
  *   orc_node_ball ......... node ball (e.RO, e.r) of Sec. 4.1 for the given
@@ -456,6 +458,41 @@ static keyed_pair make_pair(double key, int64_t a, int64_t b)
     e.i = a < b ? a : b;
     e.j = a < b ? b : a;
     return e;
+}
+
+/* Sec. 6.1, Algorithm 3 (branch and bound), its result stated directly:
+ * C = the T pairs with the smallest projected distance ||o1',o2'|| (ties by
+ * (i, j)).  The best-first search over node pairs ends with exactly these
+ * pairs: Mindist(e1, e2) bounds every pair under (e1, e2) from below, so a
+ * node pair is left out only when none of its pairs can beat the T-th
+ * distance.  Each pair of C is verified by its original distance and the k
+ * smallest by (distance, i, j) are returned.  Reading: |C| = T (the text of
+ * Sec. 6.1 and its example keep T pairs after the self-joins; the first
+ * line of the listing prints k).  T larger than n(n-1)/2 means every pair. */
+int orc_cp_bnb(const float *X, const double *Oproj, int64_t n, int d, int m, int64_t T, int64_t k,
+               int64_t *out_pairs, double *out_dists)
+{
+    const int64_t P = n * (n - 1) / 2;
+    if (n < 2 || k < 1 || T < k || k > P) return 1;
+    if (T > P) T = P;
+    topk_pairs c = {(keyed_pair *)malloc(sizeof(keyed_pair) * (size_t)T), 0, T};
+    topk_pairs r = {(keyed_pair *)malloc(sizeof(keyed_pair) * (size_t)k), 0, k};
+    if (!c.v || !r.v) { free(c.v); free(r.v); return 2; }
+    for (int64_t a = 0; a < n; a++)
+        for (int64_t b = a + 1; b < n; b++)
+            topk_push(&c, make_pair(pdist64(Oproj + a * (int64_t)m, Oproj + b * (int64_t)m, m), a, b));
+    for (int64_t e = 0; e < c.n; e++) {
+        const int64_t i = c.v[e].i, j = c.v[e].j;
+        topk_push(&r, make_pair(dist64(X + i * (int64_t)d, X + j * (int64_t)d, d), i, j));
+    }
+    for (int64_t e = 0; e < k; e++) {
+        out_pairs[2 * e] = r.v[e].i;
+        out_pairs[2 * e + 1] = r.v[e].j;
+        out_dists[e] = r.v[e].key;
+    }
+    free(c.v);
+    free(r.v);
+    return 0;
 }
 
 /* Definition 4 with c = 1: exact k closest pairs (nested-loop join). */

@@ -398,3 +398,42 @@ def test_stop_rule_placement_readings():
     assert (lit["rounds"][0], lit["rule"][0], lit["ncand"][0]) == (1, 1, 1)
     assert (bc["rounds"][0], bc["rule"][0], bc["ncand"][0]) == (2, 1, 2)
     assert lit["ids"][0, 0] == bc["ids"][0, 0] == 0
+
+
+# ------------------------------------------------- Algorithm 3 (B&B CP)
+def test_cp_bnb_all_pairs_is_exact_kcp():
+    # T >= n(n-1)/2 keeps every pair: the verified top-k is the exact kCP
+    X, _ = _c1_small(n=300, nq=1, d=16)
+    A = oracle.gen_projection(2, 15, 16).astype(np.float32)
+    pb, db = oracle.cp_bnb(X, A, 10 ** 9, 7)
+    pe, de = oracle.exact_kcp(X, 7)
+    assert np.array_equal(pb, pe) and np.array_equal(db, de)
+
+
+def test_cp_bnb_identity_projection_is_exact_kcp():
+    # A = I (m = d): projected and original distances coincide, so the T
+    # nearest projected pairs hold the exact k nearest for any T >= k
+    X, _ = _c1_small(n=400, nq=1, d=8)
+    A = np.eye(8, dtype=np.float32)
+    pe, de = oracle.exact_kcp(X, 5)
+    for T in (5, 6, 50):
+        pb, db = oracle.cp_bnb(X, A, T, 5)
+        assert np.array_equal(pb, pe) and np.array_equal(db, de)
+
+
+def test_cp_bnb_against_numpy_brute_force():
+    # an independent brute force: all pair distances in the projected space
+    # (numpy, FP64), the T smallest by (distance, i, j), then the k smallest
+    # original distances among them
+    X, _ = _c1_small(n=250, nq=1, d=24)
+    A = oracle.gen_projection(7, 15, 24).astype(np.float32)
+    O = A.astype(np.float64) @ X.astype(np.float64).T
+    i, j = np.triu_indices(len(X), 1)
+    pd = np.sqrt(((O[:, i] - O[:, j]) ** 2).sum(0))
+    T, k = 40, 6
+    sel = np.lexsort((j, i, pd))[:T]
+    od = np.sqrt(((X[i[sel]].astype(np.float64) - X[j[sel]].astype(np.float64)) ** 2).sum(1))
+    top = np.lexsort((j[sel], i[sel], od))[:k]
+    pb, db = oracle.cp_bnb(X, A, T, k)
+    assert np.array_equal(pb, np.stack([i[sel][top], j[sel][top]], 1))
+    assert np.allclose(db, od[top], rtol=1e-12, atol=0)
