@@ -285,6 +285,24 @@ pmlsh_status pmlsh_closest_pair(pmlsh_index *index, const pmlsh_cp_opts *opts,
                                 int64_t *out_pairs, float *out_dists,
                                 pmlsh_cp_stats *stats, void *stream);
 
+/* Algorithm 3, branch and bound (Sec. 6.1): the T pairs with the smallest
+ * projected distance (ties by (i, j); T = opts->T, or ceil(alpha2 n (n-1))
+ * + k when T <= 0; at least k, at most n(n-1)/2) are found by a best-first
+ * search over leaf pairs in ascending Mindist (the larger of the pivot-ring
+ * gap and ||RO1, RO2|| - r1 - r2 of the two leaf entries), starting from
+ * every leaf's self-join, stopping at the first leaf pair whose Mindist
+ * exceeds the T-th projected distance; they are verified by their original
+ * distance and the k nearest are returned.  From `opts` the call uses k, T
+ * and alpha2 (c, alpha1, t and gamma are not used).  Outputs as
+ * pmlsh_closest_pair; stats: count = pairs verified (T), lca_nodes = leaf
+ * pairs not excluded by the self-join bound, nodes_done = leaf pairs
+ * examined, self_pairs, fp64_checks.  Memory grows with T (12 bytes per kept
+ * pair plus a batch of up to 2^24 pairs).  Errors: EINVAL, ENOMEM, ECUDA,
+ * EINTERNAL (more than 4096 pairs tied inside one FP32 error band). */
+pmlsh_status pmlsh_closest_pair_bnb(pmlsh_index *index, const pmlsh_cp_opts *opts,
+                                    int64_t *out_pairs, float *out_dists,
+                                    pmlsh_cp_stats *stats, void *stream);
+
 /* ------------------------------------------------------------- serving */
 
 /* Continuous batching over one resident index.  `slots` worker threads, each

@@ -99,6 +99,7 @@ _SIGS = {
     "pmlsh_rcbc": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P, _P]),
     "pmlsh_cp_opts_default": (None, [_P]),
     "pmlsh_closest_pair": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "pmlsh_closest_pair_bnb": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pmlsh_serve_opts_default": (None, [_P]),
     "pmlsh_serve_create": (ctypes.c_int, [_P, _P, _P]),
     "pmlsh_serve_submit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
@@ -309,6 +310,19 @@ class Index:
             res["stats"] = dict(rule=sv["stop_rule"].copy(), ncand=sv["n_cand"].copy(),
                                 rounds=sv["rounds"].copy())
         return res
+
+    def closest_pairs_bnb(self, k=10, T=0, alpha2=0.0024):
+        """Algorithm 3 (branch and bound).  Returns dict(pairs, dists, stats)."""
+        o = CpOpts()
+        lib().pmlsh_cp_opts_default(ctypes.byref(o))
+        o.k, o.T, o.alpha2 = k, T, alpha2
+        pairs = np.empty((k, 2), dtype=np.int64)
+        dists = np.empty(k, dtype=np.float32)
+        st = CpStats()
+        _check(lib().pmlsh_closest_pair_bnb(self._h, ctypes.byref(o), pairs.ctypes.data_as(ctypes.c_void_p),
+                                            dists.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st), _stream()))
+        return dict(pairs=pairs, dists=dists,
+                    stats={f: getattr(st, f) for f, _ in CpStats._fields_})
 
     def knn(self, Q, k=10, c=1.5, alpha1=1 / math.e, beta=0.2809, r_min=0.0,
             precision=PMLSH_FP32_PLAIN, stop_rule=STOP_LITERAL, t=0.0, out=None,

@@ -366,6 +366,18 @@ pmlsh_status pmlsh_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *opts, int6
     return pm_closest_pair(ix, &o, out_pairs, out_dists, stats, (cudaStream_t)stream);
 }
 
+pmlsh_status pmlsh_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *opts, int64_t *out_pairs,
+                                    float *out_dists, pmlsh_cp_stats *stats, void *stream)
+{
+    PM_CHECK(ix && opts && out_pairs && out_dists, "NULL argument");
+    const pmlsh_cp_opts &o = *opts;
+    const int64_t npairs = ix->n * (ix->n - 1) / 2;
+    PM_CHECK(ix->n >= 2, "closest pairs need n >= 2");
+    PM_CHECK(o.k >= 1 && o.k <= 1024 && o.k <= npairs, "k must be in 1..min(n(n-1)/2, 1024) (got %d)", o.k);
+    PM_CHECK(o.T > 0 || (o.alpha2 > 0.0 && o.alpha2 <= 1.0), "alpha2 must be in (0,1]");
+    return pm_closest_pair_bnb(ix, &o, out_pairs, out_dists, stats, (cudaStream_t)stream);
+}
+
 pmlsh_status pmlsh_project(pmlsh_index *ix, const float *Q, int64_t nq, double *out64, float *out32,
                            void *stream)
 {

@@ -240,6 +240,119 @@ __global__ void k_pair_sort(PairExact *__restrict__ v, int n)
     for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = s[i];
 }
 
+
+// ------------------------------------------- Algorithm 3 (branch and bound)
+
+// All pairs inside leaf l keyed by their FP32 projected squared distance.
+// One block per leaf.
+__global__ void k_bnb_selfjoin(const float *__restrict__ O32, const int64_t *__restrict__ off,
+                               const int64_t *__restrict__ pairOff, PairCand *__restrict__ out)
+{
+    const int64_t l = blockIdx.x;
+    const int64_t p0 = off[l], s = off[l + 1] - p0;
+    const int64_t np = s * (s - 1) / 2;
+    for (int64_t e = threadIdx.x; e < np; e += blockDim.x) {
+        int64_t i = 0, rem = e;
+        while (rem >= s - 1 - i) { rem -= s - 1 - i; i++; }
+        const int64_t j = i + 1 + rem;
+        PairCand pc;
+        pc.key = pm_pd2_32(O32 + (p0 + i) * PM_MP, O32 + (p0 + j) * PM_MP);
+        pc.a = (int32_t)(p0 + i);
+        pc.b = (int32_t)(p0 + j);
+        out[pairOff[l] + e] = pc;
+    }
+}
+
+struct LeafPair {
+    float md;      // lower bound of the projected distance of any pair in l1 x l2
+    int32_t l1, l2;
+};
+
+// Mindist of Sec. 6.1 for leaf pairs (l1, l2), l1 < l2: the larger of
+// ||RO1, RO2|| - r1 - r2 and the gaps between the pivot rings, from the leaf
+// entries (FP32, rounded so that it stays a lower bound).  Pairs with
+// Mindist <= dT are listed.  Block per l1, threads over l2.
+__global__ void k_bnb_mindist(const float *__restrict__ meta, int s, int64_t L, float dT, LeafPair *__restrict__ out,
+                              unsigned long long *cnt, unsigned long long cap)
+{
+    const int64_t l1 = blockIdx.x;
+    const float *M1 = meta + l1 * PM_LEAF_STRIDE;
+    for (int64_t l2 = l1 + 1 + threadIdx.x; l2 < L; l2 += blockDim.x) {
+        const float *M2 = meta + l2 * PM_LEAF_STRIDE;
+        const float dc = __fsqrt_rn(pm_pd2_32(M1, M2));
+        float md = __fsub_rn(__fsub_rn(__fmul_rn(dc, 1.f - 1e-5f), M1[16]), M2[16]);
+        for (int i = 0; i < PM_MAX_PIVOTS; i++) {
+            if (i < s) {
+                // rings [min, max] of the two leaves (already widened outwards)
+                md = fmaxf(md, __fsub_rn(M2[24 + i], M1[32 + i]));
+                md = fmaxf(md, __fsub_rn(M1[24 + i], M2[32 + i]));
+            }
+        }
+        if (md <= dT) {
+            const unsigned long long slot = atomicAdd(cnt, 1ull);
+            if (slot < cap) {
+                LeafPair lp;
+                lp.md = md;
+                lp.l1 = (int32_t)l1;
+                lp.l2 = (int32_t)l2;
+                out[slot] = lp;
+            }
+        }
+    }
+}
+
+// Every cross pair of the listed leaf pairs, keyed by the FP32 projected
+// squared distance, at the listed offsets.  Block per leaf pair.
+__global__ void k_bnb_cross(const float *__restrict__ O32, const int64_t *__restrict__ off,
+                            const int2 *__restrict__ lp, const int64_t *__restrict__ lpOff,
+                            PairCand *__restrict__ out)
+{
+    const int2 pr = lp[blockIdx.x];
+    const int64_t a0 = off[pr.x], na = off[pr.x + 1] - a0;
+    const int64_t b0 = off[pr.y], nb = off[pr.y + 1] - b0;
+    const int64_t base = lpOff[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < na * nb; e += blockDim.x) {
+        const int64_t ia = e / nb, ib = e % nb;
+        PairCand pc;
+        pc.key = pm_pd2_32(O32 + (a0 + ia) * PM_MP, O32 + (b0 + ib) * PM_MP);
+        pc.a = (int32_t)(a0 + ia);
+        pc.b = (int32_t)(b0 + ib);
+        out[base + e] = pc;
+    }
+}
+
+// Entries with key < lo moved to out (order kept only per block).
+__global__ void k_pair_below(const PairCand *__restrict__ p, int64_t n, float lo, PairCand *__restrict__ out,
+                             unsigned long long *cnt)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const PairCand c = p[e];
+    if (c.key < lo) out[atomicAdd(cnt, 1ull)] = c;
+}
+
+
+// Entries with lo <= key <= hi, appended with their FP64 projected distance.
+__global__ void k_pair_band(const PairCand *__restrict__ p, int64_t n, float lo, float hi,
+                            const double *__restrict__ O64, int m, const int32_t *__restrict__ perm,
+                            PairExact *__restrict__ out, unsigned long long *cnt, unsigned long long cap)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const PairCand c = p[e];
+    if (!(c.key >= lo && c.key <= hi)) return;
+    const unsigned long long slot = atomicAdd(cnt, 1ull);
+    if (slot >= cap) return;
+    PairExact x;
+    x.dist = pm_pdist64(O64 + (int64_t)c.a * PM_MP, O64 + (int64_t)c.b * PM_MP, m);
+    const int64_t ia = perm[c.a], ib = perm[c.b];
+    x.i = ia < ib ? ia : ib;
+    x.j = ia < ib ? ib : ia;
+    x.a = c.a;
+    x.b = c.b;
+    out[slot] = x;
+}
+
 template <class T> pmlsh_status dalloc(T **p, size_t count)
 {
     PM_CUDA(cudaMalloc((void **)p, std::max<size_t>(1, count) * sizeof(T)));
@@ -382,6 +495,63 @@ pmlsh_status pair_truncate(PairCand *p, int64_t n, int64_t need, const pmlsh_ind
     PM_CUDA(cudaMemcpyAsync(p, kept.data(), keep * sizeof(PairCand), cudaMemcpyHostToDevice, st));
     PM_CUDA(cudaStreamSynchronize(st));
     *nOut = keep;
+    return PMLSH_OK;
+}
+
+
+// The T candidates of p[0, n) with the smallest (FP64 projected distance,
+// i, j) go to out[0, T) (any order): the T-th FP32 key by radix select;
+// keys below its FP32 band are in, keys inside the band are ordered by
+// (FP64 projected distance, i, j) and the first ones fill up to T.  tauHi:
+// an upper bound of the T-th FP64 projected distance.
+pmlsh_status pair_select(const PairCand *p, int64_t n, int64_t T, PairCand *out, const pmlsh_index *ix,
+                         unsigned int *hist, PairExact *scratch, unsigned long long *cnt, int64_t *fp64,
+                         double *tauHi, cudaStream_t st)
+{
+    float K;
+    PM_TRY(pair_kth(p, n, T, hist, &K, st));
+    const double tau = std::sqrt((double)K);
+    const double eps = 0x1.0p-22 * ix->maxNorm + 0x1.0p-19 * tau + 1e-300;
+    const double loD = tau - 2 * eps;
+    float lo = loD > 0 ? (float)(loD * loD) : 0.f;
+    if (loD > 0 && (double)lo > loD * loD) lo = nextafterf(lo, -INFINITY);
+    if (!(loD > 0)) lo = 0.f;
+    float hi = (float)((tau + 2 * eps) * (tau + 2 * eps));
+    if ((double)hi < (tau + 2 * eps) * (tau + 2 * eps)) hi = nextafterf(hi, INFINITY);
+    PM_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
+    if (loD > 0)
+        PM_LAUNCH("k_pair_below", st, k_pair_below<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n, lo, out, cnt));
+    PM_LAUNCH("k_pair_band", st, k_pair_band<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        p, n, loD > 0 ? lo : -INFINITY, hi, ix->O64, ix->m, ix->perm, scratch, cnt + 1, PAIR_SORT_CAP));
+    PM_CUDA(cudaGetLastError());
+    unsigned long long hc[2];
+    PM_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    const int64_t nBelow = (int64_t)hc[0], nBand = (int64_t)hc[1];
+    if (nBand > PAIR_SORT_CAP || nBelow > T || nBelow + nBand < T) {
+        pm_set_error("closest pairs: %lld candidates inside the FP32 band at the T-th projected distance "
+                     "(capacity %d)", (long long)nBand, PAIR_SORT_CAP);
+        return PMLSH_EINTERNAL;
+    }
+    *fp64 += nBand;
+    int P = 1;
+    while (P < (int)nBand) P <<= 1;
+    if (nBand > 0)
+        PM_LAUNCH("k_pair_sort", st, k_pair_sort<<<1, 1024, (size_t)P * sizeof(PairExact), st>>>(scratch, (int)nBand));
+    std::vector<PairExact> v(nBand);
+    PM_CUDA(cudaMemcpyAsync(v.data(), scratch, nBand * sizeof(PairExact), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    const int64_t need = T - nBelow;
+    std::vector<PairCand> kept(need);
+    for (int64_t e = 0; e < need; e++) {
+        kept[e].key = 0.f;
+        kept[e].a = v[e].a;
+        kept[e].b = v[e].b;
+    }
+    if (need > 0)
+        PM_CUDA(cudaMemcpyAsync(out + nBelow, kept.data(), need * sizeof(PairCand), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    *tauHi = tau + eps;
     return PMLSH_OK;
 }
 
@@ -540,5 +710,152 @@ pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *o
         stats->t = t;
         stats->T = T;
     }
+    return PMLSH_OK;
+}
+
+// Algorithm 3 (Sec. 6.1): the T pairs nearest in the projected space, found
+// by branch and bound over leaf pairs, verified, cut to the k nearest.
+//   1. every leaf's self-join, keyed by projected distance; if it yields T
+//      pairs, the T-th of them bounds d_T from above;
+//   2. Mindist of every leaf pair (a flat stand-in for the priority queue
+//      over node pairs: with a lower bound per leaf pair the same pairs are
+//      examined), the pairs with Mindist <= that bound taken in ascending
+//      (Mindist, l1, l2);
+//   3. their cross pairs in batches; after each batch the candidates are cut
+//      to the exact T nearest (FP64-resolved band at the cut) and the search
+//      stops at the first leaf pair whose Mindist exceeds the T-th distance;
+//   4. the T pairs verified in the original space, exact top-k.
+// The result equals the oracle's: the T pairs with the smallest (FP64
+// projected distance, i, j), then the k smallest (FP64 distance, i, j).
+pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
+                                 pmlsh_cp_stats *stats, cudaStream_t st)
+{
+    const int64_t n = ix->n, L = ix->L;
+    const int k = o->k;
+    const int64_t P = n * (n - 1) / 2;
+    int64_t T = o->T > 0 ? o->T : (int64_t)std::ceil(o->alpha2 * (double)n * (double)(n - 1) - 1e-9) + k;
+    T = std::min(std::max<int64_t>(T, k), P);
+    DevPtrs mem;
+    unsigned int *hist;
+    PairExact *scratch;
+    unsigned long long *cnt;
+    PM_TRY(mem.get(&hist, 2048));
+    PM_TRY(mem.get(&scratch, PAIR_SORT_CAP));
+    PM_TRY(mem.get(&cnt, 4));
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_pair_sort));
+    // 1. self-joins
+    std::vector<int64_t> pairOff(L + 1, 0);
+    for (int64_t l = 0; l < L; l++) {
+        const int64_t s = ix->leafOffH[l + 1] - ix->leafOffH[l];
+        pairOff[l + 1] = pairOff[l] + s * (s - 1) / 2;
+    }
+    const int64_t nSelf = pairOff[L];
+    // candidate buffer: up to T kept pairs followed by a batch
+    const int64_t batchCap = std::max<int64_t>((int64_t)1 << 24, nSelf);
+    PairCand *buf, *sel;
+    int64_t *dPairOff;
+    PM_TRY(mem.get(&buf, (size_t)(T + batchCap)));
+    PM_TRY(mem.get(&sel, (size_t)T));
+    PM_TRY(mem.get(&dPairOff, L + 1));
+    PM_CUDA(cudaMemcpyAsync(dPairOff, pairOff.data(), (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (nSelf > 0)
+        PM_LAUNCH("k_bnb_selfjoin", st, k_bnb_selfjoin<<<(unsigned)L, 128, 0, st>>>(ix->O32, ix->leafOff, dPairOff, buf));
+    PM_CUDA(cudaGetLastError());
+    int64_t nBuf = nSelf, fp64 = 0;
+    double dT = INFINITY;   // upper bound of the T-th projected distance
+    auto cut = [&]() -> pmlsh_status {
+        if (nBuf <= T) return PMLSH_OK;
+        double tauHi = INFINITY;
+        PM_TRY(pair_select(buf, nBuf, T, sel, ix, hist, scratch, cnt, &fp64, &tauHi, st));
+        PM_CUDA(cudaMemcpyAsync(buf, sel, T * sizeof(PairCand), cudaMemcpyDeviceToDevice, st));
+        nBuf = T;
+        dT = std::min(dT, tauHi);
+        return PMLSH_OK;
+    };
+    PM_TRY(cut());
+    // 2. leaf pairs with Mindist <= dT
+    LeafPair *dlp;
+    const unsigned long long lpCap = (unsigned long long)std::max<int64_t>(1, L * (L - 1) / 2);
+    PM_TRY(mem.get(&dlp, (size_t)lpCap));
+    PM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+    const float dT32 = std::isinf(dT) ? INFINITY : nextafterf((float)dT, INFINITY);
+    if (L > 1)
+        PM_LAUNCH("k_bnb_mindist", st, k_bnb_mindist<<<(unsigned)L, 256, 0, st>>>(ix->leafMeta, ix->s, L, dT32, dlp, cnt,
+                                                                                   lpCap));
+    PM_CUDA(cudaGetLastError());
+    unsigned long long nlp = 0;
+    PM_CUDA(cudaMemcpyAsync(&nlp, cnt, sizeof(nlp), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    std::vector<LeafPair> lps(nlp);
+    PM_CUDA(cudaMemcpyAsync(lps.data(), dlp, nlp * sizeof(LeafPair), cudaMemcpyDeviceToHost, st));
+    PM_CUDA(cudaStreamSynchronize(st));
+    std::sort(lps.begin(), lps.end(), [](const LeafPair &x, const LeafPair &y) {
+        if (x.md != y.md) return x.md < y.md;
+        if (x.l1 != y.l1) return x.l1 < y.l1;
+        return x.l2 < y.l2;
+    });
+    // 3. best first in batches
+    int2 *dPairs;
+    int64_t *dOff;
+    const size_t lpBatch = (size_t)1 << 16;
+    PM_TRY(mem.get(&dPairs, lpBatch));
+    PM_TRY(mem.get(&dOff, lpBatch));
+    int64_t examined = 0, crossPairs = 0;
+    size_t next = 0;
+    while (next < lps.size()) {
+        if ((double)lps[next].md > dT) break;   // no pair under it can beat the T-th
+        std::vector<int2> bp;
+        std::vector<int64_t> bo;
+        int64_t tot = 0;
+        while (next < lps.size() && bp.size() < lpBatch && (double)lps[next].md <= dT) {
+            const int64_t na = ix->leafOffH[lps[next].l1 + 1] - ix->leafOffH[lps[next].l1];
+            const int64_t nb = ix->leafOffH[lps[next].l2 + 1] - ix->leafOffH[lps[next].l2];
+            if (tot > 0 && tot + na * nb > batchCap) break;
+            bp.push_back(make_int2(lps[next].l1, lps[next].l2));
+            bo.push_back(nBuf + tot);
+            tot += na * nb;
+            next++;
+        }
+        if (tot > batchCap) {
+            pm_set_error("closest pairs: one leaf pair holds more pairs than the batch capacity");
+            return PMLSH_EINTERNAL;
+        }
+        PM_CUDA(cudaMemcpyAsync(dPairs, bp.data(), bp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+        PM_CUDA(cudaMemcpyAsync(dOff, bo.data(), bo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        PM_LAUNCH("k_bnb_cross", st, k_bnb_cross<<<(unsigned)bp.size(), 256, 0, st>>>(ix->O32, ix->leafOff, dPairs, dOff,
+                                                                                        buf));
+        PM_CUDA(cudaGetLastError());
+        nBuf += tot;
+        examined += (int64_t)bp.size();
+        crossPairs += tot;
+        PM_TRY(cut());
+    }
+    // 4. verification and the exact top-k
+    if (nBuf > 0)
+        PM_LAUNCH("k_pair_dist32", st, k_pair_dist32<<<(unsigned)((nBuf + 255) / 256), 256, 0, st>>>(ix->X, ix->ld, buf, nBuf));
+    TopK top;
+    PM_TRY(pair_merge(top, k, buf, nBuf, ix, hist, scratch, cnt, st));
+    std::vector<int64_t> op((size_t)2 * k, -1);
+    std::vector<float> od(k, INFINITY);
+    for (int e = 0; e < k && e < (int)top.v.size(); e++) {
+        op[2 * e] = top.v[e].i;
+        op[2 * e + 1] = top.v[e].j;
+        od[e] = (float)top.v[e].dist;
+    }
+    PM_CUDA(cudaMemcpy(out_pairs, op.data(), op.size() * sizeof(int64_t),
+                       pm_is_device_ptr(out_pairs) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    PM_CUDA(cudaMemcpy(out_dists, od.data(), od.size() * sizeof(float),
+                       pm_is_device_ptr(out_dists) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    if (stats) {
+        stats->count = nBuf;
+        stats->ub_self = INFINITY;
+        stats->lca_nodes = (int64_t)lps.size();
+        stats->nodes_done = examined;
+        stats->self_pairs = nSelf;
+        stats->fp64_checks = fp64;
+        stats->t = 0.0;
+        stats->T = T;
+    }
+    (void)crossPairs;
     return PMLSH_OK;
 }

@@ -153,6 +153,8 @@ void pm_release_work(KnnWork &w);
 // Closest pairs (cp.cu)
 pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
                              pmlsh_cp_stats *stats, cudaStream_t st);
+pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
+                             pmlsh_cp_stats *stats, cudaStream_t st);
 
 // Parameters (params.cpp)
 double pm_chi2_sf(double x, int m);

@@ -112,3 +112,64 @@ def test_cp_c4_full_size():
     _assert_same(got, ref)
     planted_set = {tuple(p) for p in planted.tolist()}
     assert {tuple(p) for p in got["pairs"].tolist()} <= planted_set
+
+
+# ------------------------------------------------ Algorithm 3 (branch and bound)
+def _bnb_both(X, A, k, T, leaf):
+    ix = pm.Index(torch.from_numpy(X).cuda(), leaf_size=leaf, proj=A)
+    got = ix.closest_pairs_bnb(k=k, T=T)
+    ix.close()
+    rp, rd = oracle.cp_bnb(X, A, T, k)
+    return got, rp, rd
+
+
+@pytest.mark.parametrize("n,d,clusters,k,T,leaf", [
+    (800, 16, 6, 5, 40, 32),          # self-joins alone give T pairs: pruned search
+    (1200, 32, 10, 10, 20000, 64),    # T beyond the self-join pairs: no bound at first
+    (300, 8, 3, 7, 10 ** 9, 16),      # every pair: the exact kCP
+    (1000 + 9, 40, 8, 12, 3000, 128), # ragged n, larger leaves
+])
+def test_cp_bnb_parity(n, d, clusters, k, T, leaf):
+    X, _, _, _ = datagen.mixture(n, d, clusters, 1.0, seed=n + 1)
+    A = oracle.gen_projection(8, 15, d).astype(np.float32)
+    got, rp, rd = _bnb_both(X, A, k, T, leaf)
+    assert got["pairs"].tolist() == rp.tolist()
+    assert np.array_equal(got["dists"], rd.astype(np.float32))
+    assert got["stats"]["count"] == min(T, n * (n - 1) // 2)
+
+
+def test_cp_bnb_duplicates_and_exact_kcp():
+    # repeated points: many pairs at projected distance 0, ties by (i, j)
+    base, _, _, _ = datagen.mixture(40, 12, 4, 1.0, seed=2)
+    X = np.repeat(base, 6, axis=0)
+    A = oracle.gen_projection(9, 15, 12).astype(np.float32)
+    got, rp, rd = _bnb_both(X, A, 15, 500, 16)
+    assert got["pairs"].tolist() == rp.tolist()
+    assert np.array_equal(got["dists"], rd.astype(np.float32))
+    got, rp, rd = _bnb_both(X, A, 15, 10 ** 9, 16)
+    ep, ed = oracle.exact_kcp(X, 15)
+    assert got["pairs"].tolist() == ep.tolist()
+    assert np.array_equal(got["dists"], ed.astype(np.float32))
+
+
+@pytest.mark.slow
+def test_cp_bnb_c4_full_size():
+    # Algorithm 3 on the closest-pair workload (n = 100,000, d = 512) with
+    # T = ceil(0.0024 n (n-1)) + k ~ 2.4e7: the returned pairs are planted
+    # pairs, their distances equal the FP64 distances, and the result equals
+    # Algorithm 4's on the same index (both find the planted pairs first)
+    w = datagen.workload("c4")
+    X, planted = w["X"], w["planted"]
+    A = oracle.gen_projection(2, 15, 512).astype(np.float32)
+    n = len(X)
+    T = int(math.ceil(0.0024 * n * (n - 1))) + 10
+    ix = pm.Index(torch.from_numpy(X).cuda(), leaf_size=256, proj=A)
+    got = ix.closest_pairs_bnb(k=10, T=T)
+    rf = ix.closest_pairs(k=10, gamma=3.0, T=T, t=oracle.params(15, 1.5, 1 / math.e)[0])
+    ix.close()
+    assert got["stats"]["count"] == T
+    planted_set = {tuple(p) for p in planted.tolist()}
+    assert {tuple(p) for p in got["pairs"].tolist()} <= planted_set
+    ex = np.sqrt(((X[got["pairs"][:, 0]].astype(np.float64) - X[got["pairs"][:, 1]].astype(np.float64)) ** 2).sum(1))
+    assert np.allclose(got["dists"], ex, rtol=1e-6, atol=0)
+    assert got["pairs"].tolist() == rf["pairs"].tolist()
