@@ -753,6 +753,29 @@ void pm_release_work(KnnWork &w)
                       &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask,
                       &w.recheck, &w.leafBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
     for (DevBuf *b : bufs) b->release();
+    w.stage.release();
+}
+
+pmlsh_status HostBuf::reserve(size_t b)
+{
+    if (b <= bytes) return PMLSH_OK;
+    release();
+    const size_t nb = std::max<size_t>(b, 4096);
+    if (cudaMallocHost(&p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        pm_set_error("pinned host allocation of %zu bytes failed", nb);
+        return PMLSH_ENOMEM;
+    }
+    bytes = nb;
+    return PMLSH_OK;
+}
+
+void HostBuf::release()
+{
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
 }
 
 pmlsh_status DevBuf::reserve(size_t b)

@@ -188,8 +188,8 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32, int *__restrict__ cntPart)
 {
     constexpr int W = QBT / 32;
-    __shared__ float sq[QBT][PM_MP];
-    __shared__ float sp[QBT][PM_MAX_PIVOTS];
+    __shared__ __align__(16) float sq[QBT][PM_MP];
+    __shared__ __align__(16) float sp[QBT][PM_MAX_PIVOTS];
     __shared__ float sRin[QBT], sRout[QBT];
     __shared__ int sCnt[QBT], sPart[QBT];
     const int b = blockIdx.y;
@@ -230,7 +230,25 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         for (int j = 0; j < 32; j++) {
             const int qq = w * 32 + j;
             if (qq >= nb) break;
-            const unsigned char c = lv ? leaf_class(sq[qq], sp[qq], s, sRin[qq], sRout[qq], Mv) : CL_OUT;
+            // the query's coordinates and pivot distances by 16-byte loads
+            float qv[PM_MP], pv[PM_MAX_PIVOTS];
+#pragma unroll
+            for (int j4 = 0; j4 < PM_MP / 4; j4++) {
+                const float4 v = ((const float4 *)sq[qq])[j4];
+                qv[4 * j4] = v.x;
+                qv[4 * j4 + 1] = v.y;
+                qv[4 * j4 + 2] = v.z;
+                qv[4 * j4 + 3] = v.w;
+            }
+#pragma unroll
+            for (int j4 = 0; j4 < PM_MAX_PIVOTS / 4; j4++) {
+                const float4 v = ((const float4 *)sp[qq])[j4];
+                pv[4 * j4] = v.x;
+                pv[4 * j4 + 1] = v.y;
+                pv[4 * j4 + 2] = v.z;
+                pv[4 * j4 + 3] = v.w;
+            }
+            const unsigned char c = lv ? leaf_class(qv, pv, s, sRin[qq], sRout[qq], Mv) : CL_OUT;
             const int fullAdd = __reduce_add_sync(0xffffffffu, c == CL_FULL ? cnt : 0);
             const int partAdd = __reduce_add_sync(0xffffffffu, c == CL_PART ? cnt : 0);
             if (lane == 0 && fullAdd) atomicAdd(&sCnt[qq], fullAdd);
@@ -1731,9 +1749,16 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     PM_LAUNCH("k_scan_single", st, k_scan_single<<<1, 1024, 0, st>>>(hist, L + 1));
     PM_LAUNCH("k_scatter_order", st, k_scatter_order<<<gq, 256, 0, st>>>(key, nq, hist, order));
     PM_CUDA(cudaGetLastError());
-    std::vector<int32_t> orderH(nq);
-    PM_CUDA(cudaMemcpyAsync(orderH.data(), order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    PM_CUDA(cudaStreamSynchronize(st));
+    // pinned staging of the per-round decisions: order [nq], bounds [2 nq],
+    // verification outputs (k-th distance [nq] f64, fp64/verified/leaves
+    // counts [3 nq], error flag)
+    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 6) + 64));
+    double *stDk = (double *)w.stage.p;
+    int32_t *stOrder = (int32_t *)(stDk + nq);
+    int *stHs = stOrder + nq, *stHp = stHs + nq, *stFp = stHp + nq, *stNv = stFp + nq, *stNl = stNv + nq,
+        *stErr = stNl + nq;
+    PM_CUDA(cudaMemcpyAsync(stOrder, order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> orderH;   // host copy, read after the first round's sync
 
     // host round state
     std::vector<double> r(nq, rmin);
@@ -1744,7 +1769,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
 
     const int bandCap = 1 << 20;
-    int *act = grow<int32_t>(w.active, nq, s);
+    int *actBuf = grow<int32_t>(w.active, nq, s);
     Thr *thr = grow<Thr>(w.thr, nq, s);
     int *cntSure = grow<int>(w.cntSure, nq, s);
     int *cntBand = grow<int>(w.cntBand, nq, s);
@@ -1796,12 +1821,18 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     std::vector<int32_t> actH;
     actH.reserve(nq);
     for (int round = 0; round < 100000; round++) {
-        actH.clear();
-        for (int64_t i = 0; i < nq; i++)
-            if (!done[orderH[i]]) actH.push_back(orderH[i]);
-        const int na = (int)actH.size();
-        if (na == 0) break;
-        PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        // round 0: every query, in the order on the device (its host copy is
+        // read after this round's first sync); later rounds: the active ones
+        int32_t *act = round == 0 ? order : actBuf;
+        int na = (int)nq;
+        if (round > 0) {
+            actH.clear();
+            for (int64_t i = 0; i < nq; i++)
+                if (!done[orderH[i]]) actH.push_back(orderH[i]);
+            na = (int)actH.size();
+            if (na == 0) break;
+            PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
         PM_CUDA(cudaMemsetAsync(inTrue, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(inN, 0, na * sizeof(int), st));
         PM_CUDA(cudaMemsetAsync(fpc, 0, (nq + 8) * sizeof(int), st));
@@ -1907,9 +1938,15 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits};
         PM_TRY(class_phase(tensor, full));
         std::vector<int> hs(na), hp(na), hb(na, 0), hin(na, 0);
-        PM_CUDA(cudaMemcpyAsync(hs.data(), cntSure, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(hp.data(), cntPart, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stHs, cntSure, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stHp, cntPart, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
+        std::memcpy(hs.data(), stHs, na * sizeof(int));
+        std::memcpy(hp.data(), stHp, na * sizeof(int));
+        if (round == 0) {
+            orderH.assign(stOrder, stOrder + nq);
+            actH.assign(stOrder, stOrder + nq);
+        }
         // The decisions of Algorithm 2 compare |S_i| only with min(B, n)
         // (rule 2: |S_i| >= B; rule 3: |S_i| = n).  Whole-leaf counts bound
         // |S_i| from below and whole partial leaves from above.  The exact
@@ -2030,15 +2067,15 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
-        std::vector<double> dkH(na);
-        std::vector<int> fpH(na), nvH(na), nlH(na);
-        PM_CUDA(cudaMemcpyAsync(nlH.data(), nverD + na, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        int errH = 0;
-        PM_CUDA(cudaMemcpyAsync(nvH.data(), nverD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(dkH.data(), dk, na * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(fpH.data(), fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(&errH, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stNl, nverD + na, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stNv, nverD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stDk, dk, na * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stFp, fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaMemcpyAsync(stErr, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
+        const std::vector<double> dkH(stDk, stDk + na);
+        const std::vector<int> fpH(stFp, stFp + na), nvH(stNv, stNv + na), nlH(stNl, stNl + na);
+        const int errH = *stErr;
         if (errH) {
             int dbgH[3] = {0, 0, 0};
             cudaMemcpy(dbgH, nverD + 2 * na + 1, sizeof(dbgH), cudaMemcpyDeviceToHost);

@@ -53,6 +53,15 @@ struct DevBuf {
     template <class T> T *as() const { return (T *)p; }
 };
 
+// A grow-only pinned host buffer (device-to-host copies that do not block
+// the host until the stream drains).
+struct HostBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    pmlsh_status reserve(size_t b);
+    void release();
+};
+
 // Per-call scratch buffers of the query path (kept in the index, grown on
 // demand, reused across calls).
 struct KnnWork {
@@ -62,6 +71,7 @@ struct KnnWork {
     DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
     DevBuf selBuf, selOff, selCnt, selTau;
     DevBuf active, misc, recheck, leafBits, cntPart, subIdx, subThr, subBits, qpca;
+    HostBuf stage;   // per-round decisions read by the host
 };
 
 struct pmlsh_index {
