@@ -732,6 +732,7 @@ void pm_free_index(pmlsh_index *ix)
     cudaFree(ix->leafMu);
     cudaFree(ix->leafRx);
     cudaFree(ix->pcaP);
+    cudaFree(ix->pcaP32);
     cudaFree(ix->leafPmu);
     cudaFree(ix->chunkOff);
     cudaFree(ix->leafChunk);
@@ -1006,6 +1007,9 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
             }
         }
         ix->muMax = muMax;
+        std::vector<float> P32(P.begin(), P.end());
+        PM_TRY(dalloc(&ix->pcaP32, P32.size()));
+        PM_CUDA(cudaMemcpyAsync(ix->pcaP32, P32.data(), P32.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         PM_TRY(dalloc(&ix->pcaP, P.size()));
         PM_TRY(dalloc(&ix->leafPmu, pmu.size()));
         PM_CUDA(cudaMemcpyAsync(ix->pcaP, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice, st));

@@ -108,38 +108,29 @@ __global__ void k_query_aux(const double *__restrict__ qp64, const float *__rest
         qpiv[q * PM_MAX_PIVOTS + i] = i < s ? sqrtf(pm_pd2_32(qp32 + q * PM_MP, piv + i * PM_MP)) : 0.f;
 }
 
-// Query coordinates along the leaf centres' principal directions (FP64
-// sums rounded to FP32) and ||q|| (FP64, rounded up to FP32).  One warp per
-// query.
-__global__ void k_query_pca(const float *__restrict__ Qd, int64_t nq, int ld, const double *__restrict__ P,
+// Query coordinates along the leaf centres' principal directions in FP32
+// (P rounded to FP32, sequential fma over the row; each coordinate within
+// (ld + 2) 2^-24 ||q|| of the exact one, which the verification's slack
+// covers) and ||q|| (FP64, rounded up to FP32).  One thread per query.
+__global__ void k_query_pca(const float *__restrict__ Qd, int64_t nq, int ld, const float *__restrict__ P,
                             float *__restrict__ qpca, float *__restrict__ qnx)
 {
-    const int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    double acc[PM_PCA];
+    const float *x = Qd + q * ld;
+    float acc[PM_PCA];
 #pragma unroll
-    for (int r = 0; r < PM_PCA; r++) acc[r] = 0.0;
+    for (int r = 0; r < PM_PCA; r++) acc[r] = 0.f;
     double nn = 0.0;
-    for (int j = lane; j < ld; j += 32) {
-        const double x = (double)Qd[q * ld + j];
-        nn = fma(x, x, nn);
+    for (int j = 0; j < ld; j++) {
+        const float xv = x[j];
+        nn = fma((double)xv, (double)xv, nn);
 #pragma unroll
-        for (int r = 0; r < PM_PCA; r++) acc[r] = fma(P[(int64_t)r * ld + j], x, acc[r]);
+        for (int r = 0; r < PM_PCA; r++) acc[r] = __fmaf_rn(P[r * ld + j], xv, acc[r]);
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        nn += __shfl_xor_sync(0xffffffffu, nn, o);
-#pragma unroll
-        for (int r = 0; r < PM_PCA; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    }
-    if (lane < PM_PCA) {
-        double v = 0.0;
-#pragma unroll
-        for (int r = 0; r < PM_PCA; r++) v = lane == r ? acc[r] : v;
-        qpca[q * PM_PCA + lane] = (float)v;
-    }
-    if (lane == 0) qnx[q] = __double2float_ru(sqrt(nn));
+    for (int r = 0; r < PM_PCA; r++) qpca[q * PM_PCA + r] = acc[r];
+    qnx[q] = __double2float_ru(sqrt(nn));
 }
 
 // Per-round thresholds for the active queries.
@@ -885,10 +876,13 @@ k_verify(VwArgs A)
         }
         __syncwarp();
         // cheap bounds first: ||P q - P mu|| <= ||q - mu|| for the
-        // orthonormal rows P (FP32 roundings of P q, P mu and the sum covered
+        // orthonormal rows P (the FP32 errors of P q, P mu and the sum covered
         // by the slack); an entry {-(l + 1), bound} holds a cheap bound,
         // {l, bound} the full one
-        const float pSlack = __fmul_rn(0x1.0p-20f, __fadd_rn(A.qnx[q], A.muMax));
+        // slack: FP32 P q ((ld + 2) 2^-24 ||q|| per coordinate, 4 x over 16),
+        // FP32 P mu and the FP32 difference and sum, rounded generously up
+        const float pSlack = __fmul_ru(1.01f, __fadd_ru(__fmul_ru((float)(4 * (ld + 2)) * 0x1.0p-24f, A.qnx[q]),
+                                                        __fmul_ru(0x1.0p-20f, __fadd_ru(A.qnx[q], A.muMax))));
         for (int e0 = 0; e0 < cnt; e0 += 32) {
             const int e = e0 + lane;
             if (e < cnt) {
@@ -1741,8 +1735,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     PM_TRY(pm_project_rows(ix, Q, nq, Qd, qp64, qp32, PM_MP, st));
     const unsigned gq = (unsigned)((nq + 255) / 256);
     PM_LAUNCH("k_query_aux", st, k_query_aux<<<gq, 256, 0, st>>>(qp64, qp32, nq, ix->piv32, ix->s, qnorm, qpiv));
-    PM_LAUNCH("k_query_pca", st, k_query_pca<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(Qd, nq, ld, ix->pcaP,
-                                                                                              qpca, qnx));
+    PM_LAUNCH("k_query_pca", st, k_query_pca<<<gq, 256, 0, st>>>(Qd, nq, ld, ix->pcaP32, qpca, qnx));
     PM_LAUNCH("k_leaf_key", st, k_leaf_key<<<gq, 256, 0, st>>>(qp32, nq, ix->treeI, ix->treeV, key));
     PM_CUDA(cudaMemsetAsync(hist, 0, (L + 1) * sizeof(int), st));
     PM_LAUNCH("k_hist", st, k_hist<<<gq, 256, 0, st>>>(key, nq, hist));
@@ -1752,11 +1745,11 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     // pinned staging of the per-round decisions: order [nq], bounds [2 nq],
     // verification outputs (k-th distance [nq] f64, fp64/verified/leaves
     // counts [3 nq], error flag)
-    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 6) + 64));
+    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 7) + 64));
     double *stDk = (double *)w.stage.p;
     int32_t *stOrder = (int32_t *)(stDk + nq);
     int *stHs = stOrder + nq, *stHp = stHs + nq, *stFp = stHp + nq, *stNv = stFp + nq, *stNl = stNv + nq,
-        *stErr = stNl + nq;
+        *stVo = stNl + nq, *stErr = stVo + nq;
     PM_CUDA(cudaMemcpyAsync(stOrder, order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> orderH;   // host copy, read after the first round's sync
 
@@ -2035,16 +2028,14 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             std::vector<int32_t> cls(na);
             int64_t hist[33] = {0};
             for (int a = 0; a < na; a++) {
-                const int64_t c = (int64_t)hs[a] + hb[a] + 1;
-                int b = 0;
-                while (b < 31 && (c >> (b + 1)) > 0) b++;
+                const uint64_t c = (uint64_t)((int64_t)hs[a] + hb[a] + 1);
+                const int b = std::min(31, 63 - __builtin_clzll(c));   // floor(log2 c)
                 cls[a] = 31 - b;   // costliest class first
                 hist[cls[a] + 1]++;
             }
             for (int b = 0; b < 32; b++) hist[b + 1] += hist[b];
-            std::vector<int32_t> ord(na);
-            for (int a = 0; a < na; a++) ord[hist[cls[a]]++] = a;
-            PM_CUDA(cudaMemcpyAsync(vOrder, ord.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            for (int a = 0; a < na; a++) stVo[hist[cls[a]]++] = a;
+            PM_CUDA(cudaMemcpyAsync(vOrder, stVo, na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         }
         const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, vPerSM * nsm));
         int2 *vLists = grow<int2>(w.partD, (size_t)vGrid * vWarps * L, s);

@@ -94,6 +94,7 @@ struct pmlsh_index {
     // principal directions of the leaf centres (orthonormal rows) and the
     // centres' coordinates along them: ||P q - P mu|| <= ||q - mu||
     double *pcaP = nullptr;      // [PM_PCA][ld] FP64
+    float *pcaP32 = nullptr;     // the same rounded to FP32
     float *leafPmu = nullptr;    // [L][PM_PCA] P mu (FP64 rounded to FP32)
     double muMax = 0.0;          // max ||mu_l|| (FP64)
     // chunks: consecutive runs of <= 32 points inside a leaf, with their own
