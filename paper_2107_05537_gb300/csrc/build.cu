@@ -263,11 +263,37 @@ __global__ void k_sample_dist(const float *__restrict__ X, int ld, int d,
 
 }  // namespace
 
+// Query batches: one thread per (row, direction), the same sequential fma
+// over the columns as k_project64, so the coordinates are bit-identical;
+// a batch of 10^4 rows then fills the GPU instead of 79 blocks.
+__global__ void k_project64_rows(const float *__restrict__ X, int64_t n, int ld, int d, int m,
+                                 const float *__restrict__ A, double *__restrict__ O64, float *__restrict__ O32,
+                                 int ostride)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * ostride) return;
+    const int64_t p = e / ostride;
+    const int j = (int)(e % ostride);
+    double acc = 0.0;
+    if (j < m) {
+        const float *x = X + p * ld, *a = A + (int64_t)j * ld;
+        for (int c = 0; c < d; c++) acc = __fma_rn((double)a[c], (double)x[c], acc);
+    }
+    if (O64) O64[p * ostride + j] = acc;
+    if (O32) O32[p * ostride + j] = __double2float_rn(acc);
+}
+
 void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const float *A,
                          double *O64, float *O32, unsigned long long *maxNormBits,
                          cudaStream_t st, int ostride)
 {
     if (n <= 0) return;
+    if (!maxNormBits && n * ostride <= ((int64_t)1 << 22)) {
+        const int64_t tot = n * ostride;
+        PM_LAUNCH("k_project64_rows", st, k_project64_rows<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, n, ld, d, m, A,
+                                                                                                    O64, O32, ostride));
+        return;
+    }
     int grid = (int)((n + PROJ_PTS - 1) / PROJ_PTS);
     PM_LAUNCH("k_project64", st, k_project64<<<grid, PROJ_PTS, 0, st>>>(X, n, ld, d, m, A, O64, O32, ostride, maxNormBits));
 }
