@@ -571,10 +571,23 @@ constexpr unsigned VW_FULL = 0xffffffffu;
 // instruction of the warp covers whole 128-byte lines of four rows; the
 // eight partial sums are added by a butterfly.  Requires ld % 32 == 0 with
 // zero padding columns in q and in the rows.
+// Prefetch hint for the line holding global address p (no fault, no result).
+__device__ __forceinline__ void pm_prefetch_l2(const void *p)
+{
+    asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L2 [ga];\n\t}" ::"l"(p));
+}
+
 __device__ __forceinline__ float warp_d2(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
 {
     const int grp = lane >> 3, g = lane & 7;
     float keep = 0.f;
+    // the loop below reads the 32 rows 4 at a time; an L2 prefetch of every
+    // line of the lane's own row first puts all 32 rows' misses in flight at
+    // once, so later groups find their lines in L2
+    if (p != nullptr) {
+        const char *pc = (const char *)p;
+        for (int b = 0; b < nf4 * 16; b += 128) pm_prefetch_l2(pc + b);
+    }
 #pragma unroll 1
     for (int j = 0; j < 8; j++) {
         const float4 *x4 = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 4 * j);
