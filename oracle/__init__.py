@@ -73,6 +73,9 @@ def lib():
         L.orc_exact_kcp.restype = i32
         L.orc_exact_kcp.argtypes = [p, i64, i32, i64, p, p]
         L.orc_node_ball.argtypes = [p, i32, p, i64, i64, p, p]
+        L.orc_distance_sample.argtypes = [p, i64, i32, u64, i64, p]
+        L.orc_cost_model.argtypes = [p, i64, i64, p, p, i32, p, p, d, p]
+        L.orc_cost_model.restype = d
         L.orc_cp_radius_filter.restype = i32
         L.orc_cp_radius_filter.argtypes = [p, p, i64, i32, i32, p, p, i64,
                                            p, p, p, p, i64, i64, d, d, i64,
@@ -268,6 +271,31 @@ def cp_radius_filter(X, A32, layout, k, t, gamma, T, Oproj=None):
         raise ValueError("orc_cp_radius_filter rejected its arguments")
     return dict(pairs=pairs, dists=dists, count=cnt.value, ub_self=ubs.value,
                 nodes=nodes.value, nodes_done=done.value)
+
+
+def distance_sample(Oproj, npairs, seed):
+    """Sec. 4.2: sorted FP64 projected distances of `npairs` sampled pairs
+    (the sample whose empirical CDF estimates F(x) = Pr[||o_i, o_j|| <= x])."""
+    Oproj = np.ascontiguousarray(Oproj, dtype=np.float64)
+    n, m = Oproj.shape
+    out = np.empty(int(npairs), dtype=np.float64)
+    lib().orc_distance_sample(_ptr(Oproj), n, m, seed, int(npairs), _ptr(out))
+    return out
+
+
+def cost_model(F, count, radius, hr_min, hr_max, rq):
+    """Sec. 4.2: (CC, sum of Pr[e]) of range(q, rq) over the nodes given by
+    their entry counts [nn], radii [nn] and pivot rings [nn][s]."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    count = np.ascontiguousarray(count, dtype=np.int64)
+    radius = np.ascontiguousarray(radius, dtype=np.float64)
+    hr_min = np.ascontiguousarray(hr_min, dtype=np.float64).reshape(len(count), -1)
+    hr_max = np.ascontiguousarray(hr_max, dtype=np.float64).reshape(len(count), -1)
+    s = hr_min.shape[1]
+    en = ctypes.c_double()
+    cc = lib().orc_cost_model(_ptr(F), len(F), len(count), _ptr(count), _ptr(radius), s,
+                              _ptr(hr_min), _ptr(hr_max), float(rq), ctypes.byref(en))
+    return cc, en.value
 
 
 def overall_ratio(dists, exact_dists):

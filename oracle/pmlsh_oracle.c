@@ -34,6 +34,12 @@
  *                           hierarchy of leaves
  *   orc_node_ball ......... node ball (e.RO, e.r) of Sec. 4.1 for the given
  *                           hierarchy
+ *   orc_distance_sample ... Sec. 4.2, distance distribution F(x) =
+ *                           Pr[||o_i, o_j|| <= x], estimated from sampled
+ *                           pairs in the projected space
+ *   orc_cost_model ........ Sec. 4.2, node access probability Pr[e] and the
+ *                           computation cost CC(range(q, r_q)) of the PM-tree
+ *                           cost model, on given node entries
  */
 #include <math.h>
 #include <stdint.h>
@@ -652,6 +658,64 @@ int orc_cp_radius_filter(const float *X, const double *Oproj, int64_t n, int d, 
     }
     free(leaf_of); free(A); free(nrad); free(tk.v);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cost model of the PM-tree (Sec. 4.2)                                      */
+
+/* F(x) = Pr[||o_i, o_j|| <= x] over pairs of D, in the projected space where
+ * the tree lives.  Reading used here: `npairs` pairs drawn from the counter
+ * generator stream `seed` exactly as orc_rmin_auto draws them (i from counter
+ * 2s, j from 2s + 1, both mod n, j = i moved to i + 1 mod n), the FP64
+ * projected distance of each, sorted ascending.  The estimate of F is the
+ * empirical CDF of this sample.                                             */
+void orc_distance_sample(const double *Oproj, int64_t n, int m, uint64_t seed, int64_t npairs,
+                         double *out_sorted)
+{
+    for (int64_t s = 0; s < npairs; s++) {
+        int64_t i = (int64_t)(orc_splitmix64(seed, 2 * (uint64_t)s) % (uint64_t)n);
+        int64_t j = (int64_t)(orc_splitmix64(seed, 2 * (uint64_t)s + 1) % (uint64_t)n);
+        if (j == i) j = (j + 1) % n;
+        out_sorted[s] = pdist64(Oproj + i * (int64_t)m, Oproj + j * (int64_t)m, m);
+    }
+    qsort(out_sorted, (size_t)npairs, sizeof(double), cmp_double);
+}
+
+/* Empirical CDF: the fraction of the sorted sample F[0..nF) that is <= x.   */
+static double ecdf(const double *F, int64_t nF, double x)
+{
+    int64_t lo = 0, hi = nF;   /* first index with F[idx] > x */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (F[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return (double)lo / (double)nF;
+}
+
+/* A node e is accessed by range(q, r_q) iff ||q, e.RO|| <= e.r + r_q and,
+ * for every pivot p_i, ||q, p_i|| - r_q <= e.HR[i].max and
+ * ||q, p_i|| + r_q >= e.HR[i].min.  With F standing for the distribution of
+ * each of those query distances:
+ *   Pr[e] = F(e.r + r_q) * prod_i (F(e.HR[i].max + r_q) - F(e.HR[i].min - r_q)),
+ *   CC    = sum_e N(e) Pr[e].
+ * Nodes are given by their entry counts N(e) [nn], radii [nn] and rings
+ * hr_min, hr_max [nn][s].  Returns CC; *expected_nodes = sum_e Pr[e].        */
+double orc_cost_model(const double *F, int64_t nF, int64_t nn, const int64_t *count, const double *radius,
+                      int s, const double *hr_min, const double *hr_max, double rq, double *expected_nodes)
+{
+    double cc = 0.0, en = 0.0;
+    for (int64_t e = 0; e < nn; e++) {
+        double pr = ecdf(F, nF, radius[e] + rq);
+        for (int i = 0; i < s; i++) {
+            double hi = ecdf(F, nF, hr_max[e * s + i] + rq);
+            double lo = ecdf(F, nF, hr_min[e * s + i] - rq);
+            pr = pr * (hi - lo);
+        }
+        cc = cc + (double)count[e] * pr;
+        en = en + pr;
+    }
+    if (expected_nodes) *expected_nodes = en;
+    return cc;
 }
 
 int orc_num_threads(void)

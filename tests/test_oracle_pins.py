@@ -437,3 +437,84 @@ def test_cp_bnb_against_numpy_brute_force():
     pb, db = oracle.cp_bnb(X, A, T, k)
     assert np.array_equal(pb, np.stack([i[sel][top], j[sel][top]], 1))
     assert np.allclose(db, od[top], rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------- cost model (Sec. 4.2)
+def test_cost_model_hand_example():
+    # Two nodes, two pivots, F the empirical CDF of {1..8}: values worked by
+    # hand from Pr[e] and CC (tests/golden/cost_model_example.json), exact
+    # binary fractions; the second radius puts arguments on sample values.
+    g = golden("cost_model_example.json")
+    for c in g["cases"]:
+        cc, en = oracle.cost_model(g["F_sample"], g["count"], g["radius"], g["hr_min"], g["hr_max"], c["rq"])
+        assert cc == c["cc"] and en == c["expected_nodes"]
+
+
+def test_cost_model_unbounded_radius_accesses_every_node():
+    # r_q beyond every distance: each factor of Pr[e] is 1 - 0 or 1, so every
+    # node is accessed and CC = sum N(e) = n.
+    rng = np.random.default_rng(3)
+    F = np.sort(rng.uniform(0, 10, 500))
+    cnt = rng.integers(1, 300, 40)
+    rad = rng.uniform(0, 3, 40)
+    lo = rng.uniform(0, 5, (40, 4))
+    hi = lo + rng.uniform(0, 5, (40, 4))
+    cc, en = oracle.cost_model(F, cnt, rad, lo, hi, 1e6)
+    assert cc == float(cnt.sum()) and en == 40.0
+
+
+def test_cost_model_point_nodes_without_pivots():
+    # s = 0 and nodes of radius 0: Pr[e] = F(r_q), CC = n F(r_q); F from
+    # numpy's sorted search (the empirical CDF counts samples <= x).
+    rng = np.random.default_rng(4)
+    F = np.sort(rng.exponential(2.0, 1000))
+    cnt = rng.integers(1, 50, 30)
+    n = int(cnt.sum())
+    for rq in (0.0, 0.3, F[17], 1.9, F[999], 50.0):
+        cc, en = oracle.cost_model(F, cnt, np.zeros(30), np.zeros((30, 0)), np.zeros((30, 0)), rq)
+        Fq = np.searchsorted(F, rq, side="right") / len(F)
+        assert cc == pytest.approx(n * Fq, rel=1e-14) and en == pytest.approx(30 * Fq, rel=1e-14)
+
+
+def test_cost_model_single_point_nodes_equal_brute_force_range_count():
+    # With one point per node, no pivots and F taken over all ordered pairs
+    # (i != j), CC = n F(r_q) = n/(n-1) times the mean number of other points
+    # within r_q of a query drawn from D: brute force over all pairs.
+    rng = np.random.default_rng(5)
+    O = rng.normal(size=(60, 5))
+    D = np.sqrt(((O[:, None, :] - O[None, :, :]) ** 2).sum(-1))
+    off = D[~np.eye(60, dtype=bool)]
+    F = np.sort(off)
+    for rq in (0.5, 1.5, 2.5, 4.0):
+        cc, _ = oracle.cost_model(F, np.ones(60, dtype=np.int64), np.zeros(60), np.zeros((60, 0)),
+                                  np.zeros((60, 0)), rq)
+        mean_count = ((D <= rq).sum(1) - 1).mean()
+        assert cc == pytest.approx(60 / 59 * mean_count, rel=1e-12)
+
+
+def test_distance_sample_two_points_and_brute_force():
+    # two points at distance 5: every sampled pair is (0, 1) or (1, 0)
+    O = np.array([[0.0, 0.0], [3.0, 4.0]])
+    v = oracle.distance_sample(O, 200, 11)
+    assert np.all(v == 5.0)
+    # the sampled pairs recomputed with numpy norms, sorted
+    rng = np.random.default_rng(6)
+    O = rng.normal(size=(97, 15)) * 10
+    npairs, seed = 3000, 21
+    v = oracle.distance_sample(O, npairs, seed)
+    ref = []
+    for s in range(npairs):
+        i = oracle.splitmix64(seed, 2 * s) % 97
+        j = oracle.splitmix64(seed, 2 * s + 1) % 97
+        if j == i:
+            j = (j + 1) % 97
+        ref.append(np.linalg.norm(O[i] - O[j]))
+    assert np.all(np.diff(v) >= 0)
+    np.testing.assert_allclose(v, np.sort(ref), rtol=1e-13)
+
+
+def test_splitmix64_published_outputs():
+    # the first three outputs of SplitMix64 (Steele, Lea, Flood, OOPSLA 2014)
+    # from state 0, as published with its reference implementation
+    assert [oracle.splitmix64(0, i) for i in range(3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
