@@ -74,7 +74,13 @@ typedef struct {
                            for M = 128, 256 and 512, pmlsh_knn with the
                            default options is timed on up to 1,024 rows of X
                            (an even stride) as queries, and the fastest index
-                           is kept (pmlsh_index_info reports its M) */
+                           is kept (pmlsh_index_info reports its M);
+                           -1 = chosen by the cost model of Sec. 4.2: of
+                           the same candidates, the index with the fewest
+                           modelled distance computations per query,
+                           L + CC(range(q, t r_min)) (pmlsh_cost_model, F
+                           from 65,536 pairs of stream seed + 6, t and r_min
+                           for the default query options) */
     int cp_leaf_size;   /* unused by pmlsh_build; see pmlsh_cp_opts */
     uint64_t seed;      /* the projection uses stream seed+2 of the
                            counter-based SplitMix64 generator with the
@@ -99,7 +105,7 @@ void pmlsh_build_opts_default(pmlsh_build_opts *o);
  *   pmlsh_closest_pair), samples the distance distribution for r_min and
  *   keeps a permuted device copy of X.  X is not referenced afterwards.
  * Errors: EINVAL (NULL pointers, n < 1, d < 1, m outside 1..16, s outside
- *   0..8, leaf_size outside 0 or 16..1024, n >= 2^31), ENOMEM, ECUDA.
+ *   0..8, leaf_size outside 0, -1 or 16..1024, n >= 2^31), ENOMEM, ECUDA.
  * On success *out owns device memory until pmlsh_free(*out). */
 pmlsh_status pmlsh_build(const float *X, int64_t n, int d,
                          const pmlsh_build_opts *opts, void *stream,
@@ -129,6 +135,52 @@ pmlsh_status pmlsh_export_layout(const pmlsh_index *index, int32_t *perm,
                                  int64_t *leaf_off, int64_t *node_lo,
                                  int64_t *node_hi, int32_t *node_left,
                                  int32_t *node_right);
+
+/* Exports the PM-tree entry of every leaf (Sec. 4.1: e.RO, e.r, e.HR[i]) as
+ * the index uses it in the Eq. 5 test, to host buffers (L from
+ * pmlsh_index_info, m the projection count):
+ *   s                    number of pivots
+ *   centre [L][m]        routing object RO (FP32)
+ *   radius [L]           covering radius r (FP32, rounded up so that it
+ *                        covers the FP32 coordinates of the leaf's points)
+ *   ring_min, ring_max [L][s]  HR[i].min / HR[i].max, widened by 1e-5
+ *   pivots [s][m]        the pivots p_i.
+ * Any pointer may be NULL.  EINVAL (NULL index), ECUDA. */
+pmlsh_status pmlsh_export_leaf_entries(const pmlsh_index *index, int *s,
+                                       float *centre, float *radius,
+                                       float *ring_min, float *ring_max,
+                                       float *pivots);
+
+/* ------------------------------------------------------------- cost model */
+
+/* Sec. 4.2 (cost model of the PM-tree): a sample of the distance
+ * distribution F(x) = Pr[||o_i, o_j|| <= x] of the indexed points in the
+ * projected space.  Pair s has ids i = v_{2s} mod n and j = v_{2s+1} mod n,
+ * v the counter-based SplitMix64 stream `seed` (j = i is moved to
+ * i + 1 mod n); each distance is the FP64 Euclidean distance of the FP64
+ * projected coordinates (sequential sum, correctly rounded square root).
+ * out_sorted [npairs] FP64 (host or device, caller-owned) receives the
+ * distances in ascending order; its empirical CDF is the estimate of F.
+ * EINVAL (n < 2, npairs outside 1..2^28), ENOMEM, ECUDA. */
+pmlsh_status pmlsh_distance_sample(const pmlsh_index *index, int64_t npairs,
+                                   uint64_t seed, double *out_sorted,
+                                   void *stream);
+
+/* Sec. 4.2: for each radius rq[r] (projected space, >= 0), the cost model's
+ *   Pr[e] = F(e.r + rq) * prod_i (F(e.HR[i].max + rq) - F(e.HR[i].min - rq))
+ * over the index's leaves e (their entries as pmlsh_export_leaf_entries
+ * gives them, widened to FP64), and
+ *   out_cc[r]    = CC(range(q, rq)) = sum_e N(e) Pr[e]   (N(e): leaf size),
+ *   out_nodes[r] = sum_e Pr[e]                           (expected leaves).
+ * F is the empirical CDF (fraction of entries <= x) of F_sorted [nF] FP64,
+ * ascending and finite, e.g. from pmlsh_distance_sample.  F_sorted, rq [nr]
+ * and the outputs [nr] may be host or device (caller-owned); either output
+ * may be NULL.  The leaves are summed on the device in a fixed order.
+ * EINVAL (F not ascending or not finite, nF outside 1..2^28, nr outside
+ * 0..65535, rq < 0 or NaN), ENOMEM, ECUDA. */
+pmlsh_status pmlsh_cost_model(const pmlsh_index *index, const double *F_sorted,
+                              int64_t nF, const double *rq, int64_t nr,
+                              double *out_cc, double *out_nodes, void *stream);
 
 /* Projects the rows of Q [nq][d] (FP32, host or device) onto the index's m
  * directions (Eq. 3, the first step of Algorithm 2): out64 [nq][m] holds the

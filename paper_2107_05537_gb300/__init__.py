@@ -92,6 +92,9 @@ _SIGS = {
     "pmlsh_get_projection": (ctypes.c_int, [_P, _P]),
     "pmlsh_get_projected": (ctypes.c_int, [_P, _P]),
     "pmlsh_export_layout": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_export_leaf_entries": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmlsh_distance_sample": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
+    "pmlsh_cost_model": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_project": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_project_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     "pmlsh_knn_opts_default": (None, [_P]),
@@ -256,6 +259,42 @@ class Index:
                                          ptr(nl), ptr(nr)))
         return dict(perm=perm, leaf_off=loff, node_lo=nlo, node_hi=nhi, node_left=nl,
                     node_right=nr)
+
+    def leaf_entries(self):
+        """PM-tree entries of the leaves (Sec. 4.1) as the Eq. 5 test uses
+        them: dict of centre [L, m], radius [L], ring_min / ring_max [L, s],
+        pivots [s, m] (FP32) and s."""
+        ns = ctypes.c_int()
+        _check(lib().pmlsh_export_leaf_entries(self._h, ctypes.byref(ns), None, None, None, None, None))
+        s = ns.value
+        centre = np.empty((self.leaves, self.m), dtype=np.float32)
+        radius = np.empty(self.leaves, dtype=np.float32)
+        rmin = np.empty((self.leaves, s), dtype=np.float32)
+        rmax = np.empty((self.leaves, s), dtype=np.float32)
+        piv = np.empty((s, self.m), dtype=np.float32)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().pmlsh_export_leaf_entries(self._h, None, ptr(centre), ptr(radius), ptr(rmin), ptr(rmax),
+                                               ptr(piv)))
+        return dict(s=s, centre=centre, radius=radius, ring_min=rmin, ring_max=rmax, pivots=piv)
+
+    def distance_sample(self, npairs=65536, seed=0):
+        """Sec. 4.2: sorted FP64 projected distances of `npairs` sampled
+        pairs (the sample whose empirical CDF estimates F)."""
+        out = np.empty(int(npairs), dtype=np.float64)
+        _check(lib().pmlsh_distance_sample(self._h, int(npairs), int(seed), out.ctypes.data_as(ctypes.c_void_p),
+                                           _stream()))
+        return out
+
+    def cost_model(self, F_sorted, rq):
+        """Sec. 4.2: (CC [nr], sum of Pr[e] [nr]) of range(q, rq) over the
+        leaves, F the empirical CDF of F_sorted."""
+        F = np.ascontiguousarray(F_sorted, dtype=np.float64)
+        r = np.ascontiguousarray(np.atleast_1d(rq), dtype=np.float64)
+        cc = np.empty(len(r), dtype=np.float64)
+        en = np.empty(len(r), dtype=np.float64)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(lib().pmlsh_cost_model(self._h, ptr(F), len(F), ptr(r), len(r), ptr(cc), ptr(en), _stream()))
+        return cc, en
 
     def project(self, Q):
         """Eq. 3 for query rows: returns (FP64 [nq, m], FP32 [nq, m]) on the

@@ -212,6 +212,53 @@ pmlsh_status build_autotuned(const float *X, int64_t n, int d, pmlsh_build_opts 
     return PMLSH_OK;
 }
 
+// Leaf-size choice by the cost model of Sec. 4.2: builds the index for each
+// candidate capacity and keeps the one with the fewest modelled distance
+// computations per query, L (one Eq. 5 test per leaf) + CC(range(q, R)),
+// at the first-round radius R = t r_min of a query with the default options
+// (k = 10, c = 1.5, alpha1 = 1/e, beta = 0.2809), F estimated from 65,536
+// sampled pairs (stream seed + 6).
+pmlsh_status build_model_tuned(const float *X, int64_t n, int d, pmlsh_build_opts o, cudaStream_t st,
+                               pmlsh_index **out)
+{
+    static const int cand[] = {128, 256, 512};
+    pmlsh_knn_opts ko;
+    pmlsh_knn_opts_default(&ko);
+    ko.k = (int)std::min<int64_t>(10, n);
+    const double t = std::sqrt(pm_chi2_upper_quantile(ko.alpha1, o.m));
+    pmlsh_index *best = nullptr;
+    double bestW = INFINITY;
+    for (int M : cand) {
+        if (M > n && best) break;
+        o.leaf_size = M;
+        pmlsh_index *ix = nullptr;
+        pmlsh_status s = build_one(X, n, d, o, st, &ix);
+        double W = 0.0;
+        if (s == PMLSH_OK && n >= 2) {
+            std::vector<double> F;
+            s = pm_distance_sample(ix, std::min<int64_t>(65536, n * (n - 1)), o.seed + 6, F, st);
+            const double R = t * pm_rmin_rule(ix, ko.beta, ko.k, ko.c);
+            double cc = 0.0;
+            if (s == PMLSH_OK) s = pm_cost_model(ix, F.data(), (int64_t)F.size(), &R, 1, &cc, nullptr, st);
+            W = (double)ix->L + cc;
+        }
+        if (s != PMLSH_OK) {
+            if (ix) pmlsh_free(ix);
+            if (best) pmlsh_free(best);
+            return s;
+        }
+        if (W < bestW) {
+            if (best) pmlsh_free(best);
+            best = ix;
+            bestW = W;
+        } else {
+            pmlsh_free(ix);
+        }
+    }
+    *out = best;
+    return PMLSH_OK;
+}
+
 }  // namespace
 
 pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opts *opts, void *stream,
@@ -227,11 +274,12 @@ pmlsh_status pmlsh_build(const float *X, int64_t n, int d, const pmlsh_build_opt
     else pmlsh_build_opts_default(&o);
     PM_CHECK(o.m >= 1 && o.m <= PM_MP, "m must be in 1..16 (got %d)", o.m);
     PM_CHECK(o.s >= 0 && o.s <= PM_MAX_PIVOTS, "s must be in 0..8 (got %d)", o.s);
-    PM_CHECK(o.leaf_size == 0 || (o.leaf_size >= 16 && o.leaf_size <= 1024),
-             "leaf_size must be 0 or 16..1024 (got %d)", o.leaf_size);
+    PM_CHECK(o.leaf_size == 0 || o.leaf_size == -1 || (o.leaf_size >= 16 && o.leaf_size <= 1024),
+             "leaf_size must be 0, -1 or 16..1024 (got %d)", o.leaf_size);
     PM_CHECK(o.rmin_pairs >= 0, "rmin_pairs must be >= 0");
     PM_CHECK(o.bf16_shadow == 0 || o.bf16_shadow == 1, "bf16_shadow must be 0 or 1");
     if (o.leaf_size == 0) return build_autotuned(X, n, d, o, (cudaStream_t)stream, out);
+    if (o.leaf_size == -1) return build_model_tuned(X, n, d, o, (cudaStream_t)stream, out);
     return build_one(X, n, d, o, (cudaStream_t)stream, out);
 }
 

@@ -167,12 +167,35 @@ pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *o
 pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
                              pmlsh_cp_stats *stats, cudaStream_t st);
 
+// Cost model of Sec. 4.2 (cost.cu)
+// Sorted FP64 projected distances of `npairs` sampled pairs (host vector).
+pmlsh_status pm_distance_sample(const pmlsh_index *ix, int64_t npairs, uint64_t seed, std::vector<double> &out,
+                                cudaStream_t st);
+// CC and sum of Pr[e] over the leaves for each radius rq[r]; F and rq on the
+// host, F sorted ascending.
+pmlsh_status pm_cost_model(const pmlsh_index *ix, const double *F, int64_t nF, const double *rq, int64_t nr,
+                           double *cc, double *nodes, cudaStream_t st);
+// The r_min rule of Sec. 5.2 for a query with these options.
+double pm_rmin_rule(const pmlsh_index *ix, double beta, int64_t k, double c);
+
 // Parameters (params.cpp)
 double pm_chi2_sf(double x, int m);
 double pm_chi2_upper_quantile(double alpha, int m);
 
 // Counter-based SplitMix64 (rng.cpp)
 uint64_t pm_splitmix64(uint64_t seed, uint64_t i);
+// The same generator for device code: value i of stream `seed` is the
+// SplitMix64 finaliser of seed + (i + 1) * 0x9E3779B97F4A7C15.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint64_t pm_splitmix64_hd(uint64_t seed, uint64_t i)
+{
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
 void pm_gaussian_projection(uint64_t seed, int m, int d, float *A);
 
 bool pm_is_device_ptr(const void *p);
