@@ -76,3 +76,19 @@ def test_argument_validation_needs_no_gpu():
     bo.m = 17
     assert L.pmlsh_build(ctypes.cast(x, ctypes.c_void_p), 1, 4, ctypes.byref(bo), None,
                          ctypes.byref(h)) == 1
+
+
+def test_cost_model_argument_validation_needs_no_gpu():
+    L = pm.lib()
+    h = ctypes.c_void_p()
+    x = (ctypes.c_float * 4)()
+    bo = pm.BuildOpts()
+    L.pmlsh_build_opts_default(ctypes.byref(bo))
+    bo.leaf_size = -2          # only 0 (measured), -1 (cost model) or 16..1024
+    assert L.pmlsh_build(ctypes.cast(x, ctypes.c_void_p), 1, 4, ctypes.byref(bo), None,
+                         ctypes.byref(h)) == 1
+    assert b"leaf_size" in L.pmlsh_last_error()
+    out = (ctypes.c_double * 4)()
+    assert L.pmlsh_distance_sample(None, 4, 0, ctypes.cast(out, ctypes.c_void_p), None) == 1
+    assert L.pmlsh_cost_model(None, ctypes.cast(out, ctypes.c_void_p), 4, None, 0, None, None, None) == 1
+    assert L.pmlsh_export_leaf_entries(None, None, None, None, None, None, None) == 1
