@@ -98,7 +98,8 @@ struct pmlsh_server {
                         std::vector<size_t> pick;
                         for (size_t i = 0; i < queue.size(); i++) {
                             const Request &r = *queue[i];
-                            if (!same_opts(r.opts, o)) continue;
+                            // the oldest request always rides (whatever its options)
+                            if (i > 0 && !same_opts(r.opts, o)) continue;
                             if (!pick.empty() && rows + r.nq > opts.max_batch_queries) break;
                             pick.push_back(i);
                             rows += r.nq;
@@ -211,8 +212,9 @@ pmlsh_status pmlsh_serve_submit(pmlsh_server *s, const float *Q, int64_t nq, con
         return PMLSH_EINVAL;
     }
     const pmlsh_knn_opts &o = *opts;
-    if (o.k < 1 || o.k > PM_MAX_K || o.k > s->ix->n || !(o.c > 1.0) || !(o.beta > 0.0 && o.beta <= 1.0) ||
-        !(o.alpha1 > 0.0 && o.alpha1 < 1.0) ||
+    if (o.k < 1 || o.k > PM_MAX_K || o.k > s->ix->n || !(o.c > 1.0) || !std::isfinite(o.c) ||
+        !(o.beta > 0.0 && o.beta <= 1.0) || !(o.alpha1 > 0.0 && o.alpha1 < 1.0) || !std::isfinite(o.r_min) ||
+        !std::isfinite(o.t) ||
         (o.precision != PMLSH_FP32_PLAIN && !(o.precision == PMLSH_BF16_TENSOR && s->ix->Bsplit)) ||
         (o.stop_rule != PMLSH_STOP_LITERAL && o.stop_rule != PMLSH_STOP_BC_CONSISTENT)) {
         pm_set_error("invalid query options");

@@ -163,3 +163,21 @@ def test_c5_serving_full_size():
     assert np.array_equal(outs[0][0][:4], ref["ids"])
     assert np.array_equal(outs[0][1][:4], ref["dists"].astype(np.float32))
     ix.close()
+
+
+def test_non_finite_options_rejected_and_server_keeps_serving(served):
+    # options that pmlsh_knn rejects are rejected at submit; a request whose
+    # options equal no other (NaN compares unequal) could otherwise never be
+    # batched, so the server must keep serving after such attempts
+    ix, Q = served
+    srv = pm.Server(ix, slots=2, max_batch_queries=512)
+    for bad in (dict(r_min=float("nan")), dict(t=float("nan")), dict(c=float("inf")),
+                dict(r_min=float("inf"))):
+        with pytest.raises(pm.PmlshError):
+            srv.submit(Q[:4], k=5, **bad)
+    rows = np.ascontiguousarray(Q[:37])
+    ids, dd = srv.wait(srv.submit(rows, k=5), timeout_ms=60_000)
+    srv.close()
+    alone = ix.knn(rows, k=5, with_stats=False)
+    np.testing.assert_array_equal(ids, alone["ids"])
+    np.testing.assert_array_equal(dd, alone["dists"])
