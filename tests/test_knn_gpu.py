@@ -138,6 +138,19 @@ def test_shapes_and_edges(n, d, m, leaf, s, k):
         _assert_parity(got, ref)
 
 
+@pytest.mark.parametrize("precision", [pm.PMLSH_FP32_PLAIN, pm.PMLSH_BF16_TENSOR])
+@pytest.mark.parametrize("n,d,m,leaf,s,k,nq", [
+    (1, 4, 15, 16, 5, 1, 5),           # a single point
+    (700, 1, 1, 16, 3, 9, 40),         # d = 1, m = 1
+    (600, 24, 15, 64, 5, 256, 20),     # the largest k
+])
+def test_extreme_shapes(n, d, m, leaf, s, k, nq, precision):
+    X, Q, _, _ = datagen.mixture(n, d, min(7, n), 1.0, seed=n + d, nq=nq)
+    A = oracle.gen_projection(11, m, d).astype(np.float32)
+    got, ref = _run_both(X, Q, A, k=k, leaf=leaf, s=s, beta=0.1, precision=precision)
+    _assert_parity(got, ref)
+
+
 def test_duplicate_points_tie_by_id():
     # 40 copies of each of 25 points: every distance ties 40 ways
     base, Q, _, _ = datagen.mixture(25, 16, 5, 1.0, seed=3, nq=20)
