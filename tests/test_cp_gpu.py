@@ -173,3 +173,21 @@ def test_cp_bnb_c4_full_size():
     ex = np.sqrt(((X[got["pairs"][:, 0]].astype(np.float64) - X[got["pairs"][:, 1]].astype(np.float64)) ** 2).sum(1))
     assert np.allclose(got["dists"], ex, rtol=1e-6, atol=0)
     assert got["pairs"].tolist() == rf["pairs"].tolist()
+
+
+@pytest.mark.parametrize("n,k,leaf", [
+    (2, 1, 16),          # a single pair
+    (3, 3, 16),          # k = n (n - 1) / 2
+    (120, 1024, 16),     # the largest k (7,140 pairs)
+])
+def test_cp_extremes_both_algorithms(n, k, leaf):
+    X, _, _, _ = datagen.mixture(n, 10, min(3, n), 1.0, seed=n + 5)
+    A = oracle.gen_projection(12, 15, 10).astype(np.float32)
+    T = 10 ** 9
+    got, ref = _both(X, A, k, 3.0, T, leaf=leaf)
+    _assert_same(got, ref)
+    got, rp, rd = _bnb_both(X, A, k, T, leaf)
+    assert got["pairs"].tolist() == rp.tolist()
+    assert np.array_equal(got["dists"], rd.astype(np.float32))
+    ep, ed = oracle.exact_kcp(X, k)
+    assert got["pairs"].tolist() == ep.tolist()
