@@ -153,9 +153,35 @@ def cpu_baseline(X, Q, A, budget_s=15.0):
     t0 = time.perf_counter()
     oracle.knn(X, A, Q[:ns], K, C, t, B, rmin, 0, Oproj=O)
     el = time.perf_counter() - t0
+    # one query per call: the oracle parallelises over queries, so this is
+    # the single-thread time per query
+    single = 8
+    t0 = time.perf_counter()
+    for i in range(single):
+        oracle.knn(X, A, Q[i:i + 1], K, C, t, B, rmin, 0, Oproj=O)
+    st_ms = (time.perf_counter() - t0) * 1000 / single
     return {"value": ns / el, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "first %d of the %d queries (FP64 Algorithm 2, OpenMP over queries), "
-                      "%.1f s" % (ns, len(Q), el)}
+                      "%.1f s" % (ns, len(Q), el),
+            "single_thread_ms_per_query": st_ms, "cpu": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, else implementer
+    and part), with the machine type."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "CPU part"):
+            vals = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(key)]
+            if vals:
+                name = vals[0] if key == "model name" else "CPU part " + vals[0]
+                break
+    except OSError:
+        pass
+    return ("%s (%s)" % (name, platform.machine())).strip() if name else platform.machine()
 
 
 def run_reference(args, ws, rank):
@@ -186,7 +212,7 @@ def run_reference(args, ws, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(per_step) + " (sample of %d queries per step)" % per_step},
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": oracle.num_threads(),
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu": cpu_model(),
                              "sample": "%d queries per step, %d steps" % (per_step, args.steps)},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -418,6 +444,14 @@ def main():
                          "algorithmic_bytes_per_launch": alg / launches_dom,
                          "avg_launch_ms": ms_dom / launches_dom})
         roof["kernels"] = {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in prof.items()}
+        # DRAM GB/s of each kernel with captured traffic (ncu bytes per query
+        # scaled to the timed queries; the capture's source must be unchanged)
+        for k2, tr2 in traffic_record().items():
+            if k2 in prof and isinstance(tr2, dict) and tr2.get("sha256") == source_sha(tr2["source"]):
+                b2 = tr2["dram_bytes_per_query"] * nq * args.steps
+                roof["kernels"][k2].update({"dram_bytes_per_launch": b2 / prof[k2][0],
+                                            "dram_gbs": b2 / (prof[k2][1] / 1000.0) / 1e9,
+                                            "dram_frac": b2 / (prof[k2][1] / 1000.0) / 1e9 / pk["hbm_gbs"]})
         roof["peak_kind"] = pk_kind
 
     # serving: open-loop Poisson stream on the resident index, both precisions
