@@ -73,35 +73,78 @@ def max_over_ranks(v, ws):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region: start()
+    returns once the first sample has arrived (so the sampler is running when
+    the region begins), begin()/end() mark the region, and stop() summarises
+    the samples taken inside it (with the first one after it, which still
+    describes its last interval)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=100, exe="nvidia-smi"):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
+        self.exe = exe
         self.p = None
+        self.lines = []
+        self.t0 = self.t1 = None
+        self.reader = None
 
-    def start(self):
+    def _read(self):
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+            for line in self.p.stdout:
+                self.lines.append((time.perf_counter(), line))
+        except Exception:
+            pass
+
+    def start(self, wait_s=5.0):
+        import threading
+        try:
+            self.p = subprocess.Popen([self.exe, "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            t = time.perf_counter()
+            while not self.lines and time.perf_counter() - t < wait_s and self.p.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.p = None
+
+    def begin(self):
+        self.t0 = time.perf_counter()
+
+    def end(self):
+        self.t1 = time.perf_counter()
 
     def stop(self):
         if self.p is None:
             return None
-        self.p.terminate()
         try:
-            out, _ = self.p.communicate(timeout=5)
+            # one more sample after the region closes
+            t = time.perf_counter()
+            while (self.t1 is not None and not any(ts > self.t1 for ts, _ in self.lines)
+                   and time.perf_counter() - t < 5 * self.interval_ms / 1000.0 + 1.0 and self.p.poll() is None):
+                time.sleep(0.005)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            if self.reader is not None:
+                self.reader.join(timeout=5)
         except Exception:
-            self.p.kill()
             return None
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        after = [ts for ts, _ in self.lines if ts > t1]
+        last = min(after) if after else t1
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for ts, line in list(self.lines):
+            if ts < t0 or ts > last:
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -116,7 +159,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": self.interval_ms}
 
 
 def peaks():
@@ -294,7 +337,7 @@ def serve_leg(pm, ix, Q, prec, rate_qps, seconds, seed):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
@@ -349,9 +392,13 @@ def main():
         sampler.start()
     barrier(ws)
     torch.cuda.synchronize()
+    if sampler:
+        sampler.begin()
     total_ms, res, prof, launches = timed_steps(step, args.steps, flush, stream, "timed_main")
     barrier(ws)
     torch.cuda.synchronize()
+    if sampler:
+        sampler.end()
     clocks = sampler.stop() if sampler else None
     total_s = max_over_ranks(total_ms / 1000.0, ws)
     value = nq * args.steps * ws / total_s
