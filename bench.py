@@ -74,11 +74,12 @@ def max_over_ranks(v, ws):
 
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region: start()
-    returns once the first sample has arrived (so the sampler is running when
-    the region begins), begin()/end() mark the region, and stop() summarises
-    the samples taken inside it (with the first one after it, which still
-    describes its last interval)."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    returns once the first sample has arrived (or after wait_s), begin()/end()
+    mark the region, and stop() summarises the samples taken inside it and the
+    first one after it.  Samples are placed by nvidia-smi's own timestamp (its
+    output may reach the pipe in bursts); lines without a readable timestamp
+    are placed by arrival, and if no sample falls in the region all are used."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -94,11 +95,11 @@ class ClockSampler:
     def _read(self):
         try:
             for line in self.p.stdout:
-                self.lines.append((time.perf_counter(), line))
+                self.lines.append((time.time(), line))
         except Exception:
             pass
 
-    def start(self, wait_s=5.0):
+    def start(self, wait_s=2.0):
         import threading
         try:
             self.p = subprocess.Popen([self.exe, "-i", str(self.gpu), "--query-gpu=" + self.Q,
@@ -106,26 +107,34 @@ class ClockSampler:
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
-            t = time.perf_counter()
-            while not self.lines and time.perf_counter() - t < wait_s and self.p.poll() is None:
+            t = time.time()
+            while not self.lines and time.time() - t < wait_s and self.p.poll() is None:
                 time.sleep(0.005)
         except Exception:
             self.p = None
 
     def begin(self):
-        self.t0 = time.perf_counter()
+        self.t0 = time.time()
 
     def end(self):
-        self.t1 = time.perf_counter()
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except Exception:
+            return None
 
     def stop(self):
         if self.p is None:
             return None
         try:
-            # one more sample after the region closes
-            t = time.perf_counter()
+            # wait for one more sample after the region closes
+            t = time.time()
             while (self.t1 is not None and not any(ts > self.t1 for ts, _ in self.lines)
-                   and time.perf_counter() - t < 5 * self.interval_ms / 1000.0 + 1.0 and self.p.poll() is None):
+                   and time.time() - t < 5 * self.interval_ms / 1000.0 + 1.0 and self.p.poll() is None):
                 time.sleep(0.005)
             self.p.terminate()
             try:
@@ -136,30 +145,26 @@ class ClockSampler:
                 self.reader.join(timeout=5)
         except Exception:
             return None
-        t0 = self.t0 if self.t0 is not None else float("-inf")
-        t1 = self.t1 if self.t1 is not None else float("inf")
-        after = [ts for ts, _ in self.lines if ts > t1]
-        last = min(after) if after else t1
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ts, line in list(self.lines):
-            if ts < t0 or ts > last:
-                continue
+        rows = []
+        for arrived, line in list(self.lines):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                rows.append((self._stamp(f[0]) or arrived, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": self.interval_ms}
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        t1 = self.t1 if self.t1 is not None else float("inf")
+        after = [r[0] for r in rows if r[0] > t1]
+        last = min(after) if after else t1
+        pick = [r for r in rows if t0 <= r[0] <= last] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in pick for nm, v in zip(names, r[3]) if v.lower().startswith("active")}
+        return {"sm_mhz": statistics.median(r[1] for r in pick), "sm_max_mhz": max(r[2] for r in pick),
+                "reasons": sorted(reasons), "samples": len(pick), "interval_ms": self.interval_ms}
 
 
 def peaks():
