@@ -80,6 +80,10 @@ def lib():
         L.orc_cp_radius_filter.argtypes = [p, p, i64, i32, i32, p, p, i64,
                                            p, p, p, p, i64, i64, d, d, i64,
                                            p, p, p, p, p, p]
+        L.orc_gamma_sample.restype = i64
+        L.orc_gamma_sample.argtypes = [i64, i64, u64, p]
+        L.orc_gamma_calibrate.restype = i32
+        L.orc_gamma_calibrate.argtypes = [p, i64, i32, p, p, i64, p, p, p, p, i64, d, p]
         L.orc_num_threads.restype = i32
         _lib = L
     return _lib
@@ -271,6 +275,34 @@ def cp_radius_filter(X, A32, layout, k, t, gamma, T, Oproj=None):
         raise ValueError("orc_cp_radius_filter rejected its arguments")
     return dict(pairs=pairs, dists=dists, count=cnt.value, ub_self=ubs.value,
                 nodes=nodes.value, nodes_done=done.value)
+
+
+def gamma_sample(n, nprime, seed):
+    """Sec. 6.3 sample: the sorted ids of min(nprime, n) distinct points
+    (partial Fisher-Yates shuffle driven by the SplitMix64 stream `seed`)."""
+    ids = np.empty(max(1, min(int(nprime), int(n))), dtype=np.int64)
+    k = lib().orc_gamma_sample(int(n), int(nprime), seed, _ptr(ids))
+    return ids[:k]
+
+
+def gamma_calibrate(Oproj, layout, pr=0.85):
+    """Sec. 6.3: gamma = lower empirical pr-quantile of R_LCA / ||o1', o2'||
+    over all pairs of the points of `layout` (Oproj indexed by point id)."""
+    Oproj = np.ascontiguousarray(Oproj, dtype=np.float64)
+    n, m = Oproj.shape
+    perm = np.ascontiguousarray(layout["perm"], dtype=np.int32)
+    loff = np.ascontiguousarray(layout["leaf_off"], dtype=np.int64)
+    nlo = np.ascontiguousarray(layout["node_lo"], dtype=np.int64)
+    nhi = np.ascontiguousarray(layout["node_hi"], dtype=np.int64)
+    nl = np.ascontiguousarray(layout["node_left"], dtype=np.int32)
+    nr = np.ascontiguousarray(layout["node_right"], dtype=np.int32)
+    g = ctypes.c_double()
+    rc = lib().orc_gamma_calibrate(_ptr(Oproj), n, m, _ptr(perm), _ptr(loff), loff.shape[0] - 1,
+                                   _ptr(nlo), _ptr(nhi), _ptr(nl), _ptr(nr), nlo.shape[0],
+                                   float(pr), ctypes.byref(g))
+    if rc != 0:
+        raise ValueError("orc_gamma_calibrate rejected its arguments")
+    return g.value
 
 
 def distance_sample(Oproj, npairs, seed):

@@ -213,6 +213,12 @@ static int cmp_keyed(const void *pa, const void *pb)
     return (a->id > b->id) - (a->id < b->id);
 }
 
+static int cmp_i64(const void *pa, const void *pb)
+{
+    int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    return (a > b) - (a < b);
+}
+
 static int cmp_double(const void *pa, const void *pb)
 {
     double a = *(const double *)pa, b = *(const double *)pb;
@@ -657,6 +663,82 @@ int orc_cp_radius_filter(const float *X, const double *Oproj, int64_t n, int d, 
         out_dists[e] = e < tk.n ? tk.v[e].key : INFINITY;
     }
     free(leaf_of); free(A); free(nrad); free(tk.v);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Setting of gamma for radius filtering (Sec. 6.3, "Determining the Setting
+ * of gamma"; Sec. 7.1 fixes Pr(gamma) = 0.85).                              */
+
+/* The sample of Sec. 6.3 and Sec. 7.2 ("we randomly sample n' points"):
+ * n' = min(nprime, n) distinct ids drawn by a partial Fisher-Yates shuffle of
+ * 0..n-1 whose i-th step swaps entry i with entry i + (v_i mod (n - i)), v_i
+ * value i of the counter-based SplitMix64 stream `seed`; the first n' entries,
+ * sorted ascending, are the sample.  Returns n'.                            */
+int64_t orc_gamma_sample(int64_t n, int64_t nprime, uint64_t seed, int64_t *ids)
+{
+    if (n < 1 || nprime < 1) return 0;
+    int64_t np = nprime < n ? nprime : n;
+    int64_t *all = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; i++) all[i] = i;
+    if (np < n)
+        for (int64_t i = 0; i < np; i++) {
+            int64_t j = i + (int64_t)(orc_splitmix64(seed, (uint64_t)i) % (uint64_t)(n - i));
+            int64_t t = all[i]; all[i] = all[j]; all[j] = t;
+        }
+    for (int64_t i = 0; i < np; i++) ids[i] = all[i];
+    free(all);
+    qsort(ids, (size_t)np, sizeof(int64_t), cmp_i64);
+    return np;
+}
+
+/* gamma of Sec. 6.3 over the pairs of a point set with a given hierarchy (the
+ * PM-tree built on the sample; data, not recomputed).  For each pair of
+ * points, the ratio R / ||o1', o2'|| with R the radius (orc_node_ball) of
+ * their lowest common node: descending from the root while both points lie
+ * in the same child; two points of one leaf have that leaf as their lowest
+ * common node.  For coincident projections the ratio is 0 when R = 0 (the
+ * node is found for every positive filter radius) and +inf otherwise.
+ * gamma is the lower empirical quantile at probability pr of the
+ * n (n - 1) / 2 ratios: the smallest ratio with at least pr of the ratios at
+ * or below it (rank ceil(pr N - 1e-9), at least 1).  Oproj is indexed by
+ * point id, perm maps positions to ids as in orc_cp_radius_filter.
+ * Returns 0, or 1 for fewer than 2 points or pr outside (0, 1].           */
+int orc_gamma_calibrate(const double *Oproj, int64_t n, int m, const int32_t *perm,
+                        const int64_t *leaf_off, int64_t L, const int64_t *nlo, const int64_t *nhi,
+                        const int32_t *nleft, const int32_t *nright, int64_t nn, double pr, double *gamma)
+{
+    if (n < 2 || !(pr > 0.0 && pr <= 1.0) || m > 64 || nn < 1) return 1;
+    double *nrad = (double *)malloc(sizeof(double) * (size_t)nn);
+    double ro[64];
+    for (int64_t e = 0; e < nn; e++)
+        orc_node_ball(Oproj, m, perm, leaf_off[nlo[e]], leaf_off[nhi[e]], ro, &nrad[e]);
+    int64_t *leaf_of = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t l = 0; l < L; l++)
+        for (int64_t a = leaf_off[l]; a < leaf_off[l + 1]; a++) leaf_of[a] = l;
+    const int64_t N = n * (n - 1) / 2;
+    double *ratio = (double *)malloc(sizeof(double) * (size_t)N);
+    int64_t c = 0;
+    for (int64_t a = 0; a < n; a++)
+        for (int64_t b = a + 1; b < n; b++) {
+            const int64_t la = leaf_of[a], lb = leaf_of[b];
+            int64_t e = 0;
+            while (nleft[e] >= 0) {
+                const int64_t x = nleft[e], y = nright[e];
+                if (la >= nlo[x] && la < nhi[x] && lb >= nlo[x] && lb < nhi[x]) e = x;
+                else if (la >= nlo[y] && la < nhi[y] && lb >= nlo[y] && lb < nhi[y]) e = y;
+                else break;
+            }
+            const double R = nrad[e];
+            const double dv = pdist64(Oproj + (int64_t)perm[a] * m, Oproj + (int64_t)perm[b] * m, m);
+            ratio[c++] = dv > 0.0 ? R / dv : (R > 0.0 ? INFINITY : 0.0);
+        }
+    qsort(ratio, (size_t)N, sizeof(double), cmp_double);
+    int64_t rank = (int64_t)ceil(pr * (double)N - 1e-9);
+    if (rank < 1) rank = 1;
+    if (rank > N) rank = N;
+    *gamma = ratio[rank - 1];
+    free(ratio); free(leaf_of); free(nrad);
     return 0;
 }
 

@@ -518,3 +518,95 @@ def test_splitmix64_published_outputs():
     # from state 0, as published with its reference implementation
     assert [oracle.splitmix64(0, i) for i in range(3)] == [
         0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_cp_budget_cut_inside_a_node_hand_counted():
+    # Algorithm 4's budget T reached inside a node (reading: the node's
+    # candidates are cut to the T + 1 - count smallest by (projected
+    # distance, i, j)); the projection onto the first coordinate makes the
+    # kept and the dropped pairs change the answer
+    g = golden("cp_tcut_example.json")
+    X = np.array(g["points"], dtype=np.float32)
+    A = np.array(g["proj"], dtype=np.float32)
+    for case in g["cases"]:
+        r = oracle.cp_radius_filter(X, A, g["layout"], g["k"], g["t"], g["gamma"], case["T"])
+        assert r["pairs"].tolist() == case["pairs"]
+        assert r["dists"].tolist() == [math.sqrt(v) for v in case["dists_sq"]]
+        assert r["count"] == case["count"]
+        assert r["ub_self"] == math.sqrt(g["ub_self_sq"])
+        assert r["nodes"] == 1 and r["nodes_done"] == 1
+
+
+def test_gamma_hand_worked_example():
+    # Sec. 6.3: gamma with Pr(gamma) = p for the ratio of the LCA radius to
+    # the projected distance, on a hand-worked three-leaf hierarchy
+    g = golden("gamma_example.json")
+    O = np.array(g["coords"], dtype=np.float64)[:, None]
+    lay = g["layout"]
+    for e, r in enumerate(g["radii"]):
+        lo, hi = lay["leaf_off"][lay["node_lo"][e]], lay["leaf_off"][lay["node_hi"][e]]
+        assert oracle.node_ball(O, lay["perm"], lo, hi)[1] == r
+    for p, want in g["expect"]:
+        assert oracle.gamma_calibrate(O, lay, p) == want
+
+
+def _numpy_gamma(O, lay, p):
+    # independent restatement: node balls from numpy, the lowest common node
+    # as the node with the fewest leaves whose range holds both leaves
+    perm = np.asarray(lay["perm"])
+    loff = np.asarray(lay["leaf_off"])
+    nlo, nhi = np.asarray(lay["node_lo"]), np.asarray(lay["node_hi"])
+    rad = []
+    for e in range(len(nlo)):
+        P = O[perm[loff[nlo[e]]:loff[nhi[e]]]]
+        c = 0.5 * (P.min(0) + P.max(0))
+        rad.append(np.sqrt(((P - c) ** 2).sum(1)).max())
+    leaf_of = np.searchsorted(loff, np.arange(len(perm)), side="right") - 1
+    ratios = []
+    for a in range(len(perm)):
+        for b in range(a + 1, len(perm)):
+            la, lb = leaf_of[a], leaf_of[b]
+            holds = [e for e in range(len(nlo)) if nlo[e] <= min(la, lb) and max(la, lb) < nhi[e]]
+            e = min(holds, key=lambda x: (nhi[x] - nlo[x], x))
+            dv = np.sqrt(((O[perm[a]] - O[perm[b]]) ** 2).sum())
+            ratios.append(rad[e] / dv if dv > 0 else (np.inf if rad[e] > 0 else 0.0))
+    return float(np.quantile(np.array(ratios), p, method="inverted_cdf")), np.array(ratios)
+
+
+@pytest.mark.parametrize("seed,n,leaf", [(1, 40, 4), (2, 57, 6), (3, 33, 33)])
+def test_gamma_against_numpy_brute_force(seed, n, leaf):
+    X = datagen.gaussian(n, 7, seed=seed)
+    A = oracle.gen_projection(seed, 3, 7).astype(np.float32)
+    O = oracle.project(X, A)
+    lay = _bisect_layout(X, leaf)
+    for p in (0.85, 0.5, 0.97, 1.0):
+        want, ratios = _numpy_gamma(O, lay, p)
+        got = oracle.gamma_calibrate(O, lay, p)
+        assert got == pytest.approx(want, rel=1e-12)
+        # a node's ball holds both points, so their distance is at most 2R
+        assert ratios.min() >= 0.5 * (1 - 1e-12) and got >= 0.5 * (1 - 1e-12)
+
+
+def test_gamma_coincident_projections():
+    # R / 0: +inf for a node of positive radius, 0 for a zero-radius node
+    O = np.array([[1.0], [1.0], [4.0], [4.0]])
+    lay = dict(perm=[0, 1, 2, 3], leaf_off=[0, 2, 4], node_lo=[0, 0, 1], node_hi=[2, 1, 2],
+               node_left=[1, -1, -1], node_right=[2, -1, -1])
+    # pairs: two zero-radius leaves (ratio 0 each), four cross pairs at
+    # distance 3 under the root of radius 1.5 (ratio 0.5 each)
+    assert oracle.gamma_calibrate(O, lay, 2 / 6) == 0.0
+    assert oracle.gamma_calibrate(O, lay, 1.0) == 0.5
+    lay1 = dict(perm=[0, 1, 2, 3], leaf_off=[0, 4], node_lo=[0], node_hi=[1],
+                node_left=[-1], node_right=[-1])
+    assert oracle.gamma_calibrate(O, lay1, 1.0) == math.inf
+
+
+def test_gamma_sample_ids():
+    for n, np_ in ((100, 10), (37, 37), (20, 50), (1000, 999)):
+        ids = oracle.gamma_sample(n, np_, 11)
+        assert len(ids) == min(n, np_)
+        assert np.all(np.diff(ids) > 0) and ids[0] >= 0 and ids[-1] < n
+    assert oracle.gamma_sample(37, 100, 5).tolist() == list(range(37))
+    # the first draw of the shuffle: entry 0 swaps with v_0 mod n
+    v0 = oracle.splitmix64(11, 0) % 100
+    assert v0 in oracle.gamma_sample(100, 1, 11).tolist()
