@@ -339,6 +339,139 @@ def serve_leg(pm, ix, Q, prec, rate_qps, seconds, seed):
             "batches": st["batches"]}
 
 
+def knn_leg(pm, ix, Q, k, c, beta, prec, steps, warmup, flush, stream, tag, r_min=0.0):
+    """One (c,k)-ANN setting timed like the main step (statistics-free call,
+    L2 flushed between steps), then once with statistics for the trace and
+    the verified rows behind the k_verify roofline."""
+    import torch
+    nq, d = Q.shape
+    ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    er = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+
+    def step():
+        return ix.knn(Q, k=k, c=c, alpha1=ALPHA1, beta=beta, r_min=r_min, precision=prec,
+                      out=(ids, dd, er), with_stats=False)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ms, _, prof, launches = timed_steps(step, steps, flush, stream, tag)
+    st = ix.knn(Q, k=k, c=c, alpha1=ALPHA1, beta=beta, r_min=r_min, precision=prec)["stats"]
+    nver = int(st["nver"].sum())
+    out = {"k": k, "c": c, "beta": beta, "queries": int(nq), "value": nq * steps / (ms / 1000.0),
+           "unit": "queries/s", "ms_per_step": ms / steps, "gpu_launches": launches,
+           "trace": {"mean_rounds": float(st["rounds"].mean()), "mean_candidates": float(st["ncand"].mean()),
+                     "mean_verified": float(st["nver"].mean()),
+                     "rule_counts": np.bincount(st["rule"], minlength=4).tolist()},
+           "kernels": {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in prof.items()}}
+    if "k_verify" in prof:
+        lv, mv = prof["k_verify"]
+        # verified rows' bytes and the query rows and results, per launch,
+        # as for the main step (rows of every round of the call)
+        alg = (nver * d * 4.0 + nq * (d * 4.0 + k * 16.0)) * steps / lv
+        pk, kind = peaks()
+        ach = alg / (mv / lv / 1000.0) / 1e9
+        out["k_verify_roofline"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                    "frac": ach / pk["hbm_gbs"], "algorithmic_bytes_per_launch": alg,
+                                    "avg_launch_ms": mv / lv, "peak_kind": kind}
+    return out
+
+
+def leg_c2_budget(pm, ix, Q, prec, steps, warmup, flush, stream):
+    """The throughput workload with beta = 0.01 (B = 10,050) and a first
+    radius two growth steps below the Sec. 5.2 rule: range rounds grow the
+    radius and the budget rule (the B nearest in projected space) decides
+    part of the queries."""
+    rmin = ix.rmin_rule(0.01, K, C) / (C * C)
+    r = knn_leg(pm, ix, Q, K, C, 0.01, prec, steps, warmup, flush, stream, "timed_budget", r_min=rmin)
+    r["r_min"] = rmin
+    r["workload"] = "1M x 128 throughput workload, beta = 0.01, r_min = Sec. 5.2 rule / c^2"
+    return r
+
+
+def leg_c3(pm, prec, steps, warmup, flush, stream):
+    """High-dimensional workload: n = 10^6, d = 960, 1,000 clusters with
+    covariance eigenvalues i^-1 (seeded rotation), 1,000 queries; (c, k) in
+    {(1.2, 1), (1.5, 10), (2.0, 100)}; leaf size 256."""
+    import torch
+    import datagen
+    w = datagen.workload("c3")
+    t0 = time.perf_counter()
+    ix = pm.Index(torch.from_numpy(w["X"]).cuda(), m=M_PROJ, leaf_size=256, seed=0)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    Qd = torch.from_numpy(w["Q"]).cuda()
+    out = {"workload": "n=1,000,000 d=960 FP32, 1,000 clusters, eigenvalues i^-1, 1,000 queries, m=15, "
+                       "beta=0.2809, leaf size 256", "build_s": build_s, "settings": []}
+    for c, k in ((1.5, 10), (1.2, 1), (2.0, 100)):
+        out["settings"].append(knn_leg(pm, ix, Qd, k, c, BETA, prec, steps, warmup, flush, stream,
+                                       "timed_c3"))
+    ix.close()
+    return out
+
+
+def leg_c4(pm):
+    """Closest pairs: n = 10^5, d = 512, 500 clusters plus 20 planted pairs at
+    distance 0.01; k = 10, m = 15, alpha2 = 0.0024 (T = alpha2 n (n - 1) + k);
+    gamma calibrated (Pr = 0.85 on 10^4 sampled points); Algorithm 4 with
+    FindLCA and Algorithm 3 (branch and bound), each timed once after one
+    untimed run, leaf size 16."""
+    import torch
+    import datagen
+    w = datagen.workload("c4")
+    X, planted = w["X"], w["planted"]
+    ix = pm.Index(torch.from_numpy(X).cuda(), m=M_PROJ, leaf_size=16, seed=0)
+    planted_set = {tuple(p) for p in planted.tolist()}
+    out = {"workload": "n=100,000 d=512 FP32, 500 clusters + 20 planted pairs at 0.01, k=10, m=15, "
+                       "alpha2=0.0024, leaf size 16"}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        pm.profile(True)
+        pm.profile_read()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        prof = pm.profile_read()
+        pm.profile(False)
+        return r, el, prof
+
+    g, el, _ = timed(lambda: ix.gamma_calibrate(0.85, nsample=10000))
+    out["gamma"] = {"value": g, "pr": 0.85, "sample": 10000, "seconds": el}
+    for nm, fn in (("radius_filter", lambda: ix.closest_pairs(k=10, gamma=g)),
+                   ("branch_and_bound", lambda: ix.closest_pairs_bnb(k=10))):
+        r, el, prof = timed(fn)
+        dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+        out[nm] = {"seconds": el, "count": int(r["stats"]["count"]),
+                   "top10_planted": sum(tuple(p) in planted_set for p in r["pairs"].tolist()),
+                   "dominant_kernel": dom,
+                   "kernels": {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in prof.items()}}
+    ix.close()
+    return out
+
+
+def leg_c5(pm, seconds):
+    """Serving workload: n = 2*10^6, d = 256 resident (2,000 clusters); an
+    open-loop Poisson stream at 5k, 20k and 50k queries/s (request sizes
+    log-uniform in [1, 4096], k in {1, 10, 100}, c = 1.5) through the
+    continuous-batching server, BF16 tensor-core count vs FP32."""
+    import torch
+    import datagen
+    w = datagen.workload("c5", nq=16384)
+    ix = pm.Index(torch.from_numpy(w["X"]).cuda(), m=M_PROJ, leaf_size=256, seed=0)
+    Q = w["Q"]
+    out = {"workload": "n=2,000,000 d=256 FP32 resident, 2,000 clusters; Poisson arrivals, request sizes "
+                       "log-uniform [1,4096], k in {1,10,100}, c=1.5, 3 slots", "seconds": seconds, "rates": {}}
+    for rate in (5_000.0, 20_000.0, 50_000.0):
+        out["rates"][str(int(rate))] = {
+            nm: serve_leg(pm, ix, Q, p, rate, seconds, seed=7)
+            for nm, p in (("bf16", pm.PMLSH_BF16_TENSOR), ("fp32", pm.PMLSH_FP32_PLAIN))}
+    ix.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +487,8 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-rate", type=float, default=50_000.0)
+    ap.add_argument("--legs", default="budget,c3,c4,c5",
+                    help="other workloads on the same line: budget,c3,c4,c5 (or none)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -514,10 +649,34 @@ def main():
         for nm, p in (("bf16", pm.PMLSH_BF16_TENSOR), ("fp32", pm.PMLSH_FP32_PLAIN)):
             serve[nm] = serve_leg(pm, ix, Q, p, args.serve_rate, args.serve_seconds, seed=5)
 
+    legs = {}
+    want = set(x for x in args.legs.split(",") if x and x != "none")
+    if rank == 0:
+        lsteps, lwarm = max(3, min(args.steps, 10)), max(3, min(args.warmup, 3))
+        if "budget" in want:
+            legs["c2_budget"] = leg_c2_budget(pm, ix, Qd, prec, lsteps, lwarm, flush, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         A = ix.projection()
         cpu = cpu_baseline(X, Q, A)
+
+    # the other workloads (each with its own index; the throughput index is
+    # freed first)
+    ix_leaf = ix.leaf_size
+    ix.close()
+    del Qd, ids, dd, er
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if "c3" in want:
+            legs["c3"] = leg_c3(pm, prec, lsteps, lwarm, flush, stream)
+            torch.cuda.empty_cache()
+        if "c4" in want:
+            legs["c4"] = leg_c4(pm)
+            torch.cuda.empty_cache()
+        if "c5" in want and args.serve_seconds > 0:
+            legs["c5_serve"] = leg_c5(pm, min(args.serve_seconds, 2.0))
+            torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws,
@@ -525,7 +684,7 @@ def main():
                 "ms_per_step": total_s * 1000 / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_desc(nq), "precision": args.precision,
-                           "leaf_size": ix.leaf_size,
+                           "leaf_size": ix_leaf,
                            "leaf_size_choice": "autotuned over 128/256/512" if args.leaf_size == 0 else "fixed",
                            "l2": "flushed between steps (512 MB write)",
                            "parallelism": "replicas" if ws > 1 else "single"},
@@ -537,9 +696,8 @@ def main():
                           "mean_leaves_visited": float(stats["leaves"].mean()),
                           "rule_counts": np.bincount(stats["rule"], minlength=4).tolist()},
                 "build_s": build_s, "with_stats": with_stats, "other_precision": other, "serve": serve,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "legs": legs}
         print(json.dumps(line), flush=True)
-    ix.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

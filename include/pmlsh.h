@@ -277,6 +277,23 @@ pmlsh_status pmlsh_knn(pmlsh_index *index, const float *Q, int64_t nq,
                        float *out_dists, float *out_err,
                        pmlsh_query_stats *stats, void *stream);
 
+/* The first radius r_min that pmlsh_knn uses when opts.r_min <= 0 (the rule
+ * of Sec. 5.2 on the index's sampled distance distribution: r* with
+ * F(r*) = min(1, (beta n + k) / n), its lower empirical quantile, then
+ * r_min = r* / c).  Errors: EINVAL (NULL pointers, beta outside (0, 1],
+ * k < 1, c <= 1). */
+pmlsh_status pmlsh_rmin(const pmlsh_index *index, double beta, int k, double c,
+                        double *r_min);
+
+/* Device scratch bytes pmlsh_knn reserves (and keeps in the index) for a
+ * batch of nq queries with this k and precision: every buffer whose size
+ * the batch fixes.  Not included: the budget selection's key buffers, which
+ * grow with the range sets of the queries that reach the budget (8 bytes per
+ * point of those sets).  Errors: EINVAL (NULL pointers, nq < 0, k outside
+ * 1..256). */
+pmlsh_status pmlsh_knn_workspace_bytes(pmlsh_index *index, int64_t nq, int k,
+                                       int precision, int64_t *bytes);
+
 /* Algorithm 1, the (r,c)-BC query (Sec. 5.1), for nq queries Q [nq][d]
  * (FP32, host or device) at one radius r > 0.  Per query, C is the closed
  * range set {o : ||o',q'|| <= t r} (no budget cut); if |C| >= beta n + 1
@@ -302,7 +319,10 @@ typedef struct {
     double alpha2;    /* budget fraction: T = ceil(alpha2 n (n-1)) + k when
                          T <= 0; default 0.0024 (Sec. 7.1) */
     int64_t T;        /* candidate-pair budget of Algorithm 4; <= 0: from alpha2 */
-    double gamma;     /* radius-filter factor (Sec. 6.3), > 0, may be +inf */
+    double gamma;     /* radius-filter factor (Sec. 6.3), may be +inf;
+                         <= 0 (default): calibrated with Pr(gamma) = 0.85
+                         (Sec. 7.1) by pmlsh_gamma_calibrate on 10,000
+                         sampled points, stream seed + 7 */
     double t;         /* projected radius factor; <= 0: from alpha1 (Eq. 9) */
 } pmlsh_cp_opts;
 
@@ -317,6 +337,7 @@ typedef struct {
     int64_t fp64_checks; /* projected-distance decisions re-taken in FP64 */
     double t;            /* t used */
     int64_t T;           /* T used */
+    double gamma;        /* gamma used (pmlsh_closest_pair) */
 } pmlsh_cp_stats;
 
 /* Algorithm 4 (radius filtering) with FindLCA (Algorithm 5) over the index's
@@ -336,6 +357,23 @@ typedef struct {
 pmlsh_status pmlsh_closest_pair(pmlsh_index *index, const pmlsh_cp_opts *opts,
                                 int64_t *out_pairs, float *out_dists,
                                 pmlsh_cp_stats *stats, void *stream);
+
+/* Setting of gamma for radius filtering (Sec. 6.3, "Determining the Setting
+ * of gamma"; Sec. 7.1 uses Pr(gamma) = 0.85).  A sample of
+ * n' = min(nsample, n) points is drawn (partial Fisher-Yates shuffle of the
+ * ids 0..n-1 whose i-th step swaps entry i with entry i + (v_i mod (n - i)),
+ * v_i value i of the counter-based SplitMix64 stream `seed`; the first n'
+ * ids, ascending) and indexed by the same build as `index` (its projection,
+ * pivot count and leaf capacity; the index itself when n' = n).  For every
+ * pair of the sample the ratio R / ||o1', o2'|| of its lowest common node's
+ * radius (the FP64 ball of pmlsh_closest_pair; the leaf for two points of
+ * one leaf) over its FP64 projected distance is formed (0 / 0 -> 0,
+ * R / 0 -> +inf), and *gamma receives the lower empirical quantile at `pr`:
+ * the smallest ratio with at least pr of the n'(n'-1)/2 ratios at or below
+ * it.  Device memory: 8 bytes per pair.  Errors: EINVAL (NULL pointers, pr
+ * outside (0, 1], nsample outside 2..32768, n < 2), ENOMEM, ECUDA. */
+pmlsh_status pmlsh_gamma_calibrate(pmlsh_index *index, double pr, int64_t nsample,
+                                   uint64_t seed, double *gamma, void *stream);
 
 /* Algorithm 3, branch and bound (Sec. 6.1): the T pairs with the smallest
  * projected distance (ties by (i, j); T = opts->T, or ceil(alpha2 n (n-1))
@@ -360,11 +398,18 @@ pmlsh_status pmlsh_closest_pair_bnb(pmlsh_index *index, const pmlsh_cp_opts *opt
 /* Continuous batching over one resident index.  `slots` worker threads, each
  * with its own CUDA stream and scratch buffers, take the oldest waiting
  * request plus every later waiting request with identical query options (up
- * to max_batch_queries rows and within mem_budget_bytes of estimated device
- * scratch; a batch over the budget runs alone) and run them as one
- * pmlsh_knn batch, so requests that arrive while others run are admitted as
- * slots and memory free up and their work overlaps on the device.  Each
- * request's results equal pmlsh_knn's on that request alone. */
+ * to max_batch_queries rows) and run them as one pmlsh_knn batch, so
+ * requests that arrive while others run are admitted as slots and memory
+ * free up and their work overlaps on the device.  Each request's results
+ * equal pmlsh_knn's on that request alone.
+ * Memory admission: a batch starts when the scratch every slot holds, the
+ * growth charged to running batches and its own growth (the bytes by
+ * which its slot's scratch buffers grow to the sizes pmlsh_knn asks for) fit
+ * mem_budget_bytes; when nothing runs, idle slots release their scratch to
+ * make room, and a batch that needs more than the budget by itself runs
+ * alone.  A slot whose batch left the total above the budget releases its
+ * scratch afterwards.  Not counted: the budget selection's key buffers
+ * (8 bytes per point in the range sets of queries that reach the budget). */
 typedef struct pmlsh_server pmlsh_server;
 
 typedef struct {
@@ -380,6 +425,9 @@ typedef struct {
     int64_t queue_depth;  /* requests waiting now */
     double p50_ms, p99_ms, mean_ms;  /* submit -> completion latency */
     double qps;           /* queries / (last completion - first submission) */
+    int64_t resident_bytes; /* device scratch the slots hold now, plus the
+                               growth charged to running batches */
+    int64_t peak_bytes;     /* the largest such total seen */
 } pmlsh_server_stats;
 
 void pmlsh_serve_opts_default(pmlsh_serve_opts *o);
@@ -396,11 +444,13 @@ pmlsh_status pmlsh_serve_submit(pmlsh_server *s, const float *Q, int64_t nq,
                                 const pmlsh_knn_opts *opts, uint64_t *ticket);
 
 /* Waits up to timeout_ms (< 0: no limit) for the ticket and copies its
- * results to host buffers ids [nq][k], dists [nq][k].  ETIMEOUT leaves the
- * ticket valid; any other return consumes it.  ECANCELED: cancelled by
- * pmlsh_serve_stop.  The query path's own errors are passed through. */
+ * results to host buffers ids [nq][k], dists [nq][k] and, unless NULL,
+ * err [nq][k] (|returned distance - FP64 distance| per result, as
+ * pmlsh_knn's out_err).  ETIMEOUT leaves the ticket valid; any other return
+ * consumes it.  ECANCELED: cancelled by pmlsh_serve_stop.  The query path's
+ * own errors are passed through. */
 pmlsh_status pmlsh_serve_wait(pmlsh_server *s, uint64_t ticket, int64_t *ids,
-                              float *dists, int timeout_ms);
+                              float *dists, float *err, int timeout_ms);
 
 /* Stops accepting requests, cancels the ones not yet started (their waits
  * return ECANCELED), lets running batches finish, joins the workers. */

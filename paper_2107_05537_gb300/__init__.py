@@ -53,7 +53,7 @@ class CpStats(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("ub_self", ctypes.c_double),
                 ("lca_nodes", ctypes.c_int64), ("nodes_done", ctypes.c_int64),
                 ("self_pairs", ctypes.c_int64), ("fp64_checks", ctypes.c_int64),
-                ("t", ctypes.c_double), ("T", ctypes.c_int64)]
+                ("t", ctypes.c_double), ("T", ctypes.c_int64), ("gamma", ctypes.c_double)]
 
 
 class ServeOpts(ctypes.Structure):
@@ -64,7 +64,8 @@ class ServeOpts(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "queries", "batches",
                                                "deferred", "canceled", "queue_depth")] + \
-               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "qps")]
+               [(f, ctypes.c_double) for f in ("p50_ms", "p99_ms", "mean_ms", "qps")] + \
+               [(f, ctypes.c_int64) for f in ("resident_bytes", "peak_bytes")]
 
 
 class QueryStats(ctypes.Structure):
@@ -103,10 +104,13 @@ _SIGS = {
     "pmlsh_cp_opts_default": (None, [_P]),
     "pmlsh_closest_pair": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pmlsh_closest_pair_bnb": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "pmlsh_gamma_calibrate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
     "pmlsh_serve_opts_default": (None, [_P]),
     "pmlsh_serve_create": (ctypes.c_int, [_P, _P, _P]),
     "pmlsh_serve_submit": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
-    "pmlsh_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int]),
+    "pmlsh_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.c_int]),
+    "pmlsh_rmin": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_double, _P]),
+    "pmlsh_knn_workspace_bytes": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P]),
     "pmlsh_serve_stop": (ctypes.c_int, [_P]),
     "pmlsh_serve_stats": (ctypes.c_int, [_P, _P]),
     "pmlsh_serve_destroy": (ctypes.c_int, [_P]),
@@ -219,7 +223,7 @@ class Index:
         h = ctypes.c_void_p()
         _check(L.pmlsh_build(xp, n, d, ctypes.byref(o), _stream(), ctypes.byref(h)))
         self._h = h
-        self.n, self.d, self.m = n, d, m
+        self.n, self.d, self.m, self.seed = n, d, m, seed
         nl, ns = ctypes.c_int64(), ctypes.c_int64()
         lsz = ctypes.c_int()
         _check(L.pmlsh_index_info(h, None, None, None, ctypes.byref(nl), ctypes.byref(lsz),
@@ -313,8 +317,29 @@ class Index:
         _check(lib().pmlsh_project(self._h, qp, nq, p64, p32, _stream()))
         return o64, o32
 
-    def closest_pairs(self, k=10, c=1.5, alpha1=1 / math.e, alpha2=0.0024, T=0, gamma=3.0, t=0.0):
-        """Algorithm 4.  Returns dict(pairs [k,2] int64, dists [k] f32, stats)."""
+    def rmin_rule(self, beta=0.2809, k=10, c=1.5):
+        """The Sec. 5.2 first radius knn() uses when r_min <= 0."""
+        r = ctypes.c_double()
+        _check(lib().pmlsh_rmin(self._h, float(beta), int(k), float(c), ctypes.byref(r)))
+        return r.value
+
+    def workspace_bytes(self, nq, k=10, precision=PMLSH_FP32_PLAIN):
+        """Device scratch knn() reserves for a batch of nq queries."""
+        b = ctypes.c_int64()
+        _check(lib().pmlsh_knn_workspace_bytes(self._h, int(nq), int(k), int(precision), ctypes.byref(b)))
+        return b.value
+
+    def gamma_calibrate(self, pr=0.85, nsample=10000, seed=None):
+        """Sec. 6.3 setting of gamma (seed defaults to the index seed + 7,
+        the stream closest_pairs uses when it calibrates)."""
+        g = ctypes.c_double()
+        sd = self.seed + 7 if seed is None else seed
+        _check(lib().pmlsh_gamma_calibrate(self._h, float(pr), int(nsample), sd, ctypes.byref(g), _stream()))
+        return g.value
+
+    def closest_pairs(self, k=10, c=1.5, alpha1=1 / math.e, alpha2=0.0024, T=0, gamma=0.0, t=0.0):
+        """Algorithm 4 (gamma <= 0: calibrated, Sec. 6.3).  Returns
+        dict(pairs [k,2] int64, dists [k] f32, stats)."""
         o = CpOpts()
         lib().pmlsh_cp_opts_default(ctypes.byref(o))
         o.k, o.c, o.alpha1, o.alpha2, o.T, o.gamma, o.t = k, c, alpha1, alpha2, T, gamma, t
@@ -433,16 +458,21 @@ class Server:
         self._k[tk.value] = (Q.shape[0], k)
         return tk.value
 
-    def wait(self, ticket, timeout_ms=-1):
+    def wait(self, ticket, timeout_ms=-1, with_err=False):
+        """(ids, dists), or (ids, dists, err) with `with_err` (|returned -
+        FP64 distance| per result)."""
         nq, k = self._k.get(ticket, (1, 1))
         ids = np.empty((nq, k), dtype=np.int64)
         dd = np.empty((nq, k), dtype=np.float32)
+        ee = np.empty((nq, k), dtype=np.float32) if with_err else None
         rc = lib().pmlsh_serve_wait(self._h, ticket, ids.ctypes.data_as(ctypes.c_void_p),
-                                    dd.ctypes.data_as(ctypes.c_void_p), int(timeout_ms))
+                                    dd.ctypes.data_as(ctypes.c_void_p),
+                                    ee.ctypes.data_as(ctypes.c_void_p) if with_err else None,
+                                    int(timeout_ms))
         if rc != 3:
             self._k.pop(ticket, None)
         _check(rc)
-        return ids, dd
+        return (ids, dd, ee) if with_err else (ids, dd)
 
     def stats(self):
         s = ServeStats()

@@ -395,7 +395,7 @@ void pmlsh_cp_opts_default(pmlsh_cp_opts *o)
     o->alpha1 = 0.36787944117144233;
     o->alpha2 = 0.0024;   // Sec. 7.1
     o->T = 0;
-    o->gamma = 3.0;
+    o->gamma = 0.0;
     o->t = 0.0;
 }
 
@@ -408,10 +408,36 @@ pmlsh_status pmlsh_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *opts, int6
     PM_CHECK(ix->n >= 2, "closest pairs need n >= 2");
     PM_CHECK(o.k >= 1 && o.k <= 1024 && o.k <= npairs, "k must be in 1..min(n(n-1)/2, 1024) (got %d)", o.k);
     PM_CHECK(o.c > 1.0, "c must be > 1");
-    PM_CHECK(o.gamma > 0.0, "gamma must be > 0 (calibration by sampling is not provided)");
+    PM_CHECK(!std::isnan(o.gamma), "gamma must not be NaN (<= 0: calibrated, Sec. 6.3)");
     PM_CHECK(o.t > 0.0 || (o.alpha1 > 0.0 && o.alpha1 < 1.0), "alpha1 must be in (0,1)");
     PM_CHECK(o.T > 0 || (o.alpha2 > 0.0 && o.alpha2 <= 1.0), "alpha2 must be in (0,1]");
     return pm_closest_pair(ix, &o, out_pairs, out_dists, stats, (cudaStream_t)stream);
+}
+
+pmlsh_status pmlsh_rmin(const pmlsh_index *ix, double beta, int k, double c, double *r_min)
+{
+    PM_CHECK(ix && r_min, "NULL argument");
+    PM_CHECK(beta > 0.0 && beta <= 1.0 && k >= 1 && c > 1.0, "beta must be in (0,1], k >= 1, c > 1");
+    *r_min = pm_rmin_rule(ix, beta, k, c);
+    return PMLSH_OK;
+}
+
+pmlsh_status pmlsh_knn_workspace_bytes(pmlsh_index *ix, int64_t nq, int k, int precision, int64_t *bytes)
+{
+    PM_CHECK(ix && bytes, "NULL argument");
+    PM_CHECK(nq >= 0 && k >= 1 && k <= PM_MAX_K, "nq must be >= 0 and k in 1..256");
+    *bytes = pm_knn_work_bytes(ix, nq, k, precision);
+    return PMLSH_OK;
+}
+
+pmlsh_status pmlsh_gamma_calibrate(pmlsh_index *ix, double pr, int64_t nsample, uint64_t seed, double *gamma,
+                                   void *stream)
+{
+    PM_CHECK(ix && gamma, "NULL argument");
+    PM_CHECK(ix->n >= 2, "gamma calibration needs n >= 2");
+    PM_CHECK(pr > 0.0 && pr <= 1.0, "pr must be in (0, 1]");
+    PM_CHECK(nsample >= 2 && nsample <= 32768, "nsample must be in 2..32768 (got %lld)", (long long)nsample);
+    return pm_gamma_calibrate(ix, pr, nsample, seed, gamma, (cudaStream_t)stream);
 }
 
 pmlsh_status pmlsh_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *opts, int64_t *out_pairs,

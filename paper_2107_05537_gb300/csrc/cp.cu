@@ -112,6 +112,67 @@ __global__ void k_node_ball(const double *__restrict__ O64, const int64_t *__res
 // < Rt (strict, Algorithm 4).  FP32: |sqrt(d'^2_32) - d'_64| <= eps, so
 // d'^2_32 < loT is surely in, > hiT surely out, and the rest is decided in
 // FP64.  Thread per first position a; loops over b > a.
+// Sec. 6.3, setting of gamma: for every pair (a, b), a < b, of the n
+// positions of a layout, R / ||o_a', o_b'|| with R the radius of their lowest
+// common node (descending from the root while both leaves lie in one child;
+// the leaf itself for two points of one leaf), FP64 projected distance with
+// the oracle's arithmetic and a correctly rounded quotient; 0 / 0 -> 0,
+// R / 0 -> +inf.  Block a writes pairs (a, b) at a n - a (a + 1) / 2 + b - a - 1.
+__global__ void k_gamma_ratio(const double *__restrict__ O64, int64_t n, int m, const int32_t *__restrict__ leafOf,
+                              const int64_t *__restrict__ node /*[N][4]: left, right, leaf lo, leaf hi*/,
+                              const double *__restrict__ rad, double *__restrict__ out, int *__restrict__ err)
+{
+    const int64_t a = blockIdx.x;
+    const int64_t base = a * n - a * (a + 1) / 2 - a - 1;
+    const int64_t la = leafOf[a];
+    for (int64_t b = a + 1 + threadIdx.x; b < n; b += blockDim.x) {
+        const int64_t lb = leafOf[b];
+        int64_t e = 0;
+        int depth = 0;
+        for (; depth < 4096; depth++) {
+            const int64_t x = node[e * 4], y = node[e * 4 + 1];
+            if (x < 0) break;
+            if (la >= node[x * 4 + 2] && la < node[x * 4 + 3] && lb >= node[x * 4 + 2] && lb < node[x * 4 + 3])
+                e = x;
+            else if (la >= node[y * 4 + 2] && la < node[y * 4 + 3] && lb >= node[y * 4 + 2] && lb < node[y * 4 + 3])
+                e = y;
+            else
+                break;
+        }
+        if (depth == 4096) atomicOr(err, 1);
+        const double R = rad[e];
+        const double dv = pm_pdist64(O64 + a * PM_MP, O64 + b * PM_MP, m);
+        out[base + b] = dv > 0.0 ? __ddiv_rn(R, dv) : (R > 0.0 ? (double)INFINITY : 0.0);
+    }
+}
+
+// 256-bin histogram of 8 bits at `shift` of the keys whose bits above them
+// equal `prefix` (non-negative doubles and +inf order like their bits).
+__global__ void k_gamma_hist(const unsigned long long *__restrict__ v, int64_t N, int shift,
+                             unsigned long long hiMask, unsigned long long prefix, unsigned int *__restrict__ hist)
+{
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = v[e];
+        if ((k & hiMask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// Rows X[pos[i]] (leaf-order copy, row length ld) -> S[i] (row length d).
+__global__ void k_gather_rows(const float *__restrict__ X, int ld, int d, const int64_t *__restrict__ pos,
+                              int64_t ns, float *__restrict__ S)
+{
+    const int64_t i = blockIdx.x;
+    if (i >= ns) return;
+    const float *x = X + pos[i] * ld;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) S[i * d + j] = x[j];
+}
+
 __global__ void k_cp_node_pairs(const float *__restrict__ O32, const double *__restrict__ O64, int m,
                                 const int32_t *__restrict__ leafOfPos, int64_t lo, int64_t hi, float loT,
                                 float hiT, double Rt, PairCand *__restrict__ out, unsigned long long *cnt,
@@ -557,13 +618,130 @@ pmlsh_status pair_select(const PairCand *p, int64_t n, int64_t T, PairCand *out,
 
 }  // namespace
 
+// gamma of Sec. 6.3 over all pairs of the index `lx` (its own layout).
+static pmlsh_status gamma_of_layout(const pmlsh_index *lx, double pr, double *gamma, cudaStream_t st)
+{
+    const int64_t n = lx->n, L = lx->L, N = (int64_t)lx->nodeLo.size();
+    const int64_t npairs = n * (n - 1) / 2;
+    DevPtrs mem;
+    // node balls (FP64, the oracle's arithmetic)
+    std::vector<int64_t> pLo(N), pHi(N), nodeH((size_t)N * 4);
+    for (int64_t e = 0; e < N; e++) {
+        pLo[e] = lx->leafOffH[lx->nodeLo[e]];
+        pHi[e] = lx->leafOffH[lx->nodeHi[e]];
+        nodeH[e * 4] = lx->nodeLeft[e];
+        nodeH[e * 4 + 1] = lx->nodeRight[e];
+        nodeH[e * 4 + 2] = lx->nodeLo[e];
+        nodeH[e * 4 + 3] = lx->nodeHi[e];
+    }
+    std::vector<int32_t> lof(n);
+    for (int64_t l = 0; l < L; l++)
+        for (int64_t p = lx->leafOffH[l]; p < lx->leafOffH[l + 1]; p++) lof[p] = (int32_t)l;
+    int64_t *dLo, *dHi, *dNode;
+    double *dRad, *ratio;
+    int32_t *dLeafOf;
+    unsigned int *hist;
+    int *err;
+    PM_TRY(mem.get(&dLo, N));
+    PM_TRY(mem.get(&dHi, N));
+    PM_TRY(mem.get(&dNode, (size_t)N * 4));
+    PM_TRY(mem.get(&dRad, N));
+    PM_TRY(mem.get(&dLeafOf, n));
+    PM_TRY(mem.get(&ratio, (size_t)npairs));
+    PM_TRY(mem.get(&hist, 256));
+    PM_TRY(mem.get(&err, 1));
+    PM_CUDA(cudaMemcpyAsync(dLo, pLo.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemcpyAsync(dHi, pHi.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemcpyAsync(dNode, nodeH.data(), N * 4 * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemcpyAsync(dLeafOf, lof.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    PM_LAUNCH("k_node_ball", st, k_node_ball<<<(unsigned)N, 256, 0, st>>>(lx->O64, dLo, dHi, lx->m, dRad));
+    PM_LAUNCH("k_gamma_ratio", st, k_gamma_ratio<<<(unsigned)(n - 1), 256, 0, st>>>(lx->O64, n, lx->m, dLeafOf, dNode,
+                                                                                     dRad, ratio, err));
+    PM_CUDA(cudaGetLastError());
+    // exact rank-th smallest ratio: radix select, 8 passes of 8 bits
+    int64_t rank = (int64_t)std::ceil(pr * (double)npairs - 1e-9);
+    rank = std::max<int64_t>(1, std::min<int64_t>(npairs, rank));
+    unsigned long long prefix = 0, hiMask = 0;
+    unsigned int hh[256];
+    const int grid = (int)std::min<int64_t>(4096, (npairs + 255) / 256);
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        PM_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), st));
+        PM_LAUNCH("k_gamma_hist", st, k_gamma_hist<<<grid, 256, 0, st>>>((const unsigned long long *)ratio, npairs,
+                                                                           shift, hiMask, prefix, hist));
+        PM_CUDA(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        int dg = 0;
+        int64_t below = 0;
+        while (dg < 255 && below + (int64_t)hh[dg] < rank) below += hh[dg++];
+        rank -= below;
+        prefix |= (unsigned long long)dg << shift;
+        hiMask |= 0xFFull << shift;
+    }
+    int herr = 0;
+    PM_CUDA(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        pm_set_error("gamma calibration: the hierarchy is deeper than 4096 levels");
+        return PMLSH_EINTERNAL;
+    }
+    double g;
+    std::memcpy(&g, &prefix, sizeof(g));
+    *gamma = g;
+    return PMLSH_OK;
+}
+
+pmlsh_status pm_gamma_calibrate(pmlsh_index *ix, double pr, int64_t nsample, uint64_t seed, double *gamma,
+                                cudaStream_t st)
+{
+    const int64_t n = ix->n;
+    if (nsample >= n) return gamma_of_layout(ix, pr, gamma, st);
+    // the sample: partial Fisher-Yates shuffle of 0..n-1 driven by the
+    // counter-based stream `seed`, the first nsample ids sorted
+    std::vector<int64_t> ids(n);
+    for (int64_t i = 0; i < n; i++) ids[i] = i;
+    for (int64_t i = 0; i < nsample; i++) {
+        const int64_t j = i + (int64_t)(pm_splitmix64(seed, (uint64_t)i) % (uint64_t)(n - i));
+        std::swap(ids[i], ids[j]);
+    }
+    ids.resize(nsample);
+    std::sort(ids.begin(), ids.end());
+    // their rows (original order) from the leaf-order copy of X
+    std::vector<int64_t> inv(n), pos(nsample);
+    for (int64_t p = 0; p < n; p++) inv[ix->permH[p]] = p;
+    for (int64_t i = 0; i < nsample; i++) pos[i] = inv[ids[i]];
+    DevPtrs mem;
+    int64_t *dPos;
+    float *S;
+    PM_TRY(mem.get(&dPos, nsample));
+    PM_TRY(mem.get(&S, (size_t)nsample * ix->d));
+    PM_CUDA(cudaMemcpyAsync(dPos, pos.data(), nsample * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PM_LAUNCH("k_gather_rows", st, k_gather_rows<<<(unsigned)nsample, 128, 0, st>>>(ix->X, ix->ld, ix->d, dPos, nsample, S));
+    PM_CUDA(cudaGetLastError());
+    // the layout of the sample: the same build with the same projection,
+    // pivot count and leaf capacity
+    pmlsh_build_opts bo;
+    pmlsh_build_opts_default(&bo);
+    bo.m = ix->m;
+    bo.s = ix->s;
+    bo.leaf_size = ix->M;
+    bo.seed = ix->seed;
+    bo.proj = ix->A_host.data();
+    bo.bf16_shadow = 0;
+    pmlsh_index *sub = nullptr;
+    pmlsh_status s = pmlsh_build(S, nsample, ix->d, &bo, st, &sub);
+    if (s == PMLSH_OK) s = gamma_of_layout(sub, pr, gamma, st);
+    pmlsh_free(sub);
+    return s;
+}
+
 pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
                              pmlsh_cp_stats *stats, cudaStream_t st)
 {
     const int64_t n = ix->n, L = ix->L;
     const int k = o->k;
     const double t = o->t > 0.0 ? o->t : std::sqrt(pm_chi2_upper_quantile(o->alpha1, ix->m));
-    const double gamma = o->gamma;
+    double gamma = o->gamma;
+    if (!(gamma > 0.0)) PM_TRY(pm_gamma_calibrate(ix, 0.85, 10000, ix->seed + 7, &gamma, st));
     const int64_t T = o->T > 0 ? o->T : (int64_t)std::ceil(o->alpha2 * (double)n * (double)(n - 1) - 1e-9) + k;
     DevPtrs mem;
     // 1. self-join of every leaf
@@ -709,6 +887,7 @@ pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *o
         stats->fp64_checks = fp64;
         stats->t = t;
         stats->T = T;
+        stats->gamma = gamma;
     }
     return PMLSH_OK;
 }
@@ -855,6 +1034,7 @@ pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_
         stats->fp64_checks = fp64;
         stats->t = 0.0;
         stats->T = T;
+        stats->gamma = o->gamma;
     }
     (void)crossPairs;
     return PMLSH_OK;

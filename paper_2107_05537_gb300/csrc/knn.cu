@@ -22,57 +22,17 @@
 //   [host]         stop rules, r <- c r for the rest
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include <cuda_bf16.h>
 
-#include "pmlsh_impl.h"
+#include "knn_shared.cuh"
 
 namespace {
 
-constexpr int QB = 64;          // queries per block
-constexpr int BCAP = 256;       // band-in entries per query
-constexpr int SELBAND = 2048;   // band at the budget cut, per query
-constexpr float SLACK = 1e-5f;  // relative slack of the conservative leaf tests
+using namespace pmk;
 
-enum : unsigned char { CL_OUT = 0, CL_FULL = 1, CL_PART = 2 };
-
-// Eq. 5 (Sec. 4.2): a leaf can hold a point of B(q', R) only if
-// ||q', RO|| <= r + R and, for every pivot p_i,
-// ||q', p_i|| - R <= HR[i].max and ||q', p_i|| + R >= HR[i].min.
-// CL_OUT: every point certainly has FP32 distance^2 > Rout^2 (out-ball);
-// CL_FULL: every point certainly has FP32 distance^2 <= Rin^2;
-// otherwise CL_PART.  Slack covers the FP32 rounding of every term.
-__device__ __forceinline__ unsigned char leaf_class(const float *q, const float *qpiv, int s,
-                                                    float Rin, float Rout, const float *M)
-{
-    // explicit round-to-nearest intrinsics: never contracted, so every kernel
-    // that inlines this test takes the same decision
-    const float lo_f = 1.f - SLACK, hi_f = 1.f + SLACK;
-    float dc = __fsqrt_rn(pm_pd2_32(q, M));
-    float rr = M[16];
-    float ro = __fmul_rn(Rout, hi_f);
-    if (__fsub_rn(__fmul_rn(dc, lo_f), rr) > ro) return CL_OUT;
-    // unrolled over the largest pivot count, so that a register copy of M
-    // is indexed by constants
-#pragma unroll
-    for (int i = 0; i < PM_MAX_PIVOTS; i++) {
-        if (i < s) {
-            float dq = qpiv[i];
-            if (__fsub_rn(__fmul_rn(dq, lo_f), M[32 + i]) > ro) return CL_OUT;
-            if (__fsub_rn(M[24 + i], __fmul_rn(dq, hi_f)) > ro) return CL_OUT;
-        }
-    }
-    if (Rin > 0.f && __fadd_rn(__fmul_rn(dc, hi_f), rr) <= __fmul_rn(Rin, lo_f)) return CL_FULL;
-    return CL_PART;
-}
-
-// |sqrt(FP32 d'^2) - FP64 d'| <= eps: coordinate rounding (2^-24 relative per
-// coordinate of o' and q') plus the FP32 sum (<= 9 u relative), doubled.
-__device__ __forceinline__ double band_eps(double R, double maxNorm, double qn)
-{
-    return 0x1.0p-23 * (maxNorm + qn) + 0x1.0p-19 * R + 1e-300;
-}
 
 // ------------------------------------------------------------ prep kernels
 
@@ -133,13 +93,6 @@ __global__ void k_query_pca(const float *__restrict__ Qd, int64_t nq, int ld, co
     qnx[q] = __double2float_ru(sqrt(nn));
 }
 
-// Per-round thresholds for the active queries.
-struct Thr {
-    double R;      // t r (FP64, as in the oracle)
-    float lo, hi;  // FP32 d'^2 <= lo: surely in; > hi: surely out
-    float lov;     // verification threshold (lo, or the budget cut)
-    float pad;     // 1: the budget selection listed this query's band-in points
-};
 
 __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const double *__restrict__ r,
                              double t, double maxNorm, const double *__restrict__ qnorm,
@@ -516,152 +469,8 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
     }
 }
 
-// ------------------------------------------------- best-first verification
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-// TMA (bulk-copy engine): global -> shared, completion counted in bytes on bar.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_async_shared()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Waits for phase `ph` of `bar` with an iteration limit; false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t ph)
-{
-    for (int it = 0; it < (1 << 22); it++)
-        if (mbar_try_wait(bar, ph)) return true;
-    return false;
-}
-
 constexpr int VW_MAXWARPS = 8;                // queries in flight per block (one per warp)
 constexpr int VW_MINBLOCKS = 4;               // blocks per SM the register budget allows
-constexpr unsigned VW_FULL = 0xffffffffu;
-
-// Squared FP32 distances ||q - x_v||^2 of up to 32 rows x_v, one per lane
-// (`p`: the lane's row, nullptr: none; the lane then gets 0).  Eight lanes
-// share a row and read its float4 columns g, g + 8, ..., so that every load
-// instruction of the warp covers whole 128-byte lines of four rows; the
-// eight partial sums are added by a butterfly.  Requires ld % 32 == 0 with
-// zero padding columns in q and in the rows.
-// Prefetch hint for the line holding global address p (no fault, no result).
-__device__ __forceinline__ void pm_prefetch_l2(const void *p)
-{
-    asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L2 [ga];\n\t}" ::"l"(p));
-}
-
-__device__ __forceinline__ float warp_d2(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
-{
-    const int grp = lane >> 3, g = lane & 7;
-    float keep = 0.f;
-    // the loop below reads the 32 rows 4 at a time; an L2 prefetch of every
-    // line of the lane's own row first puts all 32 rows' misses in flight at
-    // once, so later groups find their lines in L2
-    if (p != nullptr) {
-        const char *pc = (const char *)p;
-        for (int b = 0; b < nf4 * 16; b += 128) pm_prefetch_l2(pc + b);
-    }
-#pragma unroll 1
-    for (int j = 0; j < 8; j++) {
-        const float4 *x4 = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 4 * j);
-        float acc = 0.f;
-        if (x4 != nullptr) {
-            for (int t = g; t < nf4; t += 8) {
-                const float4 x = __ldg(x4 + t);
-                const float4 qv = q4[t];
-                float u = __fsub_rn(qv.x, x.x);
-                acc = __fmaf_rn(u, u, acc);
-                u = __fsub_rn(qv.y, x.y);
-                acc = __fmaf_rn(u, u, acc);
-                u = __fsub_rn(qv.z, x.z);
-                acc = __fmaf_rn(u, u, acc);
-                u = __fsub_rn(qv.w, x.w);
-                acc = __fmaf_rn(u, u, acc);
-            }
-        }
-        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 1));
-        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 2));
-        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 4));
-        if (g == j) keep = acc;
-    }
-    // lane (grp, g) holds row grp + 4 g
-    return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
-}
-
-// FP32 -> FP64 re-encoded with integer operations (exact, equal to the
-// conversion instruction), so that the widening does not occupy the FP64
-// pipe; zeros are re-encoded too, subnormals, infinities and NaNs use the
-// conversion instruction.
-__device__ __forceinline__ double f2d_exact(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFFu;
-    const uint64_t sign = (uint64_t)(u >> 31) << 63;
-    if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);
-    if (e == 0u || e == 0xFFu) return (double)f;
-    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
-}
-
-// pm_dist64 (FP64 sequential sum of (x_i - y_i)^2, separate multiply and
-// add, correctly rounded sqrt) with the inputs widened by f2d_exact.
-__device__ __forceinline__ double dist64_widen(const float *x, const float *y, int d)
-{
-    double s = 0.0;
-    for (int i = 0; i < d; i++) {
-        const double t = __dsub_rn(f2d_exact(x[i]), f2d_exact(y[i]));
-        s = __dadd_rn(s, __dmul_rn(t, t));
-    }
-    return __dsqrt_rn(s);
-}
-
-// FP32 d'^2 of one projected row against q' (the arithmetic of pm_pd2_32:
-// sequential over the 16 coordinates, row minus query), float4 loads.
-__device__ __forceinline__ float pd2_row(const float *__restrict__ o, const float *__restrict__ qv)
-{
-    const float4 *o4 = (const float4 *)o;
-    float s = 0.f;
-#pragma unroll
-    for (int j4 = 0; j4 < PM_MP / 4; j4++) {
-        const float4 x = __ldg(o4 + j4);
-        float t = __fsub_rn(x.x, qv[4 * j4]);
-        s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(x.y, qv[4 * j4 + 1]);
-        s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(x.z, qv[4 * j4 + 2]);
-        s = __fmaf_rn(t, t, s);
-        t = __fsub_rn(x.w, qv[4 * j4 + 3]);
-        s = __fmaf_rn(t, t, s);
-    }
-    return s;
-}
-
 struct VwArgs {
     const int32_t *act;
     int na;
@@ -1685,6 +1494,128 @@ template <class T> T *grow(DevBuf &b, size_t count, pmlsh_status &st)
 
 }  // namespace
 
+namespace {
+
+// Launch shape of the verification for rows of length ld and a top-KP of KP:
+// the grouped kernel (verify_group.cu) when its shared memory fits, the
+// single-query kernel otherwise.
+struct VerifyPlan {
+    int nsm = 148;
+    int vWarps = 0, vPerSM = 1;   // single-query kernel
+    size_t vsmem = 0;
+    int gvTR = 0, gvPerSM = 0;    // grouped kernel
+    size_t gvSmem = 0;
+    bool grouped = false;
+};
+
+pmlsh_status verify_plan(int ld, int KP, VerifyPlan &vp)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&vp.nsm, cudaDevAttrMultiProcessorCount, dev);
+    // single-query kernel: one warp per query, as many warps per block as
+    // shared memory allows (up to VW_MAXWARPS)
+    const size_t vwarp = verify_smem_warp(ld, KP);
+    vp.vWarps = (int)std::min<size_t>(VW_MAXWARPS, (size_t)(227 * 1024) / vwarp);
+    if (vp.vWarps < 1) return PMLSH_OK;
+    vp.vsmem = (size_t)vp.vWarps * vwarp;
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_verify));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vp.vPerSM, k_verify, 32 * vp.vWarps, vp.vsmem));
+    vp.vPerSM = std::max(1, vp.vPerSM);
+    vp.gvTR = gv_tile_rows(ld);
+    vp.gvSmem = vp.gvTR > 0 ? gv_smem_bytes(ld, KP, vp.gvTR) : 0;
+    if (vp.gvTR > 0 && vp.gvSmem <= (size_t)pm_max_smem_optin()) PM_TRY(gv_ctas_per_sm(vp.gvSmem, &vp.gvPerSM));
+    const char *vsel = std::getenv("PMLSH_VERIFY");
+    vp.grouped = vp.gvPerSM > 0 && vsel && std::strcmp(vsel, "group") == 0;
+    return PMLSH_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// The bytes pm_knn grows each workspace buffer to for a batch of nq queries
+// (the largest of the sizes it asks for; the budget selection's key buffers,
+// which depend on the data, are left out).
+void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
+                    std::vector<std::pair<DevBuf KnnWork::*, int64_t>> &out)
+{
+    const int64_t L = ix->L, ld = ix->ld, W32 = (L + 31) / 32;
+    const int KP = (k + 32 + 31) / 32 * 32;
+    const bool tc = precision == PMLSH_BF16_TENSOR;
+    VerifyPlan vp;
+    if (verify_plan((int)ld, KP, vp) != PMLSH_OK) vp = VerifyPlan();
+    const int64_t nlq = (nq + QB - 1) / QB, nlt = tc ? (nq + TC_QN - 1) / TC_QN : 0;
+    const int64_t nlist = std::max(nlq, nlt);
+    int64_t vscratch;
+    if (vp.grouped) {
+        const int64_t grid = std::max<int64_t>(
+            1, std::min<int64_t>((nq + GV_WARPS - 1) / GV_WARPS, (int64_t)vp.gvPerSM * vp.nsm));
+        vscratch = grid * L * 9 + 64;
+    } else {
+        const int64_t vw = std::max(1, vp.vWarps);
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((nq + vw - 1) / vw, (int64_t)vp.vPerSM * vp.nsm));
+        vscratch = grid * vw * L * 8;
+    }
+    out = {
+        {&KnnWork::Qd, nq * ld * 4}, {&KnnWork::qp64, nq * PM_MP * 8}, {&KnnWork::qp32, nq * PM_MP * 4},
+        {&KnnWork::qnorm, nq * 8}, {&KnnWork::qpiv, nq * PM_MAX_PIVOTS * 4}, {&KnnWork::keys, nq * 4},
+        {&KnnWork::order, nq * 4}, {&KnnWork::qpca, nq * (PM_PCA + 1) * 4}, {&KnnWork::keys2, (L + 1) * 4},
+        {&KnnWork::qstate, nq * 8}, {&KnnWork::outIds, nq * k * 8}, {&KnnWork::outD64, nq * k * 4},
+        {&KnnWork::outErr, nq * k * 4}, {&KnnWork::active, nq * 4}, {&KnnWork::thr, nq * (int64_t)sizeof(Thr)},
+        {&KnnWork::cntSure, nq * 4}, {&KnnWork::cntBand, nq * 4}, {&KnnWork::cntPart, nq * 4},
+        {&KnnWork::bandCnt, nq * 4}, {&KnnWork::bandIn, nq * 4}, {&KnnWork::bandInQ, nq * BCAP * 4},
+        {&KnnWork::bandQ, ((int64_t)1 << 20) * 4}, {&KnnWork::bandPos, ((int64_t)1 << 20) * 4},
+        {&KnnWork::flags, (nq + 8) * 4}, {&KnnWork::dk, nq * 8}, {&KnnWork::leafBits, nq * W32 * 4},
+        {&KnnWork::recheck, tc ? ((int64_t)1 << 23) * 8 : 0},
+        {&KnnWork::blkCnt, nlist * 4}, {&KnnWork::blkLeaves, nlist * L * 16},
+        {&KnnWork::blkMask, std::max(nlq * L * (QB / 32) * 4, nlt * L * TC_MW * 4)},
+        // the straddling sub-batch (at most the whole batch)
+        {&KnnWork::subIdx, nq * (12 + BCAP) * 4}, {&KnnWork::subThr, nq * (int64_t)sizeof(Thr)},
+        {&KnnWork::subBits, nq * W32 * 4},
+        // verification
+        {&KnnWork::partSeen, (3 * nq + 8) * 4}, {&KnnWork::partD, vscratch},
+    };
+}
+
+}  // namespace
+
+int64_t pm_knn_work_bytes(const pmlsh_index *ix, int64_t nq, int k, int precision)
+{
+    std::vector<std::pair<DevBuf KnnWork::*, int64_t>> need;
+    knn_work_needs(ix, nq, k, precision, need);
+    int64_t b = 0;
+    for (auto &e : need) b += e.second > 0 ? std::max<int64_t>(e.second, 256) : 0;
+    return b;
+}
+
+int64_t pm_knn_work_growth(const pmlsh_index *ix, int64_t nq, int k, int precision, const KnnWork &w)
+{
+    std::vector<std::pair<DevBuf KnnWork::*, int64_t>> need;
+    knn_work_needs(ix, nq, k, precision, need);
+    int64_t b = 0;
+    for (auto &e : need) {
+        const int64_t want = e.second > 0 ? std::max<int64_t>(e.second, 256) : 0;
+        const int64_t have = (int64_t)(w.*(e.first)).bytes;
+        if (want > have) b += want;   // the buffer is freed and allocated anew
+        if (want > have) b -= have;
+    }
+    return b;
+}
+
+int64_t pm_work_resident(const KnnWork &w)
+{
+    const DevBuf *bufs[] = {&w.Qd, &w.qp32, &w.qp64, &w.qnorm, &w.qpiv, &w.order, &w.keys, &w.keys2, &w.vals2,
+                            &w.sortTmp, &w.qstate, &w.thr, &w.blkCnt, &w.blkLeaves, &w.cntSure, &w.cntBand,
+                            &w.bandQ, &w.bandPos, &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen,
+                            &w.bandInQ, &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf, &w.selOff,
+                            &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask, &w.recheck, &w.leafBits,
+                            &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
+    int64_t b = 0;
+    for (const DevBuf *p : bufs) b += (int64_t)p->bytes;
+    return b;
+}
+
 pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, float *staging,
                              double *out64, float *out32, int ostride, cudaStream_t st)
 {
@@ -1795,25 +1726,15 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     uint32_t *leafBits = grow<uint32_t>(w.leafBits, (size_t)nq * W32, s);
     if (s != PMLSH_OK) return s;
 
-    int nsm = 148;
-    {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    // verification: one warp per query, as many warps per block as shared
-    // memory allows (up to VW_MAXWARPS)
-    const size_t vwarp = verify_smem_warp(ld, KP);
-    const int vWarps = (int)std::min<size_t>(VW_MAXWARPS, (size_t)(227 * 1024) / vwarp);
-    if (vWarps < 1) {
+    VerifyPlan vp;
+    PM_TRY(verify_plan(ld, KP, vp));
+    if (vp.vWarps < 1) {
         pm_set_error("d = %d is too large for the verification kernel's shared memory", d);
         return PMLSH_EINVAL;
     }
-    const size_t vsmem = (size_t)vWarps * vwarp;
-    PM_TRY(pm_allow_max_dyn_smem((const void *)k_verify));
-    int vPerSM = 1;
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vPerSM, k_verify, 32 * vWarps, vsmem));
-    vPerSM = std::max(1, vPerSM);
+    const int nsm = vp.nsm, vWarps = vp.vWarps, vPerSM = vp.vPerSM, gvTR = vp.gvTR, gvPerSM = vp.gvPerSM;
+    const size_t vsmem = vp.vsmem, gvSmem = vp.gvSmem;
+    const bool grouped = vp.grouped;
 
     const bool tensor = o->precision == PMLSH_BF16_TENSOR;
     // the tensor-core count holds all 512 TMEM columns of its SM; its
@@ -2034,27 +1955,55 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         // verification: best-first over candidate leaves, guard set, FP64.
         // Work order: the queries with the most range candidates (their
         // upper bound) first, so that the long ones do not finish last;
-        // locality order inside each of 32 logarithmic cost classes.
+        // locality order inside each of 32 logarithmic cost classes.  The
+        // grouped kernel takes groups of GV_WARPS consecutive active queries
+        // (locality order), a group's cost class being its costliest
+        // member's.
         int *nverD = grow<int>(w.partSeen, (size_t)3 * na + 8, s);
         int *vOrder = nverD + 2 * na + 8;
+        const int ngroups = (na + GV_WARPS - 1) / GV_WARPS;
         {
-            std::vector<int32_t> cls(na);
+            const int nunits = grouped ? ngroups : na;
+            std::vector<int32_t> cls(nunits, 31);
             int64_t hist[33] = {0};
             for (int a = 0; a < na; a++) {
                 const uint64_t c = (uint64_t)((int64_t)hs[a] + hb[a] + 1);
                 const int b = std::min(31, 63 - __builtin_clzll(c));   // floor(log2 c)
-                cls[a] = 31 - b;   // costliest class first
-                hist[cls[a] + 1]++;
+                const int u = grouped ? a / GV_WARPS : a;
+                cls[u] = std::min(cls[u], 31 - b);   // costliest class first
             }
+            for (int u = 0; u < nunits; u++) hist[cls[u] + 1]++;
             for (int b = 0; b < 32; b++) hist[b + 1] += hist[b];
-            for (int a = 0; a < na; a++) stVo[hist[cls[a]]++] = a;
-            PM_CUDA(cudaMemcpyAsync(vOrder, stVo, na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            for (int u = 0; u < nunits; u++) stVo[hist[cls[u]]++] = u;
+            PM_CUDA(cudaMemcpyAsync(vOrder, stVo, nunits * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         }
-        const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, vPerSM * nsm));
-        int2 *vLists = grow<int2>(w.partD, (size_t)vGrid * vWarps * L, s);
-        if (s != PMLSH_OK) return s;
         PM_CUDA(cudaMemsetAsync(nverD + 2 * na, 0, 8 * sizeof(int), st));
-        {
+        if (grouped) {
+            const int gGrid = std::max(1, std::min(ngroups, gvPerSM * nsm));
+            uint32_t *ukey = grow<uint32_t>(w.partD, (size_t)gGrid * L * 9 / 4 + 16, s);
+            if (s != PMLSH_OK) return s;
+            GvArgs ga;
+            ga.act = act; ga.na = na; ga.thr = thr; ga.qp32 = qp32; ga.qpiv = qpiv; ga.s = ix->s;
+            ga.meta = ix->leafMeta; ga.L = L; ga.O32 = ix->O32; ga.X = ix->X; ga.Qd = Qd;
+            ga.ld = ld; ga.d = d; ga.leafMu = ix->leafMu; ga.leafRx = ix->leafRx; ga.leafOff = ix->leafOff;
+            ga.KP = KP; ga.k = k;
+            ga.inN = inN; ga.inPos = inPos; ga.perm = ix->perm; ga.outIds = oIds; ga.outD = oD; ga.outErr = oE;
+            ga.dk = dk; ga.fp64cnt = fpc; ga.nverOut = nverD; ga.nleafOut = nverD + na; ga.errFlag = errFlag;
+            ga.workCtr = nverD + 2 * na; ga.dbg = nverD + 2 * na + 1; ga.n = n;
+            ga.leafBits = leafBits; ga.W32 = W32;
+            ga.O64 = ix->O64; ga.qp64 = qp64; ga.m = m; ga.inlineBand = needExact ? 0 : 1;
+            ga.leafPmu = ix->leafPmu; ga.qpca = qpca; ga.qnx = qnx;
+            ga.muMax = (float)(ix->muMax * (1.0 + 1e-6)) + 1e-30f;
+            ga.gOrder = vOrder; ga.ngroups = ngroups;
+            ga.ukey = ukey;
+            ga.uleaf = (int32_t *)(ukey + (size_t)gGrid * L);
+            ga.umask = (uint8_t *)(ga.uleaf + (size_t)gGrid * L);
+            ga.TR = gvTR;
+            PM_TRY(gv_launch(ga, gGrid, gvSmem, st));
+        } else {
+            const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, vPerSM * nsm));
+            int2 *vLists = grow<int2>(w.partD, (size_t)vGrid * vWarps * L, s);
+            if (s != PMLSH_OK) return s;
             VwArgs va;
             va.act = act; va.na = na; va.thr = thr; va.qp32 = qp32; va.qpiv = qpiv; va.s = ix->s;
             va.meta = ix->leafMeta; va.L = L; va.O32 = ix->O32; va.X = ix->X; va.Qd = Qd;

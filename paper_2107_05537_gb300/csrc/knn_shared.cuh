@@ -1,0 +1,260 @@
+// Device helpers and types shared by the query-path kernels (knn.cu and
+// verify_group.cu).  Internal to libpmlsh.
+#pragma once
+
+#include "pmlsh_impl.h"
+
+namespace pmk {
+
+constexpr int QB = 64;          // queries per block
+constexpr int BCAP = 256;       // band-in entries per query
+constexpr int SELBAND = 2048;   // band at the budget cut, per query
+constexpr float SLACK = 1e-5f;  // relative slack of the conservative leaf tests
+
+enum : unsigned char { CL_OUT = 0, CL_FULL = 1, CL_PART = 2 };
+
+// Eq. 5 (Sec. 4.2): a leaf can hold a point of B(q', R) only if
+// ||q', RO|| <= r + R and, for every pivot p_i,
+// ||q', p_i|| - R <= HR[i].max and ||q', p_i|| + R >= HR[i].min.
+// CL_OUT: every point certainly has FP32 distance^2 > Rout^2 (out-ball);
+// CL_FULL: every point certainly has FP32 distance^2 <= Rin^2;
+// otherwise CL_PART.  Slack covers the FP32 rounding of every term.
+__device__ __forceinline__ unsigned char leaf_class(const float *q, const float *qpiv, int s,
+                                                    float Rin, float Rout, const float *M)
+{
+    // explicit round-to-nearest intrinsics: never contracted, so every kernel
+    // that inlines this test takes the same decision
+    const float lo_f = 1.f - SLACK, hi_f = 1.f + SLACK;
+    float dc = __fsqrt_rn(pm_pd2_32(q, M));
+    float rr = M[16];
+    float ro = __fmul_rn(Rout, hi_f);
+    if (__fsub_rn(__fmul_rn(dc, lo_f), rr) > ro) return CL_OUT;
+    // unrolled over the largest pivot count, so that a register copy of M
+    // is indexed by constants
+#pragma unroll
+    for (int i = 0; i < PM_MAX_PIVOTS; i++) {
+        if (i < s) {
+            float dq = qpiv[i];
+            if (__fsub_rn(__fmul_rn(dq, lo_f), M[32 + i]) > ro) return CL_OUT;
+            if (__fsub_rn(M[24 + i], __fmul_rn(dq, hi_f)) > ro) return CL_OUT;
+        }
+    }
+    if (Rin > 0.f && __fadd_rn(__fmul_rn(dc, hi_f), rr) <= __fmul_rn(Rin, lo_f)) return CL_FULL;
+    return CL_PART;
+}
+
+// |sqrt(FP32 d'^2) - FP64 d'| <= eps: coordinate rounding (2^-24 relative per
+// coordinate of o' and q') plus the FP32 sum (<= 9 u relative), doubled.
+__device__ __forceinline__ double band_eps(double R, double maxNorm, double qn)
+{
+    return 0x1.0p-23 * (maxNorm + qn) + 0x1.0p-19 * R + 1e-300;
+}
+
+// Per-round thresholds for the active queries.
+struct Thr {
+    double R;      // t r (FP64, as in the oracle)
+    float lo, hi;  // FP32 d'^2 <= lo: surely in; > hi: surely out
+    float lov;     // verification threshold (lo, or the budget cut)
+    float pad;     // 1: the budget selection listed this query's band-in points
+};
+
+// ------------------------------------------------- best-first verification
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// TMA (bulk-copy engine): global -> shared, completion counted in bytes on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Waits for phase `ph` of `bar` with an iteration limit; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t ph)
+{
+    for (int it = 0; it < (1 << 22); it++)
+        if (mbar_try_wait(bar, ph)) return true;
+    return false;
+}
+
+constexpr unsigned VW_FULL = 0xffffffffu;
+
+// Squared FP32 distances ||q - x_v||^2 of up to 32 rows x_v, one per lane
+// (`p`: the lane's row, nullptr: none; the lane then gets 0).  Eight lanes
+// share a row and read its float4 columns g, g + 8, ..., so that every load
+// instruction of the warp covers whole 128-byte lines of four rows; the
+// eight partial sums are added by a butterfly.  Requires ld % 32 == 0 with
+// zero padding columns in q and in the rows.
+// Prefetch hint for the line holding global address p (no fault, no result).
+__device__ __forceinline__ void pm_prefetch_l2(const void *p)
+{
+    asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L2 [ga];\n\t}" ::"l"(p));
+}
+
+__device__ __forceinline__ float warp_d2(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
+{
+    const int grp = lane >> 3, g = lane & 7;
+    float keep = 0.f;
+    // the loop below reads the 32 rows 4 at a time; an L2 prefetch of every
+    // line of the lane's own row first puts all 32 rows' misses in flight at
+    // once, so later groups find their lines in L2
+    if (p != nullptr) {
+        const char *pc = (const char *)p;
+        for (int b = 0; b < nf4 * 16; b += 128) pm_prefetch_l2(pc + b);
+    }
+#pragma unroll 1
+    for (int j = 0; j < 8; j++) {
+        const float4 *x4 = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 4 * j);
+        float acc = 0.f;
+        if (x4 != nullptr) {
+            for (int t = g; t < nf4; t += 8) {
+                const float4 x = __ldg(x4 + t);
+                const float4 qv = q4[t];
+                float u = __fsub_rn(qv.x, x.x);
+                acc = __fmaf_rn(u, u, acc);
+                u = __fsub_rn(qv.y, x.y);
+                acc = __fmaf_rn(u, u, acc);
+                u = __fsub_rn(qv.z, x.z);
+                acc = __fmaf_rn(u, u, acc);
+                u = __fsub_rn(qv.w, x.w);
+                acc = __fmaf_rn(u, u, acc);
+            }
+        }
+        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 1));
+        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 2));
+        acc = __fadd_rn(acc, __shfl_xor_sync(VW_FULL, acc, 4));
+        if (g == j) keep = acc;
+    }
+    // lane (grp, g) holds row grp + 4 g
+    return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
+}
+
+// FP32 -> FP64 re-encoded with integer operations (exact, equal to the
+// conversion instruction), so that the widening does not occupy the FP64
+// pipe; zeros are re-encoded too, subnormals, infinities and NaNs use the
+// conversion instruction.
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+// pm_dist64 (FP64 sequential sum of (x_i - y_i)^2, separate multiply and
+// add, correctly rounded sqrt) with the inputs widened by f2d_exact.
+__device__ __forceinline__ double dist64_widen(const float *x, const float *y, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; i++) {
+        const double t = __dsub_rn(f2d_exact(x[i]), f2d_exact(y[i]));
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return __dsqrt_rn(s);
+}
+
+// FP32 d'^2 of one projected row against q' (the arithmetic of pm_pd2_32:
+// sequential over the 16 coordinates, row minus query), float4 loads.
+__device__ __forceinline__ float pd2_row(const float *__restrict__ o, const float *__restrict__ qv)
+{
+    const float4 *o4 = (const float4 *)o;
+    float s = 0.f;
+#pragma unroll
+    for (int j4 = 0; j4 < PM_MP / 4; j4++) {
+        const float4 x = __ldg(o4 + j4);
+        float t = __fsub_rn(x.x, qv[4 * j4]);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(x.y, qv[4 * j4 + 1]);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(x.z, qv[4 * j4 + 2]);
+        s = __fmaf_rn(t, t, s);
+        t = __fsub_rn(x.w, qv[4 * j4 + 3]);
+        s = __fmaf_rn(t, t, s);
+    }
+    return s;
+}
+
+
+// --------------------------------------------- grouped verification (host)
+
+// Arguments of the grouped verification kernel (verify_group.cu): the
+// per-query inputs and outputs of the single-query kernel k_verify, plus the
+// grouping of the active queries and the per-CTA scratch.
+struct GvArgs {
+    const int32_t *act;
+    int na;
+    const Thr *thr;
+    const float *qp32, *qpiv;
+    int s;
+    const float *meta;
+    int64_t L;
+    const float *O32, *X, *Qd;
+    int ld, d;
+    const float *leafMu, *leafRx;
+    const int64_t *leafOff;     // [L+1] leaf l holds positions [leafOff[l], leafOff[l+1])
+    int KP, k;
+    const int *inN, *inPos;
+    const int32_t *perm;
+    int64_t *outIds;
+    float *outD, *outErr;
+    double *dk;
+    int *fp64cnt, *nverOut, *nleafOut, *errFlag;
+    int *workCtr;               // next entry of gOrder to take (persistent CTAs)
+    int *dbg;                   // [3]: site, value, query of the first failed index check
+    int64_t n;
+    const uint32_t *leafBits;   // [na][W32]: leaves Eq. 5 does not exclude (k_class)
+    int W32;
+    const double *O64, *qp64;
+    const float *leafPmu;       // [L][PM_PCA]
+    const float *qpca, *qnx;    // [nq][PM_PCA], [nq]
+    float muMax;
+    int m;
+    int inlineBand;
+    const int32_t *gOrder;      // [ngroups] group ids, costliest first
+    int ngroups;                // group g = active entries [8 g, min(8 g + 8, na))
+    uint32_t *ukey;             // [grid][L] scratch: ordered group-minimum bound
+    int32_t *uleaf;             // [grid][L] scratch: leaf id
+    uint8_t *umask;             // [grid][L] scratch: queries of the group that list the leaf
+    int TR;                     // rows per staged tile (power of two, 4..32)
+};
+
+// Queries per group (one warp each) of the grouped verification.
+constexpr int GV_WARPS = 8;
+// Rows per staged tile for row length ld (0: ld too long for the kernel).
+int gv_tile_rows(int ld);
+// Dynamic shared memory of one CTA.
+size_t gv_smem_bytes(int ld, int KP, int TR);
+// Launches the grouped verification on `grid` persistent CTAs.
+pmlsh_status gv_launch(const GvArgs &A, int grid, size_t smem, cudaStream_t st);
+// CTAs per SM the kernel reaches with this shared memory (>= 1).
+pmlsh_status gv_ctas_per_sm(size_t smem, int *out);
+
+}  // namespace pmk

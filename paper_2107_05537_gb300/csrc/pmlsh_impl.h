@@ -160,10 +160,24 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq,
                     float *err, pmlsh_query_stats *stats, cudaStream_t st,
                     KnnWork *work = nullptr, bool rcbc = false);
 void pm_release_work(KnnWork &w);
+// Device bytes pm_knn reserves in a workspace for a batch of nq queries with
+// this k and precision: every buffer whose size the batch fixes.  Not
+// included: the budget selection's key buffers (8 bytes per point in the
+// range sets of the queries that reach the budget B in a round).
+int64_t pm_knn_work_bytes(const pmlsh_index *ix, int64_t nq, int k, int precision);
+// How many bytes the workspace w grows by for such a batch (each buffer
+// grows only to the size the batch asks for).
+int64_t pm_knn_work_growth(const pmlsh_index *ix, int64_t nq, int k, int precision, const KnnWork &w);
+// Device bytes a workspace holds now.
+int64_t pm_work_resident(const KnnWork &w);
 
 // Closest pairs (cp.cu)
 pmlsh_status pm_closest_pair(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
                              pmlsh_cp_stats *stats, cudaStream_t st);
+// gamma of Sec. 6.3 at probability pr over a sample of nsample points (all
+// points when nsample >= n) drawn from stream `seed` (cp.cu).
+pmlsh_status pm_gamma_calibrate(pmlsh_index *ix, double pr, int64_t nsample, uint64_t seed, double *gamma,
+                                cudaStream_t st);
 pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_t *out_pairs, float *out_dists,
                              pmlsh_cp_stats *stats, cudaStream_t st);
 

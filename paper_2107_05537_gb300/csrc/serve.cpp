@@ -36,6 +36,7 @@ struct Request {
     std::vector<float> Q;          // [nq][d] host copy
     std::vector<int64_t> ids;      // [nq][k]
     std::vector<float> dists;      // [nq][k]
+    std::vector<float> err;        // [nq][k] |returned - FP64 distance|
     pmlsh_status status = PMLSH_OK;
     std::string error;
     bool done = false;
@@ -60,7 +61,13 @@ struct pmlsh_server {
     std::map<uint64_t, std::shared_ptr<Request>> tickets;
     uint64_t next_ticket = 1;
     bool stopping = false;
-    int64_t bytes_in_flight = 0;
+    // device memory of the slots' workspaces: what each holds now, and the
+    // growth charged at admission to the batches still running
+    std::vector<int64_t> resident;
+    int64_t reserved = 0;
+    int inflight = 0;
+    uint64_t trim_epoch = 0;   // idle slots release their workspaces when it moves
+    int64_t peak_bytes = 0;
     // statistics
     int64_t submitted = 0, completed = 0, queries = 0, batches = 0, deferred = 0, canceled = 0;
     std::vector<double> lat_ms;
@@ -68,28 +75,45 @@ struct pmlsh_server {
     bool any_done = false;
     std::vector<std::thread> workers;
 
-    // Device bytes a batch of nq rows needs (scratch of the query path).
-    int64_t batch_bytes(int64_t nq, int k) const
+    int64_t held() const
     {
-        const int64_t L = ix->L;
-        const int64_t nblk = (nq + 63) / 64;
-        const int64_t perq = (int64_t)ix->ld * 4 + 16 * 12 + 8 * 4 + 256 * 4 + (int64_t)k * 16 + 64;
-        const int64_t grid = std::min<int64_t>(nq, 152 * 4);
-        return nq * perq + nblk * L * 4 + grid * 2 * L * 4 + (int64_t)(1 << 20) * 8 + L * 8;
+        int64_t b = reserved;
+        for (int64_t r : resident) b += r;
+        return b;
     }
 
+    // Memory admission: a batch is admitted when the slots' resident
+    // workspaces, the growth already charged to running batches and this
+    // batch's own growth of its slot's workspace (pm_knn_work_growth) fit
+    // mem_budget_bytes.  When nothing runs and a batch does not fit, the idle
+    // slots release their workspaces first; a batch that does not fit even
+    // then runs alone.  A slot whose batch left the total above the budget
+    // releases its workspace afterwards.
     void worker(int slot)
     {
         cudaSetDevice(device);
         cudaStream_t st = nullptr;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         KnnWork work;
+        uint64_t seen_epoch = 0;
         for (;;) {
             std::vector<std::shared_ptr<Request>> batch;
-            int64_t need = 0;
+            int64_t growth = 0;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
+                    if (trim_epoch != seen_epoch) {
+                        // a batch waits for the memory this idle slot holds
+                        seen_epoch = trim_epoch;
+                        if (resident[slot] > 0) {
+                            lk.unlock();
+                            pm_release_work(work);
+                            lk.lock();
+                            resident[slot] = 0;
+                            cv_work.notify_all();
+                        }
+                        continue;
+                    }
                     if (stopping && queue.empty()) break;
                     if (!queue.empty()) {
                         // the oldest request and the later ones with the same options
@@ -104,16 +128,27 @@ struct pmlsh_server {
                             pick.push_back(i);
                             rows += r.nq;
                         }
-                        need = batch_bytes(rows, o.k);
-                        // admitted when the budget allows, or alone (so that a
-                        // batch larger than the budget still runs, by itself)
-                        if (bytes_in_flight + need <= opts.mem_budget_bytes || bytes_in_flight == 0) {
+                        const int64_t g = pm_knn_work_growth(ix, rows, o.k, o.precision, work);
+                        bool admit = held() + g <= opts.mem_budget_bytes;
+                        if (!admit && inflight == 0) {
+                            if (held() - resident[slot] > 0) {
+                                seen_epoch = ++trim_epoch;
+                                cv_work.notify_all();
+                                cv_work.wait(lk);
+                                continue;
+                            }
+                            admit = true;   // alone, above the budget if it must
+                        }
+                        if (admit) {
                             for (size_t j = pick.size(); j-- > 0;) {
                                 batch.push_back(queue[pick[j]]);
                                 queue.erase(queue.begin() + (long)pick[j]);
                             }
                             std::reverse(batch.begin(), batch.end());
-                            bytes_in_flight += need;
+                            growth = g;
+                            reserved += g;
+                            inflight++;
+                            peak_bytes = std::max(peak_bytes, held());
                             break;
                         }
                         deferred++;   // waits for memory held by other slots
@@ -133,9 +168,10 @@ struct pmlsh_server {
                 at += r->nq;
             }
             std::vector<int64_t> ids((size_t)rows * o.k);
-            std::vector<float> dd((size_t)rows * o.k);
-            pmlsh_status s = pm_knn(ix, Q.data(), rows, &o, ids.data(), dd.data(), nullptr, nullptr, st, &work);
+            std::vector<float> dd((size_t)rows * o.k), ee((size_t)rows * o.k);
+            pmlsh_status s = pm_knn(ix, Q.data(), rows, &o, ids.data(), dd.data(), ee.data(), nullptr, st, &work);
             std::string err = s == PMLSH_OK ? "" : pmlsh_last_error();
+            bool trim = false;
             {
                 std::lock_guard<std::mutex> lk(mu);
                 at = 0;
@@ -146,6 +182,7 @@ struct pmlsh_server {
                     if (s == PMLSH_OK) {
                         r->ids.assign(ids.begin() + at * o.k, ids.begin() + (at + r->nq) * o.k);
                         r->dists.assign(dd.begin() + at * o.k, dd.begin() + (at + r->nq) * o.k);
+                        r->err.assign(ee.begin() + at * o.k, ee.begin() + (at + r->nq) * o.k);
                     }
                     at += r->nq;
                     r->done = true;
@@ -157,12 +194,25 @@ struct pmlsh_server {
                     t_last = now;
                 }
                 batches++;
-                bytes_in_flight -= need;
+                reserved -= growth;
+                inflight--;
+                resident[slot] = pm_work_resident(work);
+                peak_bytes = std::max(peak_bytes, held());
+                trim = held() > opts.mem_budget_bytes;
+            }
+            if (trim) {
+                pm_release_work(work);
+                std::lock_guard<std::mutex> lk(mu);
+                resident[slot] = 0;
             }
             cv_done.notify_all();
             cv_work.notify_all();
         }
         pm_release_work(work);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            resident[slot] = 0;
+        }
         cudaStreamDestroy(st);
     }
 };
@@ -198,6 +248,7 @@ pmlsh_status pmlsh_serve_create(pmlsh_index *ix, const pmlsh_serve_opts *opts, p
     }
     s->ix = ix;
     s->opts = o;
+    s->resident.assign(o.slots, 0);
     cudaGetDevice(&s->device);
     for (int i = 0; i < o.slots; i++) s->workers.emplace_back(&pmlsh_server::worker, s, i);
     *out = s;
@@ -250,7 +301,8 @@ pmlsh_status pmlsh_serve_submit(pmlsh_server *s, const float *Q, int64_t nq, con
     return PMLSH_OK;
 }
 
-pmlsh_status pmlsh_serve_wait(pmlsh_server *s, uint64_t ticket, int64_t *ids, float *dists, int timeout_ms)
+pmlsh_status pmlsh_serve_wait(pmlsh_server *s, uint64_t ticket, int64_t *ids, float *dists, float *err,
+                              int timeout_ms)
 {
     if (!s || !ids || !dists) {
         pm_set_error("NULL argument");
@@ -276,6 +328,7 @@ pmlsh_status pmlsh_serve_wait(pmlsh_server *s, uint64_t ticket, int64_t *ids, fl
     }
     std::memcpy(ids, r->ids.data(), r->ids.size() * sizeof(int64_t));
     std::memcpy(dists, r->dists.data(), r->dists.size() * sizeof(float));
+    if (err) std::memcpy(err, r->err.data(), r->err.size() * sizeof(float));
     return PMLSH_OK;
 }
 
@@ -320,6 +373,8 @@ pmlsh_status pmlsh_serve_stats(pmlsh_server *s, pmlsh_server_stats *out)
     out->deferred = s->deferred;
     out->canceled = s->canceled;
     out->queue_depth = (int64_t)s->queue.size();
+    out->resident_bytes = s->held();
+    out->peak_bytes = s->peak_bytes;
     if (!s->lat_ms.empty()) {
         std::vector<double> v(s->lat_ms);
         std::sort(v.begin(), v.end());

@@ -191,3 +191,54 @@ def test_cp_extremes_both_algorithms(n, k, leaf):
     assert np.array_equal(got["dists"], rd.astype(np.float32))
     ep, ed = oracle.exact_kcp(X, k)
     assert got["pairs"].tolist() == ep.tolist()
+
+
+# ------------------------------------------- setting of gamma (Sec. 6.3)
+
+@pytest.mark.parametrize("n,d,leaf", [(600, 16, 16), (1100 + 7, 24, 64)])
+def test_gamma_calibration_whole_index(n, d, leaf):
+    # nsample >= n: the ratios of every pair of the index's own layout
+    X, _, _, _ = datagen.mixture(n, d, 6, 1.0, seed=n)
+    A = oracle.gen_projection(3, 15, d).astype(np.float32)
+    ix = pm.Index(torch.from_numpy(X).cuda(), leaf_size=leaf, proj=A)
+    lay = ix.layout()
+    O = oracle.project(X, A)
+    for pr in (0.85, 0.5, 1.0, 1.0 / (n * (n - 1) // 2)):
+        assert ix.gamma_calibrate(pr, nsample=n) == oracle.gamma_calibrate(O, lay, pr)
+    ix.close()
+
+
+def test_gamma_calibration_sample_and_cp_default():
+    # nsample < n: the library indexes the sampled rows with the index's own
+    # projection and leaf capacity; the oracle draws the same ids and takes
+    # the sample's layout (built through the public API) as data
+    n, d, ns = 3000, 20, 700
+    X, _, _, _ = datagen.mixture(n, d, 10, 1.0, seed=4)
+    A = oracle.gen_projection(8, 15, d).astype(np.float32)
+    ix = pm.Index(X, leaf_size=32, proj=A, seed=5)
+    g = ix.gamma_calibrate(0.85, nsample=ns, seed=99)
+    ids = oracle.gamma_sample(n, ns, 99)
+    sub = pm.Index(X[ids], leaf_size=32, proj=A, seed=5)
+    ref = oracle.gamma_calibrate(oracle.project(X[ids], A), sub.layout(), 0.85)
+    sub.close()
+    assert g == ref and g >= 0.5
+    # gamma <= 0 in closest_pairs: calibrated on 10,000 points (here all)
+    # of stream seed + 7, reported in the statistics
+    k, T = 5, int(math.ceil(0.0024 * n * (n - 1))) + 5
+    got = ix.closest_pairs(k=k, T=T, gamma=0.0)
+    g0 = got["stats"]["gamma"]
+    assert g0 == ix.gamma_calibrate(0.85, nsample=10000, seed=5 + 7)
+    assert g0 == oracle.gamma_calibrate(oracle.project(X, A), ix.layout(), 0.85)
+    tt, _, _ = oracle.params(15, 1.5, 1 / math.e)
+    ref = oracle.cp_radius_filter(X, A, ix.layout(), k, tt, g0, T)
+    _assert_same(got, ref)
+    ix.close()
+
+
+def test_gamma_calibration_rejects_bad_arguments():
+    X, _, _, _ = datagen.mixture(100, 8, 3, 1.0, seed=1)
+    ix = pm.Index(X, leaf_size=16)
+    for pr, ns in ((0.0, 50), (1.5, 50), (0.85, 1), (0.85, 40000)):
+        with pytest.raises(pm.PmlshError):
+            ix.gamma_calibrate(pr, nsample=ns)
+    ix.close()

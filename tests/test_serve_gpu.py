@@ -181,3 +181,35 @@ def test_non_finite_options_rejected_and_server_keeps_serving(served):
     alone = ix.knn(rows, k=5, with_stats=False)
     np.testing.assert_array_equal(ids, alone["ids"])
     np.testing.assert_array_equal(dd, alone["dists"])
+
+
+def test_memory_admission_bounds_resident_scratch(served):
+    # admission counts every slot's resident scratch plus the growth charged
+    # to running batches: with no batch needing more than the budget by
+    # itself, the total never passes the budget.  beta = 1 keeps the budget
+    # rule (whose selection buffers grow with the data) out of play.
+    ix, Q = served
+    cap = 600
+    budget = int(1.6 * max(ix.workspace_bytes(cap, k) for k in (1, 10, 50)))
+    reqs = _requests(Q, 40, seed=3)
+    srv = pm.Server(ix, slots=3, max_batch_queries=cap, mem_budget_bytes=budget)
+    tickets = [None] * len(reqs)
+
+    def client(part):
+        for i in range(part, len(reqs), 4):
+            tickets[i] = srv.submit(reqs[i][0], k=reqs[i][1], beta=1.0)
+    threads = [threading.Thread(target=client, args=(p,)) for p in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    outs = [srv.wait(t, with_err=True) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    assert 0 < st["peak_bytes"] <= budget and st["resident_bytes"] <= budget
+    for (rows, k), (ids, dd, ee) in zip(reqs, outs):
+        alone = ix.knn(rows, k=k, beta=1.0, with_stats=False)
+        assert np.array_equal(ids, alone["ids"]) and np.array_equal(dd, alone["dists"])
+        # the per-result error bound of pmlsh_knn is passed through
+        assert np.array_equal(ee, alone["err"])
