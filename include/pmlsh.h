@@ -202,6 +202,11 @@ pmlsh_status pmlsh_project(pmlsh_index *index, const float *Q, int64_t nq,
  *   part of the library image (every GPU that loads the library holds it
  *   until the process exits), so nq * (d rounded up to a multiple of 32)
  *   must not exceed 4,194,304; larger batches are rejected with EINVAL.
+ *   With lazy module loading (the CUDA default) the driver reserves the
+ *   array when the first call on a device looks up its address, so that
+ *   first call can fail with ECUDA if the device is full; a process whose
+ *   own allocator reserves the device should make one warm-up call at
+ *   start-up, before that reservation.
  *   Outputs (out64 [nq][m] FP64, out32 [nq][m] FP32, either may be NULL)
  *   must be device memory; Q may be host or device memory.  Results are
  *   identical to pmlsh_project's.

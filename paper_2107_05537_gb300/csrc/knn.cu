@@ -507,11 +507,87 @@ struct VwArgs {
     int inlineBand;             // 1: decide FP32 band points in FP64 here (no exact count ran)
 };
 
+constexpr int VW_WIN = 64;                    // leaves per window of the best-first walk
+constexpr uint32_t VW_TAKEN = 0xFFFFFFFFu;    // list key of a leaf already windowed
+
 // Shared memory of one warp: gd[KP] f64, gid[KP] i64, q[ld], vals[KP],
-// idxs[KP], gpos[KP], q'[16], pivot distances[8], P q [PM_PCA].
+// idxs[KP], gpos[KP], q'[16], pivot distances[8], P q [PM_PCA], window keys
+// and leaves [VW_WIN], select histogram [256].
 __host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP)
 {
-    return (size_t)KP * 28 + (size_t)ld * 4 + 96 + PM_PCA * 4;
+    return (size_t)KP * 28 + (size_t)ld * 4 + 96 + PM_PCA * 4 + VW_WIN * 8 + 256 * 4;
+}
+
+// Total order of FP32 values as unsigned keys (finite and infinite values).
+__device__ __forceinline__ uint32_t vw_key(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float vw_unkey(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// The want-th smallest (1-based) of the keys list[e].y != VW_TAKEN,
+// e < cnt, by the warp: four 8-bit histogram passes (want must not exceed
+// their number).
+__device__ uint32_t warp_select(const int2 *list, int cnt, int want, uint32_t *hist, int lane)
+{
+    uint32_t prefix = 0, pmask = 0;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = lane; i < 256; i += 32) hist[i] = 0u;
+        __syncwarp();
+        for (int e = lane; e < cnt; e += 32) {
+            const uint32_t k = (uint32_t)list[e].y;
+            if (k != VW_TAKEN && (k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t h[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            h[j] = hist[lane * 8 + j];
+            sum += h[j];
+        }
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(VW_FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned hit = __ballot_sync(VW_FULL, incl >= (uint32_t)want);
+        const int fl = hit ? __ffs(hit) - 1 : 31;
+        uint32_t rem = (uint32_t)want - (incl - sum);
+        int j = 0;
+        while (j < 7 && rem > h[j]) {
+            rem -= h[j];
+            j++;
+        }
+        const int digit = __shfl_sync(VW_FULL, lane * 8 + j, fl);
+        want = (int)__shfl_sync(VW_FULL, rem, fl);
+        prefix |= (uint32_t)digit << shift;
+        pmask |= 0xFFu << shift;
+        __syncwarp();
+    }
+    return prefix;
+}
+
+// Ascending bitonic sort of VW_WIN (key, value) pairs by (key, value).
+__device__ __forceinline__ void warp_sort_win(uint32_t *key, int32_t *val, int lane)
+{
+    for (int size = 2; size <= VW_WIN; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int i = (lane / stride) * 2 * stride + lane % stride, j = i + stride;
+            const uint32_t ka = key[i], kb = key[j];
+            const int32_t va = val[i], vb = val[j];
+            const bool gt = ka > kb || (ka == kb && va > vb);
+            if (gt == ((i & size) == 0)) {
+                key[i] = kb;
+                key[j] = ka;
+                val[i] = vb;
+                val[j] = va;
+            }
+            __syncwarp();
+        }
 }
 
 #define VW_CHECK(cond, site, val)                                              \
@@ -556,6 +632,9 @@ k_verify(VwArgs A)
     float *sq = (float *)(gpos + KP);
     float *sp = sq + PM_MP;
     float *sPq = sp + PM_MAX_PIVOTS;
+    uint32_t *wkey = (uint32_t *)(sPq + PM_PCA);
+    int32_t *wleaf = (int32_t *)(wkey + VW_WIN);
+    uint32_t *whist = (uint32_t *)(wleaf + VW_WIN);
     const float4 *q4 = (const float4 *)qs;
     int2 *list = A.lists + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * L;
     const double epsv = (double)(ld + 8) * 0x1.0p-24;
@@ -617,16 +696,11 @@ k_verify(VwArgs A)
                     myMax = mm;
                     mySlot = ms;
                 }
-                __syncwarp();
-                float bm = myMax;
-                int bs = mySlot;
-                for (int o = 16; o; o >>= 1) {
-                    const float om = __shfl_xor_sync(VW_FULL, bm, o);
-                    const int os = __shfl_xor_sync(VW_FULL, bs, o);
-                    if (om > bm || (om == bm && os < bs)) { bm = om; bs = os; }
-                }
-                cmax = bm;
-                cslot = bs;
+                // values are >= +0 or +inf: their bit patterns order like them
+                const unsigned mb = __reduce_max_sync(VW_FULL, __float_as_uint(myMax));
+                const unsigned who = __ballot_sync(VW_FULL, __float_as_uint(myMax) == mb);
+                cmax = __uint_as_float(mb);
+                cslot = __shfl_sync(VW_FULL, mySlot, __ffs(who) - 1);
             }
         };
         // verifies the candidates of leaf l
@@ -699,8 +773,7 @@ k_verify(VwArgs A)
         __syncwarp();
         // cheap bounds first: ||P q - P mu|| <= ||q - mu|| for the
         // orthonormal rows P (the FP32 errors of P q, P mu and the sum covered
-        // by the slack); an entry {-(l + 1), bound} holds a cheap bound,
-        // {l, bound} the full one
+        // by the slack); an entry is {leaf, ordered key of its bound}
         // slack: FP32 P q ((ld + 2) 2^-24 ||q|| per coordinate, 4 x over 16),
         // FP32 P mu and the FP32 difference and sum, rounded generously up
         const float pSlack = __fmul_ru(1.01f, __fadd_ru(__fmul_ru((float)(4 * (ld + 2)) * 0x1.0p-24f, A.qnx[q]),
@@ -724,78 +797,67 @@ k_verify(VwArgs A)
                     s2 = __fmaf_rn(u, u, s2);
                 }
                 const float lbp = __fsub_rn(__fsub_rn(__fmul_rn(__fsqrt_rn(s2), 1.f - 0x1.0p-18f), pSlack), A.leafRx[l]);
-                list[e] = make_int2(-l - 1, __float_as_int(lbp));
+                list[e] = make_int2(l, (int)vw_key(lbp));
             }
         }
         __syncwarp();
-        // 2. best first over the listed leaves: an entry with a cheap bound
-        // gets its full bound (original-space leaf ball) when it comes first
-        // and goes back on the list; one with the full bound is visited
-        for (;;) {
-            float bl = INFINITY;
-            int be = 0x7fffffff;
-            for (int e = lane; e < cnt; e += 32) {
-                const float lb = __int_as_float(list[e].y);
-                if (lb < bl) { bl = lb; be = e; }
-            }
-            for (int o = 16; o; o >>= 1) {
-                const float ob = __shfl_xor_sync(VW_FULL, bl, o);
-                const int oe = __shfl_xor_sync(VW_FULL, be, o);
-                if (ob < bl || (ob == bl && oe < be)) { bl = ob; be = oe; }
-            }
-            if (be == 0x7fffffff || pruned(bl)) break;
-            const int x = list[be].x;
-            __syncwarp();
-            if (x < 0) {
-                // the first entry has a cheap bound: full bounds for it and up
-                // to 31 more cheap entries with bounds near it, in one pass
-                const float lim = fmaxf(bl, 0.f) + 16.f;
-                int ref = -1, nb = 0;   // lane i refines entry ref (slot i)
-                for (int e0 = 0; e0 < cnt && nb < 32; e0 += 32) {
-                    const int e = e0 + lane;
-                    bool pick = false;
-                    if (e < cnt) {
-                        const int2 v = list[e];
-                        pick = v.x < 0 && (e == be || __int_as_float(v.y) <= lim);
-                    }
-                    const unsigned m = __ballot_sync(VW_FULL, pick);
-                    if (lane >= nb && lane < nb + __popc(m)) ref = e0 + (int)__fns(m, 0, lane - nb + 1);
-                    nb = min(32, nb + __popc(m));
-                }
-                // the first entry itself, if 32 earlier ones crowded it out
-                if (__ballot_sync(VW_FULL, ref == be) == 0u && lane == 31) ref = be;
-                int lr = ref >= 0 ? -list[ref].x - 1 : -1;
-                if (__any_sync(VW_FULL, ref >= 0 && !(lr >= 0 && lr < L))) {
-                    if (ref >= 0 && !(lr >= 0 && lr < L)) VW_CHECK(false, 10, lr);
-                    break;
-                }
-                const float d2 = D2(ref >= 0 ? A.leafMu + (int64_t)lr * ld : nullptr);
-                __syncwarp();
-                if (ref >= 0)
-                    list[ref] = make_int2(lr, __float_as_int(__fsub_rn(__fmul_rn(__fsqrt_rn(d2), lbSlack), A.leafRx[lr])));
-                __syncwarp();
-                continue;
-            }
-            if (lane == 0) list[be].y = __float_as_int(INFINITY);
-            __syncwarp();
-            if (!VW_CHECK(x < L, 1, x)) break;
-            visit(x);
-            // drop the entries whose bound the tighter K now excludes
-            if (cnt > 96 && cmax < INFINITY) {
-                int kept = 0;
+        // 2. best first, in windows: the VW_WIN listed leaves with the
+        // smallest cheap bounds (warp radix select) get their full bound
+        // (original-space leaf ball) and are visited in ascending full bound
+        // until one is pruned; the next window follows while the cheap bound
+        // at the window's edge is not pruned (every leaf left has a cheap
+        // bound, and so a full bound, at least that large)
+        int remaining = cnt;
+        while (remaining > 0) {
+            const uint32_t tau = warp_select(list, cnt, min(VW_WIN, remaining), whist, lane);
+            int nw = 0;
+            for (int pass = 0; pass < 2; pass++)
                 for (int e0 = 0; e0 < cnt; e0 += 32) {
                     const int e = e0 + lane;
-                    const int2 v = e < cnt ? list[e] : make_int2(0, __float_as_int(INFINITY));
-                    const float lb = __int_as_float(v.y);
-                    const bool keep = e < cnt && lb < INFINITY && !pruned(lb);
-                    const unsigned m = __ballot_sync(VW_FULL, keep);
-                    __syncwarp();
-                    if (keep) list[kept + __popc(m & ((1u << lane) - 1u))] = v;
-                    kept += __popc(m);
+                    const int2 v = e < cnt ? list[e] : make_int2(0, (int)VW_TAKEN);
+                    const uint32_t k = (uint32_t)v.y;
+                    const bool take = k != VW_TAKEN && (pass == 0 ? k < tau : k == tau);
+                    const unsigned m = __ballot_sync(VW_FULL, take);
+                    const int at = nw + __popc(m & ((1u << lane) - 1u));
+                    if (take && at < VW_WIN) {
+                        wkey[at] = k;
+                        wleaf[at] = v.x;
+                        list[e].y = (int)VW_TAKEN;
+                    }
+                    nw = min(VW_WIN, nw + __popc(m));
                 }
-                cnt = kept;
-                __syncwarp();
+            __syncwarp();
+            if (nw == 0) break;
+            remaining -= nw;
+            // full bounds, 32 leaves per pass
+            for (int i0 = 0; i0 < nw; i0 += 32) {
+                const int i = i0 + lane;
+                bool need = i < nw && !pruned(vw_unkey(wkey[i]));
+                int lr = need ? wleaf[i] : -1;
+                if (need && !(lr >= 0 && lr < L)) {
+                    VW_CHECK(false, 10, lr);
+                    need = false;
+                    lr = -1;
+                }
+                const float d2 = D2(need ? A.leafMu + (int64_t)lr * ld : nullptr);
+                if (i < nw)
+                    wkey[i] = need ? vw_key(__fsub_rn(__fmul_rn(__fsqrt_rn(d2), lbSlack), A.leafRx[lr])) : VW_TAKEN;
             }
+            for (int i = nw + lane; i < VW_WIN; i += 32) {
+                wkey[i] = VW_TAKEN;
+                wleaf[i] = -1;
+            }
+            __syncwarp();
+            warp_sort_win(wkey, wleaf, lane);
+            for (int i = 0; i < nw; i++) {
+                const uint32_t kk = wkey[i];
+                if (kk == VW_TAKEN || pruned(vw_unkey(kk))) break;
+                const int x = wleaf[i];
+                if (!VW_CHECK(x >= 0 && x < L, 1, x)) break;
+                visit(x);
+            }
+            __syncwarp();
+            if (pruned(vw_unkey(tau))) break;
         }
         // band-in points (FP64-resolved members just inside the radius)
         const int nIn = min(A.inN[a], BCAP);
