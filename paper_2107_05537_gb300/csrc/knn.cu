@@ -675,8 +675,36 @@ k_verify(VwArgs A)
         auto pruned = [&](float lb) -> bool {
             return lb > 0.f && __fmul_rd(__fmul_rd(lb, lb), lbMulF) > __fmul_ru(cmax, cutMulF);
         };
+        int fill = 0;   // slots of the top-KP taken so far (its maximum is +inf until all are)
         // offers the lanes' values (cand) to the top-KP, in lane order
         auto offer = [&](bool cand, float v, int pos) {
+            if (fill < KP) {
+                // empty slots first: appended in lane order, no maximum to keep
+                const unsigned all = __ballot_sync(VW_FULL, cand);
+                const int rank = __popc(all & ((1u << lane) - 1u));
+                const int take = min(__popc(all), KP - fill);
+                if (cand && rank < take) {
+                    vals[fill + rank] = v;
+                    idxs[fill + rank] = pos;
+                }
+                fill += take;
+                cand = cand && rank >= take;
+                if (fill == KP) {
+                    __syncwarp();
+                    float mm = -1.f;
+                    int ms = lane;
+                    for (int j = 0; j < KPW; j++) {
+                        const float x = vals[lane + 32 * j];
+                        if (x > mm) { mm = x; ms = lane + 32 * j; }
+                    }
+                    myMax = mm;
+                    mySlot = ms;
+                    const unsigned mb = __reduce_max_sync(VW_FULL, __float_as_uint(myMax));
+                    const unsigned who = __ballot_sync(VW_FULL, __float_as_uint(myMax) == mb);
+                    cmax = __uint_as_float(mb);
+                    cslot = __shfl_sync(VW_FULL, mySlot, __ffs(who) - 1);
+                }
+            }
             unsigned bits = __ballot_sync(VW_FULL, cand && v < cmax);
             while (bits) {
                 const int src = __ffs(bits) - 1;
@@ -704,15 +732,26 @@ k_verify(VwArgs A)
             }
         };
         // verifies the candidates of leaf l
-        auto visit = [&](int l) {
+        // (lbl: the leaf's full lower bound, ||q - mu_l|| lbSlack - Rx_l)
+        auto visit = [&](int l, float lbl) {
             leaves++;
             const unsigned char cl = leaf_class(sq, sp, s, Rv, Rout, A.meta + (int64_t)l * PM_LEAF_STRIDE);
             const int cb = A.leafChunk[l], ce = A.leafChunk[l + 1];
+            // chunk bounds only if one can prune: every member lies within
+            // ub = ||q - mu_l|| + Rx_l of q (rounded up generously from lbl),
+            // and a chunk's bound never exceeds its nearest member's distance,
+            // so ub^2 <= K leaves every chunk alive
+            const float rxl = A.leafRx[l];
+            const float ubl = __fadd_ru(__fmul_ru(__fadd_ru(fmaxf(lbl, 0.f), rxl), 1.0001f), rxl);
+            const bool chunkBounds = __fmul_ru(ubl, ubl) > cmax;
             for (int c0 = cb; c0 < ce; c0 += 32) {
                 const int c = c0 + lane;
                 const bool vc = c < ce;
-                const float d2c = D2(vc ? A.chunkMu + (int64_t)c * ld : nullptr);
-                const float lbc = vc ? __fsub_rn(__fmul_rn(__fsqrt_rn(d2c), lbSlack), A.chunkRx[c]) : INFINITY;
+                float lbc = -INFINITY;
+                if (chunkBounds) {
+                    const float d2c = D2(vc ? A.chunkMu + (int64_t)c * ld : nullptr);
+                    lbc = vc ? __fsub_rn(__fmul_rn(__fsqrt_rn(d2c), lbSlack), A.chunkRx[c]) : INFINITY;
+                }
                 // the chunks' row ranges, one chunk per lane
                 const long long cOff = vc ? A.chunkOff[c] : 0, cEnd = vc ? A.chunkOff[c + 1] : 0;
                 unsigned alive = __ballot_sync(VW_FULL, vc && !pruned(lbc));
@@ -854,7 +893,7 @@ k_verify(VwArgs A)
                 if (kk == VW_TAKEN || pruned(vw_unkey(kk))) break;
                 const int x = wleaf[i];
                 if (!VW_CHECK(x >= 0 && x < L, 1, x)) break;
-                visit(x);
+                visit(x, vw_unkey(kk));
             }
             __syncwarp();
             if (pruned(vw_unkey(tau))) break;
@@ -871,26 +910,50 @@ k_verify(VwArgs A)
             offer(cand, d2, pos);
         }
         __syncwarp();
-        // 3. guard set: the k-th smallest (value, position) of the top-KP
-        float kth = INFINITY;
+        // 3. guard set: the k-th smallest value of the top-KP (radix select
+        // on the value bits: values are >= +0 or +inf)
         int nfin = 0;
-        for (int j = 0; j < KPW; j++) {
-            const int e = lane + 32 * j;
-            const float v = vals[e];
-            const int p = idxs[e];
-            int rank = 0;
-            for (int f = 0; f < KP; f++) {
-                const float vf = vals[f];
-                rank += (vf < v || (vf == v && idxs[f] < p)) ? 1 : 0;
+        for (int j = 0; j < KPW; j++) nfin += vals[lane + 32 * j] < INFINITY ? 1 : 0;
+        nfin = __reduce_add_sync(VW_FULL, nfin);
+        float K32 = INFINITY;
+        if (nfin >= k) {
+            uint32_t prefix = 0, pmask = 0;
+            int want = k;
+            for (int shift = 24; shift >= 0; shift -= 8) {
+                for (int i = lane; i < 256; i += 32) whist[i] = 0u;
+                __syncwarp();
+                for (int j = 0; j < KPW; j++) {
+                    const uint32_t kb = __float_as_uint(vals[lane + 32 * j]);
+                    if ((kb & pmask) == prefix) atomicAdd(&whist[(kb >> shift) & 255u], 1u);
+                }
+                __syncwarp();
+                uint32_t h[8], sum = 0;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    h[j] = whist[lane * 8 + j];
+                    sum += h[j];
+                }
+                uint32_t incl = sum;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(VW_FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const unsigned hit = __ballot_sync(VW_FULL, incl >= (uint32_t)want);
+                const int fl = hit ? __ffs(hit) - 1 : 31;
+                uint32_t rem = (uint32_t)want - (incl - sum);
+                int j = 0;
+                while (j < 7 && rem > h[j]) {
+                    rem -= h[j];
+                    j++;
+                }
+                const int digit = __shfl_sync(VW_FULL, lane * 8 + j, fl);
+                want = (int)__shfl_sync(VW_FULL, rem, fl);
+                prefix |= (uint32_t)digit << shift;
+                pmask |= 0xFFu << shift;
+                __syncwarp();
             }
-            if (v < INFINITY && rank == k - 1) kth = v;
-            nfin += v < INFINITY ? 1 : 0;
+            K32 = __uint_as_float(prefix);
         }
-        for (int o = 16; o; o >>= 1) {
-            nfin += __shfl_xor_sync(VW_FULL, nfin, o);
-            kth = fminf(kth, __shfl_xor_sync(VW_FULL, kth, o));
-        }
-        const float K32 = nfin >= k ? kth : INFINITY;
         const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
         // entries dropped from the top-KP are >= its final maximum
         if (lane == 0 && seen > KP && cmax <= thrv) atomicOr(A.errFlag, 16);
@@ -919,8 +982,13 @@ k_verify(VwArgs A)
         for (int e = lane; e < G; e += 32) {
             const double dv = gd[e];
             const long long iv = gid[e];
+            // non-negative doubles and +inf order like their bit patterns
+            const long long db = __double_as_longlong(dv);
             int rank = 0;
-            for (int f = 0; f < G; f++) rank += (gd[f] < dv || (gd[f] == dv && gid[f] < iv)) ? 1 : 0;
+            for (int f = 0; f < G; f++) {
+                const long long fb = __double_as_longlong(gd[f]);
+                rank += (fb < db || (fb == db && gid[f] < iv)) ? 1 : 0;
+            }
             if (rank < k) {
                 const int64_t o = (int64_t)q * k + rank;
                 const float fv = __double2float_rn(dv);

@@ -155,6 +155,57 @@ __device__ __forceinline__ float warp_d2(const float4 *__restrict__ q4, const fl
     return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
 }
 
+// Two FP32 values as one 64-bit operand of the packed (f32x2) arithmetic.
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi)
+{
+    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+
+// acc += (q - x)^2 for two coordinates at once: each half is a separate
+// round-to-nearest subtraction and fused multiply-add (the scalar
+// __fsub_rn / __fmaf_rn of that coordinate).
+__device__ __forceinline__ void f32x2_sqdiff_acc(unsigned long long &acc, unsigned long long q,
+                                                 unsigned long long x)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(q), "l"(x));
+    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(acc) : "l"(d));
+}
+
+// warp_d2 with packed arithmetic: each lane keeps two partial sums (even
+// and odd coordinates) and adds them before the butterfly, a different
+// order of the same ld non-negative terms (the verification's error bound
+// (ld + 8) 2^-24 covers any order).
+__device__ __forceinline__ float warp_d2x2(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
+{
+    const int grp = lane >> 3, g = lane & 7;
+    float keep = 0.f;
+    if (p != nullptr) {
+        const char *pc = (const char *)p;
+        for (int b = 0; b < nf4 * 16; b += 128) pm_prefetch_l2(pc + b);
+    }
+#pragma unroll 1
+    for (int j = 0; j < 8; j++) {
+        const float4 *x4 = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 4 * j);
+        unsigned long long acc = 0ull;
+        if (x4 != nullptr) {
+            for (int t = g; t < nf4; t += 8) {
+                const float4 x = __ldg(x4 + t);
+                const float4 qv = q4[t];
+                f32x2_sqdiff_acc(acc, f32x2_pack(qv.x, qv.y), f32x2_pack(x.x, x.y));
+                f32x2_sqdiff_acc(acc, f32x2_pack(qv.z, qv.w), f32x2_pack(x.z, x.w));
+            }
+        }
+        float a = __fadd_rn(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 1));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 2));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 4));
+        if (g == j) keep = a;
+    }
+    // lane (grp, g) holds row grp + 4 g
+    return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
+}
+
 // FP32 -> FP64 re-encoded with integer operations (exact, equal to the
 // conversion instruction), so that the widening does not occupy the FP64
 // pipe; zeros are re-encoded too, subnormals, infinities and NaNs use the
