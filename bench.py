@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "c-ANN queries/s at fixed ratio, 1M×128 k=50; serve p50/p99 ms vs plain FP32"
 K, C, BETA, M_PROJ = 50, 1.5, 0.2809, 15
+# precision modes of pmlsh_knn (bits: 1 tensor-core count, 2 BF16 first-pass verification)
+PRECISIONS = {"fp32": 0, "bf16": 1, "verify": 2, "rerank": 3}
 ALPHA1 = 1 / math.e
 
 
@@ -362,6 +364,7 @@ def knn_leg(pm, ix, Q, k, c, beta, prec, steps, warmup, flush, stream, tag, r_mi
            "unit": "queries/s", "ms_per_step": ms / steps, "gpu_launches": launches,
            "trace": {"mean_rounds": float(st["rounds"].mean()), "mean_candidates": float(st["ncand"].mean()),
                      "mean_verified": float(st["nver"].mean()),
+                     "first_pass_fallback_queries": int((st["fallbacks"] > 0).sum()),
                      "rule_counts": np.bincount(st["rule"], minlength=4).tolist()},
            "kernels": {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in prof.items()}}
     if "k_verify" in prof:
@@ -406,6 +409,19 @@ def leg_c3(pm, prec, steps, warmup, flush, stream):
     for c, k in ((1.5, 10), (1.2, 1), (2.0, 100)):
         out["settings"].append(knn_leg(pm, ix, Qd, k, c, BETA, prec, steps, warmup, flush, stream,
                                        "timed_c3"))
+    # BF16 first-pass verification against FP32 verification, same count
+    # mode, at (c, k) = (1.5, 10): results compared element by element
+    base = prec & ~2
+    cmp = {}
+    for nm, p2 in (("fp32_verify", base), ("bf16_verify", base | 2)):
+        r = knn_leg(pm, ix, Qd, 10, 1.5, BETA, p2, steps, warmup, flush, stream, "timed_c3_verify")
+        got = ix.knn(Qd, k=10, c=1.5, alpha1=ALPHA1, beta=BETA, precision=p2, with_stats=False)
+        r["ids"] = got["ids"]
+        r["dists"] = got["dists"]
+        cmp[nm] = r
+    same = bool(torch.equal(cmp["fp32_verify"].pop("ids"), cmp["bf16_verify"].pop("ids")) and
+                torch.equal(cmp["fp32_verify"].pop("dists"), cmp["bf16_verify"].pop("dists")))
+    out["verify_precision"] = {"k": 10, "c": 1.5, "results_identical": same, **cmp}
     ix.close()
     return out
 
@@ -452,11 +468,11 @@ def leg_c4(pm):
     return out
 
 
-def leg_c5(pm, seconds):
+def leg_c5(pm, seconds, main_name):
     """Serving workload: n = 2*10^6, d = 256 resident (2,000 clusters); an
     open-loop Poisson stream at 5k, 20k and 50k queries/s (request sizes
     log-uniform in [1, 4096], k in {1, 10, 100}, c = 1.5) through the
-    continuous-batching server, BF16 tensor-core count vs FP32."""
+    continuous-batching server, the benchmark's precision mode vs FP32."""
     import torch
     import datagen
     w = datagen.workload("c5", nq=16384)
@@ -467,7 +483,7 @@ def leg_c5(pm, seconds):
     for rate in (5_000.0, 20_000.0, 50_000.0):
         out["rates"][str(int(rate))] = {
             nm: serve_leg(pm, ix, Q, p, rate, seconds, seed=7)
-            for nm, p in (("bf16", pm.PMLSH_BF16_TENSOR), ("fp32", pm.PMLSH_FP32_PLAIN))}
+            for nm, p in ((main_name, PRECISIONS[main_name]), ("fp32", PRECISIONS["fp32"]))}
     ix.close()
     return out
 
@@ -478,7 +494,9 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=list(PRECISIONS),
+                    help="fp32: CUDA-core count, FP32 verification; bf16: tensor-core count; "
+                         "verify: BF16 first-pass verification; rerank: both")
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--leaf-size", type=int, default=0, help="leaf capacity M; 0 = autotuned by pmlsh_build")
     ap.add_argument("--ref-queries", type=int, default=96)
@@ -508,7 +526,7 @@ def main():
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     del Xd
-    prec = pm.PMLSH_BF16_TENSOR if args.precision == "bf16" else pm.PMLSH_FP32_PLAIN
+    prec = PRECISIONS[args.precision]
     Qd = torch.from_numpy(Q).cuda()
     ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
     dd = torch.empty((nq, K), dtype=torch.float32, device="cuda")
@@ -556,23 +574,27 @@ def main():
                   "ms_per_step": sms / args.steps,
                   "ids_identical": bool(torch.equal(ids, ids_main) and torch.equal(dd, dd_main))}
 
-    # the other precision on the same batch: same results, its own speed
+    # the other precision modes on the same batch: same results, own speed
     other = None
     if not args.no_fp32_compare:
-        op = pm.PMLSH_FP32_PLAIN if prec == pm.PMLSH_BF16_TENSOR else pm.PMLSH_BF16_TENSOR
-        ostep = make_step(op)
-        for _ in range(args.warmup):
-            ostep()
-        torch.cuda.synchronize()
-        barrier(ws)
-        oms, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream, "timed_other")
-        barrier(ws)
-        os_ = max_over_ranks(oms / 1000.0, ws)
-        other = {"precision": "fp32" if op == pm.PMLSH_FP32_PLAIN else "bf16",
-                 "value": nq * args.steps * ws / os_, "ms_per_step": os_ * 1000 / args.steps,
-                 "ids_identical": bool(torch.equal(ids, ids_main)),
-                 "kernels": {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in oprof.items()}}
-        ids.copy_(ids_main)
+        other = {}
+        for nm, op in PRECISIONS.items():
+            if op == prec:
+                continue
+            ostep = make_step(op)
+            for _ in range(args.warmup):
+                ostep()
+            torch.cuda.synchronize()
+            barrier(ws)
+            oms, _, oprof, _ = timed_steps(ostep, args.steps, flush, stream, "timed_other")
+            barrier(ws)
+            os_ = max_over_ranks(oms / 1000.0, ws)
+            other[nm] = {"value": nq * args.steps * ws / os_, "ms_per_step": os_ * 1000 / args.steps,
+                         "ids_identical": bool(torch.equal(ids, ids_main)),
+                         "dists_identical": bool(torch.equal(dd, dd_main)),
+                         "kernels": {k2: {"launches": v[0], "ms": round(v[1], 4)} for k2, v in oprof.items()}}
+            ids.copy_(ids_main)
+            dd.copy_(dd_main)
 
     # quality at the operating point: Eq. 11 / Eq. 12 on a query sample
     # against exact neighbours (plain PyTorch FP64 on the GPU)
@@ -646,8 +668,8 @@ def main():
     if rank == 0 and args.serve_seconds > 0:
         serve = {"rate_qps": args.serve_rate, "seconds": args.serve_seconds,
                  "note": "resident 1M x 128 index; request sizes log-uniform [1,4096], k in {1,10,100}"}
-        for nm, p in (("bf16", pm.PMLSH_BF16_TENSOR), ("fp32", pm.PMLSH_FP32_PLAIN)):
-            serve[nm] = serve_leg(pm, ix, Q, p, args.serve_rate, args.serve_seconds, seed=5)
+        for nm in dict.fromkeys((args.precision, "fp32")):
+            serve[nm] = serve_leg(pm, ix, Q, PRECISIONS[nm], args.serve_rate, args.serve_seconds, seed=5)
 
     legs = {}
     want = set(x for x in args.legs.split(",") if x and x != "none")
@@ -675,7 +697,7 @@ def main():
             legs["c4"] = leg_c4(pm)
             torch.cuda.empty_cache()
         if "c5" in want and args.serve_seconds > 0:
-            legs["c5_serve"] = leg_c5(pm, min(args.serve_seconds, 2.0))
+            legs["c5_serve"] = leg_c5(pm, min(args.serve_seconds, 2.0), args.precision)
             torch.cuda.empty_cache()
 
     if rank == 0:
@@ -694,6 +716,7 @@ def main():
                           "mean_candidates": float(stats["ncand"].mean()),
                           "mean_verified": float(stats["nver"].mean()),
                           "mean_leaves_visited": float(stats["leaves"].mean()),
+                          "first_pass_fallback_queries": int((stats["fallbacks"] > 0).sum()),
                           "rule_counts": np.bincount(stats["rule"], minlength=4).tolist()},
                 "build_s": build_s, "with_stats": with_stats, "other_precision": other, "serve": serve,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "legs": legs}

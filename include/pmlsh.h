@@ -91,7 +91,9 @@ typedef struct {
                            Sec. 5.2 (r_min rule); 0 = default 10000 */
     int bf16_shadow;    /* 1 (default) = also keep the tensor-core operand of
                            the projected points (BF16 hi/lo split, 100 bytes
-                           per point) that PMLSH_BF16_TENSOR needs */
+                           per point) that PMLSH_BF16_TENSOR needs and the BF16
+                           residual rows (2 bytes per coordinate plus 4 per
+                           point) that PMLSH_BF16_VERIFY needs */
 } pmlsh_build_opts;
 
 /* Fills `o` with the defaults above. */
@@ -224,7 +226,8 @@ pmlsh_status pmlsh_project_noalloc(const pmlsh_index *index, const float *Q,
 
 /* ------------------------------------------------------- (c,k)-ANN query */
 
-enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_TENSOR = 1 };
+/* Precision modes (bits; PMLSH_BF16_RERANK = both) */
+enum { PMLSH_FP32_PLAIN = 0, PMLSH_BF16_TENSOR = 1, PMLSH_BF16_VERIFY = 2, PMLSH_BF16_RERANK = 3 };
 enum { PMLSH_STOP_LITERAL = 0, PMLSH_STOP_BC_CONSISTENT = 1 };
 
 typedef struct {
@@ -236,14 +239,25 @@ typedef struct {
     double r_min;     /* first radius; <= 0: the Sec. 5.2 rule (r* with
                          F(rstar) = (beta n + k)/n on the sampled distance
                          distribution, r_min = rstar / c) */
-    int precision;    /* how the range rounds count projected distances:
-                         PMLSH_FP32_PLAIN on the CUDA cores; PMLSH_BF16_TENSOR
-                         on the tensor cores (q'.o' from a three-product
-                         BF16 split, FP32 accumulate), every pair whose
-                         decision that value cannot settle is recomputed
-                         exactly.  Both return the same ids, distances and
-                         statistics.  BF16_TENSOR needs an index built with
-                         bf16_shadow = 1 (else PMLSH_EINVAL) */
+    int precision;    /* bit set.  PMLSH_BF16_TENSOR: the range rounds count
+                         projected distances on the tensor cores (q'.o' from a
+                         three-product BF16 split, FP32 accumulate; every
+                         pair whose decision that value cannot settle is
+                         recomputed exactly), else on the CUDA cores.
+                         PMLSH_BF16_VERIFY: verification's first pass reads
+                         BF16 residual rows (each row minus its leaf's
+                         original-space centre, rounded to BF16) and bounds
+                         every candidate's distance from below and above;
+                         the candidates whose lower bound can reach the k-th
+                         upper bound are reranked from the FP32 rows, then
+                         FP64 where FP32 cannot decide; a query whose bounds
+                         cannot settle that set is verified again without
+                         the first pass.  PMLSH_FP32_PLAIN (0): neither.
+                         Every mode returns the same ids, distances and
+                         statistics |C|, rounds, stop rule (n_verified and
+                         leaves_visited describe the work done).  Both BF16
+                         bits need an index built with bf16_shadow = 1 (else
+                         PMLSH_EINVAL) */
     double t;         /* projected radius factor of Lemma 4; <= 0: t from
                          alpha1 by Eq. 9 (t = sqrt(chi^2_{alpha1}(m))) */
     int stop_rule;    /* PMLSH_STOP_LITERAL: stop rule 1 tested at the loop
@@ -263,6 +277,10 @@ typedef struct {
     int32_t fp64_checks;   /* decisions re-taken in FP64 */
     int32_t leaves_visited; /* leaves whose candidates were verified */
     int64_t n_verified;    /* exact distances computed, over all rounds */
+    int32_t first_pass_fallbacks; /* rounds whose BF16 first pass (precision
+                              PMLSH_BF16_VERIFY) could not settle the rerank
+                              set, so that FP32 verification redid them */
+    int32_t reserved;
 } pmlsh_query_stats;
 
 /* Algorithm 2 for nq queries Q [nq][d] (FP32, host or device).

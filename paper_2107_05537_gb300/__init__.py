@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpmlsh.so")
 
 PMLSH_FP32_PLAIN = 0
 PMLSH_BF16_TENSOR = 1
+PMLSH_BF16_VERIFY = 2
+PMLSH_BF16_RERANK = 3
 STOP_LITERAL = 0
 STOP_BC_CONSISTENT = 1
 
@@ -72,7 +74,8 @@ class QueryStats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("n_cand", ctypes.c_int64), ("r_final", ctypes.c_double),
                 ("fp64_checks", ctypes.c_int32), ("leaves_visited", ctypes.c_int32),
-                ("n_verified", ctypes.c_int64)]
+                ("n_verified", ctypes.c_int64), ("first_pass_fallbacks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 # numpy view of pmlsh_query_stats (same field offsets as the ctypes struct)
@@ -429,7 +432,8 @@ class Index:
             res["stats"] = dict(
                 rounds=sv["rounds"].copy(), rule=sv["stop_rule"].copy(),
                 ncand=sv["n_cand"].copy(), r=sv["r_final"].copy(), fp64=sv["fp64_checks"].copy(),
-                nver=sv["n_verified"].copy(), leaves=sv["leaves_visited"].copy())
+                nver=sv["n_verified"].copy(), leaves=sv["leaves_visited"].copy(),
+                fallbacks=sv["first_pass_fallbacks"].copy())
         return res
 
 

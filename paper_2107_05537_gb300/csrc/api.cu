@@ -355,10 +355,9 @@ pmlsh_status pmlsh_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_
     PM_CHECK(std::isfinite(o.t), "t must be finite");
     PM_CHECK(o.stop_rule == PMLSH_STOP_LITERAL || o.stop_rule == PMLSH_STOP_BC_CONSISTENT,
              "unknown stop_rule %d", o.stop_rule);
-    PM_CHECK(o.precision == PMLSH_FP32_PLAIN || o.precision == PMLSH_BF16_TENSOR,
-             "unknown precision mode %d", o.precision);
-    PM_CHECK(o.precision != PMLSH_BF16_TENSOR || ix->Bsplit != nullptr,
-             "PMLSH_BF16_TENSOR needs an index built with bf16_shadow = 1");
+    PM_CHECK(o.precision >= 0 && o.precision <= PMLSH_BF16_RERANK, "unknown precision mode %d", o.precision);
+    PM_CHECK(o.precision == PMLSH_FP32_PLAIN || (ix->Bsplit != nullptr && ix->Xr != nullptr),
+             "BF16 precision modes need an index built with bf16_shadow = 1");
     return pm_knn(ix, Q, nq, &o, out_ids, out_dists, out_err, stats, (cudaStream_t)stream);
 }
 
@@ -376,10 +375,9 @@ pmlsh_status pmlsh_rcbc(pmlsh_index *ix, const float *Q, int64_t nq, double r, c
     PM_CHECK(o.alpha1 > 0.0 && o.alpha1 < 1.0, "alpha1 must be in (0,1)");
     PM_CHECK(o.beta > 0.0 && o.beta <= 1.0, "beta must be in (0,1]");
     PM_CHECK(std::isfinite(o.t), "t must be finite");
-    PM_CHECK(o.precision == PMLSH_FP32_PLAIN || o.precision == PMLSH_BF16_TENSOR,
-             "unknown precision mode %d", o.precision);
-    PM_CHECK(o.precision != PMLSH_BF16_TENSOR || ix->Bsplit != nullptr,
-             "PMLSH_BF16_TENSOR needs an index built with bf16_shadow = 1");
+    PM_CHECK(o.precision >= 0 && o.precision <= PMLSH_BF16_RERANK, "unknown precision mode %d", o.precision);
+    PM_CHECK(o.precision == PMLSH_FP32_PLAIN || (ix->Bsplit != nullptr && ix->Xr != nullptr),
+             "BF16 precision modes need an index built with bf16_shadow = 1");
     o.k = 1;
     o.r_min = r;
     o.stop_rule = PMLSH_STOP_LITERAL;

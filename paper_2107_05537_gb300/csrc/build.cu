@@ -219,6 +219,32 @@ __global__ void k_leaf_orig(const float *__restrict__ X, const int64_t *__restri
     }
 }
 
+// BF16 residuals of the rows from their leaf's original-space centre, for
+// the verification's first pass: r~ = BF16(fl32(x - mu_l)) per coordinate,
+// and per row e >= ||x - mu_l - r~|| (FP64 of the FP32 and BF16 values,
+// inflated, rounded up), so that x = mu_l + r~ + delta with ||delta|| <= e.
+// One block per leaf, one warp per row.
+__global__ void k_build_resid(const float *__restrict__ X, const int64_t *__restrict__ off, int ld,
+                              const float *__restrict__ mu, uint16_t *__restrict__ Xr, float *__restrict__ rowErr)
+{
+    const int64_t l = blockIdx.x;
+    const int64_t a = off[l], b = off[l + 1];
+    const float *M = mu + l * ld;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t p = a + w; p < b; p += nw) {
+        double e2 = 0.0;
+        for (int j = lane; j < ld; j += 32) {
+            const float x = X[p * ld + j], m = M[j];
+            const __nv_bfloat16 r = __float2bfloat16_rn(__fsub_rn(x, m));
+            Xr[p * ld + j] = __bfloat16_as_ushort(r);
+            const double dl = ((double)x - (double)m) - (double)__bfloat162float(r);
+            e2 += dl * dl;
+        }
+        for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        if (lane == 0) rowErr[p] = __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + 1e-30);
+    }
+}
+
 // Tensor-core operand of the projected points: per point the 48 BF16 values
 // [hi(o') | hi(o') | lo(o')] (hi = o' rounded to BF16, lo = the rest rounded),
 // stored leaf by leaf (each leaf starts at a row that is a multiple of 16,
@@ -767,6 +793,8 @@ void pm_free_index(pmlsh_index *ix)
     cudaFree(ix->bOff);
     cudaFree(ix->Bsplit);
     cudaFree(ix->bNorm);
+    cudaFree(ix->Xr);
+    cudaFree(ix->rowErr);
     pm_release_work(ix->work);
 }
 
@@ -1059,6 +1087,12 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
         // padding rows: NaN norms, so that every comparison on them is false
         PM_CUDA(cudaMemsetAsync(ix->bNorm, 0xFF, (size_t)rows * sizeof(float), st));
         PM_LAUNCH("k_build_bsplit", st, k_build_bsplit<<<(unsigned)L, 128, 0, st>>>(ix->O32, ix->leafOff, ix->bOff, L, ix->Bsplit, ix->bNorm));
+        PM_CUDA(cudaGetLastError());
+        // BF16 residual rows for the verification's first pass
+        PM_TRY(dalloc(&ix->Xr, (size_t)n * ld));
+        PM_TRY(dalloc(&ix->rowErr, (size_t)n));
+        PM_LAUNCH("k_build_resid", st, k_build_resid<<<(unsigned)L, 256, 0, st>>>(ix->X, ix->leafOff, ld, ix->leafMu,
+                                                                                  ix->Xr, ix->rowErr));
         PM_CUDA(cudaGetLastError());
     }
     // chunks of <= 32 points inside the leaves, with their own balls

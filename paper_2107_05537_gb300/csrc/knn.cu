@@ -123,6 +123,20 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 // verification kernel walks instead of testing every leaf again, and the
 // sizes of the partially covered leaves (cntPart): with the whole-leaf
 // counts (cntSure) they bound |S_i| from below and above.
+// Eq. 5 test of k_class, per (query, leaf), with the slack of leaf_class and
+// cheaper arithmetic: the centre test on the squared distance against
+// thresholds rounded outward (no square root), the pivot-ring tests against
+// per-query thresholds precomputed with directed rounding.  Every decision is
+// implied by the exact form of leaf_class's inequalities (so a leaf called
+// out holds no point within Rout and a full one only points within Rin); the
+// two tests may differ only at those slack boundaries.
+struct ClassQ {
+    float ro;       // Rout (1 + SLACK), rounded up
+    float rinLo;    // Rin (1 - SLACK), rounded down (<= 0: no inner test)
+};
+constexpr float CL_INV_LO = 1.0f / (1.f - SLACK) * (1.f + 1e-7f);   // >= 1 / (1 - SLACK)
+constexpr float CL_INV_HI = 1.0f / (1.f + SLACK) * (1.f - 1e-7f);   // <= 1 / (1 + SLACK)
+
 template <int QBT>
 __global__ void __launch_bounds__(128)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
@@ -133,8 +147,9 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
 {
     constexpr int W = QBT / 32;
     __shared__ __align__(16) float sq[QBT][PM_MP];
-    __shared__ __align__(16) float sp[QBT][PM_MAX_PIVOTS];
-    __shared__ float sRin[QBT], sRout[QBT];
+    // per pivot: out if HR.max < lowT or HR.min > highT
+    __shared__ __align__(16) float sLow[QBT][PM_MAX_PIVOTS], sHigh[QBT][PM_MAX_PIVOTS];
+    __shared__ __align__(8) ClassQ sT[QBT];
     __shared__ int sCnt[QBT], sPart[QBT];
     const int b = blockIdx.y;
     const int a0 = b * QBT;
@@ -143,16 +158,22 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         int qq = e / PM_MP, j = e % PM_MP;
         sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
     }
-    for (int e = threadIdx.x; e < QBT * PM_MAX_PIVOTS; e += blockDim.x) {
-        int qq = e / PM_MAX_PIVOTS, i = e % PM_MAX_PIVOTS;
-        sp[qq][i] = qq < nb ? qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i] : 0.f;
-    }
     for (int qq = threadIdx.x; qq < QBT; qq += blockDim.x) {
+        float ro = 0.f, rinLo = -1.f;
         if (qq < nb) {
-            Thr T = thr[a0 + qq];
-            sRin[qq] = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
-            sRout[qq] = __fsqrt_rn(T.hi);
+            const Thr T = thr[a0 + qq];
+            const float Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
+            const float Rout = __fsqrt_rn(T.hi);
+            ro = __fmul_ru(Rout, 1.f + SLACK);
+            rinLo = Rin > 0.f ? __fmul_rd(Rin, 1.f - SLACK) : -1.f;
+            for (int i = 0; i < PM_MAX_PIVOTS; i++) {
+                const float dq = qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i];
+                sLow[qq][i] = __fsub_rd(__fmul_rd(dq, 1.f - SLACK), ro);
+                sHigh[qq][i] = __fadd_ru(__fmul_ru(dq, 1.f + SLACK), ro);
+            }
         }
+        sT[qq].ro = ro;
+        sT[qq].rinLo = rinLo;
         sCnt[qq] = 0;
         sPart[qq] = 0;
     }
@@ -168,31 +189,44 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
 #pragma unroll
     for (int j = 0; j < PM_LEAF_STRIDE; j++) Mv[j] = lv ? meta[l * PM_LEAF_STRIDE + j] : 0.f;
     const int cnt = lv ? (int)(off[l + 1] - off[l]) : 0;
+    const float rr = Mv[16];
+    unsigned long long mc[PM_MP / 2];
+#pragma unroll
+    for (int j = 0; j < PM_MP / 2; j++) mc[j] = f32x2_pack(Mv[2 * j], Mv[2 * j + 1]);
 #pragma unroll
     for (int w = 0; w < W; w++) {
         uint32_t bits = 0u;
         for (int j = 0; j < 32; j++) {
             const int qq = w * 32 + j;
             if (qq >= nb) break;
-            // the query's coordinates and pivot distances by 16-byte loads
-            float qv[PM_MP], pv[PM_MAX_PIVOTS];
+            unsigned char c = CL_OUT;
+            if (lv) {
+                // squared centre distance (packed pairs of coordinates)
+                unsigned long long acc = 0ull;
 #pragma unroll
-            for (int j4 = 0; j4 < PM_MP / 4; j4++) {
-                const float4 v = ((const float4 *)sq[qq])[j4];
-                qv[4 * j4] = v.x;
-                qv[4 * j4 + 1] = v.y;
-                qv[4 * j4 + 2] = v.z;
-                qv[4 * j4 + 3] = v.w;
-            }
+                for (int j4 = 0; j4 < PM_MP / 4; j4++) {
+                    const float4 v = ((const float4 *)sq[qq])[j4];
+                    f32x2_sqdiff_acc(acc, f32x2_pack(v.x, v.y), mc[2 * j4]);
+                    f32x2_sqdiff_acc(acc, f32x2_pack(v.z, v.w), mc[2 * j4 + 1]);
+                }
+                const float pd2lo = __fadd_rd(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+                const float pd2hi = __fadd_ru(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+                const ClassQ t = sT[qq];
+                // out: sqrt(d^2) (1 - SLACK) - r > ro, i.e. d^2 > ((ro + r) / (1 - SLACK))^2
+                const float tb = __fmul_ru(__fadd_ru(t.ro, rr), CL_INV_LO);
+                bool out = pd2lo > __fmul_ru(tb, tb);
+                if (!out) {
 #pragma unroll
-            for (int j4 = 0; j4 < PM_MAX_PIVOTS / 4; j4++) {
-                const float4 v = ((const float4 *)sp[qq])[j4];
-                pv[4 * j4] = v.x;
-                pv[4 * j4 + 1] = v.y;
-                pv[4 * j4 + 2] = v.z;
-                pv[4 * j4 + 3] = v.w;
+                    for (int i = 0; i < PM_MAX_PIVOTS; i++)
+                        if (i < s) out |= Mv[32 + i] < sLow[qq][i] || Mv[24 + i] > sHigh[qq][i];
+                }
+                if (!out) {
+                    c = CL_PART;
+                    // full: sqrt(d^2) (1 + SLACK) + r <= Rin (1 - SLACK)
+                    const float f = __fmul_rd(__fsub_rd(t.rinLo, rr), CL_INV_HI);
+                    if (t.rinLo > 0.f && f > 0.f && pd2hi <= __fmul_rd(f, f)) c = CL_FULL;
+                }
             }
-            const unsigned char c = lv ? leaf_class(qv, pv, s, sRin[qq], sRout[qq], Mv) : CL_OUT;
             const int fullAdd = __reduce_add_sync(0xffffffffu, c == CL_FULL ? cnt : 0);
             const int partAdd = __reduce_add_sync(0xffffffffu, c == CL_PART ? cnt : 0);
             if (lane == 0 && fullAdd) atomicAdd(&sCnt[qq], fullAdd);
@@ -505,6 +539,14 @@ struct VwArgs {
     float muMax;                // max ||mu_l|| (rounded up)
     int m;
     int inlineBand;             // 1: decide FP32 band points in FP64 here (no exact count ran)
+    int nwork;                  // entries of `order` to take
+    // BF16 first pass (bf16 != 0): residual rows and their rounding bounds;
+    // a query whose first-pass bounds cannot settle its rerank set is
+    // marked in redo[a] and verified again without the first pass
+    int bf16;
+    const uint16_t *Xr;
+    const float *rowErr;
+    int *redo;
 };
 
 constexpr int VW_WIN = 64;                    // leaves per window of the best-first walk
@@ -512,10 +554,14 @@ constexpr uint32_t VW_TAKEN = 0xFFFFFFFFu;    // list key of a leaf already wind
 
 // Shared memory of one warp: gd[KP] f64, gid[KP] i64, q[ld], vals[KP],
 // idxs[KP], gpos[KP], q'[16], pivot distances[8], P q [PM_PCA], window keys
-// and leaves [VW_WIN], select histogram [256].
-__host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP)
+// and leaves [VW_WIN], select histogram [256] (BF16 first pass: u[ld],
+// lows[KP]).
+__host__ __device__ __forceinline__ size_t verify_smem_warp(int ld, int KP, int bf16 = 0)
 {
-    return (size_t)KP * 28 + (size_t)ld * 4 + 96 + PM_PCA * 4 + VW_WIN * 8 + 256 * 4;
+    // BF16 first pass: also the query's residual from the current leaf centre
+    // [ld] and the first-pass lower bounds of the top-KP [KP]
+    return (size_t)KP * 28 + (size_t)ld * 4 + 96 + PM_PCA * 4 + VW_WIN * 8 + 256 * 4 +
+           (bf16 ? (size_t)ld * 4 + (size_t)KP * 4 : 0);
 }
 
 // Total order of FP32 values as unsigned keys (finite and infinite values).
@@ -622,7 +668,8 @@ k_verify(VwArgs A)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ld = A.ld, KP = A.KP, KPW = A.KP >> 5, k = A.k, s = A.s, nf4 = A.ld >> 2;
     const int64_t L = A.L;
-    unsigned char *wbase = vsm + (size_t)wib * verify_smem_warp(ld, KP);
+    const bool bfAll = A.bf16 != 0;
+    unsigned char *wbase = vsm + (size_t)wib * verify_smem_warp(ld, KP, A.bf16);
     double *gd = (double *)wbase;
     long long *gid = (long long *)(gd + KP);
     float *qs = (float *)(gid + KP);
@@ -635,6 +682,8 @@ k_verify(VwArgs A)
     uint32_t *wkey = (uint32_t *)(sPq + PM_PCA);
     int32_t *wleaf = (int32_t *)(wkey + VW_WIN);
     uint32_t *whist = (uint32_t *)(wleaf + VW_WIN);
+    float *us = (float *)(whist + 256);   // BF16 first pass: fl32(q - mu_l)
+    float *lows = us + ld;                // BF16 first pass: lower bounds (squared) of the top-KP
     const float4 *q4 = (const float4 *)qs;
     int2 *list = A.lists + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * L;
     const double epsv = (double)(ld + 8) * 0x1.0p-24;
@@ -642,12 +691,16 @@ k_verify(VwArgs A)
     // down against K (1 + 3 eps_v) rounded up, so it prunes only what the
     // exact test prunes
     const float lbMulF = __double2float_rd(1.0 - epsv), cutMulF = __double2float_ru(1.0 + 3.0 * epsv);
+    const float cutMulF5 = __double2float_ru(1.0 + 5.0 * epsv);
     const float lbSlack = 1.f - (float)((ld + 8) * 0x1.0p-24) - 1e-6f;
+    // first pass: sqrt(S) in [sqrt(s) (1 - eps_v), sqrt(s) (1 + eps_v)] for
+    // the FP32 value s of the exact sum S
+    const float epsLoF = __double2float_rd(1.0 - epsv), epsHiF = __double2float_ru(1.0 + epsv);
     for (;;) {
         int a = 0;
         if (lane == 0) a = atomicAdd(A.workCtr, 1);
         a = __shfl_sync(VW_FULL, a, 0);
-        if (a >= A.na) break;
+        if (a >= A.nwork) break;
         a = A.order[a];
         if (!VW_CHECK(a >= 0, 7, a)) break;
         const int q = A.act[a];
@@ -656,6 +709,15 @@ k_verify(VwArgs A)
         const float Rv = lov > 0.f ? __fsqrt_rn(lov) : -1.f;
         const bool inl = A.inlineBand != 0 && T.pad == 0.f;
         const float Rout = inl ? __fsqrt_rn(T.hi) : Rv;   // leaves beyond hold no candidate
+        // with the BF16 first pass: pass 0 uses it; a query whose bounds
+        // cannot settle its rerank set is verified again by pass 1 (FP32
+        // rows only), by the same warp
+        for (int pass = bfAll ? 0 : 1; pass < 2; pass++) {
+        const bool bf = pass == 0;
+        // the pruning factor: K (1 + 3 eps_v) for FP32 values; with the
+        // first pass K is an upper bound of the KP-th distance^2, and
+        // K (1 + 5 eps_v) keeps every point of the FP32 guard set unpruned
+        const float cutF = bf ? cutMulF5 : cutMulF;
         int nfp = 0;                                       // FP64 decisions (this lane)
         for (int i = lane; i < ld; i += 32) qs[i] = A.Qd[(int64_t)q * ld + i];
         if (lane < PM_MP) sq[lane] = A.qp32[(int64_t)q * PM_MP + lane];
@@ -666,18 +728,22 @@ k_verify(VwArgs A)
             idxs[e] = 0x7fffffff;
         }
         __syncwarp();
-        auto D2 = [&](const float *p) -> float { return warp_d2(q4, p, nf4, lane); };
+        auto D2 = [&](const float *p) -> float { return warp_d2x2(q4, p, nf4, lane); };
         // top-KP state: lane owns slots lane, lane + 32, ...; cmax is the
         // largest entry (the KP-th smallest so far), cslot its slot
         float cmax = INFINITY, myMax = INFINITY;
         int cslot = 0, mySlot = lane;
         int seen = 0, leaves = 0;
         auto pruned = [&](float lb) -> bool {
-            return lb > 0.f && __fmul_rd(__fmul_rd(lb, lb), lbMulF) > __fmul_ru(cmax, cutMulF);
+            return lb > 0.f && __fmul_rd(__fmul_rd(lb, lb), lbMulF) > __fmul_ru(cmax, cutF);
         };
         int fill = 0;   // slots of the top-KP taken so far (its maximum is +inf until all are)
-        // offers the lanes' values (cand) to the top-KP, in lane order
-        auto offer = [&](bool cand, float v, int pos) {
+        // BF16 first pass: the smallest lower bound (squared) of a candidate
+        // left out of the top-KP (this lane's share)
+        float dropLo = INFINITY;
+        // offers the lanes' values (cand) to the top-KP, in lane order; lo:
+        // the first pass's lower bound (squared), kept beside the value
+        auto offer = [&](bool cand, float v, float lo, int pos) {
             if (fill < KP) {
                 // empty slots first: appended in lane order, no maximum to keep
                 const unsigned all = __ballot_sync(VW_FULL, cand);
@@ -686,6 +752,7 @@ k_verify(VwArgs A)
                 if (cand && rank < take) {
                     vals[fill + rank] = v;
                     idxs[fill + rank] = pos;
+                    if (bf) lows[fill + rank] = lo;
                 }
                 fill += take;
                 cand = cand && rank >= take;
@@ -705,14 +772,23 @@ k_verify(VwArgs A)
                     cslot = __shfl_sync(VW_FULL, mySlot, __ffs(who) - 1);
                 }
             }
+            if (bf && cand && !(v < cmax)) dropLo = fminf(dropLo, lo);
             unsigned bits = __ballot_sync(VW_FULL, cand && v < cmax);
             while (bits) {
                 const int src = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const float val = __shfl_sync(VW_FULL, v, src);
                 const int ps = __shfl_sync(VW_FULL, pos, src);
-                if (!(val < cmax)) continue;
+                const float lv = bf ? __shfl_sync(VW_FULL, lo, src) : 0.f;
+                if (!(val < cmax)) {
+                    if (bf && lane == src) dropLo = fminf(dropLo, lo);
+                    continue;
+                }
                 if (lane == (cslot & 31)) {
+                    if (bf) {
+                        dropLo = fminf(dropLo, lows[cslot]);
+                        lows[cslot] = lv;
+                    }
                     vals[cslot] = val;
                     idxs[cslot] = ps;
                     float mm = -1.f;
@@ -744,6 +820,21 @@ k_verify(VwArgs A)
             const float rxl = A.leafRx[l];
             const float ubl = __fadd_ru(__fmul_ru(__fadd_ru(fmaxf(lbl, 0.f), rxl), 1.0001f), rxl);
             const bool chunkBounds = __fmul_ru(ubl, ubl) > cmax;
+            // BF16 first pass: u = fl32(q - mu_l) and a bound wErr on
+            // ||u - (q - mu_l)|| (each coordinate within 2^-24 of its value)
+            float wErr = 0.f;
+            if (bf) {
+                const float *mu = A.leafMu + (int64_t)l * ld;
+                float un = 0.f;
+                for (int i = lane; i < ld; i += 32) {
+                    const float uu = __fsub_rn(qs[i], mu[i]);
+                    us[i] = uu;
+                    un = __fmaf_ru(uu, uu, un);
+                }
+                for (int o = 16; o; o >>= 1) un = __fadd_ru(un, __shfl_xor_sync(VW_FULL, un, o));
+                wErr = __fmul_ru(0x1.0p-23f, __fsqrt_ru(__fmul_ru(un, 1.0001f)));
+                __syncwarp();
+            }
             for (int c0 = cb; c0 < ce; c0 += 32) {
                 const int c = c0 + lane;
                 const bool vc = c < ce;
@@ -777,9 +868,24 @@ k_verify(VwArgs A)
                         }
                     }
                     if (__ballot_sync(VW_FULL, cand) == 0u) continue;
-                    const float d2 = D2(cand ? A.X + (r0 + lane) * ld : nullptr);
                     seen += __popc(__ballot_sync(VW_FULL, cand));
-                    offer(cand, d2, (int)(r0 + lane));
+                    if (!bf) {
+                        const float d2 = D2(cand ? A.X + (r0 + lane) * ld : nullptr);
+                        offer(cand, d2, d2, (int)(r0 + lane));
+                    } else {
+                        // first pass: ||q - x|| within sqrt(S) +- (wErr + e_row), S the
+                        // exact ||u - r~||^2; offered by the upper bound (squared)
+                        const float s2 = warp_d2_bf16(us, cand ? A.Xr + (r0 + lane) * ld : nullptr, ld, lane);
+                        float hi2 = INFINITY, lo2 = INFINITY;
+                        if (cand) {
+                            const float ae = __fadd_ru(A.rowErr[r0 + lane], wErr);
+                            const float lo = fmaxf(0.f, __fsub_rd(__fmul_rd(__fsqrt_rd(s2), epsLoF), ae));
+                            const float hi = __fadd_ru(__fmul_ru(__fsqrt_ru(s2), epsHiF), ae);
+                            lo2 = __fmul_rd(lo, lo);
+                            hi2 = __fmul_ru(hi, hi);
+                        }
+                        offer(cand, hi2, lo2, (int)(r0 + lane));
+                    }
                 }
             }
         };
@@ -907,18 +1013,19 @@ k_verify(VwArgs A)
             const bool cand = pos >= 0;
             const float d2 = D2(cand ? A.X + (int64_t)pos * ld : nullptr);
             seen += __popc(__ballot_sync(VW_FULL, cand));
-            offer(cand, d2, pos);
+            if (!bf) offer(cand, d2, d2, pos);
+            else offer(cand, __fmul_ru(d2, epsHiF), __fmul_rd(d2, epsLoF), pos);
         }
         __syncwarp();
-        // 3. guard set: the k-th smallest value of the top-KP (radix select
-        // on the value bits: values are >= +0 or +inf)
-        int nfin = 0;
-        for (int j = 0; j < KPW; j++) nfin += vals[lane + 32 * j] < INFINITY ? 1 : 0;
-        nfin = __reduce_add_sync(VW_FULL, nfin);
-        float K32 = INFINITY;
-        if (nfin >= k) {
+        // the kk-th smallest value of the top-KP, +inf if fewer are finite
+        // (radix select on the value bits: values are >= +0 or +inf)
+        auto kth_value = [&](int kk) -> float {
+            int nf = 0;
+            for (int j = 0; j < KPW; j++) nf += vals[lane + 32 * j] < INFINITY ? 1 : 0;
+            nf = __reduce_add_sync(VW_FULL, nf);
+            if (nf < kk) return INFINITY;
             uint32_t prefix = 0, pmask = 0;
-            int want = k;
+            int want = kk;
             for (int shift = 24; shift >= 0; shift -= 8) {
                 for (int i = lane; i < 256; i += 32) whist[i] = 0u;
                 __syncwarp();
@@ -952,11 +1059,49 @@ k_verify(VwArgs A)
                 pmask |= 0xFFu << shift;
                 __syncwarp();
             }
-            K32 = __uint_as_float(prefix);
+            return __uint_as_float(prefix);
+        };
+        if (bf) {
+            // BF16 first pass -> FP32 rerank.  H = the k-th smallest upper
+            // bound; a candidate whose lower bound exceeds H (1 + 6 eps_v)
+            // is farther than the k-th nearest by more than the FP32 guard
+            // band (FP32 values within (1 + eps_v) of exact, guard factor
+            // (1 + 3 eps_v)), so the rest is the rerank set; it must hold
+            // every candidate that qualifies, including those the top-KP
+            // left out (their smallest lower bound is dropLo)
+            const float H = kth_value(k);
+            const float rthr = H < INFINITY ? __fmul_ru(H, __double2float_ru(1.0 + 6.0 * epsv)) : INFINITY;
+            // (lower bounds are >= +0 or +inf: their bits order like them)
+            dropLo = __uint_as_float(__reduce_min_sync(VW_FULL, __float_as_uint(dropLo)));
+            if (!(dropLo > rthr) && H < INFINITY) {
+                if (lane == 0) A.redo[a] = 1;
+                continue;   // pass 1: FP32 rows only
+            }
+            int nR = 0;
+            for (int j = 0; j < KPW; j++) {
+                const int e = lane + 32 * j;
+                const bool in = vals[e] < INFINITY && lows[e] <= rthr;
+                const unsigned m = __ballot_sync(VW_FULL, in);
+                if (in) gpos[nR + __popc(m & ((1u << lane) - 1u))] = idxs[e];
+                nR += __popc(m);
+            }
+            __syncwarp();
+            // exact FP32 values of the rerank set replace the top-KP
+            for (int e0 = 0; e0 < KP; e0 += 32) {
+                const int e = e0 + lane;
+                const int p = e < nR ? gpos[e] : -1;
+                const bool ok = p >= 0 && p < A.n;
+                const float d2 = D2(ok ? A.X + (int64_t)p * ld : nullptr);
+                vals[e] = ok ? d2 : INFINITY;
+                idxs[e] = ok ? p : 0x7fffffff;
+            }
+            __syncwarp();
         }
+        // 3. guard set: the k-th smallest value of the top-KP
+        const float K32 = kth_value(k);
         const float thrv = K32 < INFINITY ? (float)((double)K32 * (1.0 + 3.0 * epsv) + 1e-36) : INFINITY;
         // entries dropped from the top-KP are >= its final maximum
-        if (lane == 0 && seen > KP && cmax <= thrv) atomicOr(A.errFlag, 16);
+        if (!bf && lane == 0 && seen > KP && cmax <= thrv) atomicOr(A.errFlag, 16);
         int G = 0;
         for (int j = 0; j < KPW; j++) {
             const int e = lane + 32 * j;
@@ -1012,6 +1157,8 @@ k_verify(VwArgs A)
             A.nleafOut[a] = leaves;
         }
         __syncwarp();
+        break;
+        }
     }
 }
 
@@ -1638,14 +1785,14 @@ struct VerifyPlan {
     bool grouped = false;
 };
 
-pmlsh_status verify_plan(int ld, int KP, VerifyPlan &vp)
+pmlsh_status verify_plan(int ld, int KP, VerifyPlan &vp, bool bf16 = false)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&vp.nsm, cudaDevAttrMultiProcessorCount, dev);
     // single-query kernel: one warp per query, as many warps per block as
     // shared memory allows (up to VW_MAXWARPS)
-    const size_t vwarp = verify_smem_warp(ld, KP);
+    const size_t vwarp = verify_smem_warp(ld, KP, bf16 ? 1 : 0);
     vp.vWarps = (int)std::min<size_t>(VW_MAXWARPS, (size_t)(227 * 1024) / vwarp);
     if (vp.vWarps < 1) return PMLSH_OK;
     vp.vsmem = (size_t)vp.vWarps * vwarp;
@@ -1656,7 +1803,8 @@ pmlsh_status verify_plan(int ld, int KP, VerifyPlan &vp)
     vp.gvSmem = vp.gvTR > 0 ? gv_smem_bytes(ld, KP, vp.gvTR) : 0;
     if (vp.gvTR > 0 && vp.gvSmem <= (size_t)pm_max_smem_optin()) PM_TRY(gv_ctas_per_sm(vp.gvSmem, &vp.gvPerSM));
     const char *vsel = std::getenv("PMLSH_VERIFY");
-    vp.grouped = vp.gvPerSM > 0 && vsel && std::strcmp(vsel, "group") == 0;
+    // (the grouped kernel has no BF16 first pass)
+    vp.grouped = !bf16 && vp.gvPerSM > 0 && vsel && std::strcmp(vsel, "group") == 0;
     return PMLSH_OK;
 }
 
@@ -1672,9 +1820,10 @@ void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
 {
     const int64_t L = ix->L, ld = ix->ld, W32 = (L + 31) / 32;
     const int KP = (k + 32 + 31) / 32 * 32;
-    const bool tc = precision == PMLSH_BF16_TENSOR;
+    const bool tc = (precision & PMLSH_BF16_TENSOR) != 0;
     VerifyPlan vp;
-    if (verify_plan((int)ld, KP, vp) != PMLSH_OK) vp = VerifyPlan();
+    if (verify_plan((int)ld, KP, vp, (precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr) != PMLSH_OK)
+        vp = VerifyPlan();
     const int64_t nlq = (nq + QB - 1) / QB, nlt = tc ? (nq + TC_QN - 1) / TC_QN : 0;
     const int64_t nlist = std::max(nlq, nlt);
     int64_t vscratch;
@@ -1704,7 +1853,7 @@ void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
         {&KnnWork::subIdx, nq * (12 + BCAP) * 4}, {&KnnWork::subThr, nq * (int64_t)sizeof(Thr)},
         {&KnnWork::subBits, nq * W32 * 4},
         // verification
-        {&KnnWork::partSeen, (3 * nq + 8) * 4}, {&KnnWork::partD, vscratch},
+        {&KnnWork::partSeen, (4 * nq + 8) * 4}, {&KnnWork::partD, vscratch},
     };
 }
 
@@ -1819,11 +1968,11 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     // pinned staging of the per-round decisions: order [nq], bounds [2 nq],
     // verification outputs (k-th distance [nq] f64, fp64/verified/leaves
     // counts [3 nq], error flag)
-    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 7) + 64));
+    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 8) + 64));
     double *stDk = (double *)w.stage.p;
     int32_t *stOrder = (int32_t *)(stDk + nq);
     int *stHs = stOrder + nq, *stHp = stHs + nq, *stFp = stHp + nq, *stNv = stFp + nq, *stNl = stNv + nq,
-        *stVo = stNl + nq, *stErr = stVo + nq;
+        *stVo = stNl + nq, *stRedo = stVo + nq, *stErr = stRedo + nq;
     PM_CUDA(cudaMemcpyAsync(stOrder, order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> orderH;   // host copy, read after the first round's sync
 
@@ -1831,7 +1980,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     std::vector<double> r(nq, rmin);
     std::vector<int32_t> rounds(nq, 0), rule(nq, 0), fp64(nq, 0);
     std::vector<int64_t> ncand(nq, 0), nver(nq, 0);
-    std::vector<int32_t> nleaf(nq, 0);
+    std::vector<int32_t> nleaf(nq, 0), fallback(nq, 0);
     std::vector<char> done(nq, 0);
     PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
 
@@ -1856,8 +2005,9 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     uint32_t *leafBits = grow<uint32_t>(w.leafBits, (size_t)nq * W32, s);
     if (s != PMLSH_OK) return s;
 
+    const bool bf16v = (o->precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr;
     VerifyPlan vp;
-    PM_TRY(verify_plan(ld, KP, vp));
+    PM_TRY(verify_plan(ld, KP, vp, bf16v));
     if (vp.vWarps < 1) {
         pm_set_error("d = %d is too large for the verification kernel's shared memory", d);
         return PMLSH_EINVAL;
@@ -1866,7 +2016,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     const size_t vsmem = vp.vsmem, gvSmem = vp.gvSmem;
     const bool grouped = vp.grouped;
 
-    const bool tensor = o->precision == PMLSH_BF16_TENSOR;
+    const bool tensor = (o->precision & PMLSH_BF16_TENSOR) != 0;
     // the tensor-core count holds all 512 TMEM columns of its SM; its
     // shared memory (over half the SM's) keeps a second CTA off the SM
     if (tensor) PM_TRY(pm_allow_max_dyn_smem((const void *)k_count_tc));
@@ -2089,8 +2239,9 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         // grouped kernel takes groups of GV_WARPS consecutive active queries
         // (locality order), a group's cost class being its costliest
         // member's.
-        int *nverD = grow<int>(w.partSeen, (size_t)3 * na + 8, s);
+        int *nverD = grow<int>(w.partSeen, (size_t)4 * na + 8, s);
         int *vOrder = nverD + 2 * na + 8;
+        int *redoD = vOrder + na;   // queries left by the BF16 first pass
         const int ngroups = (na + GV_WARPS - 1) / GV_WARPS;
         {
             const int nunits = grouped ? ngroups : na;
@@ -2147,6 +2298,12 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             va.O64 = ix->O64; va.qp64 = qp64; va.m = m; va.inlineBand = needExact ? 0 : 1;
             va.leafPmu = ix->leafPmu; va.qpca = qpca; va.qnx = qnx;
             va.muMax = (float)(ix->muMax * (1.0 + 1e-6)) + 1e-30f;
+            va.nwork = na;
+            va.bf16 = bf16v ? 1 : 0;
+            va.Xr = ix->Xr;
+            va.rowErr = ix->rowErr;
+            va.redo = redoD;
+            if (bf16v) PM_CUDA(cudaMemsetAsync(redoD, 0, na * sizeof(int), st));
             PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
@@ -2155,6 +2312,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         PM_CUDA(cudaMemcpyAsync(stDk, dk, na * sizeof(double), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(stFp, fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(stErr, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (bf16v) PM_CUDA(cudaMemcpyAsync(stRedo, redoD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
         const std::vector<double> dkH(stDk, stDk + na);
         const std::vector<int> fpH(stFp, stFp + na), nvH(stNv, stNv + na), nlH(stNl, stNl + na);
@@ -2176,6 +2334,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             const bool budget = count[a] >= B;
             nver[q] += nvH[a];
             nleaf[q] += nlH[a];
+            if (bf16v) fallback[q] += stRedo[a];
             if (rcbc) {
                 // Algorithm 1: the nearest candidate if |C| >= beta n + 1 or it
                 // lies within c r, else nothing
@@ -2236,6 +2395,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             sv[q].fp64_checks = fp64[q];
             sv[q].leaves_visited = nleaf[q];
             sv[q].n_verified = nver[q];
+            sv[q].first_pass_fallbacks = fallback[q];
         }
         PM_CUDA(cudaMemcpyAsync(stats, sv.data(), nq * sizeof(pmlsh_query_stats),
                                 pm_is_device_ptr(stats) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));

@@ -206,6 +206,49 @@ __device__ __forceinline__ float warp_d2x2(const float4 *__restrict__ q4, const 
     return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
 }
 
+// ||u - r~_v||^2 in FP32 of up to 32 BF16 rows r~_v (one per lane, length
+// ld; nullptr: none, the lane then gets 0) against the FP32 vector u in
+// shared memory: eight lanes share a row (16-byte loads of 8 BF16 values),
+// packed arithmetic over coordinate pairs, the eight partial sums added by a
+// butterfly.  Requires ld % 32 == 0 with zero padding in u and the rows.
+__device__ __forceinline__ float warp_d2_bf16(const float *__restrict__ us, const uint16_t *p, int ld, int lane)
+{
+    const int grp = lane >> 3, g = lane & 7, nu4 = ld >> 3;
+    const float4 *u4 = (const float4 *)us;
+    float keep = 0.f;
+    if (p != nullptr) {
+        const char *pc = (const char *)p;
+        for (int b = 0; b < ld * 2; b += 128) pm_prefetch_l2(pc + b);
+    }
+#pragma unroll 1
+    for (int j = 0; j < 8; j++) {
+        const uint4 *x4 = (const uint4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 4 * j);
+        unsigned long long acc = 0ull;
+        if (x4 != nullptr) {
+            for (int t = g; t < nu4; t += 8) {
+                const uint4 x = __ldg(x4 + t);
+                const float4 ua = u4[2 * t], ub = u4[2 * t + 1];
+                // a 32-bit word holds two BF16 values, the lower coordinate
+                // in its low half; as FP32: the half moved to the top bits
+                f32x2_sqdiff_acc(acc, f32x2_pack(ua.x, ua.y),
+                                 ((unsigned long long)(x.x & 0xFFFF0000u) << 32) | (x.x << 16));
+                f32x2_sqdiff_acc(acc, f32x2_pack(ua.z, ua.w),
+                                 ((unsigned long long)(x.y & 0xFFFF0000u) << 32) | (x.y << 16));
+                f32x2_sqdiff_acc(acc, f32x2_pack(ub.x, ub.y),
+                                 ((unsigned long long)(x.z & 0xFFFF0000u) << 32) | (x.z << 16));
+                f32x2_sqdiff_acc(acc, f32x2_pack(ub.z, ub.w),
+                                 ((unsigned long long)(x.w & 0xFFFF0000u) << 32) | (x.w << 16));
+            }
+        }
+        float a = __fadd_rn(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 1));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 2));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 4));
+        if (g == j) keep = a;
+    }
+    return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
+}
+
 // FP32 -> FP64 re-encoded with integer operations (exact, equal to the
 // conversion instruction), so that the widening does not occupy the FP64
 // pipe; zeros are re-encoded too, subnormals, infinities and NaNs use the

@@ -108,6 +108,10 @@ struct pmlsh_index {
     int64_t *bOff = nullptr;       // [L+1] first row of each leaf (multiple of 16)
     uint16_t *Bsplit = nullptr;    // BF16 [rows][48] in the UMMA canonical layout
     float *bNorm = nullptr;        // [rows] ||o'||^2 (FP32 coordinates), NaN on padding rows
+    // BF16 residuals of the rows from their leaf centre (first pass of the
+    // verification) and per row the bound of what the rounding lost
+    uint16_t *Xr = nullptr;        // [n][ld] BF16(fl32(x - mu_leaf))
+    float *rowErr = nullptr;       // [n] >= ||x - mu_leaf - r~||
     std::vector<int64_t> bOffH;
     std::vector<int64_t> chunkOffH;
     std::vector<int32_t> leafChunkH;

@@ -266,7 +266,8 @@ pmlsh_status pmlsh_serve_submit(pmlsh_server *s, const float *Q, int64_t nq, con
     if (o.k < 1 || o.k > PM_MAX_K || o.k > s->ix->n || !(o.c > 1.0) || !std::isfinite(o.c) ||
         !(o.beta > 0.0 && o.beta <= 1.0) || !(o.alpha1 > 0.0 && o.alpha1 < 1.0) || !std::isfinite(o.r_min) ||
         !std::isfinite(o.t) ||
-        (o.precision != PMLSH_FP32_PLAIN && !(o.precision == PMLSH_BF16_TENSOR && s->ix->Bsplit)) ||
+        o.precision < 0 || o.precision > PMLSH_BF16_RERANK ||
+        (o.precision != PMLSH_FP32_PLAIN && !(s->ix->Bsplit && s->ix->Xr)) ||
         (o.stop_rule != PMLSH_STOP_LITERAL && o.stop_rule != PMLSH_STOP_BC_CONSISTENT)) {
         pm_set_error("invalid query options");
         return PMLSH_EINVAL;

@@ -425,3 +425,137 @@ def test_autotuned_leaf_size(c1):
     got = ix.knn(torch.from_numpy(Q).cuda(), k=10, t=t)
     _assert_parity(got, ref)
     ix.close()
+
+
+# BF16 first-pass verification (PMLSH_BF16_VERIFY, and with the tensor-core
+# count PMLSH_BF16_RERANK): BF16 residual rows bound each candidate's
+# distance, the candidates that can reach the k-th upper bound are reranked
+# from the FP32 rows, FP64 where FP32 cannot decide; ids, distances, error
+# bounds and the trace equal the oracle's.
+VERIFY = pm.PMLSH_BF16_VERIFY
+RERANK = pm.PMLSH_BF16_RERANK
+
+
+@pytest.mark.parametrize("precision", [VERIFY, RERANK])
+@pytest.mark.parametrize("stop_rule", [0, 1])
+def test_c1_parity_bf16_verify(c1, stop_rule, precision):
+    X, Q, A = c1
+    got, ref = _run_both(X, Q, A, k=10, stop_rule=stop_rule, precision=precision)
+    _assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("n,d,m,leaf,s,k", [
+    (1000 + 17, 37, 15, 64, 5, 7),
+    (300, 8, 3, 16, 0, 1),
+    (50, 20, 16, 64, 5, 50),
+    (2500, 64, 15, 1024, 8, 20),
+])
+def test_shapes_and_edges_bf16_verify(n, d, m, leaf, s, k):
+    X, Q, _, _ = datagen.mixture(n, d, 7, 1.0, seed=n, nq=33)
+    A = oracle.gen_projection(11, m, d).astype(np.float32)
+    for rmin in (None, 0.5):
+        got, ref = _run_both(X, Q, A, k=k, leaf=leaf, s=s, r_min=rmin, beta=0.1, precision=VERIFY)
+        _assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("n,d,m,leaf,s,k,nq", [
+    (1, 4, 15, 16, 5, 1, 5),
+    (700, 1, 1, 16, 3, 9, 40),
+    (600, 24, 15, 64, 5, 256, 20),
+])
+def test_extreme_shapes_bf16_verify(n, d, m, leaf, s, k, nq):
+    X, Q, _, _ = datagen.mixture(n, d, min(7, n), 1.0, seed=n + d, nq=nq)
+    A = oracle.gen_projection(11, m, d).astype(np.float32)
+    got, ref = _run_both(X, Q, A, k=k, leaf=leaf, s=s, beta=0.1, precision=RERANK)
+    _assert_parity(got, ref)
+
+
+def test_bf16_verify_duplicates_and_far_from_origin():
+    # 40 copies of each of 25 points (ties 40 ways at every distance), and a
+    # data set far from the origin (large residual rounding relative to the
+    # distances): the first pass must hand such queries to the rerank, or
+    # to the FP32 verification, without changing a result
+    base, Q, _, _ = datagen.mixture(25, 16, 5, 1.0, seed=3, nq=20)
+    X = np.repeat(base, 40, axis=0)
+    A = oracle.gen_projection(5, 15, 16).astype(np.float32)
+    for beta in (0.2809, 0.02):
+        got, ref = _run_both(X, Q, A, k=30, beta=beta, leaf=32, precision=VERIFY)
+        _assert_parity(got, ref)
+    X, Q, _, _ = datagen.mixture(3000, 48, 6, 1.0, seed=8, nq=40)
+    X = X + 1000.0
+    Q = Q + 1000.0
+    A = oracle.gen_projection(6, 15, 48).astype(np.float32)
+    got, ref = _run_both(X, Q, A, k=10, precision=RERANK)
+    _assert_parity(got, ref)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(k=10),
+    dict(k=10, r_min=200.0),
+    dict(k=5, beta=0.01, r_min=2.0),
+    dict(k=10, beta=1.0, r_min=400.0),
+])
+def test_no_stats_path_parity_bf16_verify(c1, kw):
+    X, Q, A = c1
+    got, ref = _run_both(X, Q[:64], A, precision=RERANK, with_stats=False, **kw)
+    assert got.get("stats") is None
+    _assert_parity(got, ref, trace=False)
+
+
+@pytest.mark.slow
+def test_c2_full_size_sampled_parity_bf16_verify():
+    w = datagen.workload("c2")
+    X, Q = w["X"], w["Q"]
+    A = oracle.gen_projection(2, 15, 128).astype(np.float32)
+    ix = pm.Index(torch.from_numpy(X).cuda(), proj=A, leaf_size=256)
+    Qd = torch.from_numpy(Q).cuda()
+    got = ix.knn(Qd, k=50, c=1.5, beta=0.2809, precision=RERANK)
+    plain = ix.knn(Qd, k=50, c=1.5, beta=0.2809)
+    fast = ix.knn(Qd, k=50, c=1.5, beta=0.2809, precision=RERANK, with_stats=False)
+    torch.cuda.synchronize()
+    ix.close()
+    assert torch.equal(got["ids"], plain["ids"]) and torch.equal(got["dists"], plain["dists"])
+    assert torch.equal(got["ids"], fast["ids"]) and torch.equal(got["dists"], fast["dists"])
+    assert torch.equal(got["err"], fast["err"])
+    for key in ("rounds", "rule", "ncand", "r"):
+        assert np.array_equal(got["stats"][key], plain["stats"][key]), key
+    rng = np.random.default_rng(2)
+    sample = np.sort(rng.choice(len(Q), size=32, replace=False))
+    t, _, _ = oracle.params(15, 1.5, 1 / E)
+    ref = oracle.knn(X, A, Q[sample], 50, 1.5, t, oracle.budget(len(X), 0.2809, 50),
+                     oracle.rmin_auto(X, 0.2809, 50, 1.5, 3), 0)
+    sub = dict(ids=got["ids"][sample], dists=got["dists"][sample], err=got["err"][sample],
+               stats={k2: v[sample] for k2, v in got["stats"].items()})
+    _assert_parity(sub, ref)
+
+
+@pytest.mark.slow
+def test_c3_full_size_sampled_parity_bf16_verify():
+    w = datagen.workload("c3")
+    X, Q = w["X"], w["Q"]
+    A = oracle.gen_projection(2, 15, X.shape[1]).astype(np.float32)
+    ix = pm.Index(torch.from_numpy(X).cuda(), proj=A, leaf_size=256)
+    Qd = torch.from_numpy(Q).cuda()
+    O = oracle.project(X, A)
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(len(Q), size=10, replace=False))
+    for c, k in ((1.2, 1), (1.5, 10), (2.0, 100)):
+        got = ix.knn(Qd, k=k, c=c, beta=0.2809, precision=RERANK)
+        plain = ix.knn(Qd, k=k, c=c, beta=0.2809, with_stats=False)
+        torch.cuda.synchronize()
+        assert torch.equal(got["ids"], plain["ids"]) and torch.equal(got["dists"], plain["dists"])
+        t, _, _ = oracle.params(15, c, 1 / E)
+        ref = oracle.knn(X, A, Q[sample], k, c, t, oracle.budget(len(X), 0.2809, k),
+                         oracle.rmin_auto(X, 0.2809, k, c, 3), 0, Oproj=O)
+        sub = dict(ids=got["ids"][sample], dists=got["dists"][sample], err=got["err"][sample],
+                   stats={k2: v[sample] for k2, v in got["stats"].items()})
+        _assert_parity(sub, ref)
+    ix.close()
+
+
+def test_bf16_verify_needs_the_residual_rows(c1):
+    X, Q, A = c1
+    ix = pm.Index(X, proj=A, bf16_shadow=False)
+    with pytest.raises(pm.PmlshError):
+        ix.knn(Q[:4], k=3, precision=VERIFY)
+    ix.close()
