@@ -340,16 +340,19 @@ namespace {
 
 struct Bisect {
     const float *O;   // [n][16] FP32 coordinates, original order
-    const float *Xh;  // [n][d] original-space points, original order (host)
-    int d;
     int m, M;
     std::vector<int32_t> perm;
-    std::vector<int64_t> leafOff;
-    std::vector<int64_t> nlo, nhi;
+    // projected-space nodes: position range, children, routing hyperplane
+    std::vector<int64_t> plo, phi;
     std::vector<int32_t> nl, nr;
     std::vector<float> nw;   // [N][16] split hyperplane normal
     std::vector<float> nt;   // [N] split threshold: right iff w . o' >= t
+    std::vector<int32_t> pre;   // [N] index of the node's segment for the refinement, -1 if inner
+    std::vector<int64_t> preLo, preHi;
     std::vector<double> key;
+    // the final layout (assemble): leaf-index ranges of the nodes, leaves, chunks
+    std::vector<int64_t> nlo, nhi;
+    std::vector<int64_t> leafOff{0};
     std::vector<int64_t> chunkOff{0};   // chunk c holds positions [chunkOff[c], chunkOff[c+1])
     std::vector<int32_t> leafChunk{0};  // leaf l holds chunks [leafChunk[l], leafChunk[l+1])
 
@@ -430,221 +433,26 @@ struct Bisect {
         t = 0.5 * (bb - aa);
     }
 
-    int32_t new_node()
+    int32_t new_node(int64_t lo, int64_t hi)
     {
-        int32_t id = (int32_t)nlo.size();
-        nlo.push_back((int64_t)leafOff.size() - 1);
-        nhi.push_back(-1);
+        int32_t id = (int32_t)plo.size();
+        plo.push_back(lo);
+        phi.push_back(hi);
         nl.push_back(-1);
         nr.push_back(-1);
         for (int j = 0; j < PM_MP; j++) nw.push_back(0.f);
         nt.push_back(0.f);
+        pre.push_back(-1);
         return id;
     }
 
-    // 2-means of perm[lo, hi) in the original space (two starts, at most 6
-    // Lloyd steps each); side[] = 1 for points nearer the second mean.
-    // Returns the number of points on side 0 and each side's sum of squared
-    // distances to its mean.
-    int64_t two_means_orig(int64_t lo, int64_t hi, std::vector<double> &ca, std::vector<double> &cb,
-                           std::vector<char> &sd, double *rad0, double *rad1)
+    // A segment the projected bisection does not split further: refined in
+    // the original space afterwards (pm_refine_leaves).
+    int32_t pre_leaf(int32_t id, int64_t lo, int64_t hi)
     {
-        auto dd = [this](const double *c, int32_t id) {
-            const float *x = Xh + (int64_t)id * d;
-            double s = 0.0;
-            for (int j = 0; j < d; j++) { double t = c[j] - (double)x[j]; s += t * t; }
-            return s;
-        };
-        auto row = [this](std::vector<double> &c, int32_t id) {
-            for (int j = 0; j < d; j++) c[j] = Xh[(int64_t)id * d + j];
-        };
-        const int64_t size = hi - lo;
-        // Lloyd steps from the given start; returns (side-0 count, SSEs)
-        auto lloyd = [&](std::vector<double> &a, std::vector<double> &b, std::vector<char> &side, double &s0,
-                         double &s1) {
-            int64_t n0 = 0;
-            side.assign(size, 0);
-            for (int it = 0; it < 6; it++) {
-                n0 = 0;
-                for (int64_t e = lo; e < hi; e++) {
-                    side[e - lo] = dd(b.data(), perm[e]) < dd(a.data(), perm[e]);
-                    n0 += !side[e - lo];
-                }
-                if (n0 == 0 || n0 == size) break;
-                std::vector<double> na(d, 0.0), nb(d, 0.0);
-                for (int64_t e = lo; e < hi; e++) {
-                    const float *x = Xh + (int64_t)perm[e] * d;
-                    double *t = side[e - lo] ? nb.data() : na.data();
-                    for (int j = 0; j < d; j++) t[j] += x[j];
-                }
-                bool moved = false;
-                for (int j = 0; j < d; j++) {
-                    double av = na[j] / (double)n0, bv = nb[j] / (double)(size - n0);
-                    moved |= av != a[j] || bv != b[j];
-                    a[j] = av;
-                    b[j] = bv;
-                }
-                if (!moved) break;
-            }
-            s0 = s1 = 0.0;
-            for (int64_t e = lo; e < hi; e++) {
-                if (side[e - lo]) s1 += dd(b.data(), perm[e]);
-                else s0 += dd(a.data(), perm[e]);
-            }
-            return n0;
-        };
-        // start 1: the mean and the point farthest from it (isolates a far
-        // group); start 2: that point and the point farthest from it (splits
-        // two large groups); the lower sum of squared deviations wins
-        std::vector<double> mu(d, 0.0), a2(d), b2(d);
-        for (int64_t e = lo; e < hi; e++)
-            for (int j = 0; j < d; j++) mu[j] += Xh[(int64_t)perm[e] * d + j];
-        for (int j = 0; j < d; j++) mu[j] /= (double)size;
-        int64_t ib = lo;
-        double best = -1.0;
-        for (int64_t e = lo; e < hi; e++) { double v = dd(mu.data(), perm[e]); if (v > best) { best = v; ib = e; } }
-        ca = mu;
-        cb.assign(d, 0.0);
-        row(cb, perm[ib]);
-        row(a2, perm[ib]);
-        int64_t ic = lo;
-        best = -1.0;
-        for (int64_t e = lo; e < hi; e++) { double v = dd(a2.data(), perm[e]); if (v > best) { best = v; ic = e; } }
-        row(b2, perm[ic]);
-        double s0, s1, t0, t1;
-        std::vector<char> side2;
-        int64_t n0 = lloyd(ca, cb, sd, s0, s1);
-        int64_t m0 = lloyd(a2, b2, side2, t0, t1);
-        if (m0 > 0 && m0 < size && (t0 + t1 < s0 + s1 || n0 == 0 || n0 == size)) {
-            sd.swap(side2);
-            ca.swap(a2);
-            cb.swap(b2);
-            n0 = m0;
-            s0 = t0;
-            s1 = t1;
-        }
-        *rad0 = s0;
-        *rad1 = s1;
-        return n0;
-    }
-
-    // Sum of squared distances of perm[lo, hi) to its mean.
-    double sse_orig(int64_t lo, int64_t hi) const
-    {
-        std::vector<double> c(d, 0.0);
-        for (int64_t e = lo; e < hi; e++)
-            for (int j = 0; j < d; j++) c[j] += Xh[(int64_t)perm[e] * d + j];
-        for (int j = 0; j < d; j++) c[j] /= (double)(hi - lo);
-        double r = 0.0;
-        for (int64_t e = lo; e < hi; e++) {
-            const float *x = Xh + (int64_t)perm[e] * d;
-            double s = 0.0;
-            for (int j = 0; j < d; j++) { double t = c[j] - (double)x[j]; s += t * t; }
-            r += s;
-        }
-        return r;
-    }
-
-    // Stable move of side-0 points of perm[lo, hi) to the front.
-    void apply_sides(int64_t lo, int64_t hi, const std::vector<char> &sd)
-    {
-        std::vector<int32_t> a, b2;
-        for (int64_t e = lo; e < hi; e++) (sd[e - lo] ? b2 : a).push_back(perm[e]);
-        std::copy(a.begin(), a.end(), perm.begin() + lo);
-        std::copy(b2.begin(), b2.end(), perm.begin() + lo + (int64_t)a.size());
-    }
-
-    // Splits a leaf's points perm[lo, hi) into chunks of at most 32 points by
-    // original-space 2-means (the unit that verification stages and bounds);
-    // points inside a chunk are kept in id order.
-    void chunks(int64_t lo, int64_t hi, std::vector<double> &ca, std::vector<double> &cb, std::vector<char> &sd)
-    {
-        const int64_t size = hi - lo;
-        if (size <= 32) {
-            std::sort(perm.begin() + lo, perm.begin() + hi);
-            chunkOff.push_back(hi);
-            return;
-        }
-        double r0, r1;
-        int64_t left = two_means_orig(lo, hi, ca, cb, sd, &r0, &r1);
-        const int64_t minside = std::max<int64_t>(1, size / 16);
-        if (left < minside || left > size - minside) {
-            left = size / 2;   // degenerate: split by position
-        } else {
-            apply_sides(lo, hi, sd);
-        }
-        chunks(lo, lo + left, ca, cb, sd);
-        chunks(lo + left, hi, ca, cb, sd);
-    }
-
-    // A projected-space leaf is refined in the original space (a leaf that
-    // straddles separate groups of points would give the verification's
-    // distance bounds nothing to prune): outliers are split off, then groups
-    // that 2-means separates well (one Gaussian blob split in two keeps almost
-    // all of its squared deviation); each part is refined again.
-    // Makes node `id` an inner node over perm[lo, lo+left) and perm[lo+left, hi),
-    // each refined again.  Routing hyperplane w = 0, t = 0: queries go right
-    // (the split is in the original space, which routing does not see).
-    int32_t refine_split(int32_t id, int64_t lo, int64_t left, int64_t hi)
-    {
-        int32_t Lc = new_node();
-        leaf(Lc, lo, lo + left);
-        int32_t Rc = new_node();
-        leaf(Rc, lo + left, hi);
-        nl[id] = Lc;
-        nr[id] = Rc;
-        nhi[id] = (int64_t)leafOff.size() - 1;
-        return id;
-    }
-
-    int32_t leaf(int32_t id, int64_t lo, int64_t hi)
-    {
-        std::vector<double> ca, cb;
-        std::vector<char> sd;
-        const int64_t size = hi - lo;
-        if (size >= 2) {
-            // (1) outliers: points farther from the mean than twice the median
-            //     distance are split off (a few stray points of other groups
-            //     would otherwise set the whole leaf's radius; in a Gaussian
-            //     blob of dimension >= 16 the largest distance stays well
-            //     below twice the median)
-            std::vector<double> mu(d, 0.0), dist(size);
-            for (int64_t e = lo; e < hi; e++)
-                for (int j = 0; j < d; j++) mu[j] += Xh[(int64_t)perm[e] * d + j];
-            for (int j = 0; j < d; j++) mu[j] /= (double)size;
-            for (int64_t e = lo; e < hi; e++) {
-                const float *x = Xh + (int64_t)perm[e] * d;
-                double s = 0.0;
-                for (int j = 0; j < d; j++) { double t = mu[j] - (double)x[j]; s += t * t; }
-                dist[e - lo] = std::sqrt(s);
-            }
-            std::vector<double> tmp(dist);
-            const int64_t kmed = size / 2;
-            std::nth_element(tmp.begin(), tmp.begin() + kmed, tmp.end());
-            const double cut = 2.0 * tmp[kmed];
-            int64_t nout = 0;
-            for (int64_t e = 0; e < size; e++) nout += dist[e] > cut;
-            if (nout > 0 && nout < size) {
-                sd.assign(size, 0);
-                for (int64_t e = 0; e < size; e++) sd[e] = dist[e] > cut;
-                apply_sides(lo, hi, sd);
-                return refine_split(id, lo, size - nout, hi);
-            }
-            // (2) separate groups: an original-space 2-means split that lowers
-            //     the sum of squared deviations below 0.85 of the whole's (a
-            //     Gaussian blob of dimension d keeps about 1 - 2/(pi d) of it;
-            //     k separate equal groups keep about (k-2)/(k-1))
-            double s0, s1;
-            int64_t left = two_means_orig(lo, hi, ca, cb, sd, &s0, &s1);
-            if (left >= 1 && left <= size - 1 && s0 + s1 < 0.85 * sse_orig(lo, hi)) {
-                apply_sides(lo, hi, sd);
-                return refine_split(id, lo, left, hi);
-            }
-        }
-        chunks(lo, hi, ca, cb, sd);
-        leafChunk.push_back((int32_t)chunkOff.size() - 1);
-        leafOff.push_back(hi);
-        nhi[id] = (int64_t)leafOff.size() - 1;
+        pre[id] = (int32_t)preLo.size();
+        preLo.push_back(lo);
+        preHi.push_back(hi);
         return id;
     }
 
@@ -657,9 +465,9 @@ struct Bisect {
     // segment falls back to the median along the same direction.
     int32_t split(int64_t lo, int64_t hi)
     {
-        const int32_t id = new_node();
+        const int32_t id = new_node(lo, hi);
         const int64_t size = hi - lo;
-        if (size <= 8) return leaf(id, lo, hi);
+        if (size <= 8) return pre_leaf(id, lo, hi);
         double w[PM_MP], t;
         two_means(lo, hi, w, t);
         for (int64_t e = lo; e < hi; e++) {
@@ -682,13 +490,13 @@ struct Bisect {
                 std::partition(perm.begin() + lo, perm.begin() + hi, [K, t](int32_t a) { return K[a] < t; });
             }
         } else {
-            if (left == 0 || left == size) return leaf(id, lo, hi);
+            if (left == 0 || left == size) return pre_leaf(id, lo, hi);
             std::vector<int32_t> saved(perm.begin() + lo, perm.begin() + hi);
             std::partition(perm.begin() + lo, perm.begin() + hi, [K, t](int32_t a) { return K[a] < t; });
             double rp = radius(lo, hi), rl = radius(lo, lo + left), rr = radius(lo + left, hi);
             if (!(std::max(rl, rr) < 0.85 * rp)) {
                 std::copy(saved.begin(), saved.end(), perm.begin() + lo);
-                return leaf(id, lo, hi);
+                return pre_leaf(id, lo, hi);
             }
         }
         for (int j = 0; j < PM_MP; j++) nw[(size_t)id * PM_MP + j] = (float)w[j];
@@ -697,8 +505,84 @@ struct Bisect {
         int32_t R = split(lo + left, hi);
         nl[id] = L;
         nr[id] = R;
-        nhi[id] = (int64_t)leafOff.size() - 1;
         return id;
+    }
+
+    // The hierarchy after the original-space refinement: the refined
+    // segments' sub-trees replace their nodes (refinement splits route
+    // queries right: w = 0, t = 0), leaves and chunks in position order, and
+    // every node's leaf-index range.
+    void assemble(const std::vector<LrResult> &res)
+    {
+        const size_t P = plo.size();
+        nlo.assign(P, 0);
+        nhi.assign(P, 0);
+        std::vector<int64_t> stack{0};
+        std::vector<char> seen(P, 0);
+        // iterative DFS: a node's leaf range opens on entry, closes on exit
+        while (!stack.empty()) {
+            const int64_t e = stack.back();
+            if (!seen[e]) {
+                seen[e] = 1;
+                nlo[e] = (int64_t)leafOff.size() - 1;
+                if (pre[e] >= 0) {
+                    expand((int32_t)e, res[pre[e]], plo[e]);
+                    nhi[e] = (int64_t)leafOff.size() - 1;
+                    stack.pop_back();
+                } else {
+                    stack.push_back(nr[e]);
+                    stack.push_back(nl[e]);
+                }
+            } else {
+                nhi[e] = (int64_t)leafOff.size() - 1;
+                stack.pop_back();
+            }
+        }
+    }
+
+    // Appends the refined segment's sub-tree below node e (local node 0).
+    void expand(int32_t e, const LrResult &r, int64_t base)
+    {
+        const int nn = (int)r.node.size();
+        std::vector<int32_t> gid(nn, -1);
+        gid[0] = e;
+        for (int i = 1; i < nn; i++) {
+            gid[i] = (int32_t)plo.size();
+            plo.push_back(base + r.node[i].x);
+            phi.push_back(base + r.node[i].y);
+            nl.push_back(-1);
+            nr.push_back(-1);
+            for (int j = 0; j < PM_MP; j++) nw.push_back(0.f);
+            nt.push_back(0.f);
+            pre.push_back(-1);
+            nlo.push_back(0);
+            nhi.push_back(0);
+        }
+        for (int i = 0; i < nn; i++)
+            if (r.node[i].z >= 0) {
+                nl[gid[i]] = gid[r.node[i].z];
+                nr[gid[i]] = gid[r.node[i].w];
+            }
+        // leaves in position order; a local node's leaves are those inside
+        // its position range
+        const int64_t firstLeaf = (int64_t)leafOff.size() - 1;
+        for (size_t li = 0; li < r.leaf.size(); li++) {
+            const int4 lf = r.leaf[li];
+            const int cEnd = li + 1 < r.leaf.size() ? r.leaf[li + 1].w : (int)r.chunkEnd.size();
+            for (int c = lf.w; c < cEnd; c++) chunkOff.push_back(base + r.chunkEnd[c]);
+            leafChunk.push_back((int32_t)chunkOff.size() - 1);
+            leafOff.push_back(base + lf.y);
+        }
+        for (int i = 1; i < nn; i++) {
+            int64_t a = -1, b = -1;
+            for (size_t li = 0; li < r.leaf.size(); li++)
+                if (r.leaf[li].x >= r.node[i].x && r.leaf[li].y <= r.node[i].y) {
+                    if (a < 0) a = firstLeaf + (int64_t)li;
+                    b = firstLeaf + (int64_t)li + 1;
+                }
+            nlo[gid[i]] = a;
+            nhi[gid[i]] = b;
+        }
     }
 };
 
@@ -939,24 +823,27 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
         std::memcpy(&mn, &mxh, sizeof(mn));
         ix->maxNorm = mn;
     }
-    std::vector<float> Xhost;
-    const float *Xh = X;
-    if (x_on_device) {
-        Xhost.resize((size_t)n * d);
-        PM_CUDA(cudaMemcpy(Xhost.data(), X, Xhost.size() * sizeof(float), cudaMemcpyDeviceToHost));
-        Xh = Xhost.data();
-    }
     Bisect bs;
     bs.O = O32h.data();
-    bs.Xh = Xh;
-    bs.d = d;
     bs.m = m;
     bs.M = ix->M;
     bs.perm.resize(n);
     bs.key.resize(n);
     std::iota(bs.perm.begin(), bs.perm.end(), 0);
-    bs.leafOff.push_back(0);
     bs.split(0, n);
+    // original-space refinement of the segments on the device, over the
+    // device copy of X (original order)
+    {
+        int32_t *permD = nullptr;
+        PM_TRY(dalloc(&permD, n));
+        struct G4 { int32_t *p; ~G4() { cudaFree(p); } } g4{permD};
+        PM_CUDA(cudaMemcpyAsync(permD, bs.perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        std::vector<LrResult> res;
+        PM_TRY(pm_refine_leaves(Xo, ld, d, permD, bs.preLo, bs.preHi, res, st));
+        PM_CUDA(cudaMemcpyAsync(bs.perm.data(), permD, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        bs.assemble(res);
+    }
     ix->permH = std::move(bs.perm);
     ix->chunkOffH = std::move(bs.chunkOff);
     ix->leafChunkH = std::move(bs.leafChunk);

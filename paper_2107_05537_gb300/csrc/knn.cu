@@ -138,7 +138,7 @@ constexpr float CL_INV_LO = 1.0f / (1.f - SLACK) * (1.f + 1e-7f);   // >= 1 / (1
 constexpr float CL_INV_HI = 1.0f / (1.f + SLACK) * (1.f - 1e-7f);   // <= 1 / (1 + SLACK)
 
 template <int QBT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, const int64_t *__restrict__ bOff,
@@ -227,10 +227,12 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                     if (t.rinLo > 0.f && f > 0.f && pd2hi <= __fmul_rd(f, f)) c = CL_FULL;
                 }
             }
-            const int fullAdd = __reduce_add_sync(0xffffffffu, c == CL_FULL ? cnt : 0);
-            const int partAdd = __reduce_add_sync(0xffffffffu, c == CL_PART ? cnt : 0);
-            if (lane == 0 && fullAdd) atomicAdd(&sCnt[qq], fullAdd);
-            if (lane == 0 && partAdd) atomicAdd(&sPart[qq], partAdd);
+            // the warp's whole-leaf and partial-leaf sizes for this query in
+            // one reduction (each at most 32 leaves x 1024 points < 2^16)
+            const unsigned both = __reduce_add_sync(
+                0xffffffffu, c == CL_FULL ? ((unsigned)cnt << 16) : (c == CL_PART ? (unsigned)cnt : 0u));
+            if (lane == 0 && (both >> 16)) atomicAdd(&sCnt[qq], (int)(both >> 16));
+            if (lane == 0 && (both & 0xFFFFu)) atomicAdd(&sPart[qq], (int)(both & 0xFFFFu));
             bits |= (uint32_t)(c == CL_PART) << j;
             // per query: the warp's 32 leaves that Eq. 5 does not exclude
             const uint32_t word = __ballot_sync(0xffffffffu, c != CL_OUT);
@@ -728,7 +730,7 @@ k_verify(VwArgs A)
             idxs[e] = 0x7fffffff;
         }
         __syncwarp();
-        auto D2 = [&](const float *p) -> float { return warp_d2x2(q4, p, nf4, lane); };
+        auto D2 = [&](const float *p) -> float { return warp_d2x4(q4, p, nf4, lane); };
         // top-KP state: lane owns slots lane, lane + 32, ...; cmax is the
         // largest entry (the KP-th smallest so far), cslot its slot
         float cmax = INFINITY, myMax = INFINITY;
@@ -875,7 +877,7 @@ k_verify(VwArgs A)
                     } else {
                         // first pass: ||q - x|| within sqrt(S) +- (wErr + e_row), S the
                         // exact ||u - r~||^2; offered by the upper bound (squared)
-                        const float s2 = warp_d2_bf16(us, cand ? A.Xr + (r0 + lane) * ld : nullptr, ld, lane);
+                        const float s2 = warp_d2_bf16x4(us, cand ? A.Xr + (r0 + lane) * ld : nullptr, ld, lane);
                         float hi2 = INFINITY, lo2 = INFINITY;
                         if (cand) {
                             const float ae = __fadd_ru(A.rowErr[r0 + lane], wErr);
@@ -1112,14 +1114,29 @@ k_verify(VwArgs A)
             G += __popc(m);
         }
         __syncwarp();
-        for (int e = lane; e < G; e += 32) {
-            const int p = gpos[e];
-            if (VW_CHECK(p >= 0 && p < A.n, 5, p)) {
-                gd[e] = dist64_widen(A.X + (int64_t)p * ld, qs, A.d);
-                gid[e] = A.perm[p];
-            } else {
-                gd[e] = INFINITY;
-                gid[e] = 0x7fffffffffffffffLL;
+        // two rows per lane at a time: two independent chains of the
+        // sequential FP64 sum (each row's own order is unchanged)
+        for (int e = lane; e < G; e += 64) {
+            const int e2 = e + 32;
+            int p = gpos[e], p2 = e2 < G ? gpos[e2] : -1;
+            if (!VW_CHECK(p >= 0 && p < A.n, 5, p)) p = -1;
+            if (e2 < G && !VW_CHECK(p2 >= 0 && p2 < A.n, 5, p2)) p2 = -1;
+            double s1 = 0.0, s2 = 0.0;
+            const float *x1 = A.X + (int64_t)max(p, 0) * ld, *x2 = A.X + (int64_t)max(p2, 0) * ld;
+            for (int i = 0; i < A.d; i++) {
+                const double qd = f2d_exact(qs[i]);
+                const double t1 = __dsub_rn(f2d_exact(x1[i]), qd);
+                s1 = __dadd_rn(s1, __dmul_rn(t1, t1));
+                if (p2 >= 0) {
+                    const double t2 = __dsub_rn(f2d_exact(x2[i]), qd);
+                    s2 = __dadd_rn(s2, __dmul_rn(t2, t2));
+                }
+            }
+            gd[e] = p >= 0 ? __dsqrt_rn(s1) : (double)INFINITY;
+            gid[e] = p >= 0 ? (long long)A.perm[p] : 0x7fffffffffffffffLL;
+            if (e2 < G) {
+                gd[e2] = p2 >= 0 ? __dsqrt_rn(s2) : (double)INFINITY;
+                gid[e2] = p2 >= 0 ? (long long)A.perm[p2] : 0x7fffffffffffffffLL;
             }
         }
         __syncwarp();
@@ -1819,10 +1836,11 @@ void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
                     std::vector<std::pair<DevBuf KnnWork::*, int64_t>> &out)
 {
     const int64_t L = ix->L, ld = ix->ld, W32 = (L + 31) / 32;
-    const int KP = (k + 32 + 31) / 32 * 32;
+    const bool bfv = (precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr;
+    const int KP = (k + (bfv ? 64 : 32) + 31) / 32 * 32;
     const bool tc = (precision & PMLSH_BF16_TENSOR) != 0;
     VerifyPlan vp;
-    if (verify_plan((int)ld, KP, vp, (precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr) != PMLSH_OK)
+    if (verify_plan((int)ld, KP, vp, bfv) != PMLSH_OK)
         vp = VerifyPlan();
     const int64_t nlq = (nq + QB - 1) / QB, nlt = tc ? (nq + TC_QN - 1) / TC_QN : 0;
     const int64_t nlist = std::max(nlq, nlt);
@@ -1938,7 +1956,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             rmin = 1.0;
         }
     }
-    const int KP = (k + 32 + 31) / 32 * 32;
+    // top-KP size: KP - k entries beyond the k-th catch the FP32 guard band;
+    // the BF16 first pass keeps more, its bounds being wider
+    const bool bf16v = (o->precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr;
+    const int KP = (k + (bf16v ? 64 : 32) + 31) / 32 * 32;
     pmlsh_status s = PMLSH_OK;
     float *Qd = grow<float>(w.Qd, (size_t)nq * ld, s);
     double *qp64 = grow<double>(w.qp64, (size_t)nq * PM_MP, s);
@@ -2005,7 +2026,6 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     uint32_t *leafBits = grow<uint32_t>(w.leafBits, (size_t)nq * W32, s);
     if (s != PMLSH_OK) return s;
 
-    const bool bf16v = (o->precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr;
     VerifyPlan vp;
     PM_TRY(verify_plan(ld, KP, vp, bf16v));
     if (vp.vWarps < 1) {

@@ -206,6 +206,48 @@ __device__ __forceinline__ float warp_d2x2(const float4 *__restrict__ q4, const 
     return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
 }
 
+// warp_d2x2 with four lanes per row: eight rows per round and four rounds,
+// each lane's loads of a round issued together (nf4 / 4 float4 per lane), so
+// that half as many dependent load rounds stand between the rows and their
+// distances; each lane sums its coordinates in two packed partial sums, the
+// four lanes of a row are added by a butterfly.  Requires nf4 % 4 == 0.
+__device__ __forceinline__ float warp_d2x4(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
+{
+    const int grp = lane >> 2, g = lane & 3;
+    float keep = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 4; j++) {
+        const float4 *x4 = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 8 * j);
+        unsigned long long acc = 0ull;
+        if (x4 != nullptr) {
+            int t = g;
+            for (; t + 28 < nf4; t += 32) {
+                float4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) x[u] = __ldg(x4 + t + 4 * u);
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float4 qv = q4[t + 4 * u];
+                    f32x2_sqdiff_acc(acc, f32x2_pack(qv.x, qv.y), f32x2_pack(x[u].x, x[u].y));
+                    f32x2_sqdiff_acc(acc, f32x2_pack(qv.z, qv.w), f32x2_pack(x[u].z, x[u].w));
+                }
+            }
+            for (; t < nf4; t += 4) {
+                const float4 x = __ldg(x4 + t);
+                const float4 qv = q4[t];
+                f32x2_sqdiff_acc(acc, f32x2_pack(qv.x, qv.y), f32x2_pack(x.x, x.y));
+                f32x2_sqdiff_acc(acc, f32x2_pack(qv.z, qv.w), f32x2_pack(x.z, x.w));
+            }
+        }
+        float a = __fadd_rn(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 1));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 2));
+        if (g == j) keep = a;
+    }
+    // lane (grp, g) holds row grp + 8 g; row v sits at lane 4 (v % 8) + v / 8
+    return __shfl_sync(VW_FULL, keep, ((lane & 7) << 2) | (lane >> 3));
+}
+
 // ||u - r~_v||^2 in FP32 of up to 32 BF16 rows r~_v (one per lane, length
 // ld; nullptr: none, the lane then gets 0) against the FP32 vector u in
 // shared memory: eight lanes share a row (16-byte loads of 8 BF16 values),
@@ -247,6 +289,47 @@ __device__ __forceinline__ float warp_d2_bf16(const float *__restrict__ us, cons
         if (g == j) keep = a;
     }
     return __shfl_sync(VW_FULL, keep, ((lane & 3) << 3) | (lane >> 2));
+}
+
+// warp_d2_bf16 with four lanes per row (eight rows per round, four rounds),
+// each lane's loads of a round issued together.  Requires ld % 32 == 0.
+__device__ __forceinline__ float warp_d2_bf16x4(const float *__restrict__ us, const uint16_t *p, int ld, int lane)
+{
+    const int grp = lane >> 2, g = lane & 3, nu4 = ld >> 3;
+    const float4 *u4 = (const float4 *)us;
+    float keep = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 4; j++) {
+        const uint4 *x4 = (const uint4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 8 * j);
+        unsigned long long acc = 0ull;
+        if (x4 != nullptr) {
+            auto step = [&](const uint4 x, int t) {
+                const float4 ua = u4[2 * t], ub = u4[2 * t + 1];
+                f32x2_sqdiff_acc(acc, f32x2_pack(ua.x, ua.y),
+                                 ((unsigned long long)(x.x & 0xFFFF0000u) << 32) | (x.x << 16));
+                f32x2_sqdiff_acc(acc, f32x2_pack(ua.z, ua.w),
+                                 ((unsigned long long)(x.y & 0xFFFF0000u) << 32) | (x.y << 16));
+                f32x2_sqdiff_acc(acc, f32x2_pack(ub.x, ub.y),
+                                 ((unsigned long long)(x.z & 0xFFFF0000u) << 32) | (x.z << 16));
+                f32x2_sqdiff_acc(acc, f32x2_pack(ub.z, ub.w),
+                                 ((unsigned long long)(x.w & 0xFFFF0000u) << 32) | (x.w << 16));
+            };
+            int t = g;
+            for (; t + 12 < nu4; t += 16) {
+                uint4 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) x[u] = __ldg(x4 + t + 4 * u);
+#pragma unroll
+                for (int u = 0; u < 4; u++) step(x[u], t + 4 * u);
+            }
+            for (; t < nu4; t += 4) step(__ldg(x4 + t), t);
+        }
+        float a = __fadd_rn(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 1));
+        a = __fadd_rn(a, __shfl_xor_sync(VW_FULL, a, 2));
+        if (g == j) keep = a;
+    }
+    return __shfl_sync(VW_FULL, keep, ((lane & 7) << 2) | (lane >> 3));
 }
 
 // FP32 -> FP64 re-encoded with integer operations (exact, equal to the

@@ -146,6 +146,20 @@ void pm_launch_project64(const float *X, int64_t n, int ld, int d, int m, const 
 void pm_launch_project64_noprof(const float *X, int64_t n, int ld, int d, int m, const float *A,
                                 double *O64, float *O32, cudaStream_t st, int ostride);
 
+// Original-space refinement of the leaf layout (layout.cu).  For each
+// segment [segLo[i], segHi[i]) of positions of permD (at most 1024 points,
+// ids into the original-order rows Xo [n][ld]), permD is reordered within the
+// segment and res[i] receives the segment's sub-hierarchy: node {begin, end,
+// left, right} (offsets from segLo[i]; local node ids, -1 for a leaf; node 0
+// is the segment itself), leaf {begin, end, node, first chunk} in position
+// order, and chunk end offsets.
+struct LrResult {
+    std::vector<int4> node, leaf;
+    std::vector<int32_t> chunkEnd;
+};
+pmlsh_status pm_refine_leaves(const float *Xo, int ld, int d, int32_t *permD, const std::vector<int64_t> &segLo,
+                              const std::vector<int64_t> &segHi, std::vector<LrResult> &res, cudaStream_t st);
+
 // Query projection (api.cu helper in knn.cu): stages Q into `staging`
 // ([nq][ld], device) and projects it.
 pmlsh_status pm_project_rows(const pmlsh_index *ix, const float *Q, int64_t nq, float *staging,
