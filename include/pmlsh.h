@@ -405,11 +405,14 @@ pmlsh_status pmlsh_gamma_calibrate(pmlsh_index *index, double pr, int64_t nsampl
  * gap and ||RO1, RO2|| - r1 - r2 of the two leaf entries), starting from
  * every leaf's self-join, stopping at the first leaf pair whose Mindist
  * exceeds the T-th projected distance; they are verified by their original
- * distance and the k nearest are returned.  From `opts` the call uses k, T
- * and alpha2 (c, alpha1, t and gamma are not used).  Outputs as
- * pmlsh_closest_pair; stats: count = pairs verified (T), lca_nodes = leaf
- * pairs not excluded by the self-join bound, nodes_done = leaf pairs
- * examined, self_pairs, fp64_checks.  Memory grows with T (12 bytes per kept
+ * distance and the k nearest are returned.  Leaf pairs are listed in bands of
+ * Mindist, the first ending near the T-th distance of a sample of 65,536
+ * projected pair distances (stream seed + 8), each later one quadrupling the
+ * sample quantile, until a band reaches the T-th distance: the result does
+ * not depend on the bands.  From `opts` the call uses k, T and alpha2 (c,
+ * alpha1, t and gamma are not used).  Outputs as pmlsh_closest_pair; stats:
+ * count = pairs verified (T), lca_nodes = leaf pairs listed, nodes_done =
+ * leaf pairs examined, self_pairs, fp64_checks.  Memory grows with T (12 bytes per kept
  * pair plus a batch of up to 2^24 pairs).  Errors: EINVAL, ENOMEM, ECUDA,
  * EINTERNAL (more than 4096 pairs tied inside one FP32 error band). */
 pmlsh_status pmlsh_closest_pair_bnb(pmlsh_index *index, const pmlsh_cp_opts *opts,

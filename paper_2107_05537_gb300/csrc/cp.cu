@@ -333,8 +333,8 @@ struct LeafPair {
 // ||RO1, RO2|| - r1 - r2 and the gaps between the pivot rings, from the leaf
 // entries (FP32, rounded so that it stays a lower bound).  Pairs with
 // Mindist <= dT are listed.  Block per l1, threads over l2.
-__global__ void k_bnb_mindist(const float *__restrict__ meta, int s, int64_t L, float dT, LeafPair *__restrict__ out,
-                              unsigned long long *cnt, unsigned long long cap)
+__global__ void k_bnb_mindist(const float *__restrict__ meta, int s, int64_t L, float dLo, float dT,
+                              LeafPair *__restrict__ out, unsigned long long *cnt, unsigned long long cap)
 {
     const int64_t l1 = blockIdx.x;
     const float *M1 = meta + l1 * PM_LEAF_STRIDE;
@@ -349,7 +349,7 @@ __global__ void k_bnb_mindist(const float *__restrict__ meta, int s, int64_t L, 
                 md = fmaxf(md, __fsub_rn(M1[24 + i], M2[32 + i]));
             }
         }
-        if (md <= dT) {
+        if (md > dLo && md <= dT) {
             const unsigned long long slot = atomicAdd(cnt, 1ull);
             if (slot < cap) {
                 LeafPair lp;
@@ -952,62 +952,91 @@ pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_
         return PMLSH_OK;
     };
     PM_TRY(cut());
-    // 2. leaf pairs with Mindist <= dT
+    // 2./3. leaf pairs in bands of Mindist, (lo, hi]: each band's pairs in
+    // ascending (Mindist, l1, l2), cut to the T nearest after each batch;
+    // the search ends at the first leaf pair whose Mindist exceeds the T-th
+    // projected distance (dT), and once a band's upper end reaches dT no
+    // later band holds such a pair.  The first band ends at a generous
+    // quantile of a sample of projected pair distances (near the T-th
+    // distance), so that the leaf pairs listed stay few; each further band
+    // quadruples the quantile.
+    std::vector<double> F;
+    PM_TRY(pm_distance_sample(ix, (int64_t)1 << 16, ix->seed + 8, F, st));
+    const double pT = (double)T / (double)P;
+    double pBand = std::min(1.0, 4.0 * pT + 64.0 / (double)F.size());
+    auto quantile = [&](double p) -> double {
+        if (p >= 1.0 || F.empty()) return INFINITY;
+        const int64_t r = std::min<int64_t>((int64_t)F.size() - 1, (int64_t)std::ceil(p * (double)F.size()));
+        return F[r];
+    };
+    double bandHi = quantile(pBand);
+    float lo32 = -INFINITY;   // FP32 end of the previous band: bands are disjoint in FP32
     LeafPair *dlp;
     const unsigned long long lpCap = (unsigned long long)std::max<int64_t>(1, L * (L - 1) / 2);
     PM_TRY(mem.get(&dlp, (size_t)lpCap));
-    PM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
-    const float dT32 = std::isinf(dT) ? INFINITY : nextafterf((float)dT, INFINITY);
-    if (L > 1)
-        PM_LAUNCH("k_bnb_mindist", st, k_bnb_mindist<<<(unsigned)L, 256, 0, st>>>(ix->leafMeta, ix->s, L, dT32, dlp, cnt,
-                                                                                   lpCap));
-    PM_CUDA(cudaGetLastError());
-    unsigned long long nlp = 0;
-    PM_CUDA(cudaMemcpyAsync(&nlp, cnt, sizeof(nlp), cudaMemcpyDeviceToHost, st));
-    PM_CUDA(cudaStreamSynchronize(st));
-    std::vector<LeafPair> lps(nlp);
-    PM_CUDA(cudaMemcpyAsync(lps.data(), dlp, nlp * sizeof(LeafPair), cudaMemcpyDeviceToHost, st));
-    PM_CUDA(cudaStreamSynchronize(st));
-    std::sort(lps.begin(), lps.end(), [](const LeafPair &x, const LeafPair &y) {
-        if (x.md != y.md) return x.md < y.md;
-        if (x.l1 != y.l1) return x.l1 < y.l1;
-        return x.l2 < y.l2;
-    });
-    // 3. best first in batches
     int2 *dPairs;
     int64_t *dOff;
     const size_t lpBatch = (size_t)1 << 16;
     PM_TRY(mem.get(&dPairs, lpBatch));
     PM_TRY(mem.get(&dOff, lpBatch));
-    int64_t examined = 0, crossPairs = 0;
-    size_t next = 0;
-    while (next < lps.size()) {
-        if ((double)lps[next].md > dT) break;   // no pair under it can beat the T-th
-        std::vector<int2> bp;
-        std::vector<int64_t> bo;
-        int64_t tot = 0;
-        while (next < lps.size() && bp.size() < lpBatch && (double)lps[next].md <= dT) {
-            const int64_t na = ix->leafOffH[lps[next].l1 + 1] - ix->leafOffH[lps[next].l1];
-            const int64_t nb = ix->leafOffH[lps[next].l2 + 1] - ix->leafOffH[lps[next].l2];
-            if (tot > 0 && tot + na * nb > batchCap) break;
-            bp.push_back(make_int2(lps[next].l1, lps[next].l2));
-            bo.push_back(nBuf + tot);
-            tot += na * nb;
-            next++;
-        }
-        if (tot > batchCap) {
-            pm_set_error("closest pairs: one leaf pair holds more pairs than the batch capacity");
-            return PMLSH_EINTERNAL;
-        }
-        PM_CUDA(cudaMemcpyAsync(dPairs, bp.data(), bp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-        PM_CUDA(cudaMemcpyAsync(dOff, bo.data(), bo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-        PM_LAUNCH("k_bnb_cross", st, k_bnb_cross<<<(unsigned)bp.size(), 256, 0, st>>>(ix->O32, ix->leafOff, dPairs, dOff,
-                                                                                        buf));
+    int64_t examined = 0, crossPairs = 0, listed = 0;
+    for (;;) {
+        const double hiCut = std::min(bandHi, dT);
+        PM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+        // the band is (lo32, hi32] in FP32 Mindist, hi32 >= hiCut
+        const float hi32 = std::isinf(hiCut) ? INFINITY : nextafterf((float)hiCut, INFINITY);
+        if (L > 1)
+            PM_LAUNCH("k_bnb_mindist", st, k_bnb_mindist<<<(unsigned)L, 256, 0, st>>>(ix->leafMeta, ix->s, L, lo32,
+                                                                                       hi32, dlp, cnt, lpCap));
         PM_CUDA(cudaGetLastError());
-        nBuf += tot;
-        examined += (int64_t)bp.size();
-        crossPairs += tot;
-        PM_TRY(cut());
+        unsigned long long nlp = 0;
+        PM_CUDA(cudaMemcpyAsync(&nlp, cnt, sizeof(nlp), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        std::vector<LeafPair> lps(nlp);
+        PM_CUDA(cudaMemcpyAsync(lps.data(), dlp, nlp * sizeof(LeafPair), cudaMemcpyDeviceToHost, st));
+        PM_CUDA(cudaStreamSynchronize(st));
+        std::sort(lps.begin(), lps.end(), [](const LeafPair &x, const LeafPair &y) {
+            if (x.md != y.md) return x.md < y.md;
+            if (x.l1 != y.l1) return x.l1 < y.l1;
+            return x.l2 < y.l2;
+        });
+        listed += (int64_t)nlp;
+        size_t next = 0;
+        bool stop = false;
+        while (next < lps.size()) {
+            if ((double)lps[next].md > dT) { stop = true; break; }   // no pair under it can beat the T-th
+            std::vector<int2> bp;
+            std::vector<int64_t> bo;
+            int64_t tot = 0;
+            while (next < lps.size() && bp.size() < lpBatch && (double)lps[next].md <= dT) {
+                const int64_t na = ix->leafOffH[lps[next].l1 + 1] - ix->leafOffH[lps[next].l1];
+                const int64_t nb = ix->leafOffH[lps[next].l2 + 1] - ix->leafOffH[lps[next].l2];
+                if (tot > 0 && tot + na * nb > batchCap) break;
+                bp.push_back(make_int2(lps[next].l1, lps[next].l2));
+                bo.push_back(nBuf + tot);
+                tot += na * nb;
+                next++;
+            }
+            if (tot > batchCap) {
+                pm_set_error("closest pairs: one leaf pair holds more pairs than the batch capacity");
+                return PMLSH_EINTERNAL;
+            }
+            PM_CUDA(cudaMemcpyAsync(dPairs, bp.data(), bp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+            PM_CUDA(cudaMemcpyAsync(dOff, bo.data(), bo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            PM_LAUNCH("k_bnb_cross", st, k_bnb_cross<<<(unsigned)bp.size(), 256, 0, st>>>(ix->O32, ix->leafOff, dPairs,
+                                                                                            dOff, buf));
+            PM_CUDA(cudaGetLastError());
+            nBuf += tot;
+            examined += (int64_t)bp.size();
+            crossPairs += tot;
+            PM_TRY(cut());
+        }
+        // done when this band reached dT (every later pair has Mindist > dT)
+        // or covered everything
+        if (stop || std::isinf(bandHi) || dT <= bandHi) break;
+        lo32 = hi32;
+        pBand = std::min(1.0, pBand * 4.0);
+        bandHi = std::max(quantile(pBand), (double)hi32);
     }
     // 4. verification and the exact top-k
     if (nBuf > 0)
@@ -1028,7 +1057,7 @@ pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_
     if (stats) {
         stats->count = nBuf;
         stats->ub_self = INFINITY;
-        stats->lca_nodes = (int64_t)lps.size();
+        stats->lca_nodes = listed;
         stats->nodes_done = examined;
         stats->self_pairs = nSelf;
         stats->fp64_checks = fp64;
