@@ -269,9 +269,13 @@ def run_reference(args, ws, rank):
 
 
 def source_sha(rel):
+    """sha256 of one source file, or of several concatenated in order."""
     import hashlib
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    h = hashlib.sha256()
+    for r in ([rel] if isinstance(rel, str) else rel):
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def timed_steps(step, steps, flush, stream, tag):
