@@ -114,144 +114,184 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 
 // ------------------------------------------------------------ range round
 
-// Block b of the active list (QBT queries) x 128 leaves: leaf classification
-// and whole-leaf counts.  Leaves that some query of the block covers only
-// partially are listed for the block as {leaf, first position, size, first
-// tensor-operand row}, each with the QBT-bit mask of those queries (bit qq
-// of word qq / 32).  Also, per query, the bit set of the leaves that Eq. 5
-// does not exclude (leafBits [active query][ceil(L / 32)]), which the
-// verification kernel walks instead of testing every leaf again, and the
-// sizes of the partially covered leaves (cntPart): with the whole-leaf
-// counts (cntSure) they bound |S_i| from below and above.
-// Eq. 5 test of k_class, per (query, leaf), with the slack of leaf_class and
-// cheaper arithmetic: the centre test on the squared distance against
-// thresholds rounded outward (no square root), the pivot-ring tests against
-// per-query thresholds precomputed with directed rounding.  Every decision is
-// implied by the exact form of leaf_class's inequalities (so a leaf called
-// out holds no point within Rout and a full one only points within Rin); the
-// two tests may differ only at those slack boundaries.
-struct ClassQ {
-    float ro;       // Rout (1 + SLACK), rounded up
-    float rinLo;    // Rin (1 - SLACK), rounded down (<= 0: no inner test)
-};
+// Leaf classification of a round (Eq. 5): for a block of QBT active queries,
+// the leaves that some query of the block covers only partially are listed
+// for the block as {leaf, first position, size, first tensor-operand row},
+// each with the QBT-bit mask of those queries (bit qq of word qq / 32).  Also,
+// per query, the bit set of the leaves that Eq. 5 does not exclude
+// (leafBits [active query][ceil(L / 32)]), which the verification kernel
+// walks instead of testing every leaf again, and the whole-leaf sizes
+// (cntSure) and partial-leaf sizes (cntPart), which bound |S_i| from below
+// and above.  The test is leaf_class's with the same slack and cheaper
+// arithmetic: the centre test on the squared distance against thresholds
+// rounded outward (no square root), the pivot-ring tests against per-query
+// thresholds precomputed with directed rounding.  Every decision is implied
+// by the exact form of leaf_class's inequalities (so a leaf called out holds
+// no point within Rout and a full one only points within Rin); the two tests
+// may differ only at those slack boundaries.
 constexpr float CL_INV_LO = 1.0f / (1.f - SLACK) * (1.f + 1e-7f);   // >= 1 / (1 - SLACK)
 constexpr float CL_INV_HI = 1.0f / (1.f + SLACK) * (1.f - 1e-7f);   // <= 1 / (1 + SLACK)
 
+// Query-stationary form: thread qq of the CTA
+// holds query qq of the block (coordinates as packed pairs and its pivot
+// thresholds in registers) and the CTA walks its share of the leaves in tiles
+// of CQ_LT, reading each leaf record with loads that every lane of a warp
+// shares.  A thread keeps its whole-leaf and partial sizes and its leaf
+// bit-set words in registers.  The centre test is the only work for a
+// (query, leaf) pair that it excludes; the pivot rings, the full-leaf test,
+// the counts and the ballot of the partial-leaf mask run only for a leaf
+// that some query of the warp keeps.  The warps' masks of a tile meet in
+// shared memory (double-buffered, one barrier per tile), where the tile's
+// partially covered leaves are listed.  Queries beyond the batch sit at
+// +1e18 on every coordinate, so the centre test excludes them.
+constexpr int CQ_LT = 256;   // leaves per tile: eight bit-set words (one 32-byte sector) per query
+// words per query in a leaf bit set: L bits padded to whole tiles
+static inline int64_t pm_leaf_words(int64_t L) { return (L + CQ_LT - 1) / CQ_LT * (CQ_LT / 32); }
+
 template <int QBT>
-__global__ void __launch_bounds__(128, 8)
+__global__ void __launch_bounds__(QBT, QBT == 256 ? 4 : 16)
 k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, const int64_t *__restrict__ bOff,
         int64_t L, int *__restrict__ cntSure, int *__restrict__ blkCnt, int4 *__restrict__ blkEnt,
         uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32, int *__restrict__ cntPart)
 {
-    constexpr int W = QBT / 32;
-    __shared__ __align__(16) float sq[QBT][PM_MP];
-    // per pivot: out if HR.max < lowT or HR.min > highT
-    __shared__ __align__(16) float sLow[QBT][PM_MAX_PIVOTS], sHigh[QBT][PM_MAX_PIVOTS];
-    __shared__ __align__(8) ClassQ sT[QBT];
-    __shared__ int sCnt[QBT], sPart[QBT];
+    constexpr int W = QBT / 32;   // warps = mask words per list entry
+    constexpr int NWD = CQ_LT / 32;   // bit-set words per query and tile
+    __shared__ uint32_t sM[2][CQ_LT][W];
+    __shared__ uint32_t sW[NWD][QBT];   // the thread's words of the tile, written out as whole sectors
     const int b = blockIdx.y;
     const int a0 = b * QBT;
     const int nb = min(QBT, na - a0);
-    for (int e = threadIdx.x; e < QBT * PM_MP; e += blockDim.x) {
-        int qq = e / PM_MP, j = e % PM_MP;
-        sq[qq][j] = qq < nb ? qp32[(int64_t)act[a0 + qq] * PM_MP + j] : 0.f;
-    }
-    for (int qq = threadIdx.x; qq < QBT; qq += blockDim.x) {
-        float ro = 0.f, rinLo = -1.f;
-        if (qq < nb) {
-            const Thr T = thr[a0 + qq];
-            const float Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
-            const float Rout = __fsqrt_rn(T.hi);
-            ro = __fmul_ru(Rout, 1.f + SLACK);
-            rinLo = Rin > 0.f ? __fmul_rd(Rin, 1.f - SLACK) : -1.f;
-            for (int i = 0; i < PM_MAX_PIVOTS; i++) {
-                const float dq = qpiv[(int64_t)act[a0 + qq] * PM_MAX_PIVOTS + i];
-                sLow[qq][i] = __fsub_rd(__fmul_rd(dq, 1.f - SLACK), ro);
-                sHigh[qq][i] = __fadd_ru(__fmul_ru(dq, 1.f + SLACK), ro);
-            }
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    for (int e = t; e < 2 * CQ_LT * W; e += QBT) (&sM[0][0][0])[e] = 0u;
+
+    unsigned long long qv[PM_MP / 2];
+    // per pivot: out if HR.max < lowT or HR.min > highT
+    float lowT[PM_MAX_PIVOTS], highT[PM_MAX_PIVOTS];
+    float roL = 0.f, rinLo = -1.f;   // Rout (1 + SLACK) CL_INV_LO rounded up; Rin (1 - SLACK) rounded down
+    const bool qv_ok = t < nb;
+    if (qv_ok) {
+        const int q = act[a0 + t];
+        const float4 *src = (const float4 *)(qp32 + (int64_t)q * PM_MP);
+#pragma unroll
+        for (int j4 = 0; j4 < PM_MP / 4; j4++) {
+            const float4 v = src[j4];
+            qv[2 * j4] = f32x2_pack(v.x, v.y);
+            qv[2 * j4 + 1] = f32x2_pack(v.z, v.w);
         }
-        sT[qq].ro = ro;
-        sT[qq].rinLo = rinLo;
-        sCnt[qq] = 0;
-        sPart[qq] = 0;
+        const Thr T = thr[a0 + t];
+        const float Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f;
+        const float ro = __fmul_ru(__fsqrt_rn(T.hi), 1.f + SLACK);
+        roL = __fmul_ru(ro, CL_INV_LO);
+        rinLo = Rin > 0.f ? __fmul_rd(Rin, 1.f - SLACK) : -1.f;
+#pragma unroll
+        for (int i = 0; i < PM_MAX_PIVOTS; i++) {
+            const float dq = qpiv[(int64_t)q * PM_MAX_PIVOTS + i];
+            // pivots beyond s never exclude
+            lowT[i] = i < s ? __fsub_rd(__fmul_rd(dq, 1.f - SLACK), ro) : -INFINITY;
+            highT[i] = i < s ? __fadd_ru(__fmul_ru(dq, 1.f + SLACK), ro) : INFINITY;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < PM_MP / 2; j++) qv[j] = f32x2_pack(1e18f, 1e18f);
+#pragma unroll
+        for (int i = 0; i < PM_MAX_PIVOTS; i++) {
+            lowT[i] = -INFINITY;
+            highT[i] = INFINITY;
+        }
     }
     __syncthreads();
-    const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool lv = l < L;
-    const int lane = threadIdx.x & 31;
-    uint32_t mw[W];
-    bool anyPart = false;
+    int sure = 0, part = 0;
+    const int64_t nTiles = (L + CQ_LT - 1) / CQ_LT;
+    int buf = 0;
+    for (int64_t tile = blockIdx.x; tile < nTiles; tile += gridDim.x, buf ^= 1) {
+        const int64_t l0 = tile * CQ_LT;
+        const int nl = L - l0 < CQ_LT ? (int)(L - l0) : CQ_LT;
+#pragma unroll 1
+        for (int w4 = 0; w4 < NWD; w4++) {
+            uint32_t bits = 0u;
+            const int jn = min(32, nl - w4 * 32);
+#pragma unroll 2
+            for (int jj = 0; jj < jn; jj++) {
+                const int j = w4 * 32 + jj;
+                const float *M = meta + (l0 + j) * PM_LEAF_STRIDE;
+                const float4 *c4 = (const float4 *)M;
+                unsigned long long acc0 = 0ull, acc1 = 0ull;
 #pragma unroll
-    for (int w = 0; w < W; w++) mw[w] = 0u;
-    float Mv[PM_LEAF_STRIDE];
-#pragma unroll
-    for (int j = 0; j < PM_LEAF_STRIDE; j++) Mv[j] = lv ? meta[l * PM_LEAF_STRIDE + j] : 0.f;
-    const int cnt = lv ? (int)(off[l + 1] - off[l]) : 0;
-    const float rr = Mv[16];
-    unsigned long long mc[PM_MP / 2];
-#pragma unroll
-    for (int j = 0; j < PM_MP / 2; j++) mc[j] = f32x2_pack(Mv[2 * j], Mv[2 * j + 1]);
-#pragma unroll
-    for (int w = 0; w < W; w++) {
-        uint32_t bits = 0u;
-        for (int j = 0; j < 32; j++) {
-            const int qq = w * 32 + j;
-            if (qq >= nb) break;
-            unsigned char c = CL_OUT;
-            if (lv) {
-                // squared centre distance (packed pairs of coordinates)
-                unsigned long long acc = 0ull;
-#pragma unroll
-                for (int j4 = 0; j4 < PM_MP / 4; j4++) {
-                    const float4 v = ((const float4 *)sq[qq])[j4];
-                    f32x2_sqdiff_acc(acc, f32x2_pack(v.x, v.y), mc[2 * j4]);
-                    f32x2_sqdiff_acc(acc, f32x2_pack(v.z, v.w), mc[2 * j4 + 1]);
+                for (int j4 = 0; j4 < PM_MP / 4; j4 += 2) {
+                    const float4 v = __ldg(c4 + j4), u = __ldg(c4 + j4 + 1);
+                    f32x2_sqdiff_acc(acc0, qv[2 * j4], f32x2_pack(v.x, v.y));
+                    f32x2_sqdiff_acc(acc1, qv[2 * j4 + 1], f32x2_pack(v.z, v.w));
+                    f32x2_sqdiff_acc(acc0, qv[2 * j4 + 2], f32x2_pack(u.x, u.y));
+                    f32x2_sqdiff_acc(acc1, qv[2 * j4 + 3], f32x2_pack(u.z, u.w));
                 }
-                const float pd2lo = __fadd_rd(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
-                const float pd2hi = __fadd_ru(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
-                const ClassQ t = sT[qq];
+                unsigned long long acc;
+                asm("add.rn.f32x2 %0, %1, %2;" : "=l"(acc) : "l"(acc0), "l"(acc1));
                 // out: sqrt(d^2) (1 - SLACK) - r > ro, i.e. d^2 > ((ro + r) / (1 - SLACK))^2
-                const float tb = __fmul_ru(__fadd_ru(t.ro, rr), CL_INV_LO);
-                bool out = pd2lo > __fmul_ru(tb, tb);
-                if (!out) {
-#pragma unroll
-                    for (int i = 0; i < PM_MAX_PIVOTS; i++)
-                        if (i < s) out |= Mv[32 + i] < sLow[qq][i] || Mv[24 + i] > sHigh[qq][i];
-                }
-                if (!out) {
-                    c = CL_PART;
-                    // full: sqrt(d^2) (1 + SLACK) + r <= Rin (1 - SLACK)
-                    const float f = __fmul_rd(__fsub_rd(t.rinLo, rr), CL_INV_HI);
-                    if (t.rinLo > 0.f && f > 0.f && pd2hi <= __fmul_rd(f, f)) c = CL_FULL;
+                const float rr = __ldg(M + 16);
+                const float lo = __fadd_rd(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+                const float tb = __fadd_ru(roL, __fmul_ru(rr, CL_INV_LO));
+                const bool in = !(lo > __fmul_ru(tb, tb));
+                if (__any_sync(VW_FULL, in)) {
+                    // pivot rings of Sec. 4.1, then the full-leaf test
+                    unsigned char c = CL_OUT;
+                    if (in) {
+                        const float4 *h4 = (const float4 *)(M + 24);   // HR.min [8], HR.max [8]
+                        const float4 n0 = __ldg(h4), n1 = __ldg(h4 + 1), x0 = __ldg(h4 + 2), x1 = __ldg(h4 + 3);
+                        const bool out = x0.x < lowT[0] || x0.y < lowT[1] || x0.z < lowT[2] || x0.w < lowT[3] ||
+                                         x1.x < lowT[4] || x1.y < lowT[5] || x1.z < lowT[6] || x1.w < lowT[7] ||
+                                         n0.x > highT[0] || n0.y > highT[1] || n0.z > highT[2] || n0.w > highT[3] ||
+                                         n1.x > highT[4] || n1.y > highT[5] || n1.z > highT[6] || n1.w > highT[7];
+                        if (!out) {
+                            c = CL_PART;
+                            // full: sqrt(d^2) (1 + SLACK) + r <= Rin (1 - SLACK)
+                            const float hi = __fadd_ru(__uint_as_float((unsigned)acc), __uint_as_float((unsigned)(acc >> 32)));
+                            const float f = __fmul_rd(__fsub_rd(rinLo, rr), CL_INV_HI);
+                            if (rinLo > 0.f && f > 0.f && hi <= __fmul_rd(f, f)) c = CL_FULL;
+                            const int n = (int)(__ldg(off + l0 + j + 1) - __ldg(off + l0 + j));
+                            if (c == CL_FULL) sure += n;
+                            else part += n;
+                            bits |= 1u << jj;
+                        }
+                    }
+                    const uint32_t m = __ballot_sync(VW_FULL, c == CL_PART);
+                    if (lane == 0) sM[buf][j][wp] = m;
                 }
             }
-            // the warp's whole-leaf and partial-leaf sizes for this query in
-            // one reduction (each at most 32 leaves x 1024 points < 2^16)
-            const unsigned both = __reduce_add_sync(
-                0xffffffffu, c == CL_FULL ? ((unsigned)cnt << 16) : (c == CL_PART ? (unsigned)cnt : 0u));
-            if (lane == 0 && (both >> 16)) atomicAdd(&sCnt[qq], (int)(both >> 16));
-            if (lane == 0 && (both & 0xFFFFu)) atomicAdd(&sPart[qq], (int)(both & 0xFFFFu));
-            bits |= (uint32_t)(c == CL_PART) << j;
-            // per query: the warp's 32 leaves that Eq. 5 does not exclude
-            const uint32_t word = __ballot_sync(0xffffffffu, c != CL_OUT);
-            if (lane == 0 && (l >> 5) < W32) leafBits[(int64_t)(a0 + qq) * W32 + (l >> 5)] = word;
+            sW[w4][t] = bits;
         }
-        mw[w] = bits;
-        anyPart |= bits != 0u;
-    }
-    if (anyPart) {
-        const int slot = atomicAdd(&blkCnt[b], 1);
-        const int64_t e = (int64_t)b * L + slot;
-        blkEnt[e] = make_int4((int)l, (int)off[l], (int)(off[l + 1] - off[l]), bOff ? (int)bOff[l] : 0);
+        // the tile's words of this query's leaf bit set: one 32-byte sector
+        // (rows are W32 words, a multiple of 8, so the sector is aligned)
+        if (qv_ok) {
+            uint4 *dst = (uint4 *)(leafBits + (int64_t)(a0 + t) * W32 + l0 / 32);
+            dst[0] = make_uint4(sW[0][t], sW[1][t], sW[2][t], sW[3][t]);
+            dst[1] = make_uint4(sW[4][t], sW[5][t], sW[6][t], sW[7][t]);
+        }
+        __syncthreads();
+        // the tile's leaves that some query of the block covers partially;
+        // the masks are cleared for the tile after next
+        for (int j = t; j < nl; j += QBT) {
+            uint32_t mw[W], any = 0u;
 #pragma unroll
-        for (int w = 0; w < W; w++) blkMask[e * W + w] = mw[w];
+            for (int w = 0; w < W; w++) {
+                mw[w] = sM[buf][j][w];
+                any |= mw[w];
+                sM[buf][j][w] = 0u;
+            }
+            if (any) {
+                const int64_t l = l0 + j;
+                const int slot = atomicAdd(&blkCnt[b], 1);
+                const int64_t e = (int64_t)b * L + slot;
+                blkEnt[e] = make_int4((int)l, (int)off[l], (int)(off[l + 1] - off[l]), bOff ? (int)bOff[l] : 0);
+#pragma unroll
+                for (int w = 0; w < W; w++) blkMask[e * W + w] = mw[w];
+            }
+        }
     }
-    __syncthreads();
-    for (int qq = threadIdx.x; qq < nb; qq += blockDim.x) {
-        if (sCnt[qq]) atomicAdd(&cntSure[a0 + qq], sCnt[qq]);
-        if (sPart[qq]) atomicAdd(&cntPart[a0 + qq], sPart[qq]);
+    if (qv_ok) {
+        if (sure) atomicAdd(&cntSure[a0 + t], sure);
+        if (part) atomicAdd(&cntPart[a0 + t], part);
     }
 }
 
@@ -336,20 +376,43 @@ __global__ void k_band64(const int *__restrict__ bandN, int bandCap, const int *
                          int *__restrict__ inN, int *__restrict__ inPos, int *__restrict__ fp64cnt,
                          int *__restrict__ errFlag)
 {
-    int nbd = min(*bandN, bandCap);
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nbd) return;
-    int a = bandA[e];
-    int64_t pos = bandPos[e];
-    int q = act[a];
-    double pd = pm_pdist64(O64 + pos * PM_MP, qp64 + (int64_t)q * PM_MP, m);
-    atomicAdd(&fp64cnt[a], 1);
-    if (pd <= thr[a].R) {
-        atomicAdd(&inTrue[a], 1);
-        int slot = atomicAdd(&inN[a], 1);
-        if (slot < BCAP) inPos[(int64_t)a * BCAP + slot] = (int)pos;
-        else atomicOr(errFlag, 2);
+    const int nbd = min(*bandN, bandCap);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nbd; e += gridDim.x * blockDim.x) {
+        const int a = bandA[e];
+        const int64_t pos = bandPos[e];
+        const int q = act[a];
+        const double pd = pm_pdist64(O64 + pos * PM_MP, qp64 + (int64_t)q * PM_MP, m);
+        atomicAdd(&fp64cnt[a], 1);
+        if (pd <= thr[a].R) {
+            atomicAdd(&inTrue[a], 1);
+            const int slot = atomicAdd(&inN[a], 1);
+            if (slot < BCAP) inPos[(int64_t)a * BCAP + slot] = (int)pos;
+            else atomicOr(errFlag, 2);
+        }
     }
+}
+
+// Zeroes up to ZL_MAX int arrays in one launch (grid-stride over each).
+constexpr int ZL_MAX = 12;
+struct ZeroList {
+    int *p[ZL_MAX];
+    int64_t n[ZL_MAX];
+    int cnt = 0;
+    void add(int *ptr, int64_t count)
+    {
+        if (ptr && count > 0 && cnt < ZL_MAX) {
+            p[cnt] = ptr;
+            n[cnt] = count;
+            cnt++;
+        }
+    }
+};
+
+__global__ void k_zero(ZeroList z)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i = 0; i < z.cnt; i++)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < z.n[i]; e += stride) z.p[i][e] = 0;
 }
 
 // --------------------------------------------------------- budget (rule 2)
@@ -1835,7 +1898,7 @@ namespace {
 void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
                     std::vector<std::pair<DevBuf KnnWork::*, int64_t>> &out)
 {
-    const int64_t L = ix->L, ld = ix->ld, W32 = (L + 31) / 32;
+    const int64_t L = ix->L, ld = ix->ld, W32 = pm_leaf_words(L);
     const bool bfv = (precision & PMLSH_BF16_VERIFY) != 0 && ix->Xr != nullptr;
     const int KP = (k + (bfv ? 64 : 32) + 31) / 32 * 32;
     const bool tc = (precision & PMLSH_BF16_TENSOR) != 0;
@@ -2022,7 +2085,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     int *bandN = fpc + nq;       // counters after the per-query array
     int *errFlag = fpc + nq + 1;
     int *recheckN = fpc + nq + 2;
-    const int W32 = (int)((L + 31) / 32);
+    const int W32 = (int)pm_leaf_words(L);
     uint32_t *leafBits = grow<uint32_t>(w.leafBits, (size_t)nq * W32, s);
     if (s != PMLSH_OK) return s;
 
@@ -2060,9 +2123,6 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             if (na == 0) break;
             PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         }
-        PM_CUDA(cudaMemsetAsync(inTrue, 0, na * sizeof(int), st));
-        PM_CUDA(cudaMemsetAsync(inN, 0, na * sizeof(int), st));
-        PM_CUDA(cudaMemsetAsync(fpc, 0, (nq + 8) * sizeof(int), st));
         PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
         // leaf classification (Eq. 5): bounds of |S_i|, leaf lists with the
         // masks of partially covering queries, per-query leaf bit sets.  The
@@ -2075,7 +2135,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             uint32_t *leafBits;
         };
         const int64_t Tdec = std::min<int64_t>(B, n);
-        auto class_phase = [&](bool tc, const CountIO &io) -> pmlsh_status {
+        auto class_phase = [&](bool tc, const CountIO &io, ZeroList z) -> pmlsh_status {
             const int nlist = tc ? (io.na + TC_QN - 1) / TC_QN : (io.na + QB - 1) / QB;
             const int mwords = tc ? TC_MW : QB / 32;
             pmlsh_status s2 = PMLSH_OK;
@@ -2083,21 +2143,34 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             int4 *blkEnt = grow<int4>(w.blkLeaves, (size_t)nlist * L, s2);
             uint32_t *blkMask = grow<uint32_t>(w.blkMask, (size_t)nlist * L * mwords, s2);
             if (s2 != PMLSH_OK) return s2;
-            PM_CUDA(cudaMemsetAsync(blkCnt, 0, nlist * sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(io.cntSure, 0, io.na * sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(io.cntPart, 0, io.na * sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(io.cntBand, 0, io.na * sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(bandN, 0, sizeof(int), st));
-            PM_CUDA(cudaMemsetAsync(recheckN, 0, sizeof(int), st));
-            dim3 gc((unsigned)((L + 127) / 128), (unsigned)nlist);
-            if (!tc)
-                PM_LAUNCH("k_class", st, k_class<QB><<<gc, 128, 0, st>>>(io.act, io.na, io.thr, qp32, qpiv, ix->s,
-                                            ix->leafMeta, ix->leafOff, nullptr, L, io.cntSure, blkCnt, blkEnt,
-                                            blkMask, io.leafBits, W32, io.cntPart));
-            else
-                PM_LAUNCH("k_class", st, k_class<TC_QN><<<gc, 128, 0, st>>>(io.act, io.na, io.thr, qp32, qpiv, ix->s,
-                                               ix->leafMeta, ix->leafOff, ix->bOff, L, io.cntSure, blkCnt, blkEnt,
-                                               blkMask, io.leafBits, W32, io.cntPart));
+            // the phase's counters (and the caller's extra arrays) in one launch
+            z.add(blkCnt, nlist);
+            z.add(io.cntSure, io.na);
+            z.add(io.cntPart, io.na);
+            z.add(io.cntBand, io.na);
+            z.add(io.inTrue, io.na);
+            z.add(io.inN, io.na);
+            z.add(io.fpc, io.na);
+            z.add(bandN, 1);
+            z.add(recheckN, 1);
+            PM_LAUNCH("k_zero", st, k_zero<<<2 * nsm, 256, 0, st>>>(z));
+            {
+                // query-stationary test: leaf tiles split evenly over enough
+                // CTAs per query block to fill the GPU once
+                const int64_t nTiles = (L + CQ_LT - 1) / CQ_LT;
+                const int perSm = tc ? 4 : 16;
+                int64_t gx = std::max<int64_t>(1, std::min<int64_t>(nTiles, ((int64_t)nsm * perSm + nlist - 1) / nlist));
+                gx = (nTiles + (nTiles + gx - 1) / gx - 1) / ((nTiles + gx - 1) / gx);
+                dim3 gq((unsigned)gx, (unsigned)nlist);
+                if (!tc)
+                    PM_LAUNCH("k_class", st, k_class<QB><<<gq, QB, 0, st>>>(io.act, io.na, io.thr, qp32, qpiv,
+                                                ix->s, ix->leafMeta, ix->leafOff, nullptr, L, io.cntSure, blkCnt,
+                                                blkEnt, blkMask, io.leafBits, W32, io.cntPart));
+                else
+                    PM_LAUNCH("k_class", st, k_class<TC_QN><<<gq, TC_QN, 0, st>>>(io.act, io.na, io.thr, qp32,
+                                                qpiv, ix->s, ix->leafMeta, ix->leafOff, ix->bOff, L, io.cntSure,
+                                                blkCnt, blkEnt, blkMask, io.leafBits, W32, io.cntPart));
+            }
             PM_CUDA(cudaGetLastError());
             return PMLSH_OK;
         };
@@ -2114,7 +2187,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                             ix->O32, blkCnt, blkEnt, blkMask, L, io.cntSure, io.cntBand, bandN,
                                             bandCap, bandA, bandPos));
             } else {
-                int splitC = std::max(1, std::min(256, (4 * nsm + nlist - 1) / nlist));
+                // one CTA per SM at a time: at most four whole waves
+                int splitC = std::max(1, std::min(256, 4 * nsm / nlist));
                 PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nlist, splitC), TC_THREADS, TC_SMEM, st>>>(
                                             io.act, io.na, io.thr, qp32, ix->Bsplit, ix->bNorm, blkCnt, blkEnt,
                                             blkMask, L, ix->maxNorm, io.cntSure, recheckN, recheckCap, recheck,
@@ -2130,40 +2204,43 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         // the sure, band and band-in counts
         auto exact_count = [&](const CountIO &io, std::vector<int> &es, std::vector<int> &eb,
                                std::vector<int> &ein) -> pmlsh_status {
-            PM_TRY(point_count(tensor, io));
+            // count, FP64 decision of the band (the band size is read on the
+            // device), and one read of the counters; if the tensor-core
+            // count left more undecided pairs than its recheck list holds,
+            // the round is counted again on the CUDA cores (same results)
             int hN[3] = {0, 0, 0};   // bandN, errFlag, recheckN
-            PM_CUDA(cudaMemcpyAsync(hN, bandN, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-            PM_CUDA(cudaStreamSynchronize(st));
-            if (tensor && hN[2] > recheckCap) {
-                // more undecided pairs than the recheck list holds: count this
-                // round on the CUDA cores instead (same results)
-                PM_TRY(class_phase(false, io));
-                PM_TRY(point_count(false, io));
+            for (int pass = 0; pass < 2; pass++) {
+                const bool tcp = tensor && pass == 0;
+                if (pass == 1) PM_TRY(class_phase(false, io, ZeroList()));
+                PM_TRY(point_count(tcp, io));
+                PM_LAUNCH("k_band64", st, k_band64<<<2 * nsm, 256, 0, st>>>(bandN, bandCap, bandA, bandPos, io.act,
+                                                       io.thr, ix->O64, qp64, m, io.inTrue, io.inN, io.inPos,
+                                                       io.fpc, errFlag));
+                PM_CUDA(cudaGetLastError());
+                es.resize(io.na);
+                eb.resize(io.na);
+                ein.resize(io.na);
                 PM_CUDA(cudaMemcpyAsync(hN, bandN, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                PM_CUDA(cudaMemcpyAsync(es.data(), io.cntSure, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
+                PM_CUDA(cudaMemcpyAsync(eb.data(), io.cntBand, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
+                PM_CUDA(cudaMemcpyAsync(ein.data(), io.inTrue, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
                 PM_CUDA(cudaStreamSynchronize(st));
+                if (!(tcp && hN[2] > recheckCap)) break;
             }
-            const int hBand = hN[0];
-            if (hBand > bandCap) {
+            if (hN[0] > bandCap) {
                 pm_set_error("more than %d projected distances fell inside the FP32 error band in one round", bandCap);
                 return PMLSH_EINTERNAL;
             }
-            // (grid sized by the capacity; empty threads exit)
-            if (hBand > 0)
-                PM_LAUNCH("k_band64", st, k_band64<<<(hBand + 255) / 256, 256, 0, st>>>(bandN, bandCap, bandA, bandPos,
-                                                             io.act, io.thr, ix->O64, qp64, m, io.inTrue, io.inN,
-                                                             io.inPos, io.fpc, errFlag));
-            PM_CUDA(cudaGetLastError());
-            es.resize(io.na);
-            eb.resize(io.na);
-            ein.resize(io.na);
-            PM_CUDA(cudaMemcpyAsync(es.data(), io.cntSure, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
-            PM_CUDA(cudaMemcpyAsync(eb.data(), io.cntBand, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
-            PM_CUDA(cudaMemcpyAsync(ein.data(), io.inTrue, io.na * sizeof(int), cudaMemcpyDeviceToHost, st));
-            PM_CUDA(cudaStreamSynchronize(st));
             return PMLSH_OK;
         };
         const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits};
-        PM_TRY(class_phase(tensor, full));
+        {
+            // this round's per-query counters and the error and list counters
+            // after them (fpc [nq + 8]) start at zero
+            ZeroList z;
+            z.add(fpc, nq + 8);
+            PM_TRY(class_phase(tensor, full, z));
+        }
         std::vector<int> hs(na), hp(na), hb(na, 0), hin(na, 0);
         PM_CUDA(cudaMemcpyAsync(stHs, cntSure, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(stHp, cntPart, na * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2204,10 +2281,9 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 *s2Band = sub + 4 * na2, *s2In = sub + 5 * na2, *s2InN = sub + 6 * na2, *s2Fp = sub + 7 * na2,
                 *s2InPos = sub + 12 * na2;
             PM_CUDA(cudaMemcpyAsync(amb, ambH.data(), na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-            PM_CUDA(cudaMemsetAsync(s2In, 0, 3 * (size_t)na2 * sizeof(int), st));   // inTrue, inN, fp64
             PM_LAUNCH("k_gather_sub", st, k_gather_sub<<<(na2 + 255) / 256, 256, 0, st>>>(amb, na2, act, thr, act2, thr2));
             const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2};
-            PM_TRY(class_phase(tensor, subIO));
+            PM_TRY(class_phase(tensor, subIO, ZeroList()));   // zeroes inTrue, inN, fp64 of the sub-batch
             std::vector<int> es, eb, ein;
             PM_TRY(exact_count(subIO, es, eb, ein));
             for (int i = 0; i < na2; i++) {

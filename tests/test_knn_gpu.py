@@ -385,6 +385,38 @@ def test_no_stats_path_sub_batch_of_straddling_queries(c1):
     assert seen_sub and seen_none, (seen_sub, seen_none)
 
 
+def test_no_stats_straddle_decided_by_band_points():
+    # A = I (m = d = 2), a query at the origin, a clump well inside the first
+    # radius R = t r_min, 200 points on the circle of radius R (their FP32
+    # distances lie inside the FP32 error band of R, so no FP32 test decides
+    # them) and far points; B lies between the clump and clump + circle, so
+    # the query's bounds straddle B and its exact count (k_gather_sub, FP64
+    # at the band) decides rule 2; results equal the oracle's with and
+    # without statistics
+    c, k, rmin = 1.5, 5, 10.0
+    t, _, _ = oracle.params(2, c, 1 / E)
+    R = t * rmin
+    rng = np.random.default_rng(7)
+    inner = rng.uniform(-0.1, 0.1, size=(40, 2)) * R
+    ang = rng.uniform(0.0, 2.0 * np.pi, size=200)
+    ring = np.stack([R * np.cos(ang), R * np.sin(ang)], 1)
+    far = rng.normal(size=(260, 2)) * R + 20.0 * R
+    X = np.concatenate([inner, ring, far]).astype(np.float32)
+    Q = np.array([[0.0, 0.0], [20.0 * R, 20.0 * R], [0.0, 0.5]], dtype=np.float32)
+    A = np.eye(2, dtype=np.float32)
+    beta = 0.2   # B = 105: 40 sure points, 240 possible
+    assert 40 < oracle.budget(len(X), beta, k) <= 240
+    pm.profile(True)
+    pm.profile_read()
+    got, ref = _run_both(X, Q, A, k=k, c=c, beta=beta, r_min=rmin, leaf=16, s=0, with_stats=False)
+    prof = pm.profile_read()
+    pm.profile(False)
+    _assert_parity(got, ref, trace=False)
+    assert "k_gather_sub" in prof and "k_band64" in prof, sorted(prof)
+    full, _ = _run_both(X, Q, A, k=k, c=c, beta=beta, r_min=rmin, leaf=16, s=0)
+    _assert_parity(full, ref)
+
+
 @pytest.mark.slow
 def test_c3_full_size_sampled_parity():
     # high-dimensional workload: n = 10^6, d = 960, anisotropic clusters;
