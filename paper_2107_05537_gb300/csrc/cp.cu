@@ -35,10 +35,15 @@ __global__ void k_cp_selfjoin(const float *__restrict__ X, int ld, const int64_t
     const int64_t p0 = off[l], s = off[l + 1] - p0;
     const int64_t np = s * (s - 1) / 2;
     for (int64_t e = threadIdx.x; e < np; e += blockDim.x) {
-        // e -> (i, j), i < j, row-major over the upper triangle
-        int64_t i = 0, rem = e;
-        while (rem >= s - 1 - i) { rem -= s - 1 - i; i++; }
-        const int64_t j = i + 1 + rem;
+        // e -> (i, j), i < j, row-major over the upper triangle: row i starts
+        // at C(i) = i (2 s - i - 1) / 2; i from the root of C(i) = e in FP64,
+        // then integer corrections (at most a step or two)
+        const double b2 = 2.0 * (double)s - 1.0;
+        int64_t i = (int64_t)((b2 - sqrt(fmax(0.0, b2 * b2 - 8.0 * (double)e))) * 0.5);
+        i = i < 0 ? 0 : (i > s - 2 ? s - 2 : i);
+        while (i > 0 && i * (2 * s - i - 1) / 2 > e) i--;
+        while (i < s - 2 && (i + 1) * (2 * s - i - 2) / 2 <= e) i++;
+        const int64_t j = i + 1 + (e - i * (2 * s - i - 1) / 2);
         const float *x = X + (p0 + i) * ld, *y = X + (p0 + j) * ld;
         float acc = 0.f;
         for (int c = 0; c < ld; c++) {
