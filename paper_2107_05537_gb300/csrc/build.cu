@@ -302,8 +302,23 @@ __global__ void k_project64_rows(const float *__restrict__ X, int64_t n, int ld,
     const int j = (int)(e % ostride);
     double acc = 0.0;
     if (j < m) {
+        // the same sequence of fmas over c = 0 .. d - 1; 16-byte loads, eight
+        // columns per step (rows are 16-byte aligned), then the tail
         const float *x = X + p * ld, *a = A + (int64_t)j * ld;
-        for (int c = 0; c < d; c++) acc = __fma_rn((double)a[c], (double)x[c], acc);
+        int c = 0;
+        for (; c + 8 <= d; c += 8) {
+            const float4 a0 = *(const float4 *)(a + c), a1 = *(const float4 *)(a + c + 4);
+            const float4 x0 = *(const float4 *)(x + c), x1 = *(const float4 *)(x + c + 4);
+            acc = __fma_rn(pm_f2d_exact(a0.x), pm_f2d_exact(x0.x), acc);
+            acc = __fma_rn(pm_f2d_exact(a0.y), pm_f2d_exact(x0.y), acc);
+            acc = __fma_rn(pm_f2d_exact(a0.z), pm_f2d_exact(x0.z), acc);
+            acc = __fma_rn(pm_f2d_exact(a0.w), pm_f2d_exact(x0.w), acc);
+            acc = __fma_rn(pm_f2d_exact(a1.x), pm_f2d_exact(x1.x), acc);
+            acc = __fma_rn(pm_f2d_exact(a1.y), pm_f2d_exact(x1.y), acc);
+            acc = __fma_rn(pm_f2d_exact(a1.z), pm_f2d_exact(x1.z), acc);
+            acc = __fma_rn(pm_f2d_exact(a1.w), pm_f2d_exact(x1.w), acc);
+        }
+        for (; c < d; c++) acc = __fma_rn(pm_f2d_exact(a[c]), pm_f2d_exact(x[c]), acc);
     }
     if (O64) O64[p * ostride + j] = acc;
     if (O32) O32[p * ostride + j] = __double2float_rn(acc);

@@ -75,24 +75,47 @@ __global__ void k_query_aux(const double *__restrict__ qp64, const float *__rest
 __global__ void k_query_pca(const float *__restrict__ Qd, int64_t nq, int ld, const float *__restrict__ P,
                             float *__restrict__ qpca, float *__restrict__ qnx)
 {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    const float *x = Qd + q * ld;
+    // one warp per query: lanes over the coordinates (16-byte loads), one
+    // partial sum per direction and lane, then a butterfly (any summation
+    // order is within the slack of the bound that uses P q)
+    const int lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;   // warp-uniform
+    const float4 *x4 = (const float4 *)(Qd + q * ld);
+    const int nf4 = ld >> 2;
     float acc[PM_PCA];
 #pragma unroll
     for (int r = 0; r < PM_PCA; r++) acc[r] = 0.f;
     double nn = 0.0;
-    for (int j = 0; j < ld; j++) {
-        const float xv = x[j];
-        nn = fma((double)xv, (double)xv, nn);
+    for (int j4 = lane; j4 < nf4; j4 += 32) {
+        const float4 xv = x4[j4];
+        nn = fma((double)xv.x, (double)xv.x, nn);
+        nn = fma((double)xv.y, (double)xv.y, nn);
+        nn = fma((double)xv.z, (double)xv.z, nn);
+        nn = fma((double)xv.w, (double)xv.w, nn);
 #pragma unroll
-        for (int r = 0; r < PM_PCA; r++) acc[r] = __fmaf_rn(P[r * ld + j], xv, acc[r]);
+        for (int r = 0; r < PM_PCA; r++) {
+            const float4 pv = ((const float4 *)(P + (int64_t)r * ld))[j4];
+            acc[r] = __fmaf_rn(pv.x, xv.x, acc[r]);
+            acc[r] = __fmaf_rn(pv.y, xv.y, acc[r]);
+            acc[r] = __fmaf_rn(pv.z, xv.z, acc[r]);
+            acc[r] = __fmaf_rn(pv.w, xv.w, acc[r]);
+        }
     }
 #pragma unroll
-    for (int r = 0; r < PM_PCA; r++) qpca[q * PM_PCA + r] = acc[r];
-    qnx[q] = __double2float_ru(sqrt(nn));
+    for (int r = 0; r < PM_PCA; r++)
+        for (int o = 16; o; o >>= 1) acc[r] = __fadd_rn(acc[r], __shfl_xor_sync(0xffffffffu, acc[r], o));
+    for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane < PM_PCA) {
+        float v = acc[0];
+#pragma unroll
+        for (int r = 1; r < PM_PCA; r++) v = lane == r ? acc[r] : v;
+        qpca[q * PM_PCA + lane] = v;
+    }
+    // ||q|| for the slack: the FP64 sum (any order, within 2^-45 relative of
+    // exact) rounded up to FP32 with a relative margin
+    if (lane == 0) qnx[q] = __double2float_ru(sqrt(nn) * (1.0 + 0x1.0p-40));
 }
-
 
 __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const double *__restrict__ r,
                              double t, double maxNorm, const double *__restrict__ qnorm,
@@ -2042,7 +2065,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     PM_TRY(pm_project_rows(ix, Q, nq, Qd, qp64, qp32, PM_MP, st));
     const unsigned gq = (unsigned)((nq + 255) / 256);
     PM_LAUNCH("k_query_aux", st, k_query_aux<<<gq, 256, 0, st>>>(qp64, qp32, nq, ix->piv32, ix->s, qnorm, qpiv));
-    PM_LAUNCH("k_query_pca", st, k_query_pca<<<gq, 256, 0, st>>>(Qd, nq, ld, ix->pcaP32, qpca, qnx));
+    PM_LAUNCH("k_query_pca", st, k_query_pca<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(Qd, nq, ld, ix->pcaP32, qpca, qnx));
     PM_LAUNCH("k_leaf_key", st, k_leaf_key<<<gq, 256, 0, st>>>(qp32, nq, ix->treeI, ix->treeV, key));
     PM_CUDA(cudaMemsetAsync(hist, 0, (L + 1) * sizeof(int), st));
     PM_LAUNCH("k_hist", st, k_hist<<<gq, 256, 0, st>>>(key, nq, hist));

@@ -336,15 +336,7 @@ __device__ __forceinline__ float warp_d2_bf16x4(const float *__restrict__ us, co
 // conversion instruction), so that the widening does not occupy the FP64
 // pipe; zeros are re-encoded too, subnormals, infinities and NaNs use the
 // conversion instruction.
-__device__ __forceinline__ double f2d_exact(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFFu;
-    const uint64_t sign = (uint64_t)(u >> 31) << 63;
-    if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);
-    if (e == 0u || e == 0xFFu) return (double)f;
-    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
-}
+__device__ __forceinline__ double f2d_exact(float f) { return pm_f2d_exact(f); }
 
 // pm_dist64 (FP64 sequential sum of (x_i - y_i)^2, separate multiply and
 // add, correctly rounded sqrt) with the inputs widened by f2d_exact.

@@ -267,6 +267,19 @@ __device__ __forceinline__ float pm_pd2_32(const float *a, const float *b)
     return s;
 }
 
+// FP32 -> FP64 widening by integer operations (exact: every FP32 value is an
+// FP64 value); subnormals, infinities and NaNs take the conversion
+// instruction.
+__device__ __forceinline__ double pm_f2d_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    if (e == 0u && (u & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
 // FP64 distance of two FP64 coordinate vectors: sequential sum, separate
 // multiply and add, correctly rounded square root.
 __device__ __forceinline__ double pm_pdist64(const double *a, const double *b, int m)
