@@ -705,7 +705,7 @@ void pm_release_work(KnnWork &w)
                       &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen, &w.bandInQ,
                       &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf,
                       &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask,
-                      &w.recheck, &w.leafBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
+                      &w.recheck, &w.leafBits, &w.fullBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
     for (DevBuf *b : bufs) b->release();
     w.stage.release();
 }

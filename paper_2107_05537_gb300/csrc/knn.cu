@@ -155,7 +155,8 @@ __global__ void k_thresholds(const int32_t *__restrict__ act, int na, const doub
 constexpr float CL_INV_LO = 1.0f / (1.f - SLACK) * (1.f + 1e-7f);   // >= 1 / (1 - SLACK)
 constexpr float CL_INV_HI = 1.0f / (1.f + SLACK) * (1.f - 1e-7f);   // <= 1 / (1 + SLACK)
 
-// Query-stationary form: thread qq of the CTA
+// Query-stationary form (and, on request, the bit set of the leaves the test
+// calls full, fullBits): thread qq of the CTA
 // holds query qq of the block (coordinates as packed pairs and its pivot
 // thresholds in registers) and the CTA walks its share of the leaves in tiles
 // of CQ_LT, reading each leaf record with loads that every lane of a warp
@@ -177,12 +178,14 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const float *__restrict__ qp32, const float *__restrict__ qpiv, int s,
         const float *__restrict__ meta, const int64_t *__restrict__ off, const int64_t *__restrict__ bOff,
         int64_t L, int *__restrict__ cntSure, int *__restrict__ blkCnt, int4 *__restrict__ blkEnt,
-        uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32, int *__restrict__ cntPart)
+        uint32_t *__restrict__ blkMask, uint32_t *__restrict__ leafBits, int W32, int *__restrict__ cntPart,
+        uint32_t *__restrict__ fullBits)
 {
     constexpr int W = QBT / 32;   // warps = mask words per list entry
     constexpr int NWD = CQ_LT / 32;   // bit-set words per query and tile
     __shared__ uint32_t sM[2][CQ_LT][W];
     __shared__ uint32_t sW[NWD][QBT];   // the thread's words of the tile, written out as whole sectors
+    __shared__ uint32_t sF[NWD][QBT];   // the same for the whole-leaf bits
     const int b = blockIdx.y;
     const int a0 = b * QBT;
     const int nb = min(QBT, na - a0);
@@ -233,7 +236,7 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
         const int nl = L - l0 < CQ_LT ? (int)(L - l0) : CQ_LT;
 #pragma unroll 1
         for (int w4 = 0; w4 < NWD; w4++) {
-            uint32_t bits = 0u;
+            uint32_t bits = 0u, fbits = 0u;
             const int jn = min(32, nl - w4 * 32);
 #pragma unroll 2
             for (int jj = 0; jj < jn; jj++) {
@@ -273,8 +276,12 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                             const float f = __fmul_rd(__fsub_rd(rinLo, rr), CL_INV_HI);
                             if (rinLo > 0.f && f > 0.f && hi <= __fmul_rd(f, f)) c = CL_FULL;
                             const int n = (int)(__ldg(off + l0 + j + 1) - __ldg(off + l0 + j));
-                            if (c == CL_FULL) sure += n;
-                            else part += n;
+                            if (c == CL_FULL) {
+                                sure += n;
+                                fbits |= 1u << jj;
+                            } else {
+                                part += n;
+                            }
                             bits |= 1u << jj;
                         }
                     }
@@ -283,6 +290,7 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
                 }
             }
             sW[w4][t] = bits;
+            sF[w4][t] = fbits;
         }
         // the tile's words of this query's leaf bit set: one 32-byte sector
         // (rows are W32 words, a multiple of 8, so the sector is aligned)
@@ -290,6 +298,11 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
             uint4 *dst = (uint4 *)(leafBits + (int64_t)(a0 + t) * W32 + l0 / 32);
             dst[0] = make_uint4(sW[0][t], sW[1][t], sW[2][t], sW[3][t]);
             dst[1] = make_uint4(sW[4][t], sW[5][t], sW[6][t], sW[7][t]);
+            if (fullBits) {
+                uint4 *fd = (uint4 *)(fullBits + (int64_t)(a0 + t) * W32 + l0 / 32);
+                fd[0] = make_uint4(sF[0][t], sF[1][t], sF[2][t], sF[3][t]);
+                fd[1] = make_uint4(sF[4][t], sF[5][t], sF[6][t], sF[7][t]);
+            }
         }
         __syncthreads();
         // the tile's leaves that some query of the block covers partially;
@@ -441,36 +454,61 @@ __global__ void k_zero(ZeroList z)
 // --------------------------------------------------------- budget (rule 2)
 
 // Collects (FP32 d'^2, position) of every point with d'^2 <= hi for one
-// budget query.  Grid (budget query, leaf chunk of 256).
-__global__ void k_collect(const int32_t *__restrict__ sel, const int32_t *__restrict__ act,
-                          const Thr *__restrict__ thr, const float *__restrict__ qp32,
-                          const float *__restrict__ qpiv, int s, const float *__restrict__ meta,
-                          const int64_t *__restrict__ off, int64_t L, const float *__restrict__ O32,
-                          const int64_t *__restrict__ selOff, const int64_t *__restrict__ selCap,
-                          int *__restrict__ selCnt, float *__restrict__ selKey,
-                          int *__restrict__ selPos, int *__restrict__ errFlag)
+// budget query.  Grid (budget query, leaf slice): a warp classifies 32
+// leaves at once (leaf_class, a lane per leaf), then takes the kept ones in
+// turn, its lanes testing 32 points at once (rows read together), and
+// appends the selected points with one atomic on the query's counter.
+__global__ void __launch_bounds__(256)
+k_collect(const int32_t *__restrict__ sel, const int32_t *__restrict__ act,
+          const Thr *__restrict__ thr, const float *__restrict__ qp32,
+          const float *__restrict__ qpiv, int s, const float *__restrict__ meta,
+          const int64_t *__restrict__ off, int64_t L, const float *__restrict__ O32,
+          const int64_t *__restrict__ selOff, const int64_t *__restrict__ selCap,
+          int *__restrict__ selCnt, float *__restrict__ selKey,
+          int *__restrict__ selPos, int *__restrict__ errFlag)
 {
     const int si = blockIdx.x;
     const int a = sel[si];
     const int q = act[a];
-    const int64_t l = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-    if (l >= L) return;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
     float qv[PM_MP], qpv[PM_MAX_PIVOTS];
     for (int j = 0; j < PM_MP; j++) qv[j] = qp32[(int64_t)q * PM_MP + j];
     for (int i = 0; i < PM_MAX_PIVOTS; i++) qpv[i] = qpiv[(int64_t)q * PM_MAX_PIVOTS + i];
-    Thr T = thr[a];
-    float Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f, Rout = __fsqrt_rn(T.hi);
-    unsigned char c = leaf_class(qv, qpv, s, Rin, Rout, meta + l * PM_LEAF_STRIDE);
-    if (c == CL_OUT) return;
-    for (int64_t pos = off[l]; pos < off[l + 1]; pos++) {
-        float v = pm_pd2_32(O32 + pos * PM_MP, qv);
-        if (c == CL_FULL || v <= T.hi) {
-            int e = atomicAdd(&selCnt[si], 1);
-            if (e < selCap[si]) {
-                selKey[selOff[si] + e] = v;
-                selPos[selOff[si] + e] = (int)pos;
-            } else {
-                atomicOr(errFlag, 64);
+    const Thr T = thr[a];
+    const float Rin = T.lo > 0.f ? __fsqrt_rn(T.lo) : -1.f, Rout = __fsqrt_rn(T.hi);
+    const int64_t base = selOff[si], cap = selCap[si];
+    const int64_t step = (int64_t)gridDim.y * wpb * 32;
+    for (int64_t l0 = ((int64_t)blockIdx.y * wpb + (threadIdx.x >> 5)) * 32; l0 < L; l0 += step) {
+        // the lanes classify 32 leaves, then the warp takes the kept ones
+        const int64_t lme = l0 + lane;
+        const unsigned char cme = lme < L ? leaf_class(qv, qpv, s, Rin, Rout, meta + lme * PM_LEAF_STRIDE) : CL_OUT;
+        unsigned kept = __ballot_sync(0xffffffffu, cme != CL_OUT);
+        while (kept) {
+            const int src = __ffs(kept) - 1;
+            kept &= kept - 1;
+            const int64_t l = l0 + src;
+            const unsigned char c = (unsigned char)__shfl_sync(0xffffffffu, (int)cme, src);
+            const int64_t p0 = off[l], p1 = off[l + 1];
+            for (int64_t b0 = p0; b0 < p1; b0 += 32) {
+                const int64_t pos = b0 + lane;
+                const bool valid = pos < p1;
+                const float v = valid ? pm_pd2_32(O32 + pos * PM_MP, qv) : INFINITY;
+                const bool take = valid && (c == CL_FULL || v <= T.hi);
+                const unsigned m = __ballot_sync(0xffffffffu, take);
+                if (m == 0u) continue;
+                int e0 = 0;
+                if (lane == 0) e0 = atomicAdd(&selCnt[si], __popc(m));
+                e0 = __shfl_sync(0xffffffffu, e0, 0);
+                if (take) {
+                    const int64_t e = (int64_t)e0 + __popc(m & ((1u << lane) - 1u));
+                    if (e < cap) {
+                        selKey[base + e] = v;
+                        selPos[base + e] = (int)pos;
+                    } else {
+                        atomicOr(errFlag, 64);
+                    }
+                }
             }
         }
     }
@@ -495,6 +533,7 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
     __shared__ int bpos[SELBAND];
     __shared__ int bid[SELBAND];
     __shared__ int sSure, sBand;
+    __shared__ unsigned int sWarp[32];
     const int si = blockIdx.x;
     const int a = sel[si];
     const int q = act[a];
@@ -504,27 +543,53 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
     if (threadIdx.x == 0) { sPrefix = 0; sNeed = (unsigned int)B; }
     const int shifts[3] = {21, 10, 0};
     const int widths[3] = {11, 11, 10};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int pass = 0; pass < 3; pass++) {
         for (int i = threadIdx.x; i < 2048; i += blockDim.x) hist[i] = 0;
         __syncthreads();
         const int sh = shifts[pass];
         const unsigned int hiMask = pass == 0 ? 0u : (0xffffffffu << (sh + widths[pass]));
         const unsigned int pre = sPrefix;
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            unsigned int k = keys[e];
-            if ((k & hiMask) == (pre & hiMask))
-                atomicAdd(&hist[(k >> sh) & ((1u << widths[pass]) - 1)], 1u);
+        const unsigned int need = sNeed;
+        // histogram: lanes with the same bin add once (keys of one query
+        // share their leading bits, so bins are few and hot)
+        for (int e0 = wid * 32; e0 < cnt; e0 += nwarp * 32) {
+            const int e = e0 + lane;
+            unsigned int bin = 0xFFFFFFFFu;
+            if (e < cnt) {
+                const unsigned int k = keys[e];
+                if ((k & hiMask) == (pre & hiMask)) bin = (k >> sh) & ((1u << widths[pass]) - 1);
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, bin);
+            if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned int)__popc(peers));
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned int need = sNeed, acc = 0;
-            int bin = 0;
-            for (; bin < (1 << widths[pass]); bin++) {
-                if (acc + hist[bin] >= need) break;
-                acc += hist[bin];
+        // the bin holding the need-th key: block-wide prefix over the bins
+        // (two per thread), the thread whose range holds it records it
+        const int nbins = 1 << widths[pass];
+        const int b0 = 2 * threadIdx.x;
+        const unsigned int h0 = b0 < nbins ? hist[b0] : 0u, h1 = b0 + 1 < nbins ? hist[b0 + 1] : 0u;
+        unsigned int incl = h0 + h1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) sWarp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned int w = lane < nwarp ? sWarp[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
             }
-            sNeed = need - acc;
-            sPrefix = pre | ((unsigned int)bin << sh);
+            if (lane < nwarp) sWarp[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned int ex = incl - (h0 + h1) + (wid > 0 ? sWarp[wid - 1] : 0u);
+        if (b0 < nbins && ex < need && need <= ex + h0 + h1) {
+            const bool first = need <= ex + h0;
+            sNeed = need - ex - (first ? 0u : h0);
+            sPrefix = pre | ((unsigned int)(first ? b0 : b0 + 1) << sh);
         }
         __syncthreads();
     }
@@ -535,9 +600,10 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
     const float HI = __double2float_ru((tau + 2.0 * eps) * (tau + 2.0 * eps));
     if (threadIdx.x == 0) { sSure = 0; sBand = 0; }
     __syncthreads();
+    int mySure = 0;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         float v = selKey[base + e];
-        if (v < LO) atomicAdd(&sSure, 1);
+        if (v < LO) mySure++;
         else if (v <= HI) {
             int slot = atomicAdd(&sBand, 1);
             if (slot < SELBAND) {
@@ -548,6 +614,8 @@ k_select(const int32_t *__restrict__ sel, const int32_t *__restrict__ act, Thr *
             }
         }
     }
+    mySure = __reduce_add_sync(0xffffffffu, mySure);
+    if (lane == 0 && mySure) atomicAdd(&sSure, mySure);
     __syncthreads();
     const int nband = sBand;
     const int need = (int)B - sSure;
@@ -620,6 +688,7 @@ struct VwArgs {
     int64_t n;      // points
     int2 *lists;    // [warps][L]: per-warp candidate leaves {leaf, lower bound bits}
     const uint32_t *leafBits;   // [na][W32]: leaves Eq. 5 does not exclude (k_class)
+    const uint32_t *fullBits;   // [na][W32]: leaves k_class calls full (all members within the radius)
     int W32;
     const double *O64, *qp64;   // FP64 projected points and queries
     const float *leafPmu;       // [L][PM_PCA] leaf centres along the principal directions
@@ -899,7 +968,12 @@ k_verify(VwArgs A)
         // (lbl: the leaf's full lower bound, ||q - mu_l|| lbSlack - Rx_l)
         auto visit = [&](int l, float lbl) {
             leaves++;
-            const unsigned char cl = leaf_class(sq, sp, s, Rv, Rout, A.meta + (int64_t)l * PM_LEAF_STRIDE);
+            // k_class's decision for this round's radius (its full test is
+            // sound for lov = its lower threshold); a query whose radius the
+            // budget selection moved (T.pad) takes the test again
+            const unsigned char cl = T.pad == 0.f
+                ? (((A.fullBits[(int64_t)a * A.W32 + (l >> 5)] >> (l & 31)) & 1u) ? CL_FULL : CL_PART)
+                : leaf_class(sq, sp, s, Rv, Rout, A.meta + (int64_t)l * PM_LEAF_STRIDE);
             const int cb = A.leafChunk[l], ce = A.leafChunk[l + 1];
             // chunk bounds only if one can prune: every member lies within
             // ub = ||q - mu_l|| + Rx_l of q (rounded up generously from lbl),
@@ -1950,6 +2024,7 @@ void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
         {&KnnWork::bandCnt, nq * 4}, {&KnnWork::bandIn, nq * 4}, {&KnnWork::bandInQ, nq * BCAP * 4},
         {&KnnWork::bandQ, ((int64_t)1 << 20) * 4}, {&KnnWork::bandPos, ((int64_t)1 << 20) * 4},
         {&KnnWork::flags, (nq + 8) * 4}, {&KnnWork::dk, nq * 8}, {&KnnWork::leafBits, nq * W32 * 4},
+        {&KnnWork::fullBits, nq * W32 * 4},
         {&KnnWork::recheck, tc ? ((int64_t)1 << 23) * 8 : 0},
         {&KnnWork::blkCnt, nlist * 4}, {&KnnWork::blkLeaves, nlist * L * 16},
         {&KnnWork::blkMask, std::max(nlq * L * (QB / 32) * 4, nlt * L * TC_MW * 4)},
@@ -1993,7 +2068,7 @@ int64_t pm_work_resident(const KnnWork &w)
                             &w.bandQ, &w.bandPos, &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen,
                             &w.bandInQ, &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf, &w.selOff,
                             &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask, &w.recheck, &w.leafBits,
-                            &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
+                            &w.fullBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
     int64_t b = 0;
     for (const DevBuf *p : bufs) b += (int64_t)p->bytes;
     return b;
@@ -2110,6 +2185,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     int *recheckN = fpc + nq + 2;
     const int W32 = (int)pm_leaf_words(L);
     uint32_t *leafBits = grow<uint32_t>(w.leafBits, (size_t)nq * W32, s);
+    uint32_t *fullBits = grow<uint32_t>(w.fullBits, (size_t)nq * W32, s);
     if (s != PMLSH_OK) return s;
 
     VerifyPlan vp;
@@ -2156,6 +2232,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             const Thr *thr;
             int *cntSure, *cntPart, *cntBand, *inTrue, *inN, *inPos, *fpc;
             uint32_t *leafBits;
+            uint32_t *fullBits;   // whole-leaf bits for the verification, or null
         };
         const int64_t Tdec = std::min<int64_t>(B, n);
         auto class_phase = [&](bool tc, const CountIO &io, ZeroList z) -> pmlsh_status {
@@ -2188,11 +2265,11 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 if (!tc)
                     PM_LAUNCH("k_class", st, k_class<QB><<<gq, QB, 0, st>>>(io.act, io.na, io.thr, qp32, qpiv,
                                                 ix->s, ix->leafMeta, ix->leafOff, nullptr, L, io.cntSure, blkCnt,
-                                                blkEnt, blkMask, io.leafBits, W32, io.cntPart));
+                                                blkEnt, blkMask, io.leafBits, W32, io.cntPart, io.fullBits));
                 else
                     PM_LAUNCH("k_class", st, k_class<TC_QN><<<gq, TC_QN, 0, st>>>(io.act, io.na, io.thr, qp32,
                                                 qpiv, ix->s, ix->leafMeta, ix->leafOff, ix->bOff, L, io.cntSure,
-                                                blkCnt, blkEnt, blkMask, io.leafBits, W32, io.cntPart));
+                                                blkCnt, blkEnt, blkMask, io.leafBits, W32, io.cntPart, io.fullBits));
             }
             PM_CUDA(cudaGetLastError());
             return PMLSH_OK;
@@ -2256,7 +2333,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             }
             return PMLSH_OK;
         };
-        const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits};
+        const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits, fullBits};
         {
             // this round's per-query counters and the error and list counters
             // after them (fpc [nq + 8]) start at zero
@@ -2305,7 +2382,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 *s2InPos = sub + 12 * na2;
             PM_CUDA(cudaMemcpyAsync(amb, ambH.data(), na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             PM_LAUNCH("k_gather_sub", st, k_gather_sub<<<(na2 + 255) / 256, 256, 0, st>>>(amb, na2, act, thr, act2, thr2));
-            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2};
+            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2, nullptr};
             PM_TRY(class_phase(tensor, subIO, ZeroList()));   // zeroes inTrue, inN, fp64 of the sub-batch
             std::vector<int> es, eb, ein;
             PM_TRY(exact_count(subIO, es, eb, ein));
@@ -2344,7 +2421,9 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             PM_CUDA(cudaMemcpyAsync(selOff, selOffH.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
             PM_CUDA(cudaMemcpyAsync(selOff + ns + 1, capH.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, st));
             PM_CUDA(cudaMemsetAsync(selCnt, 0, ns * sizeof(int), st));
-            PM_LAUNCH("k_collect", st, k_collect<<<dim3(ns, (unsigned)((L + 255) / 256)), 256, 0, st>>>(
+            // about eight 256-thread blocks per SM over all budget queries
+            const int64_t gyc = std::max<int64_t>(1, std::min<int64_t>((L + 255) / 256, ((int64_t)8 * nsm + ns - 1) / ns));
+            PM_LAUNCH("k_collect", st, k_collect<<<dim3(ns, (unsigned)gyc), 256, 0, st>>>(
                 sel, act, thr, qp32, qpiv, ix->s, ix->leafMeta, ix->leafOff, L, ix->O32, selOff,
                 selOff + ns + 1, selCnt, selKey, selPos, errFlag));
             PM_LAUNCH("k_select", st, k_select<<<ns, 1024, 0, st>>>(sel, act, thr, selOff, selCnt, selKey, selPos, B, ix->maxNorm,
@@ -2413,7 +2492,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             va.dk = dk; va.fp64cnt = fpc; va.nverOut = nverD; va.nleafOut = nverD + na; va.errFlag = errFlag;
             va.workCtr = nverD + 2 * na; va.dbg = nverD + 2 * na + 1; va.n = n; va.lists = vLists;
             va.order = vOrder;
-            va.leafBits = leafBits; va.W32 = W32;
+            va.leafBits = leafBits; va.fullBits = fullBits; va.W32 = W32;
             va.O64 = ix->O64; va.qp64 = qp64; va.m = m; va.inlineBand = needExact ? 0 : 1;
             va.leafPmu = ix->leafPmu; va.qpca = qpca; va.qnx = qnx;
             va.muMax = (float)(ix->muMax * (1.0 + 1e-6)) + 1e-30f;

@@ -70,7 +70,7 @@ struct KnnWork {
         bandIn, bandCnt;
     DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
     DevBuf selBuf, selOff, selCnt, selTau;
-    DevBuf active, misc, recheck, leafBits, cntPart, subIdx, subThr, subBits, qpca;
+    DevBuf active, misc, recheck, leafBits, fullBits, cntPart, subIdx, subThr, subBits, qpca;
     HostBuf stage;   // per-round decisions read by the host
 };
 
