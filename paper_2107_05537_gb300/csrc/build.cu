@@ -148,6 +148,46 @@ __global__ void k_leaf_ball(const double *__restrict__ O64, const int64_t *__res
 // Pivot rings e.HR[i] = [min, max] of ||o', p_i|| over the leaf, taken on the
 // FP32 coordinates and widened by 1e-5 relative so that they bound the exact
 // distances of the FP32 coordinates.
+// Radial profile of a leaf (meta [17, 24)): for g = 2 .. 8, an upper bound of
+// the ceil(g s / 8)-th largest distance of the leaf's s members from its FP32
+// centre, with the centre's rounding covered as in the leaf radius.  The
+// range count's bounds use it: a member whose radius is below d(q, centre) -
+// R lies outside the ball, one whose radius is below R - d(q, centre) inside.
+// Leaves above LR_MAXS members take the leaf radius for every rank.
+constexpr int LR_MAXS = 2048;
+__global__ void k_leaf_radii(const double *__restrict__ O64, const int64_t *__restrict__ off, int m,
+                             double maxNorm, const double *__restrict__ ro64, float *__restrict__ meta)
+{
+    __shared__ float rad[LR_MAXS];
+    const int64_t l = blockIdx.x;
+    const int64_t a = off[l];
+    const int sz = (int)(off[l + 1] - a);
+    float *M = meta + l * PM_LEAF_STRIDE;
+    if (sz > LR_MAXS) {
+        for (int g = 2 + (int)threadIdx.x; g <= 8; g += blockDim.x) M[15 + g] = M[16];
+        return;
+    }
+    const double *c = ro64 + l * PM_MP;
+    double cn = 0.0;
+    for (int j = 0; j < PM_MP; j++) cn = fma(c[j], c[j], cn);
+    const double slack = 0x1.0p-23 * (sqrt(cn) + maxNorm);
+    for (int e = threadIdx.x; e < sz; e += blockDim.x)
+        rad[e] = __double2float_ru((pm_pdist64(O64 + (a + e) * PM_MP, c, m) + slack) * (1.0 + 1e-6));
+    __syncthreads();
+    // rank of each member in descending order (ties by position); the
+    // members at ranks ceil(g s / 8) give the profile
+    for (int e = threadIdx.x; e < sz; e += blockDim.x) {
+        const float v = rad[e];
+        int rank = 0;
+        for (int f = 0; f < sz; f++) {
+            const float w = rad[f];
+            rank += (w > v || (w == v && f < e)) ? 1 : 0;
+        }
+        for (int g = 2; g <= 8; g++)
+            if (rank + 1 == (g * sz + 7) / 8) M[15 + g] = v;
+    }
+}
+
 __global__ void k_leaf_rings(const float *__restrict__ O32, const int64_t *__restrict__ off,
                              const float *__restrict__ piv, int s, float *__restrict__ meta)
 {
@@ -705,7 +745,7 @@ void pm_release_work(KnnWork &w)
                       &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen, &w.bandInQ,
                       &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf,
                       &w.selOff, &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask,
-                      &w.recheck, &w.leafBits, &w.fullBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
+                      &w.recheck, &w.leafBits, &w.fullBits, &w.cntPart, &w.cntTight, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
     for (DevBuf *b : bufs) b->release();
     w.stage.release();
 }
@@ -906,6 +946,8 @@ pmlsh_status pm_build_index(pmlsh_index *ix, const float *X, bool x_on_device,
     PM_TRY(dalloc(&ro64, (size_t)L * PM_MP));
     struct G4 { double *a; ~G4() { cudaFree(a); } } g4{ro64};
     PM_LAUNCH("k_leaf_ball", st, k_leaf_ball<<<(unsigned)L, 256, 0, st>>>(ix->O64, ix->leafOff, m, ix->maxNorm, ix->leafMeta, ro64));
+    PM_LAUNCH("k_leaf_radii", st, k_leaf_radii<<<(unsigned)L, 256, 0, st>>>(ix->O64, ix->leafOff, m, ix->maxNorm, ro64,
+                                                                          ix->leafMeta));
     PM_CUDA(cudaGetLastError());
     std::vector<float> meta((size_t)L * PM_LEAF_STRIDE);
     PM_CUDA(cudaMemcpyAsync(meta.data(), ix->leafMeta, meta.size() * sizeof(float), cudaMemcpyDeviceToHost, st));

@@ -331,6 +331,112 @@ k_class(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr,
     }
 }
 
+// Tightened bounds of |S_i| for the active queries whose whole-leaf bounds
+// (cntSure from below, cntSure + cntPart from above) straddle T = min(B, n);
+// the others exit at once.  A CTA per query walks its partially covered
+// leaves (leafBits without fullBits) and applies each leaf's radial profile
+// (meta [17, 24): for g = 2 .. 8 an upper bound v_g of the ceil(g s / 8)-th
+// largest member radius): with d the centre distance, members of radius
+// < d (1 - SLACK) - Rout (1 + SLACK) lie beyond Rout and those of radius
+// <= Rin (1 - SLACK) - d (1 + SLACK) within Rin (the leaf tests'
+// inequalities for the sub-ball of the members from that rank on).
+// cntTight[a] = (members of partial leaves surely inside, possibly inside).
+__global__ void __launch_bounds__(256)
+k_tight(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr, const float *__restrict__ qp32,
+        const float *__restrict__ meta, const int64_t *__restrict__ off, const uint32_t *__restrict__ leafBits,
+        const uint32_t *__restrict__ fullBits, int W32, int64_t L, const int *__restrict__ cntSure,
+        const int *__restrict__ cntPart, int64_t T, int2 *__restrict__ cntTight)
+{
+    // one CTA per active query; a warp compacts the partial leaves of 32
+    // bit-set words into shared memory, then its lanes take one leaf each
+    __shared__ int sLeaf[8][1024];
+    __shared__ int sRed[2][8];
+    const int a = blockIdx.x;
+    const int sure = cntSure[a], part = cntPart[a];
+    if (sure >= T || (int64_t)sure + part < T) return;   // block-uniform
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int q = act[a];
+    float qv[PM_MP];
+#pragma unroll
+    for (int j = 0; j < PM_MP; j++) qv[j] = qp32[(int64_t)q * PM_MP + j];
+    const Thr th = thr[a];
+    const float Rin = th.lo > 0.f ? __fsqrt_rn(th.lo) : -1.f;
+    const float ro = __fmul_ru(__fsqrt_rn(th.hi), 1.f + SLACK);
+    const float rinLo = Rin > 0.f ? __fmul_rd(Rin, 1.f - SLACK) : -1.f;
+    int lb = 0, ub = 0;
+    int *buf = sLeaf[wp];
+    for (int w0 = wp * 32; w0 < W32; w0 += 8 * 32) {
+        const int wi = w0 + lane;
+        uint32_t word = 0u;
+        if (wi < W32) word = leafBits[(int64_t)a * W32 + wi] & ~fullBits[(int64_t)a * W32 + wi];
+        const int c = __popc(word);
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int at = incl - c;
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1u;
+            buf[at++] = wi * 32 + b;
+        }
+        __syncwarp();
+        for (int e = lane; e < total; e += 32) {
+            const int64_t l = buf[e];
+            if (l >= L) continue;
+            const float *M = meta + l * PM_LEAF_STRIDE;
+            // FP32 squared centre distance (its rounding is within SLACK)
+            const float4 *c4 = (const float4 *)M;
+            float d2 = 0.f;
+#pragma unroll
+            for (int j4 = 0; j4 < PM_MP / 4; j4++) {
+                const float4 cc = __ldg(c4 + j4);
+                float u = __fsub_rn(qv[4 * j4], cc.x);
+                d2 = __fmaf_rn(u, u, d2);
+                u = __fsub_rn(qv[4 * j4 + 1], cc.y);
+                d2 = __fmaf_rn(u, u, d2);
+                u = __fsub_rn(qv[4 * j4 + 2], cc.z);
+                d2 = __fmaf_rn(u, u, d2);
+                u = __fsub_rn(qv[4 * j4 + 3], cc.w);
+                d2 = __fmaf_rn(u, u, d2);
+            }
+            const int n = (int)(off[l + 1] - off[l]);
+            const float tOut = __fsub_rd(__fmul_rd(__fsqrt_rd(d2), 1.f - SLACK), ro);
+            const float tIn = rinLo > 0.f ? __fsub_rd(rinLo, __fmul_ru(__fsqrt_ru(d2), 1.f + SLACK)) : -INFINITY;
+            // v_g falls with g: the smallest g passing a test gives its bound
+            int u1 = n, l1 = 0;
+            const float4 r0 = __ldg((const float4 *)(M + 16)), r1 = __ldg((const float4 *)(M + 20));
+            const float vg[7] = {r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+            for (int g = 2; g <= 8; g++) {
+                const int kg = (g * n + 7) / 8;
+                if (vg[g - 2] < tOut && u1 == n) u1 = kg - 1;
+                if (vg[g - 2] <= tIn && l1 == 0) l1 = n - kg + 1;
+            }
+            lb += l1;
+            ub += u1;
+        }
+        __syncwarp();
+    }
+    lb = __reduce_add_sync(0xffffffffu, lb);
+    ub = __reduce_add_sync(0xffffffffu, ub);
+    if (lane == 0) {
+        sRed[0][wp] = lb;
+        sRed[1][wp] = ub;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tl = 0, tu = 0;
+        for (int w = 0; w < 8; w++) {
+            tl += sRed[0][w];
+            tu += sRed[1][w];
+        }
+        cntTight[a] = make_int2(tl, tu);
+    }
+}
+
 // Per-point test in partially covered leaves (the queries of the block's
 // list mask).  Grid (block, split).
 __global__ void __launch_bounds__(256)
@@ -2021,6 +2127,7 @@ void knn_work_needs(const pmlsh_index *ix, int64_t nq, int k, int precision,
         {&KnnWork::qstate, nq * 8}, {&KnnWork::outIds, nq * k * 8}, {&KnnWork::outD64, nq * k * 4},
         {&KnnWork::outErr, nq * k * 4}, {&KnnWork::active, nq * 4}, {&KnnWork::thr, nq * (int64_t)sizeof(Thr)},
         {&KnnWork::cntSure, nq * 4}, {&KnnWork::cntBand, nq * 4}, {&KnnWork::cntPart, nq * 4},
+        {&KnnWork::cntTight, nq * 8},
         {&KnnWork::bandCnt, nq * 4}, {&KnnWork::bandIn, nq * 4}, {&KnnWork::bandInQ, nq * BCAP * 4},
         {&KnnWork::bandQ, ((int64_t)1 << 20) * 4}, {&KnnWork::bandPos, ((int64_t)1 << 20) * 4},
         {&KnnWork::flags, (nq + 8) * 4}, {&KnnWork::dk, nq * 8}, {&KnnWork::leafBits, nq * W32 * 4},
@@ -2068,7 +2175,7 @@ int64_t pm_work_resident(const KnnWork &w)
                             &w.bandQ, &w.bandPos, &w.bandIn, &w.bandCnt, &w.partD, &w.partI, &w.partSeen,
                             &w.bandInQ, &w.outD64, &w.outIds, &w.outErr, &w.dk, &w.flags, &w.selBuf, &w.selOff,
                             &w.selCnt, &w.selTau, &w.active, &w.misc, &w.blkMask, &w.recheck, &w.leafBits,
-                            &w.fullBits, &w.cntPart, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
+                            &w.fullBits, &w.cntPart, &w.cntTight, &w.subIdx, &w.subThr, &w.subBits, &w.qpca};
     int64_t b = 0;
     for (const DevBuf *p : bufs) b += (int64_t)p->bytes;
     return b;
@@ -2150,9 +2257,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     // pinned staging of the per-round decisions: order [nq], bounds [2 nq],
     // verification outputs (k-th distance [nq] f64, fp64/verified/leaves
     // counts [3 nq], error flag)
-    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 8) + 64));
+    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 8 + 8) + 64));
     double *stDk = (double *)w.stage.p;
-    int32_t *stOrder = (int32_t *)(stDk + nq);
+    int2 *stTight = (int2 *)(stDk + nq);
+    int32_t *stOrder = (int32_t *)(stTight + nq);
     int *stHs = stOrder + nq, *stHp = stHs + nq, *stFp = stHp + nq, *stNv = stFp + nq, *stNl = stNv + nq,
         *stVo = stNl + nq, *stRedo = stVo + nq, *stErr = stRedo + nq;
     PM_CUDA(cudaMemcpyAsync(stOrder, order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -2172,6 +2280,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     int *cntSure = grow<int>(w.cntSure, nq, s);
     int *cntBand = grow<int>(w.cntBand, nq, s);
     int *cntPart = grow<int>(w.cntPart, nq, s);
+    int2 *cntTight = grow<int2>(w.cntTight, nq, s);
     int *inTrue = grow<int>(w.bandCnt, nq, s);
     int *inN = grow<int>(w.bandIn, nq, s);
     int *inPos = grow<int>(w.bandInQ, (size_t)nq * BCAP, s);
@@ -2233,6 +2342,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             int *cntSure, *cntPart, *cntBand, *inTrue, *inN, *inPos, *fpc;
             uint32_t *leafBits;
             uint32_t *fullBits;   // whole-leaf bits for the verification, or null
+            int2 *cntTight;       // partial leaves' members surely / possibly inside (radial profiles), or null
         };
         const int64_t Tdec = std::min<int64_t>(B, n);
         auto class_phase = [&](bool tc, const CountIO &io, ZeroList z) -> pmlsh_status {
@@ -2253,6 +2363,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             z.add(io.fpc, io.na);
             z.add(bandN, 1);
             z.add(recheckN, 1);
+            z.add((int *)io.cntTight, io.cntTight ? 2 * io.na : 0);
             PM_LAUNCH("k_zero", st, k_zero<<<2 * nsm, 256, 0, st>>>(z));
             {
                 // query-stationary test: leaf tiles split evenly over enough
@@ -2271,6 +2382,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                                 qpiv, ix->s, ix->leafMeta, ix->leafOff, ix->bOff, L, io.cntSure,
                                                 blkCnt, blkEnt, blkMask, io.leafBits, W32, io.cntPart, io.fullBits));
             }
+            if (io.cntTight)
+                PM_LAUNCH("k_tight", st, k_tight<<<(unsigned)io.na, 256, 0, st>>>(io.act, io.na, io.thr,
+                                               qp32, ix->leafMeta, ix->leafOff, io.leafBits, io.fullBits, W32, L,
+                                               io.cntSure, io.cntPart, Tdec, io.cntTight));
             PM_CUDA(cudaGetLastError());
             return PMLSH_OK;
         };
@@ -2333,7 +2448,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             }
             return PMLSH_OK;
         };
-        const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits, fullBits};
+        const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits, fullBits,
+                           stats == nullptr ? cntTight : nullptr};
         {
             // this round's per-query counters and the error and list counters
             // after them (fpc [nq + 8]) start at zero
@@ -2342,11 +2458,14 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             PM_TRY(class_phase(tensor, full, z));
         }
         std::vector<int> hs(na), hp(na), hb(na, 0), hin(na, 0);
+        std::vector<int2> ht;
         PM_CUDA(cudaMemcpyAsync(stHs, cntSure, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(stHp, cntPart, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (full.cntTight) PM_CUDA(cudaMemcpyAsync(stTight, cntTight, na * sizeof(int2), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
         std::memcpy(hs.data(), stHs, na * sizeof(int));
         std::memcpy(hp.data(), stHp, na * sizeof(int));
+        if (full.cntTight) ht.assign(stTight, stTight + na);
         if (round == 0) {
             orderH.assign(stOrder, stOrder + nq);
             actH.assign(stOrder, stOrder + nq);
@@ -2365,9 +2484,16 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         if (needExact) {
             PM_TRY(exact_count(full, hs, hb, hin));
         } else {
+            // the bounds of |S_i| from whole leaves, tightened by the partial
+            // leaves' radial profiles; a query whose lower bound reaches
+            // min(B, n) counts as min(B, n) (rule 2, or rule 3 when n < B)
             for (int a = 0; a < na; a++) {
                 hb[a] = hp[a];
-                if (hs[a] < Tdec && (int64_t)hs[a] + hp[a] >= Tdec) ambH.push_back(a);
+                if (hs[a] >= Tdec) continue;
+                const int64_t lo = ht.empty() ? hs[a] : (int64_t)hs[a] + ht[a].x;
+                const int64_t up = ht.empty() ? (int64_t)hs[a] + hp[a] : (int64_t)hs[a] + ht[a].y;
+                if (lo >= Tdec) hin[a] = (int)(Tdec - hs[a]);
+                else if (up >= Tdec) ambH.push_back(a);
             }
         }
         if (!ambH.empty()) {
@@ -2382,7 +2508,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 *s2InPos = sub + 12 * na2;
             PM_CUDA(cudaMemcpyAsync(amb, ambH.data(), na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             PM_LAUNCH("k_gather_sub", st, k_gather_sub<<<(na2 + 255) / 256, 256, 0, st>>>(amb, na2, act, thr, act2, thr2));
-            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2, nullptr};
+            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2, nullptr, nullptr};
             PM_TRY(class_phase(tensor, subIO, ZeroList()));   // zeroes inTrue, inN, fp64 of the sub-batch
             std::vector<int> es, eb, ein;
             PM_TRY(exact_count(subIO, es, eb, ein));

@@ -13,8 +13,9 @@
 // for points, queries and pivots, so they add nothing to any distance.
 #define PM_MP 16
 // Leaf metadata, FP32, per leaf: [0,16) centre RO, [16] radius (over FP32
-// coordinates, rounded up), [17] unused, [24,32) ring minima, [32,40) ring
-// maxima (Sec. 4.1: e.RO, e.r, e.HR[s]).
+// coordinates, rounded up), [17,24) radial profile (for g = 2 .. 8 an upper
+// bound of the ceil(g s / 8)-th largest member radius), [24,32) ring minima,
+// [32,40) ring maxima (Sec. 4.1: e.RO, e.r, e.HR[s]).
 #define PM_LEAF_STRIDE 40
 #define PM_MAX_PIVOTS 8
 #define PM_MAX_K 256
@@ -70,7 +71,7 @@ struct KnnWork {
         bandIn, bandCnt;
     DevBuf partD, partI, partSeen, bandInQ, outD64, outIds, outErr, dk, flags;
     DevBuf selBuf, selOff, selCnt, selTau;
-    DevBuf active, misc, recheck, leafBits, fullBits, cntPart, subIdx, subThr, subBits, qpca;
+    DevBuf active, misc, recheck, leafBits, fullBits, cntPart, cntTight, subIdx, subThr, subBits, qpca;
     HostBuf stage;   // per-round decisions read by the host
 };
 
