@@ -2240,9 +2240,13 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     float *qnx = qpca + (size_t)nq * PM_PCA;
     int *hist = grow<int>(w.keys2, L + 1, s);
     double *rq = grow<double>(w.qstate, nq, s);
-    int64_t *oIds = grow<int64_t>(w.outIds, (size_t)nq * k, s);
-    float *oD = grow<float>(w.outD64, (size_t)nq * k, s);
-    float *oE = grow<float>(w.outErr, (size_t)nq * k, s);
+    // results go straight to the caller's arrays when those are in device
+    // memory, else to scratch copied out at the end
+    const bool idev = pm_is_device_ptr(ids), ddev = pm_is_device_ptr(dists);
+    const bool edev = err != nullptr && pm_is_device_ptr(err);
+    int64_t *oIds = idev ? ids : grow<int64_t>(w.outIds, (size_t)nq * k, s);
+    float *oD = ddev ? dists : grow<float>(w.outD64, (size_t)nq * k, s);
+    float *oE = edev ? err : grow<float>(w.outErr, (size_t)nq * k, s);
     if (s != PMLSH_OK) return s;
     PM_TRY(pm_project_rows(ix, Q, nq, Qd, qp64, qp32, PM_MP, st));
     const unsigned gq = (unsigned)((nq + 255) / 256);
@@ -2257,12 +2261,15 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     // pinned staging of the per-round decisions: order [nq], bounds [2 nq],
     // verification outputs (k-th distance [nq] f64, fp64/verified/leaves
     // counts [3 nq], error flag)
-    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 8 + 8) + 64));
+    // (plus the radii [nq] f64 and an active or straddling list [nq] sent to
+    // the device, so that every copy is asynchronous)
+    PM_TRY(w.stage.reserve((size_t)nq * (8 + 4 * 8 + 8 + 8 + 4) + 64));
     double *stDk = (double *)w.stage.p;
-    int2 *stTight = (int2 *)(stDk + nq);
+    double *stR = stDk + nq;
+    int2 *stTight = (int2 *)(stR + nq);
     int32_t *stOrder = (int32_t *)(stTight + nq);
     int *stHs = stOrder + nq, *stHp = stHs + nq, *stFp = stHp + nq, *stNv = stFp + nq, *stNl = stNv + nq,
-        *stVo = stNl + nq, *stRedo = stVo + nq, *stErr = stRedo + nq;
+        *stVo = stNl + nq, *stRedo = stVo + nq, *stList = stRedo + nq, *stErr = stList + nq;
     PM_CUDA(cudaMemcpyAsync(stOrder, order, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> orderH;   // host copy, read after the first round's sync
 
@@ -2272,7 +2279,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
     std::vector<int64_t> ncand(nq, 0), nver(nq, 0);
     std::vector<int32_t> nleaf(nq, 0), fallback(nq, 0);
     std::vector<char> done(nq, 0);
-    PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::memcpy(stR, r.data(), nq * sizeof(double));
+    PM_CUDA(cudaMemcpyAsync(rq, stR, nq * sizeof(double), cudaMemcpyHostToDevice, st));
 
     const int bandCap = 1 << 20;
     int *actBuf = grow<int32_t>(w.active, nq, s);
@@ -2329,7 +2337,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 if (!done[orderH[i]]) actH.push_back(orderH[i]);
             na = (int)actH.size();
             if (na == 0) break;
-            PM_CUDA(cudaMemcpyAsync(act, actH.data(), na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            std::memcpy(stList, actH.data(), na * sizeof(int32_t));
+            PM_CUDA(cudaMemcpyAsync(act, stList, na * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         }
         PM_LAUNCH("k_thresholds", st, k_thresholds<<<(na + 255) / 256, 256, 0, st>>>(act, na, rq, t, ix->maxNorm, qnorm, thr));
         // leaf classification (Eq. 5): bounds of |S_i|, leaf lists with the
@@ -2496,6 +2505,32 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                 else if (up >= Tdec) ambH.push_back(a);
             }
         }
+        // Verification work order, decided here so that the host's pass runs
+        // while the GPU counts the straddling sub-batch: the queries with the
+        // most range candidates (their upper bound) first, so that the long ones do not finish last;
+        // locality order inside each of 32 logarithmic cost classes.  The
+        // grouped kernel takes groups of GV_WARPS consecutive active queries
+        // (locality order), a group's cost class being its costliest
+        // member's.
+        int *nverD = grow<int>(w.partSeen, (size_t)4 * na + 8, s);
+        int *vOrder = nverD + 2 * na + 8;
+        int *redoD = vOrder + na;   // queries left by the BF16 first pass
+        const int ngroups = (na + GV_WARPS - 1) / GV_WARPS;
+        {
+            const int nunits = grouped ? ngroups : na;
+            std::vector<int32_t> cls(nunits, 31);
+            int64_t hist[33] = {0};
+            for (int a = 0; a < na; a++) {
+                const uint64_t c = (uint64_t)((int64_t)hs[a] + hb[a] + 1);
+                const int b = std::min(31, 63 - __builtin_clzll(c));   // floor(log2 c)
+                const int u = grouped ? a / GV_WARPS : a;
+                cls[u] = std::min(cls[u], 31 - b);   // costliest class first
+            }
+            for (int u = 0; u < nunits; u++) hist[cls[u] + 1]++;
+            for (int b = 0; b < 32; b++) hist[b + 1] += hist[b];
+            for (int u = 0; u < nunits; u++) stVo[hist[cls[u]]++] = u;
+            PM_CUDA(cudaMemcpyAsync(vOrder, stVo, nunits * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
         if (!ambH.empty()) {
             // exact count of the sub-batch whose bounds straddle min(B, n)
             const int na2 = (int)ambH.size();
@@ -2506,7 +2541,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             int *amb = sub, *act2 = sub + na2, *s2Sure = sub + 2 * na2, *s2Part = sub + 3 * na2,
                 *s2Band = sub + 4 * na2, *s2In = sub + 5 * na2, *s2InN = sub + 6 * na2, *s2Fp = sub + 7 * na2,
                 *s2InPos = sub + 12 * na2;
-            PM_CUDA(cudaMemcpyAsync(amb, ambH.data(), na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            std::memcpy(stList, ambH.data(), na2 * sizeof(int32_t));   // (the round's active list is on the device)
+            PM_CUDA(cudaMemcpyAsync(amb, stList, na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             PM_LAUNCH("k_gather_sub", st, k_gather_sub<<<(na2 + 255) / 256, 256, 0, st>>>(amb, na2, act, thr, act2, thr2));
             const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2, nullptr, nullptr};
             PM_TRY(class_phase(tensor, subIO, ZeroList()));   // zeroes inTrue, inN, fp64 of the sub-batch
@@ -2556,32 +2592,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                           qnorm, ix->O64, qp64, m, ix->perm, inN, inPos, fpc, errFlag));
             PM_CUDA(cudaGetLastError());
         }
-        // verification: best-first over candidate leaves, guard set, FP64.
-        // Work order: the queries with the most range candidates (their
-        // upper bound) first, so that the long ones do not finish last;
-        // locality order inside each of 32 logarithmic cost classes.  The
-        // grouped kernel takes groups of GV_WARPS consecutive active queries
-        // (locality order), a group's cost class being its costliest
-        // member's.
-        int *nverD = grow<int>(w.partSeen, (size_t)4 * na + 8, s);
-        int *vOrder = nverD + 2 * na + 8;
-        int *redoD = vOrder + na;   // queries left by the BF16 first pass
-        const int ngroups = (na + GV_WARPS - 1) / GV_WARPS;
-        {
-            const int nunits = grouped ? ngroups : na;
-            std::vector<int32_t> cls(nunits, 31);
-            int64_t hist[33] = {0};
-            for (int a = 0; a < na; a++) {
-                const uint64_t c = (uint64_t)((int64_t)hs[a] + hb[a] + 1);
-                const int b = std::min(31, 63 - __builtin_clzll(c));   // floor(log2 c)
-                const int u = grouped ? a / GV_WARPS : a;
-                cls[u] = std::min(cls[u], 31 - b);   // costliest class first
-            }
-            for (int u = 0; u < nunits; u++) hist[cls[u] + 1]++;
-            for (int b = 0; b < 32; b++) hist[b + 1] += hist[b];
-            for (int u = 0; u < nunits; u++) stVo[hist[cls[u]]++] = u;
-            PM_CUDA(cudaMemcpyAsync(vOrder, stVo, nunits * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        }
+        // verification (order uploaded above): best-first over candidate
+        // leaves, guard set, FP64
         PM_CUDA(cudaMemsetAsync(nverD + 2 * na, 0, 8 * sizeof(int), st));
         if (grouped) {
             const int gGrid = std::max(1, std::min(ngroups, gvPerSM * nsm));
@@ -2631,15 +2643,16 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
-        PM_CUDA(cudaMemcpyAsync(stNl, nverD + na, na * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(stNv, nverD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (stats) {
+            PM_CUDA(cudaMemcpyAsync(stNl, nverD + na, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaMemcpyAsync(stNv, nverD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaMemcpyAsync(stFp, fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
         PM_CUDA(cudaMemcpyAsync(stDk, dk, na * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaMemcpyAsync(stFp, fpc, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaMemcpyAsync(stErr, errFlag, sizeof(int), cudaMemcpyDeviceToHost, st));
         if (bf16v) PM_CUDA(cudaMemcpyAsync(stRedo, redoD, na * sizeof(int), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
-        const std::vector<double> dkH(stDk, stDk + na);
-        const std::vector<int> fpH(stFp, stFp + na), nvH(stNv, stNv + na), nlH(stNl, stNl + na);
+        const double *dkH = stDk;
         const int errH = *stErr;
         if (errH) {
             int dbgH[3] = {0, 0, 0};
@@ -2654,11 +2667,13 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         for (int a = 0; a < na; a++) {
             const int q = actH[a];
             rounds[q]++;
-            fp64[q] += fpH[a];
             const bool budget = count[a] >= B;
-            nver[q] += nvH[a];
-            nleaf[q] += nlH[a];
-            if (bf16v) fallback[q] += stRedo[a];
+            if (stats) {
+                fp64[q] += stFp[a];
+                nver[q] += stNv[a];
+                nleaf[q] += stNl[a];
+                if (bf16v) fallback[q] += stRedo[a];
+            }
             if (rcbc) {
                 // Algorithm 1: the nearest candidate if |C| >= beta n + 1 or it
                 // lies within c r, else nothing
@@ -2680,8 +2695,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             }
             changed = true;
         }
-        if (changed)
-            PM_CUDA(cudaMemcpyAsync(rq, r.data(), nq * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (changed) {
+            std::memcpy(stR, r.data(), nq * sizeof(double));
+            PM_CUDA(cudaMemcpyAsync(rq, stR, nq * sizeof(double), cudaMemcpyHostToDevice, st));
+        }
         if (round == 99999) {
             pm_set_error("Algorithm 2 did not stop within 100000 rounds");
             return PMLSH_EINTERNAL;
@@ -2700,15 +2717,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                                   noneD, (int)none.size(), k, oIds, oD, oE));
         }
     }
-    // results
-    const bool idev = pm_is_device_ptr(ids), ddev = pm_is_device_ptr(dists);
-    PM_CUDA(cudaMemcpyAsync(ids, oIds, (size_t)nq * k * sizeof(int64_t),
-                            idev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    PM_CUDA(cudaMemcpyAsync(dists, oD, (size_t)nq * k * sizeof(float),
-                            ddev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (err)
-        PM_CUDA(cudaMemcpyAsync(err, oE, (size_t)nq * k * sizeof(float),
-                                pm_is_device_ptr(err) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    // results held in scratch (host arrays of the caller)
+    if (!idev) PM_CUDA(cudaMemcpyAsync(ids, oIds, (size_t)nq * k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (!ddev) PM_CUDA(cudaMemcpyAsync(dists, oD, (size_t)nq * k * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (err && !edev) PM_CUDA(cudaMemcpyAsync(err, oE, (size_t)nq * k * sizeof(float), cudaMemcpyDeviceToHost, st));
     if (stats) {
         std::vector<pmlsh_query_stats> sv(nq);
         for (int64_t q = 0; q < nq; q++) {
@@ -2725,7 +2737,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                 pm_is_device_ptr(stats) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
     }
-    if (!idev || !ddev) PM_CUDA(cudaStreamSynchronize(st));
+    if (!idev || !ddev || (err && !edev)) PM_CUDA(cudaStreamSynchronize(st));
     return PMLSH_OK;
 }
 
