@@ -437,6 +437,70 @@ k_tight(const int32_t *__restrict__ act, int na, const Thr *__restrict__ thr, co
     }
 }
 
+// Block leaf lists of a gathered sub-batch from the classification its
+// queries already have (the full batch's leafBits without fullBits: the
+// partially covered leaves): for a block of QBT sub-batch queries, every
+// leaf that some of them cover partially, with their QBT-bit mask, as
+// k_class lists it; and the sub-batch's whole-leaf counts copied from the
+// batch's.  Grid (block, chunk slice); a chunk is 8 bit-set words (256
+// leaves); each warp turns its queries' words into per-leaf masks by ballots.
+template <int QBT>
+__global__ void __launch_bounds__(QBT)
+k_sublists(const int32_t *__restrict__ amb, int na2, const uint32_t *__restrict__ leafBits,
+           const uint32_t *__restrict__ fullBits, int W32, int64_t L, const int64_t *__restrict__ off,
+           const int64_t *__restrict__ bOff, const int *__restrict__ cntSureAll, int *__restrict__ cntSure,
+           int *__restrict__ blkCnt, int4 *__restrict__ blkEnt, uint32_t *__restrict__ blkMask)
+{
+    constexpr int W = QBT / 32;
+    __shared__ uint32_t sM[256][W];
+    const int b = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    const int i = b * QBT + t;
+    const bool ok = i < na2;
+    const int a = ok ? amb[i] : 0;
+    if (ok && blockIdx.y == 0) cntSure[i] = cntSureAll[a];
+    for (int c = blockIdx.y; c * 8 < W32; c += gridDim.y) {
+        uint32_t pw[8];
+        if (ok) {
+            // eight words of this query's rows: one aligned 32-byte sector each
+            const uint4 *lb = (const uint4 *)(leafBits + (int64_t)a * W32 + c * 8);
+            const uint4 *fb = (const uint4 *)(fullBits + (int64_t)a * W32 + c * 8);
+            const uint4 l0 = lb[0], l1 = lb[1], f0 = fb[0], f1 = fb[1];
+            pw[0] = l0.x & ~f0.x; pw[1] = l0.y & ~f0.y; pw[2] = l0.z & ~f0.z; pw[3] = l0.w & ~f0.w;
+            pw[4] = l1.x & ~f1.x; pw[5] = l1.y & ~f1.y; pw[6] = l1.z & ~f1.z; pw[7] = l1.w & ~f1.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) pw[k] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const unsigned any = __ballot_sync(0xffffffffu, pw[k] != 0u);
+#pragma unroll 4
+            for (int j = 0; j < 32; j++) {
+                const unsigned m = any ? __ballot_sync(0xffffffffu, (pw[k] >> j) & 1u) : 0u;
+                if (lane == 0) sM[k * 32 + j][wp] = m;
+            }
+        }
+        __syncthreads();
+        for (int j = t; j < 256; j += QBT) {
+            const int64_t l = (int64_t)c * 256 + j;
+            uint32_t mw[W], any = 0u;
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                mw[w] = sM[j][w];
+                any |= mw[w];
+            }
+            if (l < L && any) {
+                const int slot = atomicAdd(&blkCnt[b], 1);
+                const int64_t e = (int64_t)b * L + slot;
+                blkEnt[e] = make_int4((int)l, (int)off[l], (int)(off[l + 1] - off[l]), bOff ? (int)bOff[l] : 0);
+#pragma unroll
+                for (int w = 0; w < W; w++) blkMask[e * W + w] = mw[w];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Per-point test in partially covered leaves (the queries of the block's
 // list mask).  Grid (block, split).
 __global__ void __launch_bounds__(256)
@@ -2352,6 +2416,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             uint32_t *leafBits;
             uint32_t *fullBits;   // whole-leaf bits for the verification, or null
             int2 *cntTight;       // partial leaves' members surely / possibly inside (radial profiles), or null
+            const int32_t *amb;   // a gathered sub-batch: its rows in the batch (lists from the batch's bits)
         };
         const int64_t Tdec = std::min<int64_t>(B, n);
         auto class_phase = [&](bool tc, const CountIO &io, ZeroList z) -> pmlsh_status {
@@ -2374,7 +2439,19 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             z.add(recheckN, 1);
             z.add((int *)io.cntTight, io.cntTight ? 2 * io.na : 0);
             PM_LAUNCH("k_zero", st, k_zero<<<2 * nsm, 256, 0, st>>>(z));
-            {
+            if (io.amb) {
+                // a sub-batch: its block lists from the batch's leaf bits
+                const int64_t nch = (W32 + 7) / 8;
+                const int64_t gy = std::max<int64_t>(1, std::min<int64_t>(nch, ((int64_t)4 * nsm + nlist - 1) / nlist));
+                if (!tc)
+                    PM_LAUNCH("k_sublists", st, k_sublists<QB><<<dim3((unsigned)nlist, (unsigned)gy), QB, 0, st>>>(
+                                                     io.amb, io.na, leafBits, fullBits, W32, L, ix->leafOff, nullptr,
+                                                     cntSure, io.cntSure, blkCnt, blkEnt, blkMask));
+                else
+                    PM_LAUNCH("k_sublists", st, k_sublists<TC_QN><<<dim3((unsigned)nlist, (unsigned)gy), TC_QN, 0, st>>>(
+                                                     io.amb, io.na, leafBits, fullBits, W32, L, ix->leafOff, ix->bOff,
+                                                     cntSure, io.cntSure, blkCnt, blkEnt, blkMask));
+            } else {
                 // query-stationary test: leaf tiles split evenly over enough
                 // CTAs per query block to fill the GPU once
                 const int64_t nTiles = (L + CQ_LT - 1) / CQ_LT;
@@ -2458,7 +2535,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             return PMLSH_OK;
         };
         const CountIO full{act, na, thr, cntSure, cntPart, cntBand, inTrue, inN, inPos, fpc, leafBits, fullBits,
-                           stats == nullptr ? cntTight : nullptr};
+                           stats == nullptr ? cntTight : nullptr, nullptr};
         {
             // this round's per-query counters and the error and list counters
             // after them (fpc [nq + 8]) start at zero
@@ -2544,7 +2621,8 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             std::memcpy(stList, ambH.data(), na2 * sizeof(int32_t));   // (the round's active list is on the device)
             PM_CUDA(cudaMemcpyAsync(amb, stList, na2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
             PM_LAUNCH("k_gather_sub", st, k_gather_sub<<<(na2 + 255) / 256, 256, 0, st>>>(amb, na2, act, thr, act2, thr2));
-            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2, nullptr, nullptr};
+            const CountIO subIO{act2, na2, thr2, s2Sure, s2Part, s2Band, s2In, s2InN, s2InPos, s2Fp, bits2, nullptr,
+                                nullptr, amb};
             PM_TRY(class_phase(tensor, subIO, ZeroList()));   // zeroes inTrue, inN, fp64 of the sub-batch
             std::vector<int> es, eb, ein;
             PM_TRY(exact_count(subIO, es, eb, ein));
