@@ -988,7 +988,8 @@ __device__ __forceinline__ void warp_sort_win(uint32_t *key, int32_t *val, int l
 //     value provably contain the exact k nearest; they are recomputed in
 //     FP64 and ranked by (FP64 distance, id).
 // The result equals verifying every candidate.
-__global__ void __launch_bounds__(32 * VW_MAXWARPS, VW_MINBLOCKS)
+template <bool WIDE>
+__global__ void __launch_bounds__(32 * VW_MAXWARPS, WIDE ? 2 : VW_MINBLOCKS)
 k_verify(VwArgs A)
 {
     extern __shared__ __align__(16) unsigned char vsm[];
@@ -1055,7 +1056,9 @@ k_verify(VwArgs A)
             idxs[e] = 0x7fffffff;
         }
         __syncwarp();
-        auto D2 = [&](const float *p) -> float { return warp_d2x4(q4, p, nf4, lane); };
+        auto D2 = [&](const float *p) -> float {
+            return WIDE ? warp_d2x4w(q4, p, nf4, lane) : warp_d2x4(q4, p, nf4, lane);
+        };
         // top-KP state: lane owns slots lane, lane + 32, ...; cmax is the
         // largest entry (the KP-th smallest so far), cslot its slot
         float cmax = INFINITY, myMax = INFINITY;
@@ -2126,6 +2129,7 @@ namespace {
 struct VerifyPlan {
     int nsm = 148;
     int vWarps = 0, vPerSM = 1;   // single-query kernel
+    int vPerSMw = 1;              // its register-rich form (for batches that fit one wave of it)
     size_t vsmem = 0;
     int gvTR = 0, gvPerSM = 0;    // grouped kernel
     size_t gvSmem = 0;
@@ -2143,9 +2147,12 @@ pmlsh_status verify_plan(int ld, int KP, VerifyPlan &vp, bool bf16 = false)
     vp.vWarps = (int)std::min<size_t>(VW_MAXWARPS, (size_t)(227 * 1024) / vwarp);
     if (vp.vWarps < 1) return PMLSH_OK;
     vp.vsmem = (size_t)vp.vWarps * vwarp;
-    PM_TRY(pm_allow_max_dyn_smem((const void *)k_verify));
-    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vp.vPerSM, k_verify, 32 * vp.vWarps, vp.vsmem));
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_verify<false>));
+    PM_TRY(pm_allow_max_dyn_smem((const void *)k_verify<true>));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vp.vPerSM, k_verify<false>, 32 * vp.vWarps, vp.vsmem));
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&vp.vPerSMw, k_verify<true>, 32 * vp.vWarps, vp.vsmem));
     vp.vPerSM = std::max(1, vp.vPerSM);
+    vp.vPerSMw = std::max(1, vp.vPerSMw);
     vp.gvTR = gv_tile_rows(ld);
     vp.gvSmem = vp.gvTR > 0 ? gv_smem_bytes(ld, KP, vp.gvTR) : 0;
     if (vp.gvTR > 0 && vp.gvSmem <= (size_t)pm_max_smem_optin()) PM_TRY(gv_ctas_per_sm(vp.gvSmem, &vp.gvPerSM));
@@ -2376,6 +2383,7 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
         return PMLSH_EINVAL;
     }
     const int nsm = vp.nsm, vWarps = vp.vWarps, vPerSM = vp.vPerSM, gvTR = vp.gvTR, gvPerSM = vp.gvPerSM;
+    const int vPerSMw = vp.vPerSMw;
     const size_t vsmem = vp.vsmem, gvSmem = vp.gvSmem;
     const bool grouped = vp.grouped;
 
@@ -2696,7 +2704,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             ga.TR = gvTR;
             PM_TRY(gv_launch(ga, gGrid, gvSmem, st));
         } else {
-            const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, vPerSM * nsm));
+            // a batch that one wave of the register-rich form holds takes it
+            // (more loads in flight per lane; resident warps do not limit it)
+            const bool wide = na <= vPerSMw * nsm * vWarps;
+            const int vGrid = std::max(1, std::min((na + vWarps - 1) / vWarps, (wide ? vPerSMw : vPerSM) * nsm));
             int2 *vLists = grow<int2>(w.partD, (size_t)vGrid * vWarps * L, s);
             if (s != PMLSH_OK) return s;
             VwArgs va;
@@ -2718,7 +2729,10 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
             va.rowErr = ix->rowErr;
             va.redo = redoD;
             if (bf16v) PM_CUDA(cudaMemsetAsync(redoD, 0, na * sizeof(int), st));
-            PM_LAUNCH("k_verify", st, k_verify<<<vGrid, 32 * vWarps, vsmem, st>>>(va));
+            if (wide)
+                PM_LAUNCH("k_verify", st, k_verify<true><<<vGrid, 32 * vWarps, vsmem, st>>>(va));
+            else
+                PM_LAUNCH("k_verify", st, k_verify<false><<<vGrid, 32 * vWarps, vsmem, st>>>(va));
         }
         PM_CUDA(cudaGetLastError());
         if (stats) {

@@ -248,6 +248,62 @@ __device__ __forceinline__ float warp_d2x4(const float4 *__restrict__ q4, const 
     return __shfl_sync(VW_FULL, keep, ((lane & 7) << 2) | (lane >> 3));
 }
 
+// warp_d2x4 with two of its eight-row groups in flight at once (for kernels
+// with registers to spare): sixteen 16-byte loads per lane are issued
+// together, halving the dependent load rounds again; the same sums per row.
+__device__ __forceinline__ float warp_d2x4w(const float4 *__restrict__ q4, const float *p, int nf4, int lane)
+{
+    const int grp = lane >> 2, g = lane & 3;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float keep = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 4; j += 2) {
+        const float4 *xa = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 8 * j);
+        const float4 *xb = (const float4 *)__shfl_sync(VW_FULL, (unsigned long long)p, grp + 8 * (j + 1));
+        unsigned long long accA = 0ull, accB = 0ull;
+        if (xa != nullptr || xb != nullptr) {
+            int t = g;
+            for (; t + 28 < nf4; t += 32) {
+                float4 a[8], b[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    a[u] = xa != nullptr ? __ldg(xa + t + 4 * u) : zero;
+                    b[u] = xb != nullptr ? __ldg(xb + t + 4 * u) : zero;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const float4 qv = q4[t + 4 * u];
+                    const unsigned long long q0 = f32x2_pack(qv.x, qv.y), q1 = f32x2_pack(qv.z, qv.w);
+                    f32x2_sqdiff_acc(accA, q0, f32x2_pack(a[u].x, a[u].y));
+                    f32x2_sqdiff_acc(accA, q1, f32x2_pack(a[u].z, a[u].w));
+                    f32x2_sqdiff_acc(accB, q0, f32x2_pack(b[u].x, b[u].y));
+                    f32x2_sqdiff_acc(accB, q1, f32x2_pack(b[u].z, b[u].w));
+                }
+            }
+            for (; t < nf4; t += 4) {
+                const float4 a = xa != nullptr ? __ldg(xa + t) : zero;
+                const float4 b = xb != nullptr ? __ldg(xb + t) : zero;
+                const float4 qv = q4[t];
+                const unsigned long long q0 = f32x2_pack(qv.x, qv.y), q1 = f32x2_pack(qv.z, qv.w);
+                f32x2_sqdiff_acc(accA, q0, f32x2_pack(a.x, a.y));
+                f32x2_sqdiff_acc(accA, q1, f32x2_pack(a.z, a.w));
+                f32x2_sqdiff_acc(accB, q0, f32x2_pack(b.x, b.y));
+                f32x2_sqdiff_acc(accB, q1, f32x2_pack(b.z, b.w));
+            }
+        }
+        float sa = __fadd_rn(__uint_as_float((unsigned)accA), __uint_as_float((unsigned)(accA >> 32)));
+        float sb = __fadd_rn(__uint_as_float((unsigned)accB), __uint_as_float((unsigned)(accB >> 32)));
+        sa = __fadd_rn(sa, __shfl_xor_sync(VW_FULL, sa, 1));
+        sb = __fadd_rn(sb, __shfl_xor_sync(VW_FULL, sb, 1));
+        sa = __fadd_rn(sa, __shfl_xor_sync(VW_FULL, sa, 2));
+        sb = __fadd_rn(sb, __shfl_xor_sync(VW_FULL, sb, 2));
+        if (g == j) keep = sa;
+        if (g == j + 1) keep = sb;
+    }
+    // lane (grp, g) holds row grp + 8 g; row v sits at lane 4 (v % 8) + v / 8
+    return __shfl_sync(VW_FULL, keep, ((lane & 7) << 2) | (lane >> 3));
+}
+
 // ||u - r~_v||^2 in FP32 of up to 32 BF16 rows r~_v (one per lane, length
 // ld; nullptr: none, the lane then gets 0) against the FP32 vector u in
 // shared memory: eight lanes share a row (16-byte loads of 8 BF16 values),
