@@ -2496,8 +2496,16 @@ pmlsh_status pm_knn(pmlsh_index *ix, const float *Q, int64_t nq, const pmlsh_knn
                                             ix->O32, blkCnt, blkEnt, blkMask, L, io.cntSure, io.cntBand, bandN,
                                             bandCap, bandA, bandPos));
             } else {
-                // one CTA per SM at a time: at most four whole waves
-                int splitC = std::max(1, std::min(256, 4 * nsm / nlist));
+                // one CTA per SM at a time: the fewest waves (of up to four)
+                // whose CTAs fill at least 95% of their SM slots, each CTA
+                // taking a share of its block's list (the prologue, building
+                // the block's query operand rows, is paid once per CTA)
+                int splitC = 1;
+                for (int wv = 1; wv <= 4; wv++) {
+                    splitC = std::max(1, std::min(256, wv * nsm / nlist));
+                    const int64_t tot = (int64_t)nlist * splitC, waves = (tot + nsm - 1) / nsm;
+                    if ((double)tot >= 0.95 * (double)(waves * nsm)) break;
+                }
                 PM_LAUNCH("k_count_tc", st, k_count_tc<<<dim3(nlist, splitC), TC_THREADS, TC_SMEM, st>>>(
                                             io.act, io.na, io.thr, qp32, ix->Bsplit, ix->bNorm, blkCnt, blkEnt,
                                             blkMask, L, ix->maxNorm, io.cntSure, recheckN, recheckCap, recheck,
