@@ -1258,26 +1258,47 @@ k_verify(VwArgs A)
         // FP32 P mu and the FP32 difference and sum, rounded generously up
         const float pSlack = __fmul_ru(1.01f, __fadd_ru(__fmul_ru((float)(4 * (ld + 2)) * 0x1.0p-24f, A.qnx[q]),
                                                         __fmul_ru(0x1.0p-20f, __fadd_ru(A.qnx[q], A.muMax))));
-        for (int e0 = 0; e0 < cnt; e0 += 32) {
-            const int e = e0 + lane;
-            if (e < cnt) {
-                const int l = list[e].x;
-                const float4 *pm4 = (const float4 *)(A.leafPmu + (int64_t)l * PM_PCA);
-                float s2 = 0.f;
+        // two batches of 32 entries per step: their leaf records are loaded
+        // together (a dependent list -> record chain per step, not per batch)
+        for (int e0 = 0; e0 < cnt; e0 += 64) {
+            const int ea = e0 + lane, eb = e0 + 32 + lane;
+            const int la = ea < cnt ? list[ea].x : 0, lb = eb < cnt ? list[eb].x : 0;
+            const float4 *pa = (const float4 *)(A.leafPmu + (int64_t)la * PM_PCA);
+            const float4 *pb = (const float4 *)(A.leafPmu + (int64_t)lb * PM_PCA);
+            float4 va[PM_PCA / 4], vb[PM_PCA / 4];
 #pragma unroll
-                for (int r4 = 0; r4 < PM_PCA / 4; r4++) {
-                    const float4 pmv = __ldg(pm4 + r4);
-                    float u = __fsub_rn(sPq[4 * r4], pmv.x);
-                    s2 = __fmaf_rn(u, u, s2);
-                    u = __fsub_rn(sPq[4 * r4 + 1], pmv.y);
-                    s2 = __fmaf_rn(u, u, s2);
-                    u = __fsub_rn(sPq[4 * r4 + 2], pmv.z);
-                    s2 = __fmaf_rn(u, u, s2);
-                    u = __fsub_rn(sPq[4 * r4 + 3], pmv.w);
-                    s2 = __fmaf_rn(u, u, s2);
-                }
-                const float lbp = __fsub_rn(__fsub_rn(__fmul_rn(__fsqrt_rn(s2), 1.f - 0x1.0p-18f), pSlack), A.leafRx[l]);
-                list[e] = make_int2(l, (int)vw_key(lbp));
+            for (int r4 = 0; r4 < PM_PCA / 4; r4++) {
+                va[r4] = __ldg(pa + r4);
+                vb[r4] = __ldg(pb + r4);
+            }
+            const float rxa = A.leafRx[la], rxb = A.leafRx[lb];
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int r4 = 0; r4 < PM_PCA / 4; r4++) {
+                float u = __fsub_rn(sPq[4 * r4], va[r4].x);
+                sa = __fmaf_rn(u, u, sa);
+                u = __fsub_rn(sPq[4 * r4 + 1], va[r4].y);
+                sa = __fmaf_rn(u, u, sa);
+                u = __fsub_rn(sPq[4 * r4 + 2], va[r4].z);
+                sa = __fmaf_rn(u, u, sa);
+                u = __fsub_rn(sPq[4 * r4 + 3], va[r4].w);
+                sa = __fmaf_rn(u, u, sa);
+                u = __fsub_rn(sPq[4 * r4], vb[r4].x);
+                sb = __fmaf_rn(u, u, sb);
+                u = __fsub_rn(sPq[4 * r4 + 1], vb[r4].y);
+                sb = __fmaf_rn(u, u, sb);
+                u = __fsub_rn(sPq[4 * r4 + 2], vb[r4].z);
+                sb = __fmaf_rn(u, u, sb);
+                u = __fsub_rn(sPq[4 * r4 + 3], vb[r4].w);
+                sb = __fmaf_rn(u, u, sb);
+            }
+            if (ea < cnt) {
+                const float lbp = __fsub_rn(__fsub_rn(__fmul_rn(__fsqrt_rn(sa), 1.f - 0x1.0p-18f), pSlack), rxa);
+                list[ea] = make_int2(la, (int)vw_key(lbp));
+            }
+            if (eb < cnt) {
+                const float lbp = __fsub_rn(__fsub_rn(__fmul_rn(__fsqrt_rn(sb), 1.f - 0x1.0p-18f), pSlack), rxb);
+                list[eb] = make_int2(lb, (int)vw_key(lbp));
             }
         }
         __syncwarp();
