@@ -1137,6 +1137,25 @@ k_verify(VwArgs A)
                 cslot = __shfl_sync(VW_FULL, mySlot, __ffs(who) - 1);
             }
         };
+        // FP32 pass: candidate rows wait in a warp queue (the histogram
+        // space, unused while leaves are visited) and their distances are
+        // taken 32 at a time, so a chunk with few candidates does not cost a
+        // whole 32-row distance pass; the K that prunes meanwhile is that of
+        // the rows already offered, never below the exact one
+        int *cq = (int *)whist;
+        int qn = 0;
+        auto flushq = [&](int nq) {
+            const bool c = lane < nq;
+            const int pos = c ? cq[lane] : 0;
+            const int rest = qn - nq;
+            const int mv = lane < rest ? cq[nq + lane] : 0;
+            __syncwarp();
+            if (lane < rest) cq[lane] = mv;
+            qn = rest;
+            __syncwarp();
+            const float d2 = D2(c ? A.X + (int64_t)pos * ld : nullptr);
+            offer(c, d2, d2, pos);
+        };
         // verifies the candidates of leaf l
         // (lbl: the leaf's full lower bound, ||q - mu_l|| lbSlack - Rx_l)
         auto visit = [&](int l, float lbl) {
@@ -1205,8 +1224,11 @@ k_verify(VwArgs A)
                     if (__ballot_sync(VW_FULL, cand) == 0u) continue;
                     seen += __popc(__ballot_sync(VW_FULL, cand));
                     if (!bf) {
-                        const float d2 = D2(cand ? A.X + (r0 + lane) * ld : nullptr);
-                        offer(cand, d2, d2, (int)(r0 + lane));
+                        const unsigned cm = __ballot_sync(VW_FULL, cand);
+                        if (cand) cq[qn + __popc(cm & ((1u << lane) - 1u))] = (int)(r0 + lane);
+                        qn += __popc(cm);
+                        __syncwarp();
+                        if (qn >= 32) flushq(32);
                     } else {
                         // first pass: ||q - x|| within sqrt(S) +- (wErr + e_row), S the
                         // exact ||u - r~||^2; offered by the upper bound (squared)
@@ -1358,6 +1380,7 @@ k_verify(VwArgs A)
                 visit(x, vw_unkey(kk));
             }
             __syncwarp();
+            if (qn > 0) flushq(qn);
             if (pruned(vw_unkey(tau))) break;
         }
         // band-in points (FP64-resolved members just inside the radius)
