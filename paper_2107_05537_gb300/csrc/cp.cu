@@ -367,6 +367,144 @@ __global__ void k_bnb_mindist(const float *__restrict__ meta, int s, int64_t L, 
     }
 }
 
+// Listed leaf pairs in ascending (Mindist, l1, l2) on the device: a 64-bit
+// key per pair, the order-preserving bits of Mindist (+0 and -0 taken as
+// one) above the pair's rank in (l1, l2) order, l1 (2L - l1 - 1) / 2 +
+// l2 - l1 - 1 (below 2^32 when L(L - 1)/2 is), sorted by a stable LSD radix
+// sort of 8-bit digits and decoded back.
+constexpr int RS_THREADS = 256, RS_ITEMS = 32;   // keys per block and pass: 8,192
+constexpr int64_t LP_GPU_MAX_L = 92682;         // L (L - 1) / 2 < 2^32
+
+__device__ __forceinline__ int64_t lp_rank_base(int64_t l1, int64_t L) { return l1 * (2 * L - l1 - 1) / 2; }
+
+__global__ void k_lp_key(const LeafPair *__restrict__ lp, int64_t n, int64_t L, unsigned long long *__restrict__ key)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const LeafPair x = lp[e];
+    const unsigned int u = __float_as_uint(__fadd_rn(x.md, 0.f));
+    const unsigned int ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    const int64_t rk = lp_rank_base(x.l1, L) + (x.l2 - x.l1 - 1);
+    key[e] = ((unsigned long long)ord << 32) | (unsigned long long)(uint32_t)rk;
+}
+
+// digit counts of each block's keys, digit-major: hist[d * nb + block]
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_hist(const unsigned long long *__restrict__ key, int64_t n, int shift, unsigned int *__restrict__ hist, int nb)
+{
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * RS_THREADS * RS_ITEMS;
+    const int64_t b1 = b0 + (int64_t)RS_THREADS * RS_ITEMS < n ? b0 + (int64_t)RS_THREADS * RS_ITEMS : n;
+    for (int64_t e = b0 + threadIdx.x; e < b1; e += RS_THREADS) atomicAdd(&h[(unsigned)(key[e] >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive prefix sum of h[0, N) in place, one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned int *__restrict__ h, int64_t N)
+{
+    __shared__ unsigned int ws[32];
+    const int64_t seg = (N + 1023) / 1024;
+    const int64_t t0 = threadIdx.x * seg, t1 = t0 + seg < N ? t0 + seg : N;
+    unsigned int sum = 0u;
+    for (int64_t i = t0; i < t1; i++) sum += h[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned int x = ws[lane], xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += v;
+        }
+        ws[lane] = xi - x;
+    }
+    __syncthreads();
+    unsigned int run = ws[w] + incl - sum;
+    for (int64_t i = t0; i < t1; i++) {
+        const unsigned int v = h[i];
+        h[i] = run;
+        run += v;
+    }
+}
+
+// stable scatter by one digit: each block walks its keys in order, 256 per
+// round; a key's place is its digit's running base plus the keys of that
+// digit before it in the round (earlier warps, then earlier lanes)
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_scatter(const unsigned long long *__restrict__ in, unsigned long long *__restrict__ out, int64_t n, int shift,
+             const unsigned int *__restrict__ off, int nb)
+{
+    constexpr int NW = RS_THREADS / 32;
+    __shared__ unsigned int base[256];
+    __shared__ unsigned int wc[NW][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    base[t] = off[(int64_t)t * nb + blockIdx.x];
+    const int64_t b0 = (int64_t)blockIdx.x * RS_THREADS * RS_ITEMS;
+    for (int r = 0; r < RS_ITEMS; r++) {
+        for (int j = 0; j < NW; j++) wc[j][t] = 0u;
+        __syncthreads();
+        const int64_t e = b0 + (int64_t)r * RS_THREADS + t;
+        const bool valid = e < n;
+        const unsigned long long k = valid ? in[e] : 0ull;
+        const unsigned int d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
+        const unsigned int peers = __match_any_sync(0xffffffffu, d);
+        const int rankW = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rankW == 0) wc[w][d] = (unsigned)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned int pos = base[d] + (unsigned)rankW;
+            for (int j = 0; j < w; j++) pos += wc[j][d];
+            out[pos] = k;
+        }
+        __syncthreads();
+        unsigned int add = 0u;
+        for (int j = 0; j < NW; j++) add += wc[j][t];
+        base[t] += add;
+        __syncthreads();
+    }
+}
+
+// keys back to leaf pairs; flags a key out of order (bit 1) or a rank that
+// does not decode to l1 < l2 < L (bit 2)
+__global__ void k_lp_decode(const unsigned long long *__restrict__ key, int64_t n, int64_t L,
+                            LeafPair *__restrict__ out, int *__restrict__ bad)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const unsigned long long k = key[e];
+    if (e > 0 && key[e - 1] > k) atomicOr(bad, 1);
+    const unsigned int ord = (unsigned int)(k >> 32);
+    const unsigned int u = (ord & 0x80000000u) ? (ord & 0x7fffffffu) : ~ord;
+    const int64_t rk = (int64_t)(k & 0xffffffffull);
+    // l1: the largest l with lp_rank_base(l) <= rk (root of the quadratic,
+    // then at most a few steps of correction)
+    const double A = 2.0 * (double)L - 1.0;
+    const double disc = A * A - 8.0 * (double)rk;
+    int64_t l1 = (int64_t)floor((A - sqrt(disc > 0.0 ? disc : 0.0)) * 0.5);
+    l1 = l1 < 0 ? 0 : (l1 > L - 2 ? L - 2 : l1);
+    for (int it = 0; it < 4 && l1 + 1 <= L - 2 && lp_rank_base(l1 + 1, L) <= rk; it++) l1++;
+    for (int it = 0; it < 4 && l1 > 0 && lp_rank_base(l1, L) > rk; it++) l1--;
+    const int64_t l2 = rk - lp_rank_base(l1, L) + l1 + 1;
+    LeafPair x;
+    x.md = __uint_as_float(u);
+    x.l1 = (int32_t)l1;
+    x.l2 = (int32_t)l2;
+    if (!(l1 >= 0 && l1 < l2 && l2 < L)) {
+        atomicOr(bad, 2);
+        x.l1 = 0;
+        x.l2 = 1;
+    }
+    out[e] = x;
+}
+
 // Every cross pair of the listed leaf pairs, keyed by the FP32 projected
 // squared distance, at the listed offsets.  Block per leaf pair.
 __global__ void k_bnb_cross(const float *__restrict__ O32, const int64_t *__restrict__ off,
@@ -984,6 +1122,9 @@ pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_
     const size_t lpBatch = (size_t)1 << 16;
     PM_TRY(mem.get(&dPairs, lpBatch));
     PM_TRY(mem.get(&dOff, lpBatch));
+    unsigned long long *keyA = nullptr, *keyB = nullptr;   // device sort of the listed leaf pairs
+    unsigned int *rsHist = nullptr;
+    unsigned long long keyCap = 0;
     int64_t examined = 0, crossPairs = 0, listed = 0;
     for (;;) {
         const double hiCut = std::min(bandHi, dT);
@@ -997,14 +1138,49 @@ pmlsh_status pm_closest_pair_bnb(pmlsh_index *ix, const pmlsh_cp_opts *o, int64_
         unsigned long long nlp = 0;
         PM_CUDA(cudaMemcpyAsync(&nlp, cnt, sizeof(nlp), cudaMemcpyDeviceToHost, st));
         PM_CUDA(cudaStreamSynchronize(st));
+        const bool gpuSort = L <= LP_GPU_MAX_L && nlp > 1;
+        if (gpuSort) {
+            // ascending (Mindist, l1, l2) by the device radix sort
+            if (nlp > keyCap) {
+                PM_TRY(mem.get(&keyA, (size_t)nlp));
+                PM_TRY(mem.get(&keyB, (size_t)nlp));
+                PM_TRY(mem.get(&rsHist, (size_t)256 * ((nlp + RS_THREADS * RS_ITEMS - 1) / (RS_THREADS * RS_ITEMS))));
+                keyCap = nlp;
+            }
+            const int64_t nl = (int64_t)nlp;
+            const int nb = (int)((nl + RS_THREADS * RS_ITEMS - 1) / (RS_THREADS * RS_ITEMS));
+            const unsigned g = (unsigned)((nl + 255) / 256);
+            PM_LAUNCH("k_lp_key", st, k_lp_key<<<g, 256, 0, st>>>(dlp, nl, L, keyA));
+            unsigned long long *src = keyA, *dst = keyB;
+            for (int shift = 0; shift < 64; shift += 8) {
+                PM_LAUNCH("k_rs_hist", st, k_rs_hist<<<(unsigned)nb, RS_THREADS, 0, st>>>(src, nl, shift, rsHist, nb));
+                PM_LAUNCH("k_rs_scan", st, k_rs_scan<<<1, 1024, 0, st>>>(rsHist, (int64_t)256 * nb));
+                PM_LAUNCH("k_rs_scatter", st, k_rs_scatter<<<(unsigned)nb, RS_THREADS, 0, st>>>(src, dst, nl, shift,
+                                                                                              rsHist, nb));
+                std::swap(src, dst);
+            }
+            PM_CUDA(cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned long long), st));
+            PM_LAUNCH("k_lp_decode", st, k_lp_decode<<<g, 256, 0, st>>>(src, nl, L, dlp, (int *)(cnt + 1)));
+            PM_CUDA(cudaGetLastError());
+        }
         std::vector<LeafPair> lps(nlp);
         PM_CUDA(cudaMemcpyAsync(lps.data(), dlp, nlp * sizeof(LeafPair), cudaMemcpyDeviceToHost, st));
-        PM_CUDA(cudaStreamSynchronize(st));
-        std::sort(lps.begin(), lps.end(), [](const LeafPair &x, const LeafPair &y) {
-            if (x.md != y.md) return x.md < y.md;
-            if (x.l1 != y.l1) return x.l1 < y.l1;
-            return x.l2 < y.l2;
-        });
+        if (gpuSort) {
+            unsigned long long badH = 0;
+            PM_CUDA(cudaMemcpyAsync(&badH, cnt + 1, sizeof(badH), cudaMemcpyDeviceToHost, st));
+            PM_CUDA(cudaStreamSynchronize(st));
+            if (badH != 0) {
+                pm_set_error("closest pairs: the device sort of %llu leaf pairs failed its check (%llu)", nlp, badH);
+                return PMLSH_EINTERNAL;
+            }
+        } else {
+            PM_CUDA(cudaStreamSynchronize(st));
+            std::sort(lps.begin(), lps.end(), [](const LeafPair &x, const LeafPair &y) {
+                if (x.md != y.md) return x.md < y.md;
+                if (x.l1 != y.l1) return x.l1 < y.l1;
+                return x.l2 < y.l2;
+            });
+        }
         listed += (int64_t)nlp;
         size_t next = 0;
         bool stop = false;

@@ -138,6 +138,22 @@ def test_cp_bnb_parity(n, d, clusters, k, T, leaf):
     assert got["stats"]["count"] == min(T, n * (n - 1) // 2)
 
 
+def test_cp_bnb_many_listed_leaf_pairs():
+    # 20,000 points in four clusters, leaves of <= 16 points (L >= 1,250):
+    # the first Mindist band lists the leaf pairs of overlapping balls in each
+    # cluster, more than the 8,192 keys one block of the device sort of the
+    # listing takes (the oracle keeps its T = 2,000 pairs by insertion, so T
+    # stays small)
+    n, k, T = 20000, 9, 2000
+    X, _, _, _ = datagen.mixture(n, 8, 4, 1.0, seed=31)
+    A = oracle.gen_projection(10, 15, 8).astype(np.float32)
+    got, rp, rd = _bnb_both(X, A, k, T, 16)
+    assert got["stats"]["lca_nodes"] > 8192
+    assert got["pairs"].tolist() == rp.tolist()
+    assert np.array_equal(got["dists"], rd.astype(np.float32))
+    assert got["stats"]["count"] == T
+
+
 def test_cp_bnb_duplicates_and_exact_kcp():
     # repeated points: many pairs at projected distance 0, ties by (i, j)
     base, _, _, _ = datagen.mixture(40, 12, 4, 1.0, seed=2)
