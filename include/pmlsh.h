@@ -413,9 +413,10 @@ pmlsh_status pmlsh_gamma_calibrate(pmlsh_index *index, double pr, int64_t nsampl
  * alpha1, t and gamma are not used).  Outputs as pmlsh_closest_pair; stats:
  * count = pairs verified (T), lca_nodes = leaf pairs listed, nodes_done =
  * leaf pairs examined, self_pairs, fp64_checks.  Memory grows with T (12 bytes per kept
- * pair plus a batch of up to 2^24 pairs) and with the leaf pairs of a band
- * (12 bytes each, 28 while they are ordered: on the device, by a radix sort,
- * for up to 92,682 leaves; on the host beyond).  Errors: EINVAL, ENOMEM,
+ * pair plus a batch of up to 2^24 pairs) and with the leaf count L: a listing
+ * buffer of 12 bytes per leaf pair, L(L-1)/2, and 16 bytes per listed leaf
+ * pair while a band is ordered (on the device by a radix sort for up to
+ * 92,682 leaves, on the host beyond).  Errors: EINVAL, ENOMEM,
  * ECUDA, EINTERNAL (more than 4096 pairs tied inside one FP32 error band; a
  * device ordering that fails its check). */
 pmlsh_status pmlsh_closest_pair_bnb(pmlsh_index *index, const pmlsh_cp_opts *opts,
